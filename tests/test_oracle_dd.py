@@ -1,0 +1,72 @@
+"""Pins for the domain-decomposition oracle: the literal dense forms of Eqs. Sto_Schur,
+Fcc_2 and NNCP2 against the solve-based application, SPD properties of S and M_NNC^{-1},
+the partition of unity (Eq. det_scaling), node classes, and DD-PCG agreement with the
+global direct solve."""
+import numpy as np
+import pytest
+
+import sg_workloads as w
+from oracle import dd, sg
+
+
+@pytest.fixture(scope="module")
+def small():
+    prob = w.config("small")
+    return prob, dd.DDSolver(prob, explicit=True)
+
+
+def test_node_classes(small):
+    prob, d = small
+    part = d.part
+    N, s, H = prob.N, prob.s, prob.N // prob.s
+    assert part.corner.size == (s - 1) ** 2
+    # interface nodes: internal grid lines minus the Dirichlet end points
+    n_lines = 2 * (s - 1) * (N - 1) - (s - 1) ** 2
+    assert part.iface.size == n_lines
+    assert np.all(part.mult[[part.iface_index[g] for g in part.corner]] == 4)
+    rem = [g for g in part.iface if g not in part.corner_index]
+    assert np.all(part.mult[[part.iface_index[g] for g in rem]] == 2)
+
+
+def test_partition_of_unity(small):
+    _, d = small
+    acc = np.zeros(d.nG * d.P)
+    for L in d.loc:
+        np.add.at(acc, L["R"], L["D"])
+    assert np.allclose(acc, 1.0)
+
+
+def test_solve_based_equals_explicit(small):
+    _, d = small
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(d.nG * d.P)
+    Sx = d.schur(x)
+    assert np.abs(Sx - d.S_explicit @ x).max() < 1e-10 * np.abs(Sx).max()
+    z = d.precond(x)
+    assert np.abs(z - d.Minv_explicit @ x).max() < 1e-10 * np.abs(z).max()
+    assert np.allclose(d.Fcc, d.Fcc_explicit, rtol=1e-10, atol=1e-10 * np.abs(d.Fcc).max())
+
+
+def test_spd(small):
+    _, d = small
+    S, Mi = d.S_explicit, d.Minv_explicit
+    assert np.abs(S - S.T).max() < 1e-9 * np.abs(S).max()
+    assert np.abs(Mi - Mi.T).max() < 1e-9 * np.abs(Mi).max()
+    assert np.linalg.eigvalsh(S).min() > 0
+    assert np.linalg.eigvalsh(Mi).min() > 0
+    ev = np.linalg.eigvals(Mi @ S).real
+    assert ev.max() / ev.min() < 20  # two-level NN keeps the preconditioned system well conditioned
+
+
+@pytest.mark.parametrize("name", ["tiny", "small", "pulse32"])
+def test_dd_pcg_matches_direct(name):
+    prob = w.config(name)
+    sgp = sg.SGProblem(prob)
+    d = dd.DDSolver(prob)
+    U1, V1, A1 = sg.run_direct(sgp, 5)
+    U2, V2, A2, it = dd.run_dd(sgp, d, 5, tol=1e-13)
+    assert np.linalg.norm(U1 - U2) < 1e-10 * np.linalg.norm(U1)
+    assert np.linalg.norm(A1 - A2) < 1e-8 * np.linalg.norm(A1)
+    # at the workload tolerance the iteration count stays in the paper's range (~4)
+    _, _, _, it = dd.run_dd(sgp, d, 5)
+    assert max(i for i, _ in it) <= 8
