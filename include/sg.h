@@ -1,0 +1,156 @@
+/*
+ * sg.h -- C ABI of the GB300 stochastic-Galerkin domain-decomposition wave solver.
+ *
+ * The library advances the intrusive stochastic Galerkin (Hermite chaos) semi-discretisation
+ * of the 2-D acoustic wave equation with a log-normal squared wave speed
+ *     u_tt + eta u_t - div(c_s(x, xi) grad u) = f          (Sec. 4, Eq. acous_sto)
+ * with Newmark-beta (gamma = 1/2, zeta = 1/4, Sec. 2).  Each time step solves the transient
+ * system K~ U_{n+1} = F~_{n+1} (Eq. K_T_Sto) by PCG on the non-overlapping domain
+ * decomposition interface (Schur complement, Eq. Sto_Schur) preconditioned by the
+ * probabilistic two-level Neumann-Neumann preconditioner (Eq. NNCP2).  All per-step work runs
+ * in the library's own CUDA kernels on one GPU.
+ *
+ * Conventions
+ *   - Every entry point returns SG_OK (0) or a negative SG_E* code; sg_strerror() names it.
+ *   - Caller-owned input structs are read during the call only; nothing is retained.
+ *   - A handle owns all of its device memory (allocated in sg_setup, released in sg_destroy).
+ *   - All device work of a handle is issued on the CUDA stream given to sg_setup (NULL means
+ *     the legacy default stream); the calls below synchronise that stream before returning
+ *     unless stated otherwise.
+ *   - A handle is not thread-safe: one host thread at a time.
+ *   - Field layout for sg_get_field / sg_get_state / sg_set_state: node-major over the free
+ *     nodes (x index fastest, then y; node (i, j) for 1 <= i, j <= N-1), PCE mode fastest:
+ *     value(i, j, k) is element ((j-1) (N-1) + (i-1)) * P + k.  PCE modes follow the graded
+ *     multi-index order (total degree, then descending lexicographic), orthonormal basis.
+ */
+#ifndef SG_H
+#define SG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SG_OK         0
+#define SG_EINVAL    -1   /* invalid argument (sizes, pointers, parameters)                 */
+#define SG_ENOMEM    -2   /* device or host allocation failed                               */
+#define SG_ECUDA     -3   /* a CUDA runtime call failed (the message is kept per handle)    */
+#define SG_ENOTCONV  -4   /* PCG reached max_iter before ||r||/||G|| <= tol                 */
+#define SG_ENUMERIC  -5   /* NaN/Inf or loss of positive definiteness detected              */
+#define SG_ETIMEOUT  -6   /* a bounded device-side wait expired                             */
+#define SG_ENOTSUP   -7   /* configuration outside what this build supports                 */
+
+/* ---- precision modes (sg_params.precision) ---- */
+#define SG_FP64      0    /* every kernel computes in FP64                                  */
+#define SG_MIXED     1    /* FP32 subdomain solves + FP64 refinement inside an FP64 outer PCG */
+
+/* ---- warm start (sg_params.warm) ---- */
+#define SG_WARM_PREV     0   /* previous step's interface solution (Alg. 1)                 */
+#define SG_WARM_LEARNED  1   /* learned predictor (extension; falls back to SG_WARM_PREV)   */
+
+/* ---- sources (sg_source.kind) ---- */
+#define SG_SRC_NONE    0
+#define SG_SRC_PULSE   1  /* u0 = amp exp(-((x-x0)^2 + (y-y0)^2) / width^2), v0 = 0 (Eq. initial_2Dwave) */
+#define SG_SRC_RICKER  2  /* f = amp r(t) delta(x - (x0, y0)), r Ricker of peak frequency freq      */
+
+typedef struct sg_handle_s* sg_handle;
+
+/* Structured grid: N x N cells on the unit square, each cell split along (i,j)->(i+1,j+1),
+ * homogeneous Dirichlet boundary; partition into nsub_x x nsub_y equal subdomains
+ * (N divisible by both). */
+typedef struct { int N; int nsub_x; int nsub_y; } sg_grid;
+
+/* Gaussian field g = g0 + sum_n sqrt(lambda_n) phi_n(x) xi_n with covariance
+ * sigma^2 exp(-|dx|/bx - |dy|/by) (Sec. 4, Eqs. CovarKer2D, KLE); M random variables. */
+typedef struct { int M; double sigma; double bx; double by; double g0; } sg_kl;
+
+/* Output PCE order p (P = C(M+p, p) terms) and input (coefficient) order p_in. */
+typedef struct { int p; int p_in; } sg_pce;
+
+typedef struct {
+  double dt;          /* time step                                                          */
+  double tol;         /* outer PCG: stop when ||r||_2 / ||G_Gamma||_2 <= tol                */
+  double alpha0;      /* Rayleigh damping C = alpha0 M + alpha1 K (Rayleigh appendix)       */
+  double alpha1;
+  int    max_iter;    /* outer PCG iteration cap (SG_ENOTCONV beyond)                       */
+  int    precision;   /* SG_FP64 or SG_MIXED                                                */
+  int    warm;        /* SG_WARM_PREV or SG_WARM_LEARNED                                    */
+  double inner_tol;   /* subdomain solves: relative residual target (0 = automatic)         */
+  int    inner_max_iter; /* subdomain solves: iteration cap (0 = automatic)                 */
+} sg_params;
+
+typedef struct { int kind; double x0, y0, width, freq, amp; } sg_source;
+
+/* Per-call statistics of sg_step. */
+typedef struct {
+  int    steps;           /* steps advanced by this call                                    */
+  int    step_index;      /* time-step counter of the handle after the call                 */
+  int    iters_last;      /* outer PCG iterations of the last step                          */
+  long long iters_total;  /* outer PCG iterations summed over this call's steps              */
+  long long inner_total;  /* subdomain-solver iterations summed over this call's steps       */
+  double relres_last;     /* final ||r|| / ||G_Gamma|| of the last step                      */
+  double ms;              /* wall time of the call measured with CUDA events on the stream  */
+} sg_stats;
+
+/* Problem sizes, for allocating caller buffers. */
+typedef struct {
+  int N, nsub, P, P_in, n_free, n_gamma, n_corner, n_sub_nodes;
+  long long device_bytes;  /* device memory owned by the handle                              */
+} sg_sizes;
+
+/* Build the solver: KL eigenpairs (analytic, separable exponential kernel), log-normal PCE of
+ * c_s at element centroids (Eqs. c0pce, LNL0), Hermite triple products G_ijk, subdomain
+ * operators, mean-operator line factorisations, coarse basis and F_cc^{-1} (Eq. Fcc_2), and the
+ * initial state (u0, v0 = 0, consistent a0).  `stream` is a cudaStream_t or NULL.
+ * Errors: SG_EINVAL for invalid sizes/parameters, SG_ENOMEM, SG_ECUDA, SG_ENUMERIC if a
+ * factorisation meets a non-positive pivot.  On error *out is NULL. */
+int sg_setup(const sg_grid* grid, const sg_kl* kl, const sg_pce* pce, const sg_params* params,
+             const sg_source* src, void* stream, sg_handle* out);
+
+/* Advance nsteps Newmark steps (Alg. 1 loop, stochastic form of Sec. 5): effective load
+ * (Eqs. fparts, UmCm), condensed RHS G_Gamma, PCG with M_NNC^{-1}, interior recovery, Newmark
+ * update.  stats may be NULL.  Returns SG_ENOTCONV (state still advanced) if a step hit
+ * max_iter, SG_ENUMERIC on NaN/Inf. */
+int sg_step(sg_handle h, int nsteps, sg_stats* stats);
+
+/* Advance nsteps steps of every handle in hs[0..n) (independent problems of any sizes);
+ * out_n[i] receives handle i's statistics (may be NULL).  Handles must share one stream. */
+int sg_solve_batch(sg_handle* hs, int n, int nsteps, sg_stats* out_n);
+
+/* Copy the displacement PCE coefficients U_n.  mode = -1: all P modes (n_free * P values,
+ * layout above); 0 <= mode < P: that mode only (n_free values).  dst is device memory when
+ * on_device != 0, else host memory. */
+int sg_get_field(sg_handle h, int mode, double* dst, int on_device);
+
+/* Mean (mode 0) and variance (sum over k >= 1 of U_k^2, orthonormal basis) of U_n on the free
+ * nodes into host or device arrays of n_free doubles each; either pointer may be NULL. */
+int sg_get_moments(sg_handle h, double* mean, double* var, int on_device);
+
+/* Checkpoint: state = [U | V | A] (3 * n_free * P doubles, layout above) followed by one
+ * double holding the step index.  sg_set_state restores it (the PCG warm start is reset to the
+ * interface restriction of U). */
+int sg_get_state(sg_handle h, double* dst, int on_device);
+int sg_set_state(sg_handle h, const double* src, int on_device);
+
+/* Host-buffer entry point for end-to-end use: for each of nsteps steps, copies that step's
+ * deterministic nodal load (n_free doubles from f_host + s * n_free, added to mode 0 of the
+ * built-in source term) host->device, advances one step, and copies the step's mean field
+ * (n_free doubles to u_host + s * n_free) device->host.  f_host may be NULL (no extra load);
+ * u_host may be NULL.  Host buffers should be pinned for asynchronous copies. */
+int sg_step_host(sg_handle h, int nsteps, const double* f_host, double* u_host, sg_stats* stats);
+
+int sg_get_sizes(sg_handle h, sg_sizes* out);
+
+/* Per-step outer iteration counts of the last sg_step call (up to cap entries); returns the
+ * number written or a negative code. */
+int sg_get_iters(sg_handle h, int* iters, double* relres, int cap);
+
+int sg_destroy(sg_handle h);
+const char* sg_strerror(int code);
+/* Message of the last CUDA failure seen by h (or by sg_setup when h is NULL). */
+const char* sg_last_error(sg_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SG_H */

@@ -1,0 +1,220 @@
+"""ctypes binding of the C ABI in include/sg.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+SG_FP64, SG_MIXED = 0, 1
+SG_WARM_PREV, SG_WARM_LEARNED = 0, 1
+SG_ENOTCONV = -4
+
+
+class SGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"sg error {code}: {msg}")
+        self.code = code
+
+
+class Grid(C.Structure):
+    _fields_ = [("N", C.c_int), ("nsub_x", C.c_int), ("nsub_y", C.c_int)]
+
+
+class KL(C.Structure):
+    _fields_ = [("M", C.c_int), ("sigma", C.c_double), ("bx", C.c_double), ("by", C.c_double), ("g0", C.c_double)]
+
+
+class PCE(C.Structure):
+    _fields_ = [("p", C.c_int), ("p_in", C.c_int)]
+
+
+class Params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("tol", C.c_double), ("alpha0", C.c_double), ("alpha1", C.c_double),
+                ("max_iter", C.c_int), ("precision", C.c_int), ("warm", C.c_int),
+                ("inner_tol", C.c_double), ("inner_max_iter", C.c_int)]
+
+
+class Source(C.Structure):
+    _fields_ = [("kind", C.c_int), ("x0", C.c_double), ("y0", C.c_double), ("width", C.c_double),
+                ("freq", C.c_double), ("amp", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("steps", C.c_int), ("step_index", C.c_int), ("iters_last", C.c_int),
+                ("iters_total", C.c_longlong), ("inner_total", C.c_longlong), ("relres_last", C.c_double),
+                ("ms", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Sizes(C.Structure):
+    _fields_ = [("N", C.c_int), ("nsub", C.c_int), ("P", C.c_int), ("P_in", C.c_int), ("n_free", C.c_int),
+                ("n_gamma", C.c_int), ("n_corner", C.c_int), ("n_sub_nodes", C.c_int),
+                ("device_bytes", C.c_longlong)]
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.OUT
+
+
+def load_library(path: Optional[str] = None):
+    """Load libsg; raises if it is missing (there is no fallback implementation)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run paper_2512_23027_gb300.build.build())")
+    lib = C.CDLL(path)
+    P = C.POINTER
+    D = P(C.c_double)
+    lib.sg_setup.argtypes = [P(Grid), P(KL), P(PCE), P(Params), P(Source), C.c_void_p, P(C.c_void_p)]
+    lib.sg_step.argtypes = [C.c_void_p, C.c_int, P(Stats)]
+    lib.sg_solve_batch.argtypes = [P(C.c_void_p), C.c_int, C.c_int, P(Stats)]
+    lib.sg_get_field.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int]
+    lib.sg_get_moments.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+    lib.sg_get_state.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
+    lib.sg_set_state.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
+    lib.sg_step_host.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, P(Stats)]
+    lib.sg_get_sizes.argtypes = [C.c_void_p, P(Sizes)]
+    lib.sg_get_iters.argtypes = [C.c_void_p, P(C.c_int), D, C.c_int]
+    lib.sg_destroy.argtypes = [C.c_void_p]
+    lib.sg_strerror.argtypes = [C.c_int]
+    lib.sg_strerror.restype = C.c_char_p
+    lib.sg_last_error.argtypes = [C.c_void_p]
+    lib.sg_last_error.restype = C.c_char_p
+    for f in ("sg_setup", "sg_step", "sg_solve_batch", "sg_get_field", "sg_get_moments", "sg_get_state",
+              "sg_set_state", "sg_step_host", "sg_get_sizes", "sg_get_iters", "sg_destroy"):
+        getattr(lib, f).restype = C.c_int
+    _LIB = lib
+    return lib
+
+
+def _ptr(a) -> int:
+    """Address of a contiguous numpy array or torch tensor."""
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _on_device(a) -> int:
+    return int(bool(getattr(a, "is_cuda", False)))
+
+
+class Solver:
+    """One SG-DD wave problem on the GPU (wraps an sg_handle)."""
+
+    def __init__(self, prob, precision: int = SG_FP64, warm: int = SG_WARM_PREV, stream=None,
+                 tol: Optional[float] = None, inner_tol: float = 0.0, inner_max_iter: int = 0,
+                 max_iter: Optional[int] = None):
+        self.lib = load_library()
+        self.prob = prob
+        s = prob.source
+        self._grid = Grid(prob.N, prob.s, prob.s)
+        self._kl = KL(prob.M, prob.sigma, prob.bx, prob.by, prob.g0)
+        self._pce = PCE(prob.p, prob.p_in)
+        self._prm = Params(prob.dt, prob.tol if tol is None else tol, prob.alpha0, prob.alpha1,
+                           prob.max_iter if max_iter is None else max_iter, precision, warm, inner_tol,
+                           inner_max_iter)
+        self._src = Source(s.kind, s.x0, s.y0, s.width, s.freq, s.amp)
+        st = 0
+        if stream is not None:
+            st = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self.stream = st
+        h = C.c_void_p()
+        rc = self.lib.sg_setup(C.byref(self._grid), C.byref(self._kl), C.byref(self._pce), C.byref(self._prm),
+                               C.byref(self._src), C.c_void_p(st), C.byref(h))
+        if rc != 0:
+            raise SGError(rc, self.lib.sg_last_error(None).decode())
+        self.h = h
+        sz = Sizes()
+        self._check(self.lib.sg_get_sizes(self.h, C.byref(sz)))
+        self.sizes = {f: getattr(sz, f) for f, _ in Sizes._fields_}
+        self.P = sz.P
+        self.n_free = sz.n_free
+
+    def _check(self, rc, allow_notconv=False):
+        if rc == 0 or (allow_notconv and rc == SG_ENOTCONV):
+            return rc
+        raise SGError(rc, (self.lib.sg_strerror(rc) or b"").decode() + ": " +
+                      (self.lib.sg_last_error(self.h) or b"").decode())
+
+    def step(self, n: int = 1, allow_notconv: bool = False) -> dict:
+        st = Stats()
+        rc = self._check(self.lib.sg_step(self.h, n, C.byref(st)), allow_notconv)
+        d = st.as_dict()
+        d["rc"] = rc
+        return d
+
+    def iters(self, cap: int = 1 << 20):
+        it = (C.c_int * cap)()
+        rr = (C.c_double * cap)()
+        n = self.lib.sg_get_iters(self.h, it, rr, cap)
+        return list(it[:n]), list(rr[:n])
+
+    def field(self, mode: int = -1, out=None):
+        """Displacement PCE coefficients U_n: (n_free, P) for mode = -1, else (n_free,).
+        `out` may be a float64 numpy array or a CUDA torch tensor."""
+        shape = (self.n_free, self.P) if mode < 0 else (self.n_free,)
+        if out is None:
+            out = np.zeros(shape)
+        self._check(self.lib.sg_get_field(self.h, mode, C.c_void_p(_ptr(out)), _on_device(out)))
+        return out
+
+    def moments(self):
+        mean = np.zeros(self.n_free)
+        var = np.zeros(self.n_free)
+        self._check(self.lib.sg_get_moments(self.h, C.c_void_p(_ptr(mean)), C.c_void_p(_ptr(var)), 0))
+        return mean, var
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.zeros(3 * self.n_free * self.P + 1)
+        self._check(self.lib.sg_get_state(self.h, C.c_void_p(_ptr(out)), _on_device(out)))
+        return out
+
+    def set_state(self, state):
+        self._check(self.lib.sg_set_state(self.h, C.c_void_p(_ptr(state)), _on_device(state)))
+
+    def step_host(self, n: int, f_host=None, u_host=None) -> dict:
+        st = Stats()
+        fp = C.c_void_p(_ptr(f_host)) if f_host is not None else None
+        up = C.c_void_p(_ptr(u_host)) if u_host is not None else None
+        self._check(self.lib.sg_step_host(self.h, n, fp, up, C.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def solve_batch(solvers: Sequence[Solver], nsteps: int):
+    lib = load_library()
+    n = len(solvers)
+    hs = (C.c_void_p * n)(*[s.h for s in solvers])
+    st = (Stats * n)()
+    rc = lib.sg_solve_batch(hs, n, nsteps, st)
+    if rc not in (0, SG_ENOTCONV):
+        raise SGError(rc, (lib.sg_strerror(rc) or b"").decode())
+    return [s.as_dict() for s in st]

@@ -1,0 +1,310 @@
+// Host-side set-up math (see sg_host.hpp).  Plain C++17, no architecture-specific code.
+#include "sg_host.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <functional>
+#include <map>
+
+namespace sgh {
+
+static double fact(int n) {
+  double f = 1.0;
+  for (int i = 2; i <= n; ++i) f *= i;
+  return f;
+}
+
+// Graded multi-indices |alpha| <= p; inside a degree, descending lexicographic order.
+std::vector<std::vector<int>> multi_indices(int M, int p) {
+  std::vector<std::vector<int>> out;
+  for (int d = 0; d <= p; ++d) {
+    std::vector<std::vector<int>> level;
+    std::vector<int> a(M, 0);
+    std::function<void(int, int)> rec = [&](int pos, int left) {
+      if (pos == M - 1) {
+        a[pos] = left;
+        level.push_back(a);
+        return;
+      }
+      for (int v = left; v >= 0; --v) {  // larger leading entries first
+        a[pos] = v;
+        rec(pos + 1, left - v);
+      }
+    };
+    if (M > 0) rec(0, d);
+    else if (d == 0) level.push_back({});
+    out.insert(out.end(), level.begin(), level.end());
+  }
+  return out;
+}
+
+// <psi_a psi_b psi_c> for normalised probabilists' Hermite polynomials (Sec. 4, G_ijk):
+// sqrt(a! b! c!) / ((s-a)! (s-b)! (s-c)!) with s = (a+b+c)/2 integral and >= max(a,b,c).
+double hermite_triple(int a, int b, int c) {
+  int t = a + b + c;
+  if (t & 1) return 0.0;
+  int s = t / 2;
+  if (s < a || s < b || s < c) return 0.0;
+  return std::sqrt(fact(a) * fact(b) * fact(c)) / (fact(s - a) * fact(s - b) * fact(s - c));
+}
+
+double ricker(double t, double f) {
+  const double pi = 3.14159265358979323846;
+  double tau = t - 1.0 / f;
+  double a = (pi * f * tau) * (pi * f * tau);
+  return (1.0 - 2.0 * a) * std::exp(-a);
+}
+
+// ---- KL of exp(-c|x-y|) on [-1/2, 1/2]: roots by bisection on the monotone branches ----
+struct Eig1 { double lam, w; int parity; };
+
+static double bisect(const std::function<double(double)>& f, double lo, double hi) {
+  double flo = f(lo);
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    double fm = f(mid);
+    if ((fm > 0) == (flo > 0)) { lo = mid; flo = fm; } else { hi = mid; }
+    if (hi - lo <= 1e-16 * std::max(1.0, std::fabs(mid))) break;
+  }
+  return 0.5 * (lo + hi);
+}
+
+static std::vector<Eig1> eig1d(double b, int n) {
+  const double pi = 3.14159265358979323846;
+  double c = 1.0 / b;
+  std::vector<Eig1> out;
+  for (int k = 0; (int)out.size() < n; ++k) {
+    // even: c - w tan(w/2) = 0 on (2k pi, 2k pi + pi), decreasing
+    double w = bisect([c](double x) { return c - x * std::tan(0.5 * x); },
+                      2 * k * pi + 1e-10, 2 * k * pi + pi - 1e-10);
+    out.push_back({2 * c / (w * w + c * c), w, 0});
+    if ((int)out.size() == n) break;
+    // odd: w + c tan(w/2) = 0 on (2k pi + pi, 2k pi + 2 pi), increasing
+    w = bisect([c](double x) { return x + c * std::tan(0.5 * x); },
+               2 * k * pi + pi + 1e-10, 2 * k * pi + 2 * pi - 1e-10);
+    out.push_back({2 * c / (w * w + c * c), w, 1});
+  }
+  return out;
+}
+
+static double phi1(double x, const Eig1& e) {
+  double u = x - 0.5;
+  if (e.parity == 0) return std::cos(e.w * u) / std::sqrt(0.5 + std::sin(e.w) / (2 * e.w));
+  return std::sin(e.w * u) / std::sqrt(0.5 - std::sin(e.w) / (2 * e.w));
+}
+
+std::string build_problem(Problem& pr, int N, int sx, int sy, int M, double sigma, double bx,
+                          double by, double g0, int p, int p_in, double dt, double alpha0,
+                          double alpha1, const SourceDesc& src) {
+  if (N < 2 || sx < 1 || sy < 1 || sx != sy) return "grid: N >= 2 and nsub_x == nsub_y >= 1 required";
+  if (N % sx) return "grid: N must be divisible by the subdomain count";
+  if (M < 0 || M > 12 || p < 0 || p_in < 0 || p > 10 || p_in > 20) return "pce/kl: unsupported M, p or p_in";
+  if (!(dt > 0) || !(sigma >= 0)) return "params: dt > 0 and sigma >= 0 required";
+  if (M > 0 && !(bx > 0 && by > 0)) return "kl: correlation lengths must be positive";
+  pr.N = N; pr.s = sx; pr.H = N / sx; pr.L = pr.H + 1; pr.nl = pr.L * pr.L; pr.nsub = sx * sx;
+  pr.M = M; pr.p = p; pr.p_in = p_in; pr.sigma = sigma; pr.bx = bx; pr.by = by; pr.g0 = g0;
+  pr.dt = dt; pr.alpha0 = alpha0; pr.alpha1 = alpha1; pr.h = 1.0 / N; pr.src = src;
+  auto Aout = multi_indices(M, p);
+  auto Ain = multi_indices(M, p_in);
+  pr.P = (int)Aout.size();
+  pr.PI = (int)Ain.size();
+  pr.alpha_out = Aout;
+  const int P = pr.P, PI = pr.PI, H = pr.H, L = pr.L, nl = pr.nl, nsub = pr.nsub;
+
+  // triple products grouped by output mode k
+  pr.gk_ptr.assign(P + 1, 0);
+  pr.gk_i.clear(); pr.gk_j.clear(); pr.gk_v.clear();
+  for (int k = 0; k < P; ++k) {
+    for (int i = 0; i < PI; ++i)
+      for (int j = 0; j < P; ++j) {
+        double v = 1.0;
+        for (int d = 0; d < M && v != 0.0; ++d) v *= hermite_triple(Ain[i][d], Aout[j][d], Aout[k][d]);
+        if (v != 0.0) { pr.gk_i.push_back(i); pr.gk_j.push_back(j); pr.gk_v.push_back(v); }
+      }
+    pr.gk_ptr[k + 1] = (int)pr.gk_v.size();
+  }
+
+  // KL modes: products of 1-D eigenpairs, top M by lambda, ties -> lower y index, then x index
+  std::vector<Eig1> ex = eig1d(bx > 0 ? bx : 1.0, M + 1), ey = eig1d(by > 0 ? by : 1.0, M + 1);
+  struct Cand { double lam; int ix, iy; };
+  std::vector<Cand> cand;
+  for (int ix = 0; ix <= M; ++ix)
+    for (int iy = 0; iy <= M; ++iy) cand.push_back({ex[ix].lam * ey[iy].lam, ix, iy});
+  std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) {
+    if (a.lam != b.lam) return a.lam > b.lam;
+    if (a.iy != b.iy) return a.iy < b.iy;
+    return a.ix < b.ix;
+  });
+  cand.resize(M);
+  pr.kl_lambda.resize(M);
+  for (int n = 0; n < M; ++n) pr.kl_lambda[n] = cand[n].lam;
+
+  // PCE coefficients of exp(g) at a point: c_alpha = exp(g0 + |g|^2/2) prod g_n^a_n / sqrt(a_n!)
+  auto coef_at = [&](double x, double y, double* c) {
+    std::vector<double> g(M);
+    double s2 = 0.0;
+    for (int n = 0; n < M; ++n) {
+      g[n] = sigma * std::sqrt(cand[n].lam) * phi1(x, ex[cand[n].ix]) * phi1(y, ey[cand[n].iy]);
+      s2 += g[n] * g[n];
+    }
+    double c0 = std::exp(g0 + 0.5 * s2);
+    for (int i = 0; i < PI; ++i) {
+      double v = c0;
+      for (int n = 0; n < M; ++n) {
+        int a = Ain[i][n];
+        if (a) v *= std::pow(g[n], a) / std::sqrt(fact(a));
+      }
+      c[i] = v;
+    }
+  };
+  const double h = pr.h;
+  // element coefficients of the whole mesh: T1 centroid (i+2/3, j+1/3) h, T2 (i+1/3, j+2/3) h
+  std::vector<double> cT1((size_t)N * N * PI), cT2((size_t)N * N * PI);
+  for (int j = 0; j < N; ++j)
+    for (int i = 0; i < N; ++i) {
+      coef_at((i + 2.0 / 3.0) * h, (j + 1.0 / 3.0) * h, &cT1[((size_t)j * N + i) * PI]);
+      coef_at((i + 1.0 / 3.0) * h, (j + 2.0 / 3.0) * h, &cT2[((size_t)j * N + i) * PI]);
+    }
+
+  // node classes and maps
+  auto gfree = [&](int I, int J) { return I >= 1 && I <= N - 1 && J >= 1 && J <= N - 1; };
+  auto on_iface = [&](int I, int J) { return gfree(I, J) && (I % H == 0 || J % H == 0); };
+  auto is_corner = [&](int I, int J) { return gfree(I, J) && I % H == 0 && J % H == 0; };
+  std::map<long long, int> gmap, cmap;  // global node id -> interface / corner index
+  for (int J = 1; J <= N - 1; ++J)
+    for (int I = 1; I <= N - 1; ++I) {
+      if (on_iface(I, J)) gmap[(long long)J * (N + 1) + I] = (int)gmap.size();
+      if (is_corner(I, J)) cmap[(long long)J * (N + 1) + I] = (int)cmap.size();
+    }
+  pr.nG = (int)gmap.size();
+  pr.nC = (int)cmap.size();
+  pr.cls.assign((size_t)nsub * nl, DIRICHLET);
+  pr.gidx.assign((size_t)nsub * nl, -1);
+  pr.cidx.assign((size_t)nsub * nl, -1);
+  pr.cells.assign((size_t)nsub * nl, 0);
+  pr.kapE.assign((size_t)nsub * nl * PI, 0.0);
+  pr.kapN.assign((size_t)nsub * nl * PI, 0.0);
+  pr.owners.assign((size_t)pr.nG * 4, -1);
+  pr.cowners.assign((size_t)pr.nC * 4, -1);
+  pr.Dw.assign(pr.nG, 0.0);
+  pr.n_gam.assign(nsub, 0);
+  pr.loc_corner.assign((size_t)nsub * 4, -1);
+  pr.n_loc_corner.assign(nsub, 0);
+  pr.free_of_local.assign((size_t)nsub * nl, -1);
+  pr.n_free = (N - 1) * (N - 1);
+  pr.free_owner.assign(pr.n_free, -1);
+  pr.u0_local.assign((size_t)nsub * nl, 0.0);
+  std::vector<int> mult(pr.nG, 0), cmult(pr.nC, 0);
+  std::vector<std::vector<int>> gam(nsub);
+  for (int sy_ = 0; sy_ < sx; ++sy_)
+    for (int sx_ = 0; sx_ < sx; ++sx_) {
+      int sub = sy_ * sx + sx_;
+      for (int lj = 0; lj <= H; ++lj)
+        for (int li = 0; li <= H; ++li) {
+          int I = sx_ * H + li, J = sy_ * H + lj, ln = lj * L + li;
+          size_t o = (size_t)sub * nl + ln;
+          uint8_t cb = 0;
+          if (li > 0 && lj > 0) cb |= 1;
+          if (li < H && lj > 0) cb |= 2;
+          if (li > 0 && lj < H) cb |= 4;
+          if (li < H && lj < H) cb |= 8;
+          pr.cells[o] = cb;
+          if (!gfree(I, J)) continue;
+          long long gid = (long long)J * (N + 1) + I;
+          int fidx = (J - 1) * (N - 1) + (I - 1);
+          pr.free_of_local[o] = fidx;
+          if (pr.free_owner[fidx] < 0) pr.free_owner[fidx] = (int)o;
+          if (is_corner(I, J)) {
+            pr.cls[o] = CORNER;
+            int c = cmap[gid];
+            pr.cidx[o] = c;
+            pr.cowners[(size_t)c * 4 + cmult[c]++] = (int)o;
+            pr.loc_corner[(size_t)sub * 4 + pr.n_loc_corner[sub]++] = ln;
+          } else if (on_iface(I, J)) {
+            pr.cls[o] = REMAINING;
+          } else {
+            pr.cls[o] = INTERIOR;
+          }
+          if (on_iface(I, J)) {
+            int g = gmap[gid];
+            pr.gidx[o] = g;
+            pr.owners[(size_t)g * 4 + mult[g]++] = (int)o;
+            gam[sub].push_back(ln);
+          }
+          if (src.kind == 1) {
+            double x = I * h - src.x0, y = J * h - src.y0;
+            pr.u0_local[o] = src.amp * std::exp(-(x * x + y * y) / (src.width * src.width));
+          }
+        }
+      // stiffness edge weights from the subdomain's own elements (graph-Laplacian form of the
+      // P1 stiffness on right triangles: each leg carries half the element coefficient, the
+      // hypotenuse none)
+      for (int lj = 0; lj <= H; ++lj)
+        for (int li = 0; li <= H; ++li) {
+          int I = sx_ * H + li, J = sy_ * H + lj, ln = lj * L + li;
+          double* kE = &pr.kapE[((size_t)sub * nl + ln) * PI];
+          double* kN = &pr.kapN[((size_t)sub * nl + ln) * PI];
+          for (int i = 0; i < PI; ++i) {
+            double e = 0.0, n = 0.0;
+            if (li < H) {
+              if (lj < H) e += 0.5 * cT1[((size_t)J * N + I) * PI + i];
+              if (lj > 0) e += 0.5 * cT2[((size_t)(J - 1) * N + I) * PI + i];
+            }
+            if (lj < H) {
+              if (li > 0) n += 0.5 * cT1[((size_t)J * N + (I - 1)) * PI + i];
+              if (li < H) n += 0.5 * cT2[((size_t)J * N + I) * PI + i];
+            }
+            kE[i] = e;
+            kN[i] = n;
+          }
+        }
+    }
+  for (int g = 0; g < pr.nG; ++g) pr.Dw[g] = 1.0 / mult[g];
+  pr.max_corner = 0;
+  pr.nGam = 0;
+  for (int s_ = 0; s_ < nsub; ++s_) {
+    pr.n_gam[s_] = (int)gam[s_].size();
+    pr.nGam = std::max(pr.nGam, pr.n_gam[s_]);
+    pr.max_corner = std::max(pr.max_corner, pr.n_loc_corner[s_]);
+  }
+  pr.gam_ln.assign((size_t)nsub * std::max(pr.nGam, 1), -1);
+  for (int s_ = 0; s_ < nsub; ++s_)
+    for (int q = 0; q < pr.n_gam[s_]; ++q) pr.gam_ln[(size_t)s_ * pr.nGam + q] = gam[s_][q];
+
+  // point load nodes: P1 values at the source point, split over owning subdomains with D_s
+  pr.load_node.clear(); pr.load_w.clear();
+  if (src.kind == 2) {
+    int i = std::min((int)std::floor(src.x0 / h), N - 1);
+    int j = std::min((int)std::floor(src.y0 / h), N - 1);
+    double fx = src.x0 / h - i, fy = src.y0 / h - j;
+    int vi[3], vj[3];
+    double vw[3];
+    if (fy <= fx) {
+      vi[0] = i; vj[0] = j; vw[0] = 1.0 - fx;
+      vi[1] = i + 1; vj[1] = j; vw[1] = fx - fy;
+      vi[2] = i + 1; vj[2] = j + 1; vw[2] = fy;
+    } else {
+      vi[0] = i; vj[0] = j; vw[0] = 1.0 - fy;
+      vi[1] = i + 1; vj[1] = j + 1; vw[1] = fx;
+      vi[2] = i; vj[2] = j + 1; vw[2] = fy - fx;
+    }
+    for (int v = 0; v < 3; ++v) {
+      if (vw[v] == 0.0 || !gfree(vi[v], vj[v])) continue;
+      // every subdomain whose closed region contains the node receives D_s * value
+      std::vector<int> own;
+      for (int sy_ = 0; sy_ < sx; ++sy_)
+        for (int sx_ = 0; sx_ < sx; ++sx_) {
+          int li = vi[v] - sx_ * H, lj = vj[v] - sy_ * H;
+          if (li < 0 || li > H || lj < 0 || lj > H) continue;
+          own.push_back((sy_ * sx + sx_) * nl + lj * L + li);
+        }
+      for (int o : own) {
+        pr.load_node.push_back(o);
+        pr.load_w.push_back(src.amp * vw[v] / (double)own.size());
+      }
+    }
+  }
+  return "";
+}
+
+}  // namespace sgh

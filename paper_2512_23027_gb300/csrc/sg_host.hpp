@@ -1,0 +1,69 @@
+// Host-side construction of the stochastic Galerkin problem data (set-up only).
+//
+// Everything here runs once in sg_setup: Hermite multi-indices and triple products (Sec. 4,
+// G_ijk), the analytic KL eigenpairs of the separable exponential kernel (Sec. 4,
+// Eqs. CovarKer2D, KLE), the log-normal PCE of c_s at element centroids (Eqs. c0pce, LNL0),
+// the structured P1 stencils of each subdomain, the node classes of the partition (Sec. 3) and
+// the interface / corner maps.  The per-step path never touches these host arrays.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace sgh {
+
+enum NodeClass : uint8_t { DIRICHLET = 0, INTERIOR = 1, REMAINING = 2, CORNER = 3 };
+
+struct SourceDesc { int kind; double x0, y0, width, freq, amp; };
+
+struct Problem {
+  // sizes
+  int N = 0, s = 0, H = 0, L = 0, nl = 0, nsub = 0;
+  int M = 0, p = 0, p_in = 0, P = 0, PI = 0;
+  double sigma = 0, bx = 0, by = 0, g0 = 0;
+  double dt = 0, alpha0 = 0, alpha1 = 0;
+  double h = 0;
+  // Hermite triple products, grouped by the output mode k: entries [gk_ptr[k], gk_ptr[k+1])
+  std::vector<int> gk_ptr;
+  std::vector<int> gk_i, gk_j;
+  std::vector<double> gk_v;
+  // per subdomain, per local node (ln = lj * L + li)
+  std::vector<uint8_t> cls;        // nsub * nl
+  std::vector<double> kapE, kapN;  // nsub * nl * PI : stiffness edge weights to (li+1,lj), (li,lj+1)
+  std::vector<uint8_t> cells;      // nsub * nl : bit0 cell(li-1,lj-1) bit1 cell(li,lj-1) bit2 cell(li-1,lj) bit3 cell(li,lj)
+  // interface maps
+  int nG = 0, nC = 0, nGam = 0;            // global interface nodes, corners, max local interface nodes
+  std::vector<int> gidx;                   // nsub * nl : global interface index or -1
+  std::vector<int> cidx;                   // nsub * nl : global corner index or -1
+  std::vector<int> owners;                 // nG * 4 : (sub * nl + ln) of owning subdomains, -1 padded
+  std::vector<int> cowners;                // nC * 4 : same for corners
+  std::vector<double> Dw;                  // nG : 1 / multiplicity
+  std::vector<int> gam_ln;                 // nsub * nGam : local interface nodes (ascending ln), -1 padded
+  std::vector<int> n_gam;                  // nsub
+  std::vector<int> loc_corner;             // nsub * 4 : local corner ln, -1 padded
+  std::vector<int> n_loc_corner;           // nsub
+  int max_corner = 0;                      // max local corners per subdomain
+  // free nodes (global order) -> owning (sub * nl + ln) used for output
+  int n_free = 0;
+  std::vector<int> free_owner;             // n_free
+  std::vector<int> free_of_local;          // nsub * nl : global free index or -1
+  // initial displacement (local layout, mode 0) and point-load nodes
+  std::vector<double> u0_local;            // nsub * nl
+  std::vector<int> load_node;              // (sub * nl + ln) per entry
+  std::vector<double> load_w;              // P1 value * partition weight
+  SourceDesc src{};
+  // KL / PCE diagnostics
+  std::vector<double> kl_lambda;           // M
+  std::vector<std::vector<int>> alpha_out; // P multi-indices
+};
+
+// Returns "" on success, else an error message.
+std::string build_problem(Problem& pr, int N, int sx, int sy, int M, double sigma, double bx,
+                          double by, double g0, int p, int p_in, double dt, double alpha0,
+                          double alpha1, const SourceDesc& src);
+
+std::vector<std::vector<int>> multi_indices(int M, int p);
+double hermite_triple(int a, int b, int c);
+double ricker(double t, double f);
+
+}  // namespace sgh
