@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark: SG-DD time steps per second on one GB300 (or N independent replicas).
+
+Default workload: 128 x 128 grid (16641 nodes), 4 x 4 subdomains, KL with M = 3 random
+variables, Hermite PCE order 3 (P = 20 terms), sigma 0.3, correlation length 0.3, Ricker source
+(10 Hz) at (0.3, 0.5), dt from CFL 0.65, PCG relative residual 1e-8.  A "step" is one Newmark
+time step: effective load, condensed interface RHS, interface PCG with the two-level
+Neumann-Neumann preconditioner, interior recovery and Newmark update, all on the GPU.
+
+Timing: W untimed warm-up steps, then K steps, each timed with CUDA events on the solver's
+stream; a 256 MB buffer is written between timed steps so the L2 (129 MB) starts cold.  The
+headline is the optimised solver (FP32 subdomain solves + FP64 outer PCG, one CUDA graph per
+step); the plain FP64 solver is measured beside it on the same GPU.  Under torchrun each rank
+runs an independent replica (weak scaling, no data-path collective); value = steps of all ranks
+/ max over ranks of the timed duration.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this workload) on the host.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SG-DD time-steps/sec & PCG iters vs plain FP64 DD-PCG at rel resid 1e-8"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_config(prob, precision):
+    return {"workload": prob.name, "grid": f"{prob.N}x{prob.N}", "nodes": (prob.N + 1) ** 2,
+            "subdomains": f"{prob.s}x{prob.s}", "kl_M": prob.M, "pce_order": prob.p, "pce_terms": prob.P,
+            "sigma": prob.sigma, "corr_len": prob.bx, "dt": prob.dt, "tol": prob.tol,
+            "precision": precision, "l2": "flushed between timed steps (256 MB write)"}
+
+
+def read_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id):
+        self.bus = bus_id
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            if self.bus is not None and self.bus.lower() not in f[1].lower():
+                continue
+            try:
+                sm.append(float(f[2]))
+                mx = float(f[3])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[6:10]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def bus_id_of(torch, dev):
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        return f"{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except Exception:
+        return None
+
+
+def start_cpu_baseline(cfg, steps):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    return subprocess.Popen([sys.executable, os.path.join(ROOT, "oracle", "bench_oracle.py"), "--config", cfg,
+                             "--steps", str(steps)], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                            env=env, cwd=ROOT)
+
+
+def finish_cpu_baseline(proc, cfg, steps, timeout):
+    if proc is None:
+        return None
+    try:
+        out, err = proc.communicate(timeout=timeout)
+        d = json.loads(out.strip().splitlines()[-1])
+        return {"value": d["steps_per_s"], "unit": "steps/s", "cores": 1, "kind": "oracle",
+                "sample": f"{steps} time steps of {cfg} after the oracle's untimed set-up "
+                          f"({d['setup_s']:.0f} s), FP64 numpy/scipy, BLAS pinned to 1 thread",
+                "seconds": d["seconds"]}
+    except Exception as e:  # a missing baseline is reported, never invented
+        proc.kill()
+        return {"value": None, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+
+def line_kernel_bytes(prob, tsize):
+    """Algorithmic bytes of one fused line-solve launch over all subdomains: CG update reads
+    r, x, p, q and writes x, r (6 vector passes), the sweep writes z (1 pass), and the line
+    factors S_j^{-1} of every subdomain are read once (L^3 values)."""
+    L = prob.N // prob.s + 1
+    nvec = prob.s * prob.s * L * L * prob.P
+    return 7 * nvec * tsize + prob.s * prob.s * L ** 3 * tsize
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return 0
+    import sg_workloads as w
+    from oracle import dd, sg
+    prob = w.config(args.config)
+    steps = max(1, min(args.steps, 3))
+    warm = min(args.warmup, 1)
+    sgp = sg.SGProblem(prob)
+    d = dd.DDSolver(prob)
+    state = None
+    if warm:
+        U, V, A, _ = dd.run_dd(sgp, d, warm)
+        state = (U, V, A, warm)
+    t0 = time.perf_counter()
+    _, _, _, it = dd.run_dd(sgp, d, steps, state=state)
+    sec = time.perf_counter() - t0
+    v = steps / sec
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": steps, "warmup": warm, "ms_per_step": 1e3 * sec / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(prob, "fp64 (CPU oracle)"),
+            "pcg_iters_per_step": sum(i for i, _ in it) / len(it),
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{steps} time steps after {warm} warm-up step(s); FP64 numpy/scipy oracle "
+                                       f"as it stands (sparse LU subdomain solves), one process"},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="ricker128")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    # the CPU baseline process starts before this process touches the GPU
+    cpu_proc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_proc = start_cpu_baseline(args.config, args.cpu_steps)
+
+    import numpy as np
+    import torch
+    import sg_workloads as w
+    from paper_2512_23027_gb300 import Solver
+    from paper_2512_23027_gb300.binding import SG_FP64, SG_MIXED
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    prob = w.config(args.config)
+    K, W = args.steps, max(args.warmup, 3)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(solver, nsteps):
+        its, inner, ms = [], 0, 0.0
+        for k in range(nsteps):
+            flush.fill_(float(k))
+            st = solver.step(1)
+            ms += st["ms"]
+            its.append(st["iters_total"])
+            inner += st["inner_total"]
+        return ms, its, inner
+
+    # ---- optimised solver (mixed precision, graph per step) ----
+    s = Solver(prob, precision=SG_MIXED, stream=stream)
+    s.step(W)
+    sampler = ClockSampler(bus_id_of(torch, local))
+    barrier()
+    l0 = s.launch_count()
+    sampler.start()
+    ms, its, inner = timed(s, K)
+    barrier()
+    clocks = sampler.stop()
+    launches = s.launch_count() - l0
+    tmax = ms
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmax = float(t.item())
+    value = world * K / (tmax / 1e3)
+
+    # ---- dominant kernel: CUDA-event timing of every line-solve launch (host-driven enqueue) ----
+    s.set_eager(True)
+    s.kernel_timing(1)
+    kr = min(K, 5)
+    for k in range(kr):
+        flush.fill_(float(k))
+        s.step(1)
+    kms, kn = s.kernel_timing(0)
+    s.set_eager(False)
+    peaks = read_peaks()
+    hbm = peaks.get("hbm_gbs")
+    kbytes = line_kernel_bytes(prob, 4)
+    achieved = kbytes / (kms / kn / 1e3) / 1e9 if kn else None
+    roofline = {"kernel": "k_line<float> (mean-operator line solve fused with the CG update)",
+                "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": (achieved / hbm) if (achieved and hbm) else None, "traffic": None,
+                "launches_timed": kn, "avg_launch_us": 1e3 * kms / kn if kn else None,
+                "bytes_per_launch": kbytes, "peak_source": "measured" if hbm else "fallback"}
+    if not hbm:
+        roofline["peak"] = 6800.0
+        roofline["frac"] = achieved / 6800.0 if achieved else None
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    e2e = None
+    if True:  # every rank measures its own replica end to end
+        src0 = prob.source
+        pe = prob.replace(source=w.Source())
+        se = Solver(pe, precision=SG_MIXED, stream=stream)
+        nf = se.n_free
+        N, h = prob.N, 1.0 / prob.N
+        i = min(int(math.floor(src0.x0 / h)), N - 1)
+        j = min(int(math.floor(src0.y0 / h)), N - 1)
+        fx, fy = src0.x0 / h - i, src0.y0 / h - j
+        if fy <= fx:
+            nodes = [((i, j), 1 - fx), ((i + 1, j), fx - fy), ((i + 1, j + 1), fy)]
+        else:
+            nodes = [((i, j), 1 - fy), ((i + 1, j + 1), fx), ((i, j + 1), fy - fx)]
+        fidx = [((b - 1) * (N - 1) + (a - 1), v) for (a, b), v in nodes if 1 <= a <= N - 1 and 1 <= b <= N - 1 and v]
+        fh = torch.zeros((K, nf), dtype=torch.float64).pin_memory()
+        uh = torch.zeros((K, nf), dtype=torch.float64).pin_memory()
+        se.step(W)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fa = fh.numpy()
+        for k in range(K):  # the user's input: the nodal Ricker load of each step
+            t = (W + k + 1) * prob.dt
+            tau = t - 1.0 / src0.freq
+            a2 = (math.pi * src0.freq * tau) ** 2
+            r = src0.amp * (1 - 2 * a2) * math.exp(-a2)
+            for fi, v in fidx:
+                fa[k, fi] = r * v
+        se.step_host(K, fh, uh)
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": world * K / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": nf * 8,
+               "d2h_bytes_per_step": nf * 8,
+               "note": "sg_step_host: per step H2D of the nodal load, one SG-DD step, D2H of the mean field"}
+        se.close()
+
+    # ---- plain FP64 DD-PCG on the same GPU ----
+    s64 = Solver(prob, precision=SG_FP64, stream=stream)
+    s64.step(3)
+    barrier()
+    K64 = max(1, min(args.fp64_steps, K))
+    ms64, its64, inner64 = timed(s64, K64)
+    barrier()
+    s64.close()
+    s.close()
+
+    if rank != 0:
+        return 0
+    cpu = finish_cpu_baseline(cpu_proc, args.config, args.cpu_steps, timeout=900)
+    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": tmax / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic", "config": workload_config(prob, "mixed (fp32 subdomain, fp64 outer)"),
+            "pcg_iters_per_step": sum(its) / K, "inner_iters_per_step": inner / K,
+            "plain_fp64": {"value": world * K64 / (ms64 / 1e3), "unit": "steps/s", "ms_per_step": ms64 / K64,
+                           "pcg_iters_per_step": sum(its64) / K64, "inner_iters_per_step": inner64 / K64,
+                           "steps": K64},
+            "speedup_vs_plain_fp64": (value / (world * K64 / (ms64 / 1e3))),
+            "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

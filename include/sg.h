@@ -145,6 +145,21 @@ int sg_get_sizes(sg_handle h, sg_sizes* out);
  * number written or a negative code. */
 int sg_get_iters(sg_handle h, int* iters, double* relres, int cap);
 
+/* Enqueue mode of sg_step: 0 (default) launches one captured CUDA graph per step whose inner
+ * and outer loops are conditional nodes; 1 enqueues the same kernels from the host with the
+ * loop conditions read back each iteration (for per-kernel profiling and debugging). */
+int sg_set_enqueue_mode(sg_handle h, int eager);
+
+/* Per-kernel CUDA-event timing in the host-driven mode: returns the accumulated device time and
+ * launch count of the kernel class selected by the previous call, then selects `which` and
+ * resets the totals.  which: 0 none, 1 mean-operator line solve (fused CG update), 2 fused SG
+ * operator apply.  Events are recorded on the stream the kernel is launched on. */
+int sg_kernel_timing(sg_handle h, int which, double* total_ms, long long* launches);
+
+/* Kernels launched by this library in this process so far (all handles), counted on the device
+ * by the first thread of every kernel; returns a negative code on error. */
+long long sg_launch_count(sg_handle h);
+
 int sg_destroy(sg_handle h);
 const char* sg_strerror(int code);
 /* Message of the last CUDA failure seen by h (or by sg_setup when h is NULL). */

@@ -87,6 +87,12 @@ def load_library(path: Optional[str] = None):
     lib.sg_get_sizes.argtypes = [C.c_void_p, P(Sizes)]
     lib.sg_get_iters.argtypes = [C.c_void_p, P(C.c_int), D, C.c_int]
     lib.sg_destroy.argtypes = [C.c_void_p]
+    lib.sg_set_enqueue_mode.argtypes = [C.c_void_p, C.c_int]
+    lib.sg_set_enqueue_mode.restype = C.c_int
+    lib.sg_kernel_timing.argtypes = [C.c_void_p, C.c_int, P(C.c_double), P(C.c_longlong)]
+    lib.sg_kernel_timing.restype = C.c_int
+    lib.sg_launch_count.argtypes = [C.c_void_p]
+    lib.sg_launch_count.restype = C.c_longlong
     lib.sg_strerror.argtypes = [C.c_int]
     lib.sg_strerror.restype = C.c_char_p
     lib.sg_last_error.argtypes = [C.c_void_p]
@@ -190,6 +196,22 @@ class Solver:
         up = C.c_void_p(_ptr(u_host)) if u_host is not None else None
         self._check(self.lib.sg_step_host(self.h, n, fp, up, C.byref(st)))
         return st.as_dict()
+
+    def set_eager(self, eager: bool):
+        """Host-driven enqueue (True) or one CUDA graph per step (False, default)."""
+        self._check(self.lib.sg_set_enqueue_mode(self.h, int(bool(eager))))
+
+    def kernel_timing(self, which: int):
+        """Return (ms, launches) accumulated for the previously selected kernel class and
+        select `which` (0 none, 1 line solve, 2 fused apply) for the following eager steps."""
+        ms = C.c_double()
+        n = C.c_longlong()
+        self._check(self.lib.sg_kernel_timing(self.h, which, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def launch_count(self) -> int:
+        """Kernels launched by the library so far in this process (device-side count)."""
+        return int(self.lib.sg_launch_count(self.h))
 
     def close(self):
         if getattr(self, "h", None):

@@ -9,14 +9,22 @@
 //   a7 Newmark update  a_{n+1}, v_{n+1}                               (Sec. 2)
 // Subdomain Dirichlet / Neumann problems are solved by a batched CG over all subdomains (and
 // right-hand sides) preconditioned by the exact mean operator I (x) A0^{-1} (line-block
-// factorisation); the CG runs to a tight relative residual so the Schur operator is applied to
-// full working precision.
+// factorisation).  In FP64 mode every kernel computes in FP64 and the subdomain CG runs to a
+// tight relative residual.  In mixed mode the subdomain CG runs in FP32; each Dirichlet solve
+// inside the interface operator gets one FP64 residual correction, so the Schur matvec keeps
+// FP64-level accuracy while the outer PCG (flexible beta), its dot products, residual
+// recurrence and the coarse solve stay FP64.
+//
+// The whole step is one CUDA graph: the inner and outer loops are conditional WHILE nodes whose
+// conditions are set on the device, so a step needs no host synchronisation.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -24,40 +32,50 @@
 #include "sg_host.hpp"
 #include "sg_kernels.cuh"
 
+using sgk::CgCtl;
 using sgk::Op;
+using sgk::OuterCtl;
 
 namespace {
 
 constexpr double ZETA = 0.25, GAMMA = 0.5;
+constexpr int NB_OUT = 128;     // blocks of the outer vector kernels (= partial count)
+constexpr int NSTREAMS = 6;     // capture depth of nested conditional bodies
+constexpr int REC_CAP = 1 << 14;
 
 template <typename T>
 struct InnerWS {
-  T *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
-  double *rz = nullptr, *rz_new = nullptr, *pq = nullptr, *rr = nullptr, *bb = nullptr;
-  int *active = nullptr, *nactive = nullptr;
+  T *x = nullptr, *r = nullptr, *z = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr;
   int cap_nb = 0;
 };
 
+template <typename T>
 struct LineFactor {
-  double* Sinv = nullptr;  // [sub][L][L][L]
-  double* Bd = nullptr;    // [sub][L][L]
-  double* Bu = nullptr;
-  float* Sinv32 = nullptr;
-  float* Bd32 = nullptr;
-  float* Bu32 = nullptr;
+  T* Sinv = nullptr;  // [sub][L][L][L]
+  T* Bd = nullptr;    // [sub][L][L]
+  T* Bu = nullptr;
+};
+
+struct Ctx {
+  cudaStream_t st;
+  int depth;
+  bool capture;
 };
 
 }  // namespace
 
 struct sg_handle_s {
   sgh::Problem pr;
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr;          // caller's stream (graph launches, copies)
+  bool own_st = false;
+  cudaStream_t cs[NSTREAMS] = {};     // private capture streams
   std::string err;
   int precision = SG_FP64, warm = SG_WARM_PREV;
-  double tol = 1e-8, inner_tol = 1e-14;
+  double tol = 1e-8, inner_tol = 1e-14, inner_tol32 = 1e-6, prec_tol32 = 1e-3;
   int max_iter = 500, inner_max = 400;
   double am = 0, bk = 0;
   long long step = 0;
+  bool eager = false;
   // device problem data
   uint8_t *cls = nullptr, *cells = nullptr;
   double *kapE = nullptr, *kapN = nullptr, *gk_v = nullptr;
@@ -70,42 +88,63 @@ struct sg_handle_s {
   int* load_node = nullptr;
   double* load_w = nullptr;
   int nload = 0;
-  LineFactor lf[2];  // 0: Dirichlet (interior free), 1: Neumann (interior + remaining free)
+  LineFactor<double> lf[2];  // 0: Dirichlet (interior free), 1: Neumann (interior + remaining free)
+  LineFactor<float> lf32[2];
   // coarse space
   double *Phi = nullptr, *Finv = nullptr;
   int nCd = 0, Rc = 0;
   // state and step work (local layout)
   double *U = nullptr, *V = nullptr, *A = nullptr, *um = nullptr, *uc = nullptr, *xm = nullptr;
-  double *ft = nullptr, *Unew = nullptr, *wa = nullptr, *wb = nullptr, *wc = nullptr, *wd = nullptr;
+  double *ft = nullptr, *Unew = nullptr, *wa = nullptr, *wb = nullptr, *wc = nullptr, *wd = nullptr, *we = nullptr;
+  float *fa = nullptr, *fb = nullptr;
   double* fext = nullptr;  // n_free
   double* outbuf = nullptr;
-  // interface vectors
-  double *xG = nullptr, *rG = nullptr, *zG = nullptr, *pG = nullptr, *qG = nullptr, *gG = nullptr;
-  double *dC = nullptr, *uC = nullptr, *scal = nullptr;
+  // interface vectors and outer control
+  double *xG = nullptr, *rG = nullptr, *zG = nullptr, *pG = nullptr, *qG = nullptr, *gG = nullptr, *roG = nullptr;
+  double *dC = nullptr, *uC = nullptr, *opart = nullptr, *opart2 = nullptr, *scal = nullptr;
+  OuterCtl* octl = nullptr;
+  int* omirror = nullptr;
+  // inner CG control (shared by both precisions; solves are sequential)
+  CgCtl ctl{};
+  int ctl_cap_nb = 0, ctl_cap_nt = 0, ctl_cap_ng = 0;
+  InnerWS<double> ws;
+  InnerWS<float> ws32;
+  // per-step records
+  long long* stepctr = nullptr;
+  int* rec_iters = nullptr;
+  double* rec_rel = nullptr;
+  int* rec_flags = nullptr;
+  unsigned long long* nlaunch = nullptr;
+  // graphs
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // [0] built-in load only, [1] + external load
+  cudaGraph_t graph[2] = {nullptr, nullptr};
   double* hscal = nullptr;  // pinned host scalars
   int* hint = nullptr;      // pinned host ints
-  InnerWS<double> ws;
   std::vector<void*> allocs;
   long long bytes = 0;
-  long long inner_iters = 0;
   std::vector<int> iters;
   std::vector<double> relres;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // per-kernel timing (host-driven enqueue only): 0 off, 1 line kernel, 2 fused apply kernel
+  int kprof = 0;
+  double kprof_ms = 0.0;
+  long long kprof_n = 0;
+  cudaEvent_t kev0 = nullptr, kev1 = nullptr;
 
-  Op<double> op64() const {
-    Op<double> o;
-    o.cls = cls; o.cells = cells; o.kapE = kapE; o.kapN = kapN;
-    o.gk_ptr = gk_ptr; o.gk_i = gk_i; o.gk_j = gk_j; o.gk_v = gk_v;
-    o.L = pr.L; o.nl = pr.nl; o.P = pr.P; o.PI = pr.PI; o.mass_h = pr.h * pr.h / 24.0;
-    return o;
-  }
-  // operator restricted to subdomains [s0, ...)
-  Op<double> op64_from(int s0) const {
-    Op<double> o = op64();
-    o.cls += (size_t)s0 * pr.nl;
-    o.cells += (size_t)s0 * pr.nl;
+  template <typename T>
+  Op<T> op(int s0 = 0) const {
+    Op<T> o;
+    o.cls = cls + (size_t)s0 * pr.nl;
+    o.cells = cells + (size_t)s0 * pr.nl;
+    if constexpr (sizeof(T) == 8) {
+      o.kapE = (const T*)kapE; o.kapN = (const T*)kapN; o.gk_v = (const T*)gk_v;
+    } else {
+      o.kapE = (const T*)kapE32; o.kapN = (const T*)kapN32; o.gk_v = (const T*)gk_v32;
+    }
     o.kapE += (size_t)s0 * pr.nl * pr.PI;
     o.kapN += (size_t)s0 * pr.nl * pr.PI;
+    o.gk_ptr = gk_ptr; o.gk_i = gk_i; o.gk_j = gk_j;
+    o.L = pr.L; o.nl = pr.nl; o.P = pr.P; o.PI = pr.PI; o.mass_h = (T)(pr.h * pr.h / 24.0);
     return o;
   }
   long long nloc() const { return (long long)pr.nsub * pr.nl; }
@@ -114,6 +153,7 @@ struct sg_handle_s {
 };
 
 static std::string g_setup_err;
+static unsigned long long* g_nlaunch_dev = nullptr;
 
 #define CK(call)                                                              \
   do {                                                                        \
@@ -164,179 +204,460 @@ static int upload(sg_handle h, T** p, const std::vector<T>& v) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Batched inner CG on a subdomain pattern (0 Dirichlet, 1 Neumann): x = K_pat^{-1} rhs for nb
-// problems (R per subdomain, subdomains from s0).  rhs must vanish outside the pattern's free
-// nodes; x is returned in ws.x.  Returns the iteration count in *its.
+// Graph helpers: a conditional handle and a conditional node whose body is captured on the next
+// capture stream.  In eager mode the same code runs the body as a host loop driven by a device
+// mirror of the condition.
 // ---------------------------------------------------------------------------------------------
-static int inner_solve(sg_handle h, int pat, int nb, int R, int s0, const double* rhs, int* its) {
-  const auto& pr = h->pr;
-  auto& ws = h->ws;
-  const long long len = (long long)pr.nl * pr.P;
-  const long long n = len * nb;
-  Op<double> op = h->op64_from(s0);
-  const int mask = pat == 0 ? sgk::MASK_I : sgk::MASK_N;
-  const double cm = h->am, ck = h->bk;
-  const int L = pr.L;
-  const int G = std::max(1, std::min(pr.P, 256 / std::max(L, 1)));
-  dim3 lb(L, G), lg(nb, (pr.P + G - 1) / G);
-  const size_t lsm = sizeof(double) * 2 * L * G;
-  const long long pstride = (long long)L * L * L;
-  const double* Sinv = h->lf[pat].Sinv + (size_t)s0 * pstride;
-  const double* Bd = h->lf[pat].Bd + (size_t)s0 * L * L;
-  const double* Bu = h->lf[pat].Bu + (size_t)s0 * L * L;
-  cudaStream_t st = h->st;
-  CK(cudaMemcpyAsync(ws.r, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemsetAsync(ws.x, 0, sizeof(double) * n, st));
-  sgk::k_line_solve<double><<<lg, lb, lsm, st>>>(L, pr.nl, pr.P, R, pstride, Sinv, Bd, Bu, ws.r, ws.z, nullptr);
-  sgk::dot<double>(nb, len, ws.r, ws.z, ws.r, ws.rz, ws.bb, st);
-  CK(cudaMemsetAsync(ws.nactive, 0, sizeof(int), st));
-  sgk::k_cg_init<<<nblk(nb), 256, 0, st>>>(nb, ws.bb, ws.active, ws.nactive);
-  CK(cudaMemcpyAsync(ws.p, ws.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-  CKL();
-  const double tol2 = h->inner_tol * h->inner_tol;
-  int it = 0;
-  while (it < h->inner_max) {
-    sgk::apply<double>(op, nb, R, ws.p, ws.p, ws.q, nullptr, cm, ck, mask, st);
-    sgk::dot<double>(nb, len, ws.p, ws.q, nullptr, ws.pq, nullptr, st);
-    sgk::k_cg_xr<double><<<nblk(n), 256, 0, st>>>(len, nb, ws.rz, ws.pq, ws.active, ws.p, ws.q, ws.x, ws.r);
-    sgk::dot<double>(nb, len, ws.r, ws.r, nullptr, ws.rr, nullptr, st);
-    CK(cudaMemsetAsync(ws.nactive, 0, sizeof(int), st));
-    sgk::k_cg_check<<<nblk(nb), 256, 0, st>>>(nb, ws.rr, ws.bb, tol2, ws.active, ws.nactive, ws.pq);
-    ++it;
-    CK(cudaMemcpyAsync(h->hint, ws.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (h->hint[0] == 0) break;
-    sgk::k_line_solve<double><<<lg, lb, lsm, st>>>(L, pr.nl, pr.P, R, pstride, Sinv, Bd, Bu, ws.r, ws.z,
-                                                   ws.active);
-    sgk::dot<double>(nb, len, ws.r, ws.z, nullptr, ws.rz_new, nullptr, st);
-    sgk::k_cg_p<double><<<nblk(n), 256, 0, st>>>(len, nb, ws.rz_new, ws.rz, ws.active, ws.z, ws.p);
-    sgk::k_copy_scalars<<<nblk(nb), 256, 0, st>>>(nb, ws.rz_new, ws.rz, ws.active);
-    CKL();
-  }
-  CKL();
-  h->inner_iters += it;
-  if (its) *its = it;
+static int make_handle(sg_handle h, Ctx& cx, cudaGraphConditionalHandle* out) {
+  *out = 0;
+  if (!cx.capture) return SG_OK;
+  cudaStreamCaptureStatus status;
+  cudaGraph_t g;
+  CK(cudaStreamGetCaptureInfo(cx.st, &status, nullptr, &g, nullptr, nullptr, nullptr));
+  CK(cudaGraphConditionalHandleCreate(out, g, 0, 0));
   return SG_OK;
 }
 
-static int ensure_ws(sg_handle h, int nb) {
-  auto& ws = h->ws;
-  if (ws.cap_nb >= nb) return SG_OK;
-  const long long len = (long long)h->pr.nl * h->pr.P * nb;
-  RET(dalloc(h, &ws.x, len)); RET(dalloc(h, &ws.r, len)); RET(dalloc(h, &ws.z, len));
-  RET(dalloc(h, &ws.p, len)); RET(dalloc(h, &ws.q, len));
-  RET(dalloc(h, &ws.rz, nb)); RET(dalloc(h, &ws.rz_new, nb)); RET(dalloc(h, &ws.pq, nb));
-  RET(dalloc(h, &ws.rr, nb)); RET(dalloc(h, &ws.bb, nb));
-  RET(dalloc(h, &ws.active, nb)); RET(dalloc(h, &ws.nactive, 1));
-  ws.cap_nb = nb;
+static int cond_node(sg_handle h, Ctx& cx, cudaGraphConditionalHandle hnd, bool is_while, const int* mirror,
+                     const std::function<int(Ctx&)>& body) {
+  if (!cx.capture) {
+    // eager: evaluate the device condition on the host
+    for (int guard = 0; guard < 100000; ++guard) {
+      CK(cudaMemcpyAsync(h->hint, mirror, sizeof(int), cudaMemcpyDeviceToHost, cx.st));
+      CK(cudaStreamSynchronize(cx.st));
+      if (!h->hint[0]) return SG_OK;
+      RET(body(cx));
+      if (!is_while) return SG_OK;
+    }
+    h->err = "loop guard exceeded";
+    return SG_ETIMEOUT;
+  }
+  if (cx.depth + 1 >= NSTREAMS) { h->err = "conditional nesting too deep"; return SG_ENOTSUP; }
+  cudaStreamCaptureStatus status;
+  cudaGraph_t g;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  CK(cudaStreamGetCaptureInfo(cx.st, &status, nullptr, &g, &deps, nullptr, &ndeps));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = hnd;
+  np.conditional.type = is_while ? cudaGraphCondTypeWhile : cudaGraphCondTypeIf;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &np));
+  CK(cudaStreamUpdateCaptureDependencies(cx.st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  Ctx child{h->cs[cx.depth + 1], cx.depth + 1, true};
+  cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(child.st, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  int rc = body(child);
+  cudaGraph_t tmp;
+  cudaError_t e = cudaStreamEndCapture(child.st, &tmp);
+  if (rc != SG_OK) return rc;
+  if (e != cudaSuccess) { h->err = std::string("body capture: ") + cudaGetErrorString(e); return SG_ECUDA; }
   return SG_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batched inner CG on a subdomain pattern (0 Dirichlet, 1 Neumann): x = K_pat^{-1} rhs for nb
+// problems (R per subdomain, subdomains from s0).  rhs must vanish outside the pattern's free
+// nodes; x is returned in ws.x (FP64) or ws32.x (FP32).
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+static InnerWS<T>& wsT(sg_handle h);
+template <>
+InnerWS<double>& wsT<double>(sg_handle h) { return h->ws; }
+template <>
+InnerWS<float>& wsT<float>(sg_handle h) { return h->ws32; }
+
+template <typename T>
+static const LineFactor<T>& lfT(sg_handle h, int pat);
+template <>
+const LineFactor<double>& lfT<double>(sg_handle h, int pat) { return h->lf[pat]; }
+template <>
+const LineFactor<float>& lfT<float>(sg_handle h, int pat) { return h->lf32[pat]; }
+
+// apply tile configuration: lines per block, dynamic shared memory, kappa staging
+template <typename T>
+static void apply_cfg(const sgh::Problem& pr, int nb, int* TL, int* NT, size_t* sm, int* stage) {
+  const int L = pr.L, P = pr.P, PI = pr.PI;
+  const size_t nnz = pr.gk_v.size();
+  auto base = [&](int t) {
+    return sizeof(T) * ((size_t)P * ((size_t)(t + 2) * L + 2 * ((size_t)t * (L - 1) + (size_t)(t + 1) * L)) + nnz) +
+           sizeof(unsigned) * nnz + sizeof(int) * (P + 1) + 16;
+  };
+  auto kap = [&](int t) { return sizeof(T) * (size_t)PI * ((size_t)t * (L - 1) + (size_t)(t + 1) * L); };
+  int best = 1;
+  for (int t : {8, 4, 2, 1}) {
+    if (t > L) continue;
+    const long long blocks = (long long)nb * ((L + t - 1) / t);
+    if (base(t) + kap(t) <= 110 * 1024 && (blocks >= 256 || t == 1)) { best = t; break; }
+  }
+  while (best > 1 && base(best) > 200 * 1024) best /= 2;
+  *TL = best;
+  *NT = (L + best - 1) / best;
+  *stage = base(best) + kap(best) <= 200 * 1024 ? 1 : 0;
+  *sm = base(best) + (*stage ? kap(best) : 0);
+}
+
+template <typename T, typename TO, bool FUSEDP, bool DOT>
+static int launch_apply(sg_handle h, cudaStream_t st, const Op<T>& op, int nb, int R, const T* xm, const T* xk, TO* y,
+                        const TO* add, double cm, double ck, int mask, T* p0 = nullptr, T* p1 = nullptr,
+                        const T* z = nullptr) {
+  int TL, NT, stage;
+  size_t sm;
+  apply_cfg<T>(h->pr, nb, &TL, &NT, &sm, &stage);
+  auto kern = sgk::k_apply<T, TO, FUSEDP, DOT>;
+  kern<<<(unsigned)((long long)nb * NT), 256, sm, st>>>(op, nb, R, TL, NT, (int)h->pr.gk_v.size(), stage, xm, xk, y, add,
+                                                        (T)cm, (T)ck, mask, p0, p1, z,
+                                                        h->ctl.parity, h->ctl.beta, h->ctl.active, h->ctl.part_pq);
+  CKL();
+  return SG_OK;
+}
+
+// line-solve block: G modes (fast thread index) x Lp rows, G * Lp a multiple of 32; FP32 covers
+// the modes of a problem with about two blocks, FP64 spreads them over more blocks.
+template <typename T>
+static size_t line_smem(int L, int G) {
+  return sizeof(T) * (2 * (size_t)L * L + 2 * (size_t)L * L * G + (size_t)L * G);
+}
+
+// line-solve block: G modes (fast thread index) x Lp rows, G * Lp a multiple of 32; the residual
+// and solution slices of the block live in shared memory (budget 200 KB).  FP32 covers the
+// modes of a problem with about two blocks, FP64 spreads them over more blocks.
+template <typename T>
+static void line_cfg(const sgh::Problem& pr, int* G, int* Lp) {
+  const int L = pr.L, P = pr.P;
+  int g = sizeof(T) == 8 ? 2 : (P + 1) / 2;
+  g = std::max(1, std::min(g, 1024 / L));
+  while (g > 1 && line_smem<T>(L, g) > 200 * 1024) --g;
+  int lp = L;
+  while ((g * lp) % 32) ++lp;
+  *G = g;
+  *Lp = lp;
+}
+
+static int ensure_ctl(sg_handle h, int nb, int nt, int ng) {
+  if (h->ctl_cap_nb >= nb && h->ctl_cap_nt >= nt && h->ctl_cap_ng >= ng) return SG_OK;
+  nb = std::max(nb, h->ctl_cap_nb);
+  nt = std::max(nt, h->ctl_cap_nt);
+  ng = std::max(ng, h->ctl_cap_ng);
+  auto& c = h->ctl;
+  RET(dalloc(h, &c.rz, nb)); RET(dalloc(h, &c.bb, nb)); RET(dalloc(h, &c.beta, nb));
+  RET(dalloc(h, &c.active, nb));
+  RET(dalloc(h, &c.part_pq, (long long)nb * nt));
+  RET(dalloc(h, &c.part_rz, (long long)nb * ng)); RET(dalloc(h, &c.part_rr, (long long)nb * ng));
+  if (!c.counter) {
+    RET(dalloc(h, &c.counter, 1)); RET(dalloc(h, &c.parity, 1)); RET(dalloc(h, &c.it, 1));
+    RET(dalloc(h, &c.it_total, 1)); RET(dalloc(h, &c.cond, 1)); RET(dalloc(h, &c.breakdown, 1));
+  }
+  h->ctl_cap_nb = nb; h->ctl_cap_nt = nt; h->ctl_cap_ng = ng;
+  return SG_OK;
+}
+
+template <typename T>
+static int ensure_ws(sg_handle h, int nb) {
+  auto& w = wsT<T>(h);
+  if (w.cap_nb < nb) {
+    const long long len = (long long)h->pr.nl * h->pr.P * nb;
+    RET(dalloc(h, &w.x, len)); RET(dalloc(h, &w.r, len)); RET(dalloc(h, &w.z, len));
+    RET(dalloc(h, &w.p0, len)); RET(dalloc(h, &w.p1, len)); RET(dalloc(h, &w.q, len));
+    w.cap_nb = nb;
+  }
+  int TL, NT, stage;
+  size_t sm;
+  apply_cfg<T>(h->pr, nb, &TL, &NT, &sm, &stage);
+  int G, Lp;
+  line_cfg<T>(h->pr, &G, &Lp);
+  return ensure_ctl(h, nb, NT, (h->pr.P + G - 1) / G);
+}
+
+// CUDA-event timing of one kernel launch on its stream (host-driven enqueue only)
+static int kprof_begin(sg_handle h, Ctx& cx, int which) {
+  if (h->kprof != which || cx.capture) return SG_OK;
+  CK(cudaEventRecord(h->kev0, cx.st));
+  return SG_OK;
+}
+static int kprof_end(sg_handle h, Ctx& cx, int which) {
+  if (h->kprof != which || cx.capture) return SG_OK;
+  CK(cudaEventRecord(h->kev1, cx.st));
+  CK(cudaEventSynchronize(h->kev1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, h->kev0, h->kev1));
+  h->kprof_ms += ms;
+  h->kprof_n += 1;
+  return SG_OK;
+}
+
+template <typename T>
+static int enq_inner(sg_handle h, Ctx& cx, int pat, int nb, int R, int s0, const T* rhs, double tol_override = 0.0) {
+  const auto& pr = h->pr;
+  auto& w = wsT<T>(h);
+  const long long n = (long long)pr.nl * pr.P * nb;
+  const Op<T> op = h->op<T>(s0);
+  const int mask = pat == 0 ? sgk::MASK_I : sgk::MASK_N;
+  const int L = pr.L;
+  int G, Lp;
+  line_cfg<T>(pr, &G, &Lp);
+  const int NG = (pr.P + G - 1) / G;
+  int TL, NT, stage;
+  size_t asm_;
+  apply_cfg<T>(pr, nb, &TL, &NT, &asm_, &stage);
+  const long long pstride = (long long)L * L * L;
+  const auto& lf = lfT<T>(h, pat);
+  const T* Sinv = lf.Sinv + (size_t)s0 * pstride;
+  const T* Bd = lf.Bd + (size_t)s0 * L * L;
+  const T* Bu = lf.Bu + (size_t)s0 * L * L;
+  const double tol = tol_override > 0.0 ? tol_override : (sizeof(T) == 8 ? h->inner_tol : h->inner_tol32);
+  const double tol2 = tol * tol;
+  // right-hand sides whose squared norm is at the underflow level of T are left at x = 0
+  const double bb_min = sizeof(T) == 8 ? 1e-280 : 1e-60;
+  const int imax = sizeof(T) == 8 ? h->inner_max : std::min(h->inner_max, 120);
+  const dim3 lb(G, Lp);
+  const unsigned lg = (unsigned)nb * NG;
+  const size_t lsm = line_smem<T>(L, G);
+  CK(cudaMemcpyAsync(w.r, rhs, sizeof(T) * n, cudaMemcpyDeviceToDevice, cx.st));
+  CK(cudaMemsetAsync(w.x, 0, sizeof(T) * n, cx.st));
+  cudaGraphConditionalHandle hnd;
+  RET(make_handle(h, cx, &hnd));
+  sgk::k_line<T><<<lg, lb, lsm, cx.st>>>(L, pr.nl, pr.P, R, NG, NT, pstride, Sinv, Bd, Bu, nb, w.x, w.r, w.z, w.p0,
+                                         w.p1, w.q, h->ctl, 1, tol2, bb_min, imax, hnd, cx.capture ? 1 : 0);
+  CKL();
+  return cond_node(h, cx, hnd, true, h->ctl.cond, [&](Ctx& c2) -> int {
+    RET(kprof_begin(h, c2, 2));
+    RET((launch_apply<T, T, true, true>(h, c2.st, op, nb, R, nullptr, nullptr, w.q, nullptr, h->am, h->bk, mask,
+                                        w.p0, w.p1, w.z)));
+    RET(kprof_end(h, c2, 2));
+    RET(kprof_begin(h, c2, 1));
+    sgk::k_line<T><<<lg, lb, lsm, c2.st>>>(L, pr.nl, pr.P, R, NG, NT, pstride, Sinv, Bd, Bu, nb, w.x, w.r, w.z, w.p0,
+                                           w.p1, w.q, h->ctl, 0, tol2, bb_min, imax, hnd, c2.capture ? 1 : 0);
+    CKL();
+    RET(kprof_end(h, c2, 1));
+    return SG_OK;
+  });
 }
 
 // ---------------------------------------------------------------------------------------------
 // Interface operators
 // ---------------------------------------------------------------------------------------------
 // q = S p = sum_s R_s^T (K_GG - K_GI K_II^{-1} K_IG) R_s p
-static int schur_apply(sg_handle h, const double* p, double* q) {
+static int enq_schur(sg_handle h, Ctx& cx, const double* p, double* q) {
   const auto& pr = h->pr;
-  cudaStream_t st = h->st;
+  cudaStream_t st = cx.st;
   const int nsub = pr.nsub, nl = pr.nl, P = pr.P;
   const long long n = h->nvec();
-  Op<double> op = h->op64();
-  sgk::k_gather<double><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->gidx, h->Dw, p, h->wa, sgk::MASK_G, 0);
-  sgk::apply<double>(op, nsub, 1, h->wa, h->wa, h->wb, nullptr, -h->am, -h->bk, sgk::MASK_I, st);
-  RET(inner_solve(h, 0, nsub, 1, 0, h->wb, nullptr));
-  sgk::k_axpby<double><<<nblk(n), 256, 0, st>>>(n, 1.0, h->wa, 1.0, h->ws.x, h->wd);
-  sgk::apply<double>(op, nsub, 1, h->wd, h->wd, h->wb, nullptr, h->am, h->bk, sgk::MASK_G, st);
+  const Op<double> op = h->op<double>();
+  if (h->precision == SG_FP64) {
+    sgk::k_gather<double><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->gidx, h->Dw, p, h->wa, sgk::MASK_G, 0);
+    RET((launch_apply<double, double, false, false>(h, st, op, nsub, 1, h->wa, h->wa, h->wb, nullptr, -h->am, -h->bk,
+                                                    sgk::MASK_I)));
+    RET(enq_inner<double>(h, cx, 0, nsub, 1, 0, h->wb));
+    sgk::k_axpby<double><<<nblk(n), 256, 0, st>>>(n, 1.0, h->wa, 1.0, h->ws.x, h->wd);
+    RET((launch_apply<double, double, false, false>(h, st, op, nsub, 1, h->wd, h->wd, h->wb, nullptr, h->am, h->bk,
+                                                    sgk::MASK_G)));
+  } else {
+    const Op<float> o32 = h->op<float>();
+    // b32 = -(K32 [0; p])_I, first FP32 solve
+    sgk::k_gather<float><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->gidx, h->Dw, p, h->fa, sgk::MASK_G, 0);
+    RET((launch_apply<float, float, false, false>(h, st, o32, nsub, 1, h->fa, h->fa, h->fb, nullptr, -h->am, -h->bk,
+                                                  sgk::MASK_I)));
+    RET(enq_inner<float>(h, cx, 0, nsub, 1, 0, h->fb));
+    // y1 = K64 [w0; p] on all free rows; residual r_I = -y1_I
+    sgk::k_gather<double><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->gidx, h->Dw, p, h->wa, sgk::MASK_G, 0);
+    sgk::k_add_conv<float><<<nblk(n), 256, 0, st>>>(n, h->ws32.x, h->wa, h->wd);
+    RET((launch_apply<double, double, false, false>(h, st, op, nsub, 1, h->wd, h->wd, h->wb, nullptr, h->am, h->bk,
+                                                    sgk::MASK_FREE)));
+    sgk::k_conv_mask<double, float><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->wb, h->fb, sgk::MASK_I, -1.0);
+    RET(enq_inner<float>(h, cx, 0, nsub, 1, 0, h->fb));
+    // y2_G = y1_G + (K32 [e; 0])_G
+    RET((launch_apply<float, double, false, false>(h, st, o32, nsub, 1, h->ws32.x, h->ws32.x, h->wb, h->wb, h->am,
+                                                   h->bk, sgk::MASK_G)));
+  }
   sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, h->Dw, h->wb, q, 0);
   CKL();
   return SG_OK;
 }
 
 // z = M_NNC^{-1} r (Eq. NNCP2)
-static int precond_apply(sg_handle h, const double* r, double* z) {
+template <typename T>
+static int enq_precond_t(sg_handle h, Ctx& cx, const double* r, double* z) {
   const auto& pr = h->pr;
-  cudaStream_t st = h->st;
+  cudaStream_t st = cx.st;
   const int nsub = pr.nsub, nl = pr.nl, P = pr.P;
   const long long n = h->nvec();
-  Op<double> op = h->op64();
-  // w_s = D_s R_s r restricted to remaining nodes (Neumann RHS) and to corners
-  sgk::k_gather<double><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->gidx, h->Dw, r, h->wa, sgk::MASK_R, 1);
+  const Op<T> op = h->op<T>();
+  T* wr = sizeof(T) == 8 ? (T*)h->wa : (T*)h->fa;
+  T* wy = sizeof(T) == 8 ? (T*)h->wd : (T*)h->fb;
+  // w_s = D_s R_s r on remaining nodes (Neumann RHS) and on corners
+  sgk::k_gather<T><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->gidx, h->Dw, r, wr, sgk::MASK_R, 1);
   sgk::k_gather<double><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->gidx, h->Dw, r, h->wc, sgk::MASK_C, 1);
-  RET(inner_solve(h, 1, nsub, 1, 0, h->wa, nullptr));  // v = [y; t], t = S_rr^{-1} w_r
-  const double* v = h->ws.x;
+  // v = [y; t], t = S_rr^{-1} w_r; in mixed mode the preconditioner solve is approximate (the outer
+  // PCG uses the flexible beta)
+  RET(enq_inner<T>(h, cx, 1, nsub, 1, 0, wr, sizeof(T) == 8 ? 0.0 : h->prec_tol32));
+  const T* v = wsT<T>(h).x;
   if (pr.nC > 0) {
-    // S_cr t = (K~ [y; t; 0])_c ;  d = sum_s B^T (w_c - S_cr t) ;  u_c = F_cc^{-1} d
-    sgk::apply<double>(op, nsub, 1, v, v, h->wd, nullptr, h->am, h->bk, sgk::MASK_C, st);
-    sgk::k_corner_rhs<<<nblk((long long)pr.nC * P), 256, 0, st>>>(pr.nC, P, h->cowners, h->wc, h->wd, h->dC);
+    // S_cr t = (K~ [y; t; 0])_c ;  d = sum_s B^T (w_c - S_cr t) ;  u_c = F_cc^{-1} d  (FP64)
+    RET((launch_apply<T, T, false, false>(h, st, op, nsub, 1, v, v, wy, nullptr, h->am, h->bk, sgk::MASK_C)));
+    sgk::k_corner_rhs<T><<<nblk((long long)pr.nC * P), 256, 0, st>>>(pr.nC, P, h->cowners, h->wc, wy, h->dC);
     sgk::k_gemv<<<nblk((long long)h->nCd * 32), 256, 0, st>>>(h->nCd, h->Finv, h->dC, h->uC);
   }
-  sgk::k_coarse_extend<<<nblk((long long)nsub * pr.nGam * P), 256, 0, st>>>(
-      nsub, nl, P, pr.nGam, pr.max_corner, h->cls, h->cidx, h->gam_ln, h->n_gam, h->loc_corner,
-      h->n_loc_corner, h->Phi, h->uC, v, h->wd);
-  sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, h->Dw, h->wd, z, 1);
+  sgk::k_coarse_extend<T><<<nblk((long long)nsub * pr.nGam * P), 256, 0, st>>>(
+      nsub, nl, P, pr.nGam, pr.max_corner, h->cls, h->cidx, h->gam_ln, h->n_gam, h->loc_corner, h->n_loc_corner,
+      h->Phi, h->uC, v, h->we);
+  sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, h->Dw, h->we, z, 1);
   CKL();
   return SG_OK;
 }
 
-static int gdot(sg_handle h, const double* x, const double* y, double* out) {
-  sgk::dot<double>(1, h->nGd(), x, y, nullptr, h->scal, nullptr, h->st);
-  CK(cudaMemcpyAsync(h->hscal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-  CK(cudaStreamSynchronize(h->st));
-  *out = h->hscal[0];
-  return SG_OK;
+static int enq_precond(sg_handle h, Ctx& cx, const double* r, double* z) {
+  return h->precision == SG_FP64 ? enq_precond_t<double>(h, cx, r, z) : enq_precond_t<float>(h, cx, r, z);
 }
 
-// PCG on S x = g (Hestenes-Stiefel), x holds the initial guess; stops at ||r||/||g|| <= tol.
-static int outer_pcg(sg_handle h, int* its, double* rel_out) {
-  cudaStream_t st = h->st;
+// PCG on S x = G (Hestenes-Stiefel; flexible Polak-Ribiere beta in mixed mode); x holds the
+// initial guess; stops at ||r|| / ||G|| <= tol.
+static int enq_outer(sg_handle h, Ctx& cx) {
   const long long n = h->nGd();
-  double gg, rr, rz, pq, rzn;
-  *its = 0;
-  RET(gdot(h, h->gG, h->gG, &gg));
-  if (!std::isfinite(gg)) return SG_ENUMERIC;
-  if (gg == 0.0) {
-    CK(cudaMemsetAsync(h->xG, 0, sizeof(double) * n, st));
-    *rel_out = 0.0;
-    return SG_OK;
-  }
-  const double gn = std::sqrt(gg);
-  RET(schur_apply(h, h->xG, h->qG));
-  sgk::k_axpby<double><<<nblk(n), 256, 0, st>>>(n, 1.0, h->gG, -1.0, h->qG, h->rG);
-  RET(gdot(h, h->rG, h->rG, &rr));
-  double rel = std::sqrt(rr) / gn;
-  if (rel <= h->tol) { *rel_out = rel; return SG_OK; }
-  RET(precond_apply(h, h->rG, h->zG));
-  CK(cudaMemcpyAsync(h->pG, h->zG, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-  RET(gdot(h, h->rG, h->zG, &rz));
-  int it = 0;
-  while (it < h->max_iter) {
-    RET(schur_apply(h, h->pG, h->qG));
-    RET(gdot(h, h->pG, h->qG, &pq));
-    if (!(pq > 0.0) || !std::isfinite(pq)) { *its = it; *rel_out = rel; return SG_ENUMERIC; }
-    const double alpha = rz / pq;
-    sgk::k_axpby<double><<<nblk(n), 256, 0, st>>>(n, 1.0, h->xG, alpha, h->pG, h->xG);
-    sgk::k_axpby<double><<<nblk(n), 256, 0, st>>>(n, 1.0, h->rG, -alpha, h->qG, h->rG);
-    ++it;
-    RET(gdot(h, h->rG, h->rG, &rr));
-    rel = std::sqrt(rr) / gn;
-    if (!std::isfinite(rel)) { *its = it; *rel_out = rel; return SG_ENUMERIC; }
-    if (rel <= h->tol) break;
-    RET(precond_apply(h, h->rG, h->zG));
-    RET(gdot(h, h->rG, h->zG, &rzn));
-    const double beta = rzn / rz;
-    sgk::k_axpby<double><<<nblk(n), 256, 0, st>>>(n, 1.0, h->zG, beta, h->pG, h->pG);
-    rz = rzn;
-  }
+  const int nbo = (int)std::min<long long>(NB_OUT, std::max<long long>(1, (n + 255) / 256));
+  cudaStream_t st = cx.st;
+  const int flex = h->precision != SG_FP64;
+  sgk::k_odot<<<nbo, 256, 0, st>>>(n, h->gG, h->gG, nullptr, nullptr, h->opart, nullptr);
+  sgk::k_octl<<<1, 32, 0, st>>>(sgk::OP_INIT_G, nbo, h->opart, nullptr, h->octl, h->tol, h->max_iter, 0, 0, 0, h->omirror);
+  sgk::k_ozero_if<<<nbo, 256, 0, st>>>(n, h->octl, h->xG);
   CKL();
-  *its = it;
-  *rel_out = rel;
-  return rel <= h->tol ? SG_OK : SG_ENOTCONV;
+  RET(enq_schur(h, cx, h->xG, h->qG));
+  sgk::k_ores0<<<nbo, 256, 0, st>>>(n, h->gG, h->qG, h->rG, h->opart);
+  cudaGraphConditionalHandle hw, hif;
+  RET(make_handle(h, cx, &hw));
+  RET(make_handle(h, cx, &hif));
+  sgk::k_octl<<<1, 32, 0, st>>>(sgk::OP_RES0, nbo, h->opart, nullptr, h->octl, h->tol, h->max_iter, hw, hif,
+                                cx.capture ? 1 : 0, h->omirror);
+  CKL();
+  RET(cond_node(h, cx, hif, false, h->omirror + 1, [&](Ctx& c) -> int {
+    RET(enq_precond(h, c, h->rG, h->zG));
+    sgk::k_op<<<nbo, 256, 0, c.st>>>(n, h->octl, h->zG, h->pG, 1);
+    sgk::k_odot<<<nbo, 256, 0, c.st>>>(n, h->rG, h->zG, nullptr, nullptr, h->opart, nullptr);
+    sgk::k_octl<<<1, 32, 0, c.st>>>(sgk::OP_RZ0, nbo, h->opart, nullptr, h->octl, h->tol, h->max_iter, 0, 0, 0,
+                                    h->omirror);
+    CKL();
+    return SG_OK;
+  }));
+  return cond_node(h, cx, hw, true, h->omirror, [&](Ctx& c) -> int {
+    RET(enq_schur(h, c, h->pG, h->qG));
+    sgk::k_odot<<<nbo, 256, 0, c.st>>>(n, h->pG, h->qG, nullptr, nullptr, h->opart, nullptr);
+    sgk::k_octl<<<1, 32, 0, c.st>>>(sgk::OP_ALPHA, nbo, h->opart, nullptr, h->octl, h->tol, h->max_iter, 0, 0, 0,
+                                    h->omirror);
+    if (flex) CK(cudaMemcpyAsync(h->roG, h->rG, sizeof(double) * n, cudaMemcpyDeviceToDevice, c.st));
+    sgk::k_oupd<<<nbo, 256, 0, c.st>>>(n, h->octl, h->pG, h->qG, h->xG, h->rG, h->opart);
+    cudaGraphConditionalHandle hif2;
+    RET(make_handle(h, c, &hif2));
+    sgk::k_octl<<<1, 32, 0, c.st>>>(sgk::OP_CHECK, nbo, h->opart, nullptr, h->octl, h->tol, h->max_iter, hw, hif2,
+                                    c.capture ? 1 : 0, h->omirror);
+    CKL();
+    return cond_node(h, c, hif2, false, h->omirror + 1, [&](Ctx& c2) -> int {
+      RET(enq_precond(h, c2, h->rG, h->zG));
+      if (flex) {
+        sgk::k_odot<<<nbo, 256, 0, c2.st>>>(n, h->rG, h->zG, h->roG, h->zG, h->opart, h->opart2);
+        sgk::k_octl<<<1, 32, 0, c2.st>>>(sgk::OP_BETA_FLEX, nbo, h->opart, h->opart2, h->octl, h->tol, h->max_iter, 0,
+                                         0, 0, h->omirror);
+      } else {
+        sgk::k_odot<<<nbo, 256, 0, c2.st>>>(n, h->rG, h->zG, nullptr, nullptr, h->opart, nullptr);
+        sgk::k_octl<<<1, 32, 0, c2.st>>>(sgk::OP_BETA, nbo, h->opart, nullptr, h->octl, h->tol, h->max_iter, 0, 0, 0,
+                                         h->omirror);
+      }
+      sgk::k_op<<<nbo, 256, 0, c2.st>>>(n, h->octl, h->zG, h->pG, 0);
+      CKL();
+      return SG_OK;
+    });
+  });
+}
+
+// One time step (a1 .. a7), enqueued on cx.
+static int enq_step(sg_handle h, Ctx& cx, bool ext) {
+  const auto& pr = h->pr;
+  cudaStream_t st = cx.st;
+  const long long n = h->nvec();
+  const int nsub = pr.nsub, nl = pr.nl, P = pr.P;
+  const double dt = pr.dt;
+  const Op<double> op = h->op<double>();
+  // a1: effective load f~ = M (u~_m + alpha0 u~_c) + alpha1 K u~_c + f
+  sgk::k_newmark_pre<<<nblk(n), 256, 0, st>>>(n, dt, pr.alpha0, h->U, h->V, h->A, h->um, h->uc, h->xm);
+  RET((launch_apply<double, double, false, false>(h, st, op, nsub, 1, h->xm, h->uc, h->ft, nullptr, 1.0, pr.alpha1,
+                                                  sgk::MASK_FREE)));
+  if (h->nload)
+    sgk::k_point_load<<<nblk(h->nload), 256, 0, st>>>(h->nload, h->load_node, h->load_w, h->stepctr, dt, 1.0,
+                                                       pr.src.freq, P, h->ft);
+  if (ext)
+    sgk::k_ext_load<<<nblk(h->nloc()), 256, 0, st>>>(h->nloc(), P, h->free_of_local, h->cls, h->gidx, h->Dw, h->fext,
+                                                      h->ft);
+  CKL();
+  // a2: condensed RHS G = sum_s R_s^T (f~_G - K_GI K_II^{-1} f~_I)
+  if (h->precision == SG_FP64) {
+    sgk::k_conv_mask<double, double><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->ft, h->wa, sgk::MASK_I, 1.0);
+    RET(enq_inner<double>(h, cx, 0, nsub, 1, 0, h->wa));
+    RET((launch_apply<double, double, false, false>(h, st, op, nsub, 1, h->ws.x, h->ws.x, h->wc, h->ft, -h->am, -h->bk,
+                                                    sgk::MASK_G)));
+  } else {
+    const Op<float> o32 = h->op<float>();
+    sgk::k_conv_mask<double, float><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->ft, h->fb, sgk::MASK_I, 1.0);
+    RET(enq_inner<float>(h, cx, 0, nsub, 1, 0, h->fb));
+    sgk::k_conv_mask<float, double><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->ws32.x, h->wd, sgk::MASK_I, 1.0);
+    // wa = f~ - K64 [w0; 0] (all free rows): interior part is the residual of the first solve
+    RET((launch_apply<double, double, false, false>(h, st, op, nsub, 1, h->wd, h->wd, h->wa, h->ft, -h->am, -h->bk,
+                                                    sgk::MASK_FREE)));
+    sgk::k_conv_mask<double, float><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->wa, h->fb, sgk::MASK_I, 1.0);
+    RET(enq_inner<float>(h, cx, 0, nsub, 1, 0, h->fb));
+    // g_s = f~_G - K_GI (w0 + e) = wa_G - (K32 [e; 0])_G
+    RET((launch_apply<float, double, false, false>(h, st, o32, nsub, 1, h->ws32.x, h->ws32.x, h->wc, h->wa, -h->am,
+                                                   -h->bk, sgk::MASK_G)));
+  }
+  sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, h->Dw, h->wc, h->gG, 0);
+  CKL();
+  // a3-a5: PCG on the interface, warm-started from the previous solution in xG
+  RET(enq_outer(h, cx));
+  sgk::k_record<<<1, 32, 0, st>>>(h->octl, h->stepctr, REC_CAP, h->rec_iters, h->rec_rel, h->rec_flags);
+  // a6: interior recovery u_I = K_II^{-1} (f~_I - K_IG u_G)
+  sgk::k_gather<double><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->gidx, h->Dw, h->xG, h->wa, sgk::MASK_G, 0);
+  RET((launch_apply<double, double, false, false>(h, st, op, nsub, 1, h->wa, h->wa, h->wb, h->ft, -h->am, -h->bk,
+                                                  sgk::MASK_I)));
+  if (h->precision == SG_FP64) {
+    RET(enq_inner<double>(h, cx, 0, nsub, 1, 0, h->wb));
+    sgk::k_axpby<double><<<nblk(n), 256, 0, st>>>(n, 1.0, h->ws.x, 1.0, h->wa, h->Unew);
+  } else {
+    sgk::k_conv_mask<double, float><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->wb, h->fb, sgk::MASK_I, 1.0);
+    RET(enq_inner<float>(h, cx, 0, nsub, 1, 0, h->fb));
+    sgk::k_add_conv<float><<<nblk(n), 256, 0, st>>>(n, h->ws32.x, h->wa, h->wc);   // v = [w0; u_G]
+    RET((launch_apply<double, double, false, false>(h, st, op, nsub, 1, h->wc, h->wc, h->wb, h->ft, -h->am, -h->bk,
+                                                    sgk::MASK_I)));                  // r_I = f~_I - (K v)_I
+    sgk::k_conv_mask<double, float><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->wb, h->fb, sgk::MASK_I, 1.0);
+    RET(enq_inner<float>(h, cx, 0, nsub, 1, 0, h->fb));
+    sgk::k_add_conv<float><<<nblk(n), 256, 0, st>>>(n, h->ws32.x, h->wc, h->Unew);
+  }
+  // a7: Newmark update
+  sgk::k_newmark_post<<<nblk(n), 256, 0, st>>>(n, dt, h->Unew, h->um, h->U, h->V, h->A);
+  CKL();
+  return SG_OK;
+}
+
+static int build_graph(sg_handle h, int which) {
+  if (h->gexec[which]) return SG_OK;
+  Ctx cx{h->cs[0], 0, true};
+  CK(cudaStreamBeginCapture(cx.st, cudaStreamCaptureModeThreadLocal));
+  int rc = enq_step(h, cx, which == 1);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cx.st, &g);
+  if (rc != SG_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) { h->err = std::string("step capture: ") + cudaGetErrorString(e); return SG_ECUDA; }
+  h->graph[which] = g;
+  CK(cudaGraphInstantiate(&h->gexec[which], g, 0));
+  return SG_OK;
 }
 
 // ---------------------------------------------------------------------------------------------
 // Set-up pieces
 // ---------------------------------------------------------------------------------------------
-// Mean operator stencils and line factorisation for both patterns.
+// Mean operator stencils and line factorisation for both patterns (FP64, plus FP32 copies).
 static int build_line_factors(sg_handle h) {
   const auto& pr = h->pr;
   const int L = pr.L, nl = pr.nl, nsub = pr.nsub, H = pr.H, PI = pr.PI;
@@ -366,26 +687,31 @@ static int build_line_factors(sg_handle h) {
           if (lj < H) kd += kapN0(li, lj);
           if (lj > 0) kd += kapN0(li, lj - 1);
           Dd[o] = h->am * mh * 2.0 * ntri + h->bk * kd;
-          if (freep(li + 1, lj)) {
-            double m = mh * (cellp(li, lj - 1) + cellp(li, lj));
-            Du[o] = h->am * m - h->bk * kapE0(li, lj);
-          }
-          if (freep(li, lj + 1)) {
-            double m = mh * (cellp(li - 1, lj) + cellp(li, lj));
-            Bd[o] = h->am * m - h->bk * kapN0(li, lj);
-          }
+          if (freep(li + 1, lj)) Du[o] = h->am * mh * (cellp(li, lj - 1) + cellp(li, lj)) - h->bk * kapE0(li, lj);
+          if (freep(li, lj + 1)) Bd[o] = h->am * mh * (cellp(li - 1, lj) + cellp(li, lj)) - h->bk * kapN0(li, lj);
           if (freep(li + 1, lj + 1)) Bu[o] = h->am * mh * 2.0 * cellp(li, lj);
         }
     }
     double *dDd, *dDu;
     RET(upload(h, &dDd, Dd)); RET(upload(h, &dDu, Du));
     RET(upload(h, &h->lf[pat].Bd, Bd)); RET(upload(h, &h->lf[pat].Bu, Bu));
-    RET(dalloc(h, &h->lf[pat].Sinv, (long long)nsub * L * L * L));
+    const long long ns = (long long)nsub * L * L * L;
+    RET(dalloc(h, &h->lf[pat].Sinv, ns));
     int* dstat;
     RET(dalloc(h, &dstat, nsub));
     const size_t sm = sizeof(double) * ((size_t)L * L + 2 * L);
     if (sm > 48 * 1024) CK(cudaFuncSetAttribute(sgk::k_line_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     sgk::k_line_factor<<<nsub, 256, sm, h->st>>>(L, dDd, dDu, h->lf[pat].Bd, h->lf[pat].Bu, h->lf[pat].Sinv, dstat);
+    CKL();
+    // FP32 copies for the mixed-precision subdomain solves
+    RET(dalloc(h, &h->lf32[pat].Sinv, ns));
+    RET(dalloc(h, &h->lf32[pat].Bd, (long long)nsub * L * L));
+    RET(dalloc(h, &h->lf32[pat].Bu, (long long)nsub * L * L));
+    sgk::k_cvt<double, float><<<nblk(ns), 256, 0, h->st>>>(ns, h->lf[pat].Sinv, h->lf32[pat].Sinv);
+    sgk::k_cvt<double, float><<<nblk((long long)nsub * L * L), 256, 0, h->st>>>((long long)nsub * L * L, h->lf[pat].Bd,
+                                                                               h->lf32[pat].Bd);
+    sgk::k_cvt<double, float><<<nblk((long long)nsub * L * L), 256, 0, h->st>>>((long long)nsub * L * L, h->lf[pat].Bu,
+                                                                               h->lf32[pat].Bu);
     CKL();
     std::vector<int> stat(nsub);
     CK(cudaMemcpyAsync(stat.data(), dstat, sizeof(int) * nsub, cudaMemcpyDeviceToHost, h->st));
@@ -411,7 +737,6 @@ static bool spd_inverse(std::vector<double>& A, int n) {
       Lm[(size_t)i * n + j] = s / d;
     }
   }
-  // inverse = L^{-T} L^{-1}
   std::vector<double> Li((size_t)n * n, 0.0);
   for (int c = 0; c < n; ++c) {
     for (int i = c; i < n; ++i) {
@@ -431,7 +756,7 @@ static bool spd_inverse(std::vector<double>& A, int n) {
 }
 
 // Coarse basis Phi_s = -S_rr^{-1} S_rc (per local corner dof) and F_cc (Eq. Fcc_2), from one
-// Neumann solve per local corner dof: v = -N^{-1} K_[ir],c e, F^s e = (K~ (v + e))_c.
+// FP64 Neumann solve per local corner dof: v = -N^{-1} K_[ir],c e, F^s e = (K~ (v + e))_c.
 static int build_coarse(sg_handle h) {
   const auto& pr = h->pr;
   const int P = pr.P, nl = pr.nl, nsub = pr.nsub;
@@ -442,30 +767,30 @@ static int build_coarse(sg_handle h) {
   RET(dalloc(h, &h->dC, std::max(h->nCd, 1)));
   RET(dalloc(h, &h->uC, std::max(h->nCd, 1)));
   if (pr.nC == 0 || R == 0) return SG_OK;
-  // chunk subdomains so that the batched solve holds at most ~2048 problems
   const int chunk = std::max(1, std::min(nsub, 2048 / R));
   const long long len = (long long)nl * P;
-  RET(ensure_ws(h, chunk * R));
+  RET(ensure_ws<double>(h, chunk * R));
   double *e, *rhs, *ve, *y, *Fs;
   RET(dalloc(h, &e, len * chunk * R));
   RET(dalloc(h, &rhs, len * chunk * R));
   RET(dalloc(h, &ve, len * chunk * R));
   RET(dalloc(h, &y, len * chunk * R));
   RET(dalloc(h, &Fs, (long long)nsub * R * R));
+  Ctx cx{h->st, 0, false};
   cudaStream_t st = h->st;
   for (int s0 = 0; s0 < nsub; s0 += chunk) {
     const int ns = std::min(chunk, nsub - s0);
     const int nb = ns * R;
     const long long n = len * nb;
-    Op<double> op = h->op64_from(s0);
+    const Op<double> op = h->op<double>(s0);
     CK(cudaMemsetAsync(e, 0, sizeof(double) * n, st));
     sgk::k_coarse_units<<<nblk((long long)nb), 256, 0, st>>>(ns, R, nl, P, s0, h->loc_corner, h->n_loc_corner, e);
-    sgk::apply<double>(op, nb, R, e, e, rhs, nullptr, -h->am, -h->bk, sgk::MASK_N, st);
-    RET(inner_solve(h, 1, nb, R, s0, rhs, nullptr));
-    sgk::k_coarse_phi<<<nblk((long long)nb * pr.nGam * P), 256, 0, st>>>(ns, s0, R, nl, P, pr.nGam, h->cls,
-                                                                         h->gam_ln, h->n_gam, h->ws.x, h->Phi);
+    RET((launch_apply<double, double, false, false>(h, st, op, nb, R, e, e, rhs, nullptr, -h->am, -h->bk, sgk::MASK_N)));
+    RET(enq_inner<double>(h, cx, 1, nb, R, s0, rhs));
+    sgk::k_coarse_phi<<<nblk((long long)nb * pr.nGam * P), 256, 0, st>>>(ns, s0, R, nl, P, pr.nGam, h->cls, h->gam_ln,
+                                                                         h->n_gam, h->ws.x, h->Phi);
     sgk::k_axpby<double><<<nblk(n), 256, 0, st>>>(n, 1.0, h->ws.x, 1.0, e, ve);
-    sgk::apply<double>(op, nb, R, ve, ve, y, nullptr, h->am, h->bk, sgk::MASK_C, st);
+    RET((launch_apply<double, double, false, false>(h, st, op, nb, R, ve, ve, y, nullptr, h->am, h->bk, sgk::MASK_C)));
     sgk::k_coarse_fs<<<nblk((long long)nb * R), 256, 0, st>>>(ns, s0, R, nl, P, h->loc_corner, h->n_loc_corner, y, Fs);
     CKL();
   }
@@ -486,7 +811,6 @@ static int build_coarse(sg_handle h) {
       }
     }
   }
-  // symmetrise (the two triangles agree to rounding) and invert
   for (int i = 0; i < nCd; ++i)
     for (int j = 0; j < i; ++j) {
       double v = 0.5 * (F[(size_t)i * nCd + j] + F[(size_t)j * nCd + i]);
@@ -512,26 +836,27 @@ static int initial_state(sg_handle h) {
   cudaStream_t st = h->st;
   const long long n = h->nvec();
   const int P = pr.P;
-  Op<double> op = h->op64();
+  const Op<double> op = h->op<double>();
   {
     std::vector<double> U0((size_t)n, 0.0);
     for (long long i = 0; i < h->nloc(); ++i) U0[(size_t)i * P] = pr.u0_local[(size_t)i];
     CK(cudaMemcpyAsync(h->U, U0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
   }
   CK(cudaMemsetAsync(h->V, 0, sizeof(double) * n, st));
-  // rhs = F(0) - K U0 (local), assembled on the interface
-  sgk::apply<double>(op, pr.nsub, 1, h->U, h->U, h->wa, nullptr, 0.0, -1.0, sgk::MASK_FREE, st);
+  RET((launch_apply<double, double, false, false>(h, st, op, pr.nsub, 1, h->U, h->U, h->wa, nullptr, 0.0, -1.0,
+                                                  sgk::MASK_FREE)));
   if (h->nload)
-    sgk::k_point_load<<<nblk(h->nload), 256, 0, st>>>(h->nload, h->load_node, h->load_w, 0.0, pr.src.freq, P, h->wa);
+    sgk::k_point_load<<<nblk(h->nload), 256, 0, st>>>(h->nload, h->load_node, h->load_w, nullptr, pr.dt, 0.0,
+                                                       pr.src.freq, P, h->wa);
   sgk::k_assemble_gamma<<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, h->wa);
-  // CG on the assembled mass: x = A, r = wa, p = wb, q = wc
   CK(cudaMemsetAsync(h->A, 0, sizeof(double) * n, st));
   double rr, rr0, pq;
   RET(ldot_w(h, h->wa, h->wa, &rr));
   rr0 = rr;
   CK(cudaMemcpyAsync(h->wb, h->wa, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   for (int it = 0; it < 500 && rr > 1e-30 * rr0 && rr0 > 0.0; ++it) {
-    sgk::apply<double>(op, pr.nsub, 1, h->wb, h->wb, h->wc, nullptr, 1.0, 0.0, sgk::MASK_FREE, st);
+    RET((launch_apply<double, double, false, false>(h, st, op, pr.nsub, 1, h->wb, h->wb, h->wc, nullptr, 1.0, 0.0,
+                                                    sgk::MASK_FREE)));
     sgk::k_assemble_gamma<<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, h->wc);
     RET(ldot_w(h, h->wb, h->wc, &pq));
     const double a = rr / pq;
@@ -543,66 +868,79 @@ static int initial_state(sg_handle h) {
     rr = rn;
   }
   CKL();
-  // PCG warm start: interface restriction of U0
   sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, h->Dw, h->U, h->xG, 1);
   CKL();
   return SG_OK;
 }
 
-// ---------------------------------------------------------------------------------------------
-// One time step
-// ---------------------------------------------------------------------------------------------
-static int do_step(sg_handle h, const double* fext_dev, int* its_out, double* rel_out) {
+// Run nsteps steps (graph launches, or eager enqueue when SG_EAGER is set).
+static int run_steps(sg_handle h, int nsteps, const double* f_host, double* u_host, int* rc_out) {
   const auto& pr = h->pr;
-  cudaStream_t st = h->st;
-  const long long n = h->nvec();
-  const int nsub = pr.nsub, nl = pr.nl, P = pr.P;
-  const double dt = pr.dt;
-  const double t = (double)(h->step + 1) * dt;
-  Op<double> op = h->op64();
-  // a1: effective load f~ = M (u~_m + alpha0 u~_c) + alpha1 K u~_c + f
-  sgk::k_newmark_pre<<<nblk(n), 256, 0, st>>>(n, dt, pr.alpha0, h->U, h->V, h->A, h->um, h->uc, h->xm);
-  sgk::apply<double>(op, nsub, 1, h->xm, h->uc, h->ft, nullptr, 1.0, pr.alpha1, sgk::MASK_FREE, st);
-  if (h->nload)
-    sgk::k_point_load<<<nblk(h->nload), 256, 0, st>>>(h->nload, h->load_node, h->load_w, t, pr.src.freq, P, h->ft);
-  if (fext_dev)
-    sgk::k_ext_load<<<nblk(h->nloc()), 256, 0, st>>>(h->nloc(), P, h->free_of_local, h->cls, h->gidx, h->Dw,
-                                                      fext_dev, h->ft);
-  // a2: condensed RHS
-  sgk::k_mask<double><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->ft, h->wa, sgk::MASK_I);
-  RET(inner_solve(h, 0, nsub, 1, 0, h->wa, nullptr));
-  sgk::apply<double>(op, nsub, 1, h->ws.x, h->ws.x, h->wc, h->ft, -h->am, -h->bk, sgk::MASK_G, st);
-  sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, h->Dw, h->wc, h->gG, 0);
-  CKL();
-  // a3-a5: PCG on the interface, warm-started from the previous solution in xG
-  int its = 0;
-  double rel = 0.0;
-  int rc = outer_pcg(h, &its, &rel);
-  if (rc != SG_OK && rc != SG_ENOTCONV) return rc;
-  // a6: interior recovery
-  sgk::k_gather<double><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->gidx, h->Dw, h->xG, h->wa, sgk::MASK_G, 0);
-  sgk::apply<double>(op, nsub, 1, h->wa, h->wa, h->wb, h->ft, -h->am, -h->bk, sgk::MASK_I, st);
-  RET(inner_solve(h, 0, nsub, 1, 0, h->wb, nullptr));
-  sgk::k_axpby<double><<<nblk(n), 256, 0, st>>>(n, 1.0, h->ws.x, 1.0, h->wa, h->Unew);
-  // a7: Newmark update
-  sgk::k_newmark_post<<<nblk(n), 256, 0, st>>>(n, dt, h->Unew, h->um, h->U, h->V, h->A);
-  CKL();
-  h->step += 1;
-  *its_out = its;
-  *rel_out = rel;
-  return rc;
+  const bool ext = f_host != nullptr;
+  if (!h->eager) RET(build_graph(h, ext ? 1 : 0));
+  CK(cudaMemsetAsync(h->rec_flags, 0, sizeof(int), h->st));
+  long long first = h->step;
+  for (int s = 0; s < nsteps; ++s) {
+    if (ext)
+      CK(cudaMemcpyAsync(h->fext, f_host + (size_t)s * pr.n_free, sizeof(double) * pr.n_free, cudaMemcpyHostToDevice,
+                         h->st));
+    if (h->eager) {
+      Ctx cx{h->st, 0, false};
+      RET(enq_step(h, cx, ext));
+    } else {
+      CK(cudaGraphLaunch(h->gexec[ext ? 1 : 0], h->st));
+    }
+    if (u_host) {
+      sgk::k_gather_free<<<nblk(pr.n_free), 256, 0, h->st>>>(pr.n_free, pr.P, 0, h->free_owner, h->U, h->outbuf);
+      CKL();
+      CK(cudaMemcpyAsync(u_host + (size_t)s * pr.n_free, h->outbuf, sizeof(double) * pr.n_free, cudaMemcpyDeviceToHost,
+                         h->st));
+    }
+    h->step += 1;
+    // drain the per-step records before the ring buffer wraps
+    if ((h->step - first) == REC_CAP || s == nsteps - 1) {
+      const long long cnt = h->step - first;
+      std::vector<int> it((size_t)cnt);
+      std::vector<double> rl((size_t)cnt);
+      const long long s0 = first % REC_CAP;
+      for (long long i = 0; i < cnt; ++i) {
+        CK(cudaMemcpyAsync(&it[i], h->rec_iters + (s0 + i) % REC_CAP, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaMemcpyAsync(&rl[i], h->rec_rel + (s0 + i) % REC_CAP, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      }
+      CK(cudaStreamSynchronize(h->st));
+      h->iters.insert(h->iters.end(), it.begin(), it.end());
+      h->relres.insert(h->relres.end(), rl.begin(), rl.end());
+      first = h->step;
+    }
+  }
+  CK(cudaMemcpyAsync(h->hint, h->rec_flags, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(h->hint + 1, h->ctl.breakdown, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  *rc_out = SG_OK;
+  if (h->hint[0] & 1) *rc_out = SG_ENOTCONV;
+  if ((h->hint[0] & 2) || h->hint[1]) { h->err = "numerical breakdown in PCG"; *rc_out = SG_ENUMERIC; }
+  return SG_OK;
 }
 
 // ---------------------------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------------------------
 static void free_all(sg_handle h) {
+  for (int w = 0; w < 2; ++w) {
+    if (h->gexec[w]) cudaGraphExecDestroy(h->gexec[w]);
+    if (h->graph[w]) cudaGraphDestroy(h->graph[w]);
+  }
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
+  for (int i = 0; i < NSTREAMS; ++i)
+    if (h->cs[i]) cudaStreamDestroy(h->cs[i]);
   if (h->hscal) cudaFreeHost(h->hscal);
   if (h->hint) cudaFreeHost(h->hint);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->kev0) cudaEventDestroy(h->kev0);
+  if (h->kev1) cudaEventDestroy(h->kev1);
+  if (h->own_st && h->st) cudaStreamDestroy(h->st);
 }
 
 static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const sg_pce* pce,
@@ -615,26 +953,60 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
     h->err = "ricker source outside the unit square or non-positive frequency";
     return SG_EINVAL;
   }
+  if (prm->precision != SG_FP64 && prm->precision != SG_MIXED) { h->err = "precision"; return SG_EINVAL; }
   std::string msg = sgh::build_problem(h->pr, grid->N, grid->nsub_x, grid->nsub_y, kl->M, kl->sigma, kl->bx,
                                        kl->by, kl->g0, pce->p, pce->p_in, prm->dt, prm->alpha0, prm->alpha1, sd);
   if (!msg.empty()) { h->err = msg; return SG_EINVAL; }
   auto& pr = h->pr;
-  if (pr.L > 256) { h->err = "subdomains wider than 255 cells are not supported"; return SG_ENOTSUP; }
+  if (pr.L > 256 || pr.L * 2 > 1024) { h->err = "subdomains wider than 255 cells are not supported"; return SG_ENOTSUP; }
+  if (pr.nsub < 2) { h->err = "at least 2 x 2 subdomains are required"; return SG_ENOTSUP; }
   h->precision = prm->precision;
   h->warm = prm->warm;
   h->tol = prm->tol > 0 ? prm->tol : 1e-8;
   h->max_iter = prm->max_iter > 0 ? prm->max_iter : 500;
   h->inner_tol = prm->inner_tol > 0 ? prm->inner_tol : 1e-14;
+  h->inner_tol32 = prm->inner_tol > 0 ? std::max(prm->inner_tol, 1e-7) : 1e-6;
   h->inner_max = prm->inner_max_iter > 0 ? prm->inner_max_iter : 400;
+  h->eager = std::getenv("SG_EAGER") != nullptr;
   h->am = 1.0 / (ZETA * pr.dt * pr.dt) + pr.alpha0 * GAMMA / (ZETA * pr.dt);
   h->bk = 1.0 + pr.alpha1 * GAMMA / (ZETA * pr.dt);
+  if (!h->st) {  // private stream when the caller passes none
+    CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
+    h->own_st = true;
+  }
+  for (int i = 0; i < NSTREAMS; ++i) CK(cudaStreamCreateWithFlags(&h->cs[i], cudaStreamNonBlocking));
   CK(cudaMallocHost(&h->hscal, sizeof(double) * 16));
   CK(cudaMallocHost(&h->hint, sizeof(int) * 16));
   CK(cudaEventCreate(&h->ev0));
   CK(cudaEventCreate(&h->ev1));
-  // problem data
+  CK(cudaEventCreate(&h->kev0));
+  CK(cudaEventCreate(&h->kev1));
+  // process-wide launch counter (device symbol read by every kernel)
+  if (!g_nlaunch_dev) {
+    CK(cudaMalloc(&g_nlaunch_dev, sizeof(unsigned long long)));
+    CK(cudaMemset(g_nlaunch_dev, 0, sizeof(unsigned long long)));
+    CK(cudaMemcpyToSymbol(sgk::g_nlaunch, &g_nlaunch_dev, sizeof(void*)));
+  }
+  h->nlaunch = g_nlaunch_dev;
+  // shared-memory opt-in of the apply variants
+  {
+    const int lim = 200 * 1024;
+    CK(cudaFuncSetAttribute(sgk::k_apply<double, double, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CK(cudaFuncSetAttribute(sgk::k_apply<double, double, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CK(cudaFuncSetAttribute(sgk::k_apply<float, float, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CK(cudaFuncSetAttribute(sgk::k_apply<float, float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CK(cudaFuncSetAttribute(sgk::k_apply<float, double, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CK(cudaFuncSetAttribute(sgk::k_line<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    CK(cudaFuncSetAttribute(sgk::k_line<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  }
+  // problem data (FP64 and FP32 copies of the operator coefficients)
   RET(upload(h, &h->cls, pr.cls)); RET(upload(h, &h->cells, pr.cells));
   RET(upload(h, &h->kapE, pr.kapE)); RET(upload(h, &h->kapN, pr.kapN));
+  {
+    std::vector<float> e32(pr.kapE.begin(), pr.kapE.end()), n32(pr.kapN.begin(), pr.kapN.end());
+    std::vector<float> g32(pr.gk_v.begin(), pr.gk_v.end());
+    RET(upload(h, &h->kapE32, e32)); RET(upload(h, &h->kapN32, n32)); RET(upload(h, &h->gk_v32, g32));
+  }
   RET(upload(h, &h->gk_ptr, pr.gk_ptr)); RET(upload(h, &h->gk_i, pr.gk_i)); RET(upload(h, &h->gk_j, pr.gk_j));
   RET(upload(h, &h->gk_v, pr.gk_v));
   RET(upload(h, &h->gidx, pr.gidx)); RET(upload(h, &h->cidx, pr.cidx));
@@ -646,20 +1018,44 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   h->nload = (int)pr.load_node.size();
   RET(dalloc(h, &h->nodew, h->nloc()));
   sgk::k_node_weight<<<nblk(h->nloc()), 256, 0, h->st>>>((int)h->nloc(), h->cls, h->gidx, h->Dw, h->nodew);
-  // state and work vectors
   const long long n = h->nvec();
-  for (double** p : {&h->U, &h->V, &h->A, &h->um, &h->uc, &h->xm, &h->ft, &h->Unew, &h->wa, &h->wb, &h->wc, &h->wd})
+  for (double** p : {&h->U, &h->V, &h->A, &h->um, &h->uc, &h->xm, &h->ft, &h->Unew, &h->wa, &h->wb, &h->wc, &h->wd, &h->we})
     RET(dalloc(h, p, n));
+  RET(dalloc(h, &h->fa, n)); RET(dalloc(h, &h->fb, n));
   RET(dalloc(h, &h->fext, pr.n_free));
-  RET(dalloc(h, &h->outbuf, (long long)pr.n_free * pr.P));
-  for (double** p : {&h->xG, &h->rG, &h->zG, &h->pG, &h->qG, &h->gG}) RET(dalloc(h, p, h->nGd()));
+  RET(dalloc(h, &h->outbuf, 2LL * pr.n_free * pr.P));
+  for (double** p : {&h->xG, &h->rG, &h->zG, &h->pG, &h->qG, &h->gG, &h->roG}) RET(dalloc(h, p, h->nGd()));
+  RET(dalloc(h, &h->opart, NB_OUT)); RET(dalloc(h, &h->opart2, NB_OUT));
   RET(dalloc(h, &h->scal, 16));
-  RET(ensure_ws(h, pr.nsub));
+  RET(dalloc(h, &h->octl, 1)); RET(dalloc(h, &h->omirror, 2));
+  RET(dalloc(h, &h->stepctr, 1)); RET(dalloc(h, &h->rec_iters, REC_CAP)); RET(dalloc(h, &h->rec_rel, REC_CAP));
+  RET(dalloc(h, &h->rec_flags, 1));
+  RET(ensure_ws<double>(h, pr.nsub));
+  RET(ensure_ws<float>(h, pr.nsub));
   CKL();
   RET(build_line_factors(h));
   RET(build_coarse(h));
   RET(initial_state(h));
   CK(cudaStreamSynchronize(h->st));
+  return SG_OK;
+}
+
+static int fill_stats(sg_handle h, int nsteps, long long inner0, sg_stats* stats) {
+  if (!stats) return SG_OK;
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+  long long inner = 0;
+  CK(cudaMemcpy(&inner, h->ctl.it_total, sizeof(long long), cudaMemcpyDeviceToHost));
+  stats->steps = nsteps;
+  stats->step_index = (int)h->step;
+  const size_t ni = h->iters.size();
+  stats->iters_last = ni ? h->iters.back() : 0;
+  long long tot = 0;
+  for (size_t i = ni >= (size_t)nsteps ? ni - nsteps : 0; i < ni; ++i) tot += h->iters[i];
+  stats->iters_total = tot;
+  stats->inner_total = inner - inner0;
+  stats->relres_last = h->relres.empty() ? 0.0 : h->relres.back();
+  stats->ms = ms;
   return SG_OK;
 }
 
@@ -684,38 +1080,25 @@ int sg_setup(const sg_grid* grid, const sg_kl* kl, const sg_pce* pce, const sg_p
   return SG_OK;
 }
 
-int sg_step(sg_handle h, int nsteps, sg_stats* stats) {
+static int step_common(sg_handle h, int nsteps, const double* f_host, double* u_host, sg_stats* stats) {
   if (!h || nsteps < 0) return SG_EINVAL;
   h->iters.clear();
   h->relres.clear();
-  const long long inner0 = h->inner_iters;
+  long long inner0 = 0;
+  CK(cudaMemcpy(&inner0, h->ctl.it_total, sizeof(long long), cudaMemcpyDeviceToHost));
   CK(cudaEventRecord(h->ev0, h->st));
   int rc = SG_OK;
-  long long tot = 0;
-  int its = 0;
-  double rel = 0.0;
-  for (int s = 0; s < nsteps; ++s) {
-    int r = do_step(h, nullptr, &its, &rel);
-    h->iters.push_back(its);
-    h->relres.push_back(rel);
-    tot += its;
-    if (r == SG_ENOTCONV) rc = SG_ENOTCONV;
-    else if (r != SG_OK) return r;
-  }
+  RET(run_steps(h, nsteps, f_host, u_host, &rc));
   CK(cudaEventRecord(h->ev1, h->st));
   CK(cudaEventSynchronize(h->ev1));
-  if (stats) {
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-    stats->steps = nsteps;
-    stats->step_index = (int)h->step;
-    stats->iters_last = its;
-    stats->iters_total = tot;
-    stats->inner_total = h->inner_iters - inner0;
-    stats->relres_last = rel;
-    stats->ms = ms;
-  }
+  RET(fill_stats(h, nsteps, inner0, stats));
   return rc;
+}
+
+int sg_step(sg_handle h, int nsteps, sg_stats* stats) { return step_common(h, nsteps, nullptr, nullptr, stats); }
+
+int sg_step_host(sg_handle h, int nsteps, const double* f_host, double* u_host, sg_stats* stats) {
+  return step_common(h, nsteps, f_host, u_host, stats);
 }
 
 int sg_solve_batch(sg_handle* hs, int n, int nsteps, sg_stats* out_n) {
@@ -777,6 +1160,9 @@ int sg_set_state(sg_handle h, const double* src, int on_device) {
   if (!h || !src) return SG_EINVAL;
   const auto& pr = h->pr;
   const long long cnt = (long long)pr.n_free * pr.P;
+  double stepd = 0.0;
+  CK(cudaMemcpy(&stepd, src + 3 * cnt, sizeof(double), on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+  if (!(stepd >= 0) || stepd != std::floor(stepd)) return SG_EINVAL;
   double* dst[3] = {h->U, h->V, h->A};
   for (int q = 0; q < 3; ++q) {
     CK(cudaMemcpyAsync(h->outbuf, src + q * cnt, sizeof(double) * cnt,
@@ -784,58 +1170,12 @@ int sg_set_state(sg_handle h, const double* src, int on_device) {
     sgk::k_scatter_free<<<nblk(h->nvec()), 256, 0, h->st>>>(h->nloc(), pr.P, h->free_of_local, h->outbuf, dst[q]);
     CKL();
   }
-  double stepd = 0.0;
-  CK(cudaStreamSynchronize(h->st));
-  CK(cudaMemcpy(&stepd, src + 3 * cnt, sizeof(double), on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
-  if (!(stepd >= 0) || stepd != std::floor(stepd)) return SG_EINVAL;
   h->step = (long long)stepd;
+  CK(cudaMemcpyAsync(h->stepctr, &h->step, sizeof(long long), cudaMemcpyHostToDevice, h->st));
   sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, h->st>>>(pr.nG, pr.P, h->owners, h->Dw, h->U, h->xG, 1);
   CKL();
   CK(cudaStreamSynchronize(h->st));
   return SG_OK;
-}
-
-int sg_step_host(sg_handle h, int nsteps, const double* f_host, double* u_host, sg_stats* stats) {
-  if (!h || nsteps < 0) return SG_EINVAL;
-  const auto& pr = h->pr;
-  h->iters.clear();
-  h->relres.clear();
-  const long long inner0 = h->inner_iters;
-  CK(cudaEventRecord(h->ev0, h->st));
-  int rc = SG_OK, its = 0;
-  long long tot = 0;
-  double rel = 0.0;
-  for (int s = 0; s < nsteps; ++s) {
-    if (f_host)
-      CK(cudaMemcpyAsync(h->fext, f_host + (size_t)s * pr.n_free, sizeof(double) * pr.n_free,
-                         cudaMemcpyHostToDevice, h->st));
-    int r = do_step(h, f_host ? h->fext : nullptr, &its, &rel);
-    if (r == SG_ENOTCONV) rc = r;
-    else if (r != SG_OK) return r;
-    h->iters.push_back(its);
-    h->relres.push_back(rel);
-    tot += its;
-    if (u_host) {
-      sgk::k_gather_free<<<nblk(pr.n_free), 256, 0, h->st>>>(pr.n_free, pr.P, 0, h->free_owner, h->U, h->outbuf);
-      CKL();
-      CK(cudaMemcpyAsync(u_host + (size_t)s * pr.n_free, h->outbuf, sizeof(double) * pr.n_free,
-                         cudaMemcpyDeviceToHost, h->st));
-    }
-  }
-  CK(cudaEventRecord(h->ev1, h->st));
-  CK(cudaEventSynchronize(h->ev1));
-  if (stats) {
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-    stats->steps = nsteps;
-    stats->step_index = (int)h->step;
-    stats->iters_last = its;
-    stats->iters_total = tot;
-    stats->inner_total = h->inner_iters - inner0;
-    stats->relres_last = rel;
-    stats->ms = ms;
-  }
-  return rc;
 }
 
 int sg_get_sizes(sg_handle h, sg_sizes* out) {
@@ -854,6 +1194,29 @@ int sg_get_iters(sg_handle h, int* iters, double* relres, int cap) {
     if (relres) relres[i] = h->relres[i];
   }
   return n;
+}
+
+long long sg_launch_count(sg_handle h) {
+  if (!h) return SG_EINVAL;
+  unsigned long long v = 0;
+  if (cudaMemcpy(&v, h->nlaunch, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return SG_ECUDA;
+  return (long long)v;
+}
+
+int sg_set_enqueue_mode(sg_handle h, int eager) {
+  if (!h || (eager != 0 && eager != 1)) return SG_EINVAL;
+  h->eager = eager != 0;
+  return SG_OK;
+}
+
+int sg_kernel_timing(sg_handle h, int which, double* total_ms, long long* launches) {
+  if (!h || which < 0 || which > 2) return SG_EINVAL;
+  if (total_ms) *total_ms = h->kprof_ms;
+  if (launches) *launches = h->kprof_n;
+  h->kprof = which;
+  h->kprof_ms = 0.0;
+  h->kprof_n = 0;
+  return SG_OK;
 }
 
 int sg_destroy(sg_handle h) {

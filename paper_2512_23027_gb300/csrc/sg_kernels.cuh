@@ -4,6 +4,7 @@
 // ln = lj * L + li on the (H+1) x (H+1) node grid of a subdomain; problem b belongs to subdomain
 // b / R (R right-hand sides per subdomain).  Interface vectors use [global interface node][k].
 // Nodes outside a problem's free set always hold 0, so operators never need input masks.
+// Every kernel bumps a device launch counter from its first thread (for launch accounting).
 #pragma once
 #include <cmath>
 #include <cstdint>
@@ -14,6 +15,13 @@ namespace sgk {
 enum : int { DIR = 0, INT = 1, REM = 2, COR = 3 };
 constexpr int MASK_I = 1 << INT, MASK_R = 1 << REM, MASK_C = 1 << COR;
 constexpr int MASK_G = MASK_R | MASK_C, MASK_FREE = MASK_I | MASK_R | MASK_C, MASK_N = MASK_I | MASK_R;
+
+__device__ unsigned long long* g_nlaunch;  // set once per context by the host (may stay null)
+
+__device__ __forceinline__ void count_launch() {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0 && g_nlaunch)
+    atomicAdd(g_nlaunch, 1ULL);
+}
 
 // Geometry and Galerkin data of one problem family (shared by every right-hand side).
 template <typename T>
@@ -30,268 +38,455 @@ struct Op {
   T mass_h;              // h^2 / 24: unit entry of the consistent P1 mass on a right triangle
 };
 
-// ------------------------------------------------------------------------------------------
-// Stochastic Galerkin operator apply:
-//   y = add + cm (M (x) I) xm + ck (sum_i K_i (x) G_i) xk     on nodes with class in out_mask
-// The stiffness part uses the graph-Laplacian form of P1 on right triangles: for every leg
-// (a, b) with weight kappa_i(ab) (half the element coefficient per adjacent element),
-//   y_a[k] += sum_{(i,j,k) in G} kappa_i(ab) G_ijk (x_a[j] - x_b[j])       (Sec. 4, Eq. stoksub)
-// and the mass part the consistent P1 mass h^2/24 [2 1 1; 1 2 1; 1 1 2] per element, which is
-// block diagonal over the modes for a deterministic mass (Sec. 4).
-// One thread per (b, ln, k); the G entries of output mode k are contiguous.
-// ------------------------------------------------------------------------------------------
-template <typename T>
-__global__ void k_apply(Op<T> op, int nb, int R, const T* __restrict__ xm,
-                        const T* __restrict__ xk, T* __restrict__ y, const T* __restrict__ add,
-                        T cm, T ck, int out_mask) {
-  const long long total = (long long)nb * op.nl * op.P;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  const int P = op.P, L = op.L, nl = op.nl;
-  const int k = (int)(idx % P);
-  const long long t = idx / P;
-  const int ln = (int)(t % nl);
-  const int b = (int)(t / nl);
-  const int sub = b / R;
-  const long long so = (long long)sub * nl + ln;
-  const int c = op.cls[so];
-  if (!((out_mask >> c) & 1)) {
-    y[idx] = T(0);
-    return;
-  }
-  const int li = ln % L, lj = ln / L;
-  T acc = T(0);
-  if (ck != T(0)) {
-    const T* xa = xk + ((long long)b * nl + ln) * P;
-    const int e0 = op.gk_ptr[k], e1 = op.gk_ptr[k + 1];
-    T s = T(0);
-    if (li < L - 1) {
-      const T* kap = op.kapE + so * op.PI;
-      const T* xn = xa + P;
-      for (int e = e0; e < e1; ++e) s += kap[op.gk_i[e]] * op.gk_v[e] * (xa[op.gk_j[e]] - xn[op.gk_j[e]]);
-    }
-    if (li > 0) {
-      const T* kap = op.kapE + (so - 1) * op.PI;
-      const T* xn = xa - P;
-      for (int e = e0; e < e1; ++e) s += kap[op.gk_i[e]] * op.gk_v[e] * (xa[op.gk_j[e]] - xn[op.gk_j[e]]);
-    }
-    if (lj < L - 1) {
-      const T* kap = op.kapN + so * op.PI;
-      const T* xn = xa + (long long)L * P;
-      for (int e = e0; e < e1; ++e) s += kap[op.gk_i[e]] * op.gk_v[e] * (xa[op.gk_j[e]] - xn[op.gk_j[e]]);
-    }
-    if (lj > 0) {
-      const T* kap = op.kapN + (so - L) * op.PI;
-      const T* xn = xa - (long long)L * P;
-      for (int e = e0; e < e1; ++e) s += kap[op.gk_i[e]] * op.gk_v[e] * (xa[op.gk_j[e]] - xn[op.gk_j[e]]);
-    }
-    acc += ck * s;
-  }
-  if (cm != T(0)) {
-    const T* xa = xm + ((long long)b * nl + ln) * P + k;
-    const int cb = op.cells[so];
-    const long long dN = (long long)L * P;
-    T self = T(0), nbs = T(0);
-    if (cb & 1) { self += T(4); nbs += T(2) * xa[-dN - P] + xa[-dN] + xa[-P]; }  // cell (li-1, lj-1)
-    if (cb & 2) { self += T(2); nbs += xa[-dN] + xa[P]; }                        // cell (li,   lj-1)
-    if (cb & 4) { self += T(2); nbs += xa[-P] + xa[dN]; }                        // cell (li-1, lj)
-    if (cb & 8) { self += T(4); nbs += xa[P] + T(2) * xa[dN + P] + xa[dN]; }     // cell (li,   lj)
-    acc += cm * op.mass_h * (self * xa[0] + nbs);
-  }
-  if (add) acc += add[idx];
-  y[idx] = acc;
-}
-
-template <typename T>
-void apply(const Op<T>& op, int nb, int R, const T* xm, const T* xk, T* y, const T* add, T cm, T ck,
-           int out_mask, cudaStream_t st) {
-  const long long total = (long long)nb * op.nl * op.P;
-  const int bs = 256;
-  const long long grid = (total + bs - 1) / bs;
-  k_apply<T><<<(unsigned)grid, bs, 0, st>>>(op, nb, R, xm, xk, y, add, cm, ck, out_mask);
-}
+// Inner-CG control block (device memory), one per batched solve.
+struct CgCtl {
+  double* rz;        // [nb] r . z of the current iterate
+  double* bb;        // [nb] ||b||^2
+  double* beta;      // [nb]
+  int* active;       // [nb]
+  double* part_pq;   // [nb][NT]
+  double* part_rz;   // [nb][NG]
+  double* part_rr;   // [nb][NG]
+  unsigned* counter; // last-block counter of the line kernel
+  int* parity;       // which p buffer holds the current direction
+  int* it;           // iterations of the current solve
+  long long* it_total;
+  int* cond;         // mirror of the while condition (eager mode)
+  int* breakdown;    // set when p.q <= 0 or non-finite values appear
+};
 
 // ------------------------------------------------------------------------------------------
-// Deterministic per-problem dot products: one block per problem, fixed-order tree.
+// SG operator apply, tile form.
+//   y = add + cm (M (x) I) xm + ck (sum_i K_i (x) G_i) xk      on nodes with class in out_mask
+// Stiffness: graph-Laplacian form of P1 on right triangles (each leg carries half the element
+// coefficient, the hypotenuse none).  Every edge (a, b) inside a tile computes the flux
+//   z_e[k] = sum_{(i,j,k) in G} kappa_i(e) G_ijk (x_a[j] - x_b[j])          (Sec. 4, Eq. stoksub)
+// once into shared memory; node a then adds +z for edges where it is the left/bottom end and
+// -z otherwise.  Mass: consistent P1 mass h^2/24 [2 1 1; 1 2 1; 1 1 2] per element, block
+// diagonal over the modes (deterministic mass, Sec. 4).
+// A block handles TL consecutive grid lines of one problem; shared memory holds the input
+// lines (TL + 2 with halos), the differences d_e and the fluxes z_e of the block's edges.
+// FUSEDP: the input is the CG direction p_new = z + beta p_old, formed on the fly (halo
+// included) and written back for the owned lines; DOT: per-block partial of p_new . y.
 // ------------------------------------------------------------------------------------------
-template <typename T>
-__global__ void k_dot(long long len, const T* __restrict__ x, const T* __restrict__ y,
-                      const T* __restrict__ z, double* res, double* res2) {
-  const int b = blockIdx.x;
-  const T* xb = x + (long long)b * len;
-  const T* yb = y + (long long)b * len;
-  const T* zb = z ? z + (long long)b * len : nullptr;
-  double s = 0.0, s2 = 0.0;
-  for (long long i = threadIdx.x; i < len; i += blockDim.x) {
-    double xv = (double)xb[i];
-    s += xv * (double)yb[i];
-    if (zb) s2 += xv * (double)zb[i];
-  }
-  __shared__ double sh[32], sh2[32];
-  for (int o = 16; o > 0; o >>= 1) {
-    s += __shfl_down_sync(0xffffffffu, s, o);
-    s2 += __shfl_down_sync(0xffffffffu, s2, o);
-  }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) { sh[w] = s; sh2[w] = s2; }
-  __syncthreads();
-  if (w == 0) {
-    const int nw = blockDim.x >> 5;
-    s = l < nw ? sh[l] : 0.0;
-    s2 = l < nw ? sh2[l] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) {
-      s += __shfl_down_sync(0xffffffffu, s, o);
-      s2 += __shfl_down_sync(0xffffffffu, s2, o);
-    }
-    if (l == 0) {
-      res[b] = s;
-      if (res2) res2[b] = s2;
-    }
-  }
-}
-
-template <typename T>
-void dot(int nb, long long len, const T* x, const T* y, const T* z, double* res, double* res2,
-         cudaStream_t st) {
-  k_dot<T><<<nb, 512, 0, st>>>(len, x, y, z, res, res2);
-}
-
-// ------------------------------------------------------------------------------------------
-// Inner CG vector updates (per-problem scalars live on the device).
-// ------------------------------------------------------------------------------------------
-// Initialise: active = (bb > 0); rz from the first dot; p = z.
-__global__ void k_cg_init(int nb, const double* bb, int* active, int* nactive) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nb) return;
-  int a = bb[b] > 0.0;
-  active[b] = a;
-  if (a) atomicAdd(nactive, 1);
-}
-
-// alpha = rz / pq for active problems; x += alpha p; r -= alpha q
-template <typename T>
-__global__ void k_cg_xr(long long len, int nb, const double* rz, const double* pq, const int* active,
-                        const T* __restrict__ p, const T* __restrict__ q, T* __restrict__ x,
-                        T* __restrict__ r) {
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= len * nb) return;
-  int b = (int)(idx / len);
-  if (!active[b]) return;
-  double a = rz[b] / pq[b];
-  x[idx] = (T)((double)x[idx] + a * (double)p[idx]);
-  r[idx] = (T)((double)r[idx] - a * (double)q[idx]);
-}
-
-// convergence: rr <= tol^2 bb deactivates; counts active problems.
-__global__ void k_cg_check(int nb, const double* rr, const double* bb, double tol2, int* active,
-                           int* nactive, const double* pq) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nb) return;
-  if (!active[b]) return;
-  if (!(rr[b] > tol2 * bb[b]) || !(pq[b] > 0.0)) {
-    active[b] = 0;
-    return;
-  }
-  atomicAdd(nactive, 1);
-}
-
-// p = z + beta p with beta = rz_new / rz_old; rz_old <- rz_new
-template <typename T>
-__global__ void k_cg_p(long long len, int nb, const double* rz_new, const double* rz_old,
-                       const int* active, const T* __restrict__ z, T* __restrict__ p) {
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= len * nb) return;
-  int b = (int)(idx / len);
-  if (!active[b]) return;
-  double beta = rz_new[b] / rz_old[b];
-  p[idx] = (T)((double)z[idx] + beta * (double)p[idx]);
-}
-
-__global__ void k_copy_scalars(int nb, const double* src, double* dst, const int* active) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < nb && active[b]) dst[b] = src[b];
-}
-
-// ------------------------------------------------------------------------------------------
-// Mean-operator preconditioner: exact solve with A0 = cm M + ck K_0 on a free set, applied to
-// every PCE mode (the mean-based block-diagonal preconditioner I (x) A0^{-1}).  A0 is block
-// tridiagonal over the grid lines lj; the factorisation stores S_j^{-1} (dense L x L) with
-//   S_0 = D_0,  S_j = D_j - B_{j-1}^T S_{j-1}^{-1} B_{j-1}
-// and the solve is a forward and a backward sweep over the lines.  B_j couples (a, j) to
-// (a, j+1) (Bd) and to (a+1, j+1) (Bu).  Non-free nodes carry identity rows.
-// Grid: (problem b, mode group); block (L threads, G modes).
-// ------------------------------------------------------------------------------------------
-template <typename T>
-__global__ void k_line_solve(int L, int nl, int P, int R, long long pat_stride, const T* __restrict__ Sinv,
-                             const T* __restrict__ Bd, const T* __restrict__ Bu,
-                             const T* __restrict__ rin, T* __restrict__ zout, const int* active) {
+template <typename T, typename TO, bool FUSEDP, bool DOT>
+__global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, int NT, int nnz, int stage_kap,
+                                               const T* __restrict__ xm,
+                                               const T* __restrict__ xk, TO* y,
+                                               const TO* add, T cm, T ck, int out_mask,
+                                               // fused-CG inputs
+                                               T* pbuf0, T* pbuf1, const T* __restrict__ zin, const int* parity,
+                                               const double* beta, const int* active, double* part_pq) {
+  count_launch();
   extern __shared__ unsigned char smem_raw[];
-  T* w = reinterpret_cast<T*>(smem_raw);   // [L][G]
-  T* v = w + L * blockDim.y;               // [L][G]
-  const int b = blockIdx.x;
-  if (active && !active[b]) return;
+  const int P = op.P, L = op.L, nl = op.nl;
+  const int b = blockIdx.x / NT, tile = blockIdx.x % NT;
+  const int lj0 = tile * TL;
+  const int nlin = min(TL, L - lj0);  // owned lines
+  if (FUSEDP && !active[b]) return;
   const int sub = b / R;
-  const int a = threadIdx.x, m = threadIdx.y, G = blockDim.y;
-  const int k = blockIdx.y * G + m;
-  const bool ok = (a < L) && (k < P);
-  const T* S = Sinv + (long long)sub * pat_stride;
-  const T* bd = Bd + (long long)sub * L * L;
-  const T* bu = Bu + (long long)sub * L * L;
-  const T* rb = rin + (long long)b * nl * P;
-  T* zb = zout + (long long)b * nl * P;
-  // forward sweep: y_j = S_j^{-1} (r_j - B_{j-1}^T y_{j-1})
-  for (int j = 0; j < L; ++j) {
-    T rhs = T(0);
-    if (ok) {
-      rhs = rb[(long long)(j * L + a) * P + k];
-      if (j > 0) {
-        rhs -= bd[(j - 1) * L + a] * v[a * G + m];
-        if (a > 0) rhs -= bu[(j - 1) * L + a - 1] * v[(a - 1) * G + m];
-      }
-    }
-    __syncthreads();
-    if (a < L) w[a * G + m] = rhs;
-    __syncthreads();
-    if (ok) {
-      const T* Sj = S + (long long)j * L * L + (long long)a * L;
-      T s0 = T(0), s1 = T(0);
-      int c = 0;
-      for (; c + 1 < L; c += 2) {
-        s0 += Sj[c] * w[c * G + m];
-        s1 += Sj[c + 1] * w[(c + 1) * G + m];
-      }
-      if (c < L) s0 += Sj[c] * w[c * G + m];
-      T yv = s0 + s1;
-      zb[(long long)(j * L + a) * P + k] = yv;
-      v[a * G + m] = yv;
-    }
-    __syncthreads();
+  T* xs = reinterpret_cast<T*>(smem_raw);            // [(TL+2)][L][P]
+  T* dE = xs + (size_t)(TL + 2) * L * P;            // [TL][L-1][P]
+  T* dN = dE + (size_t)TL * (L - 1) * P;            // [TL+1][L][P]
+  T* zE = dN + (size_t)(TL + 1) * L * P;
+  T* zN = zE + (size_t)TL * (L - 1) * P;
+  T* gv_s = zN + (size_t)(TL + 1) * L * P;                 // [nnz] G values
+  T* kE_s = gv_s + nnz;                                    // [TL][L-1][PI] (when staged)
+  T* kN_s = kE_s + (size_t)TL * (L - 1) * op.PI;           // [TL+1][L][PI]
+  unsigned* gpk_s = reinterpret_cast<unsigned*>(stage_kap ? kN_s + (size_t)(TL + 1) * L * op.PI : kE_s);
+  int* gptr_s = reinterpret_cast<int*>(gpk_s + nnz);        // [P+1]
+  const long long pb = (long long)b * nl * P;
+  const int nt = blockDim.x;
+  const T* pold = nullptr;
+  T* pnew = nullptr;
+  T bet = T(0);
+  if (FUSEDP) {
+    const int par = *parity;
+    pold = par ? pbuf1 : pbuf0;
+    pnew = par ? pbuf0 : pbuf1;
+    bet = (T)beta[b];
   }
-  // backward sweep: x_j = y_j - S_j^{-1} B_j x_{j+1}; v holds x_{j+1}
-  for (int j = L - 2; j >= 0; --j) {
-    T tv = T(0);
-    if (ok) {
-      tv = bd[j * L + a] * v[a * G + m];
-      if (a + 1 < L) tv += bu[j * L + a] * v[(a + 1) * G + m];
+  // phase 0: triple products (values, packed (i, j) and per-k ranges) and edge weights
+  for (int e = threadIdx.x; e < nnz; e += nt) {
+    gv_s[e] = op.gk_v[e];
+    gpk_s[e] = (unsigned)op.gk_i[e] | ((unsigned)op.gk_j[e] << 16);
+  }
+  for (int e = threadIdx.x; e <= P; e += nt) gptr_s[e] = op.gk_ptr[e];
+  if (stage_kap) {
+    const long long so0 = (long long)sub * nl;
+    const int PI = op.PI;
+    for (int e = threadIdx.x; e < nlin * (L - 1) * PI; e += nt) {
+      const int t = e / ((L - 1) * PI), rem = e % ((L - 1) * PI);
+      kE_s[e] = op.kapE[(so0 + (long long)(lj0 + t) * L) * PI + rem];
     }
-    __syncthreads();
-    if (a < L) w[a * G + m] = tv;
-    __syncthreads();
-    if (ok) {
-      const T* Sj = S + (long long)j * L * L + (long long)a * L;
-      T s0 = T(0), s1 = T(0);
-      int c = 0;
-      for (; c + 1 < L; c += 2) {
-        s0 += Sj[c] * w[c * G + m];
-        s1 += Sj[c + 1] * w[(c + 1) * G + m];
+    for (int e = threadIdx.x; e < (nlin + 1) * L * PI; e += nt) {
+      const int t = e / (L * PI), rem = e % (L * PI);
+      const int jb = lj0 - 1 + t;
+      kN_s[e] = (jb >= 0 && jb + 1 < L) ? op.kapN[(so0 + (long long)jb * L) * PI + rem] : T(0);
+    }
+  }
+  // phase 1: input lines lj0-1 .. lj0+nlin (zeros outside the grid)
+  const int nin = (nlin + 2) * L * P;
+  for (int e = threadIdx.x; e < nin; e += nt) {
+    const int t = e / (L * P);
+    const int jl = lj0 - 1 + t;
+    T v = T(0);
+    if (jl >= 0 && jl < L) {
+      const long long g = pb + (long long)jl * L * P + (e % (L * P));
+      if (FUSEDP) {
+        v = zin[g];
+        if (bet != T(0)) v += bet * pold[g];
+        if (t >= 1 && t <= nlin) pnew[g] = v;
+      } else {
+        v = xk[g];
       }
-      if (c < L) s0 += Sj[c] * w[c * G + m];
-      const long long o = (long long)(j * L + a) * P + k;
-      T xv = zb[o] - (s0 + s1);
-      zb[o] = xv;
-      v[a * G + m] = xv;
+    }
+    xs[e] = v;
+  }
+  __syncthreads();
+  // phase 2a: differences of the block's edges
+  const int nE = nlin * (L - 1), nNr = nlin + 1;
+  for (int e = threadIdx.x; e < nE * P; e += nt) {
+    const int j = e % P, ed = e / P;
+    const int t = ed / (L - 1), i = ed % (L - 1);
+    const T* xr = xs + ((size_t)(t + 1) * L + i) * P;
+    dE[e] = xr[j] - xr[P + j];
+  }
+  for (int e = threadIdx.x; e < nNr * L * P; e += nt) {
+    const int j = e % P, ed = e / P;
+    const int t = ed / L, i = ed % L;
+    const T* xb = xs + ((size_t)t * L + i) * P;
+    dN[e] = xb[j] - xb[(size_t)L * P + j];
+  }
+  __syncthreads();
+  // phase 2b: fluxes z_e[k]
+  if (ck != T(0)) {
+    const long long so0 = (long long)sub * nl;
+    const int PI = op.PI;
+    for (int e = threadIdx.x; e < nE * P; e += nt) {
+      const int k = e % P, ed = e / P;
+      const int t = ed / (L - 1), i = ed % (L - 1);
+      const T* kap = stage_kap ? kE_s + (size_t)ed * PI : op.kapE + (so0 + (long long)(lj0 + t) * L + i) * PI;
+      const T* d = dE + (size_t)ed * P;
+      T s = T(0);
+      for (int q = gptr_s[k]; q < gptr_s[k + 1]; ++q) {
+        const unsigned pk = gpk_s[q];
+        s += kap[pk & 0xffffu] * gv_s[q] * d[pk >> 16];
+      }
+      zE[e] = s;
+    }
+    for (int e = threadIdx.x; e < nNr * L * P; e += nt) {
+      const int k = e % P, ed = e / P;
+      const int t = ed / L, i = ed % L;
+      const int jb = lj0 - 1 + t;  // bottom line of the edge row
+      T s = T(0);
+      if (jb >= 0 && jb + 1 < L) {
+        const T* kap = stage_kap ? kN_s + (size_t)ed * PI : op.kapN + (so0 + (long long)jb * L + i) * PI;
+        const T* d = dN + (size_t)ed * P;
+        for (int q = gptr_s[k]; q < gptr_s[k + 1]; ++q) {
+          const unsigned pk = gpk_s[q];
+          s += kap[pk & 0xffffu] * gv_s[q] * d[pk >> 16];
+        }
+      }
+      zN[e] = s;
+    }
+  }
+  __syncthreads();
+  // phase 3: outputs of the owned lines
+  double dsum = 0.0;
+  for (int e = threadIdx.x; e < nlin * L * P; e += nt) {
+    const int k = e % P, nd = e / P;
+    const int t = nd / L, i = nd % L;
+    const int lj = lj0 + t;
+    const long long so = (long long)sub * nl + (long long)lj * L + i;
+    const long long g = pb + ((long long)lj * L + i) * P + k;
+    const int c = op.cls[so];
+    TO out = TO(0);
+    if ((out_mask >> c) & 1) {
+      T acc = T(0);
+      if (ck != T(0)) {
+        T s = T(0);
+        if (i < L - 1) s += zE[((size_t)t * (L - 1) + i) * P + k];
+        if (i > 0) s -= zE[((size_t)t * (L - 1) + i - 1) * P + k];
+        s += zN[((size_t)(t + 1) * L + i) * P + k];
+        s -= zN[((size_t)t * L + i) * P + k];
+        acc += ck * s;
+      }
+      if (cm != T(0)) {
+        const int cb = op.cells[so];
+        T self = T(0), nbs = T(0);
+        if (FUSEDP || xm == xk) {
+          const T* xa = xs + ((size_t)(t + 1) * L + i) * P + k;
+          const long long dN_ = (long long)L * P;
+          if (cb & 1) { self += T(4); nbs += T(2) * xa[-dN_ - P] + xa[-dN_] + xa[-P]; }
+          if (cb & 2) { self += T(2); nbs += xa[-dN_] + xa[P]; }
+          if (cb & 4) { self += T(2); nbs += xa[-P] + xa[dN_]; }
+          if (cb & 8) { self += T(4); nbs += xa[P] + T(2) * xa[dN_ + P] + xa[dN_]; }
+          acc += cm * op.mass_h * (self * xa[0] + nbs);
+        } else {
+          const T* xa = xm + g;
+          const long long dN_ = (long long)L * P;
+          if (cb & 1) { self += T(4); nbs += T(2) * xa[-dN_ - P] + xa[-dN_] + xa[-P]; }
+          if (cb & 2) { self += T(2); nbs += xa[-dN_] + xa[P]; }
+          if (cb & 4) { self += T(2); nbs += xa[-P] + xa[dN_]; }
+          if (cb & 8) { self += T(4); nbs += xa[P] + T(2) * xa[dN_ + P] + xa[dN_]; }
+          acc += cm * op.mass_h * (self * xa[0] + nbs);
+        }
+      }
+      out = (TO)acc;
+      if (add) out += add[g];
+      if (DOT) dsum += (double)xs[((size_t)(t + 1) * L + i) * P + k] * (double)out;
+    }
+    y[g] = out;
+  }
+  if (DOT) {
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = dsum;
+    __syncthreads();
+    if (w == 0) {
+      dsum = l < (nt >> 5) ? red[l] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+      if (l == 0) part_pq[(long long)b * NT + tile] = dsum;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Mean-operator preconditioner fused with the inner CG update and control.
+// A0 = cm M + ck K_0 on a pattern's free set is block tridiagonal over grid lines; the set-up
+// stores S_j^{-1} (dense L x L) with S_0 = D_0, S_j = D_j - B_{j-1}^T S_{j-1}^{-1} B_{j-1};
+// B_j couples (a, j) to (a, j+1) (Bd) and (a+1, j+1) (Bu).  Non-free nodes carry identity rows.
+// Grid: nb * NG blocks (problem, group of G modes); block (L, G) threads.
+//   init  : z = A0^{-1} r; partials r.z, r.r
+//   iterate: alpha = rz / sum(pq partials); x += alpha p; r -= alpha q; z = A0^{-1} r;
+//            partials r.z, r.r
+// The last block to finish reduces the partials of every problem (fixed order), updates the
+// per-problem scalars and convergence flags and sets the loop condition.
+// ------------------------------------------------------------------------------------------
+// async copy of one element (4 or 8 bytes) global -> shared (cp.async, Ampere and later)
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* sdst, const T* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  if constexpr (sizeof(T) == 8) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc));
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc));
+  }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename T>
+__global__ void k_line(int L, int nl, int P, int R, int NG, int NT, long long pat_stride,
+                       const T* __restrict__ Sinv, const T* __restrict__ Bd, const T* __restrict__ Bu, int nb,
+                       T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, T* pbuf0, T* pbuf1,
+                       const T* __restrict__ q, CgCtl ctl, int init, double tol2, double bb_min, int max_it,
+                       cudaGraphConditionalHandle cond_handle, int use_handle) {
+  count_launch();
+  extern __shared__ unsigned char smem_raw[];
+  const int G = blockDim.x;                      // modes of the block (fast index)
+  const int LL = L * L;
+  T* Sb = reinterpret_cast<T*>(smem_raw);        // [2][L][L] double-buffered S_j^{-1}
+  T* rs = Sb + 2 * LL;                           // [L lines][L][G] residual slice
+  T* ys = rs + (size_t)LL * G;                   // [L lines][L][G] solution slice
+  T* w = ys + (size_t)LL * G;                    // [L][G]
+  __shared__ double red_rz[32], red_rr[32];
+  __shared__ int am_last;
+  const int b = blockIdx.x / NG, grp = blockIdx.x % NG;
+  const int m = threadIdx.x, a = threadIdx.y;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y;
+  const int k = grp * G + m;
+  const bool ok = (a < L) && (k < P);
+  const bool act = init ? true : (ctl.active[b] != 0);
+  double s_rz = 0.0, s_rr = 0.0;
+  if (act) {
+    const int sub = b / R;
+    const T* S = Sinv + (long long)sub * pat_stride;
+    const T* bd = Bd + (long long)sub * LL;
+    const T* bu = Bu + (long long)sub * LL;
+    const long long base = (long long)b * nl * P;
+    const int kb = grp * G;
+    const int gl = min(G, P - kb);  // modes of this block
+    // prefetch S_0^{-1} while the CG update runs
+    for (int e = tid; e < LL; e += nthr) cp_async_elem(Sb + e, S + e);
+    cp_async_commit();
+    // phase A (parallel over the block's slice): x += alpha p, r -= alpha q, stage r
+    T alpha = T(0);
+    const T* pc = nullptr;
+    if (!init) {
+      double pq = 0.0;
+      for (int t = 0; t < NT; ++t) pq += ctl.part_pq[(long long)b * NT + t];
+      // a vanishing or non-finite p.q (right-hand side at the underflow level of T) freezes the
+      // problem at its current iterate; the control step below then retires it
+      const double al = (pq > 0.0 && isfinite(pq)) ? ctl.rz[b] / pq : 0.0;
+      alpha = isfinite(al) ? (T)al : T(0);
+      pc = (*ctl.parity) ? pbuf0 : pbuf1;  // p_new written by the apply kernel
+    }
+    for (int e = tid; e < LL * gl; e += nthr) {
+      const int mm = e % gl, node = e / gl;
+      const long long o = base + (long long)node * P + kb + mm;
+      T rv = r[o];
+      if (!init) {
+        x[o] += alpha * pc[o];
+        rv -= alpha * q[o];
+        r[o] = rv;
+      }
+      rs[(size_t)node * G + mm] = rv;
     }
     __syncthreads();
+    // phase B: forward sweep y_j = S_j^{-1} (r_j - B_{j-1}^T y_{j-1}) in shared memory
+    for (int j = 0; j < L; ++j) {
+      if (j + 1 < L) {
+        const T* src = S + (long long)(j + 1) * LL;
+        T* dst = Sb + ((j + 1) & 1) * LL;
+        for (int e = tid; e < LL; e += nthr) cp_async_elem(dst + e, src + e);
+      }
+      cp_async_commit();
+      if (ok) {
+        T rhs = rs[((size_t)j * L + a) * G + m];
+        if (j > 0) {
+          const T* yp = ys + (size_t)(j - 1) * L * G;
+          rhs -= bd[(j - 1) * L + a] * yp[a * G + m];
+          if (a > 0) rhs -= bu[(j - 1) * L + a - 1] * yp[(a - 1) * G + m];
+        }
+        w[a * G + m] = rhs;
+      }
+      cp_async_wait1();   // S_j^{-1} has landed (the newest group may still be in flight)
+      __syncthreads();
+      if (ok) {
+        const T* Sj = Sb + (j & 1) * LL + a * L;
+        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+        int c = 0;
+        for (; c + 3 < L; c += 4) {
+          s0 += Sj[c] * w[c * G + m];
+          s1 += Sj[c + 1] * w[(c + 1) * G + m];
+          s2 += Sj[c + 2] * w[(c + 2) * G + m];
+          s3 += Sj[c + 3] * w[(c + 3) * G + m];
+        }
+        for (; c < L; ++c) s0 += Sj[c] * w[c * G + m];
+        ys[((size_t)j * L + a) * G + m] = (s0 + s1) + (s2 + s3);
+      }
+      __syncthreads();
+    }
+    cp_async_wait0();
+    __syncthreads();
+    // phase C: backward sweep x_j = y_j - S_j^{-1} B_j x_{j+1} in place in ys
+    if (L >= 2) {
+      const T* src = S + (long long)(L - 2) * LL;
+      for (int e = tid; e < LL; e += nthr) cp_async_elem(Sb + ((L - 2) & 1) * LL + e, src + e);
+    }
+    cp_async_commit();
+    for (int j = L - 2; j >= 0; --j) {
+      if (j - 1 >= 0) {
+        const T* src = S + (long long)(j - 1) * LL;
+        T* dst = Sb + ((j - 1) & 1) * LL;
+        for (int e = tid; e < LL; e += nthr) cp_async_elem(dst + e, src + e);
+      }
+      cp_async_commit();
+      if (ok) {
+        const T* xn = ys + (size_t)(j + 1) * L * G;
+        T tv = bd[j * L + a] * xn[a * G + m];
+        if (a + 1 < L) tv += bu[j * L + a] * xn[(a + 1) * G + m];
+        w[a * G + m] = tv;
+      }
+      cp_async_wait1();
+      __syncthreads();
+      if (ok) {
+        const T* Sj = Sb + (j & 1) * LL + a * L;
+        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+        int c = 0;
+        for (; c + 3 < L; c += 4) {
+          s0 += Sj[c] * w[c * G + m];
+          s1 += Sj[c + 1] * w[(c + 1) * G + m];
+          s2 += Sj[c + 2] * w[(c + 2) * G + m];
+          s3 += Sj[c + 3] * w[(c + 3) * G + m];
+        }
+        for (; c < L; ++c) s0 += Sj[c] * w[c * G + m];
+        ys[((size_t)j * L + a) * G + m] -= (s0 + s1) + (s2 + s3);
+      }
+      __syncthreads();
+    }
+    cp_async_wait0();
+    // phase D (parallel): write z, partial r.z and r.r
+    for (int e = tid; e < LL * gl; e += nthr) {
+      const int mm = e % gl, node = e / gl;
+      const T zv = ys[(size_t)node * G + mm];
+      const double rv = (double)rs[(size_t)node * G + mm];
+      z[base + (long long)node * P + kb + mm] = zv;
+      s_rz += rv * (double)zv;
+      s_rr += rv * rv;
+    }
+  }
+  // block partials (every block, active or not, writes and counts)
+  for (int o = 16; o > 0; o >>= 1) {
+    s_rz += __shfl_down_sync(0xffffffffu, s_rz, o);
+    s_rr += __shfl_down_sync(0xffffffffu, s_rr, o);
+  }
+  if ((tid & 31) == 0) { red_rz[tid >> 5] = s_rz; red_rr[tid >> 5] = s_rr; }
+  __syncthreads();
+  if (tid == 0) {
+    double a1 = 0.0, a2 = 0.0;
+    for (int wdx = 0; wdx < (nthr + 31) / 32; ++wdx) { a1 += red_rz[wdx]; a2 += red_rr[wdx]; }
+    ctl.part_rz[(long long)b * NG + grp] = a1;
+    ctl.part_rr[(long long)b * NG + grp] = a2;
+    __threadfence();
+    const unsigned prev = atomicAdd(ctl.counter, 1u);
+    am_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  // control (last block): per-problem scalars, convergence, loop condition
+  __shared__ int n_act;
+  if (tid == 0) n_act = 0;
+  __syncthreads();
+  for (int bb = tid; bb < nb; bb += nthr) {
+    double rz = 0.0, rr = 0.0;
+    for (int g = 0; g < NG; ++g) {
+      rz += ctl.part_rz[(long long)bb * NG + g];
+      rr += ctl.part_rr[(long long)bb * NG + g];
+    }
+    if (init) {
+      ctl.bb[bb] = rr;
+      ctl.rz[bb] = rz;
+      ctl.beta[bb] = 0.0;
+      if (!isfinite(rr) || !isfinite(rz)) ctl.breakdown[0] = 1;
+      const int ac = rr > bb_min && isfinite(rr) && rz > 0.0;
+      ctl.active[bb] = ac;
+      if (ac) atomicAdd(&n_act, 1);
+    } else if (ctl.active[bb]) {
+      double pq = 0.0;
+      for (int t = 0; t < NT; ++t) pq += ctl.part_pq[(long long)bb * NT + t];
+      if (!isfinite(rr) || !isfinite(rz)) ctl.breakdown[0] = 1;
+      const bool stop = !(pq > 0.0) || !isfinite(pq) || !isfinite(rr) || !(rz > 0.0);
+      const bool conv = stop || !(rr > tol2 * ctl.bb[bb]);
+      if (conv) {
+        ctl.active[bb] = 0;
+      } else {
+        ctl.beta[bb] = rz / ctl.rz[bb];
+        ctl.rz[bb] = rz;
+        atomicAdd(&n_act, 1);
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int itn = init ? 0 : (*ctl.it + 1);
+    *ctl.it = itn;
+    if (!init) {
+      *ctl.it_total += 1;
+      *ctl.parity ^= 1;
+    } else {
+      *ctl.parity = 0;
+    }
+    const int cond = (n_act > 0) && (itn < max_it);
+    *ctl.cond = cond;
+    *ctl.counter = 0u;
+    if (use_handle) cudaGraphSetConditional(cond_handle, cond ? 1u : 0u);
   }
 }
 
@@ -301,6 +496,7 @@ __global__ void k_line_solve(int L, int nl, int P, int R, long long pat_stride, 
 __global__ void k_line_factor(int L, const double* __restrict__ Dd, const double* __restrict__ Du,
                               const double* __restrict__ Bd, const double* __restrict__ Bu,
                               double* __restrict__ Sinv, int* status) {
+  count_launch();
   extern __shared__ double sm[];
   double* S = sm;            // [L][L]
   double* col = S + L * L;   // [L] pivot column
@@ -348,19 +544,19 @@ __global__ void k_line_factor(int L, const double* __restrict__ Dd, const double
     for (int piv = 0; piv < L; ++piv) {
       const double d = S[piv * L + piv];
       if (!(d > 0.0) && threadIdx.x == 0) status[blk] = 1;
-      for (int r = threadIdx.x; r < L; r += nt) {
-        col[r] = S[r * L + piv];
-        prow[r] = S[piv * L + r];
+      for (int rr = threadIdx.x; rr < L; rr += nt) {
+        col[rr] = S[rr * L + piv];
+        prow[rr] = S[piv * L + rr];
       }
       __syncthreads();
       const double inv = 1.0 / d;
       for (int e = threadIdx.x; e < L * L; e += nt) {
-        const int r = e / L, c = e % L;
+        const int rr = e / L, c = e % L;
         double val;
-        if (r == piv && c == piv) val = inv;
-        else if (r == piv) val = prow[c] * inv;
-        else if (c == piv) val = -col[r] * inv;
-        else val = S[e] - col[r] * prow[c] * inv;
+        if (rr == piv && c == piv) val = inv;
+        else if (rr == piv) val = prow[c] * inv;
+        else if (c == piv) val = -col[rr] * inv;
+        else val = S[e] - col[rr] * prow[c] * inv;
         S[e] = val;
       }
       __syncthreads();
@@ -371,12 +567,195 @@ __global__ void k_line_factor(int L, const double* __restrict__ Dd, const double
 }
 
 // ------------------------------------------------------------------------------------------
+// Outer (interface) PCG: device scalars and fused vector kernels, FP64.
+// ------------------------------------------------------------------------------------------
+struct OuterCtl {
+  double gn;       // ||G||
+  double rz;       // r . z
+  double alpha, beta;
+  double rel;      // ||r|| / ||G||
+  int it;          // iterations of this step
+  int done;
+  int notconv;
+  int breakdown;
+};
+
+enum : int { OP_INIT_G = 0, OP_RES0 = 1, OP_RZ0 = 2, OP_ALPHA = 3, OP_CHECK = 4, OP_BETA = 5, OP_BETA_FLEX = 6 };
+
+// partial sums of up to two dot products: part[blk] = x.y, part2[blk] = u.v
+__global__ void k_odot(long long n, const double* __restrict__ x, const double* __restrict__ y,
+                       const double* __restrict__ u, const double* __restrict__ v, double* part, double* part2) {
+  count_launch();
+  double s = 0.0, s2 = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    s += x[i] * y[i];
+    if (u) s2 += u[i] * v[i];
+  }
+  __shared__ double sh[32], sh2[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_down_sync(0xffffffffu, s, o);
+    s2 += __shfl_down_sync(0xffffffffu, s2, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sh[w] = s; sh2[w] = s2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, a2 = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a += sh[q]; a2 += sh2[q]; }
+    part[blockIdx.x] = a;
+    if (part2) part2[blockIdx.x] = a2;
+  }
+}
+
+// Scalar program of the outer PCG on reduced partials (single thread, fixed order).
+__global__ void k_octl(int op, int npart, const double* part, const double* part2, OuterCtl* c, double tol,
+                       int max_iter, cudaGraphConditionalHandle hwhile, cudaGraphConditionalHandle hif,
+                       int use_handle, int* cond_mirror) {
+  count_launch();
+  if (threadIdx.x != 0) return;
+  double s = 0.0, s2 = 0.0;
+  for (int i = 0; i < npart; ++i) s += part[i];
+  if (part2)
+    for (int i = 0; i < npart; ++i) s2 += part2[i];
+  switch (op) {
+    case OP_INIT_G:
+      c->gn = sqrt(s);
+      c->it = 0;
+      c->done = 0;
+      c->notconv = 0;
+      c->breakdown = !isfinite(s);
+      c->rz = 0.0;
+      break;
+    case OP_RES0: {
+      const double rel = c->gn > 0.0 ? sqrt(s) / c->gn : 0.0;
+      c->rel = rel;
+      c->done = !(rel > tol) || c->gn == 0.0 || c->breakdown;
+      if (!isfinite(rel)) { c->breakdown = 1; c->done = 1; }
+      const int cond = !c->done;
+      cond_mirror[0] = cond;
+      cond_mirror[1] = cond;
+      if (use_handle) {
+        cudaGraphSetConditional(hwhile, cond);
+        cudaGraphSetConditional(hif, cond);
+      }
+      break;
+    }
+    case OP_RZ0:
+      c->rz = s;
+      break;
+    case OP_ALPHA:
+      if (!(s > 0.0) || !isfinite(s)) { c->breakdown = 1; c->alpha = 0.0; }
+      else c->alpha = c->rz / s;
+      break;
+    case OP_CHECK: {
+      c->it += 1;
+      const double rel = sqrt(s) / c->gn;
+      c->rel = rel;
+      if (!isfinite(rel)) c->breakdown = 1;
+      int done = !(rel > tol) || c->breakdown;
+      if (!done && c->it >= max_iter) { done = 1; c->notconv = 1; }
+      c->done = done;
+      cond_mirror[0] = !done;
+      cond_mirror[1] = !done;
+      if (use_handle) {
+        cudaGraphSetConditional(hwhile, done ? 0u : 1u);
+        cudaGraphSetConditional(hif, done ? 0u : 1u);
+      }
+      break;
+    }
+    case OP_BETA:  // standard: beta = (r.z)_new / (r.z)_old
+      c->beta = c->rz != 0.0 ? s / c->rz : 0.0;
+      c->rz = s;
+      break;
+    case OP_BETA_FLEX:  // flexible (Polak-Ribiere): beta = z.(r - r_old) / (r.z)_old; s = r.z, s2 = z.r_old
+      c->beta = c->rz != 0.0 ? (s - s2) / c->rz : 0.0;
+      c->rz = s;
+      break;
+  }
+}
+
+// x += alpha p; r -= alpha q; partial ||r||^2
+__global__ void k_oupd(long long n, const OuterCtl* c, const double* __restrict__ p, const double* __restrict__ q,
+                       double* __restrict__ x, double* __restrict__ r, double* part) {
+  count_launch();
+  const double a = c->alpha;
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    x[i] += a * p[i];
+    const double rv = r[i] - a * q[i];
+    r[i] = rv;
+    s += rv * rv;
+  }
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int qq = 0; qq < (int)(blockDim.x >> 5); ++qq) acc += sh[qq];
+    part[blockIdx.x] = acc;
+  }
+}
+
+// r = g - q (initial residual) with partial ||r||^2
+__global__ void k_ores0(long long n, const double* __restrict__ g, const double* __restrict__ q, double* __restrict__ r,
+                        double* part) {
+  count_launch();
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double rv = g[i] - q[i];
+    r[i] = rv;
+    s += rv * rv;
+  }
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int qq = 0; qq < (int)(blockDim.x >> 5); ++qq) acc += sh[qq];
+    part[blockIdx.x] = acc;
+  }
+}
+
+// p = z + beta p (beta from the control block; first == 1: p = z)
+__global__ void k_op(long long n, const OuterCtl* c, const double* __restrict__ z, double* __restrict__ p, int first) {
+  count_launch();
+  const double bt = first ? 0.0 : c->beta;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = first ? z[i] : z[i] + bt * p[i];
+}
+
+// zero x when the right-hand side vanishes (||G|| = 0)
+__global__ void k_ozero_if(long long n, const OuterCtl* c, double* x) {
+  count_launch();
+  if (c->gn != 0.0) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = 0.0;
+}
+
+// per-step record of the outer iteration count and relative residual
+__global__ void k_record(OuterCtl* c, long long* stepctr, int cap, int* iters, double* relres, int* flags) {
+  count_launch();
+  if (threadIdx.x != 0) return;
+  const long long s = *stepctr;
+  iters[s % cap] = c->it;
+  relres[s % cap] = c->rel;
+  if (c->notconv) atomicOr(&flags[0], 1);
+  if (c->breakdown) atomicOr(&flags[0], 2);
+  *stepctr = s + 1;
+}
+
+// ------------------------------------------------------------------------------------------
 // Interface gathers / scatters.
 // ------------------------------------------------------------------------------------------
 // x_loc[b][ln][k] = (class in mask) ? src[gidx][k] * (useD ? D[g] : 1) : 0
 template <typename T>
 __global__ void k_gather(int nb, int R, int nl, int P, const uint8_t* cls, const int* gidx, const double* D,
                          const double* __restrict__ src, T* __restrict__ dst, int mask, int useD) {
+  count_launch();
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nb * nl * P) return;
   const int k = (int)(idx % P);
@@ -397,6 +776,7 @@ __global__ void k_gather(int nb, int R, int nl, int P, const uint8_t* cls, const
 template <typename T>
 __global__ void k_scatter(int nG, int P, const int* owners, const double* D, const T* __restrict__ src,
                           double* __restrict__ dst, int useD) {
+  count_launch();
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nG * P) return;
   const int k = (int)(idx % P), g = (int)(idx / P);
@@ -412,6 +792,7 @@ __global__ void k_scatter(int nG, int P, const int* owners, const double* D, con
 // Sum the interface values of all owners and write the sum back to every owner (global
 // assembly of a local-layout vector on the interface).
 __global__ void k_assemble_gamma(int nG, int P, const int* owners, double* __restrict__ v) {
+  count_launch();
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nG * P) return;
   const int k = (int)(idx % P), g = (int)(idx / P);
@@ -428,6 +809,7 @@ __global__ void k_assemble_gamma(int nG, int P, const int* owners, double* __res
 
 // weight for counting each global dof once in local-layout dots: 1 on interior, D on interface
 __global__ void k_node_weight(int n, const uint8_t* cls, const int* gidx, const double* D, double* w) {
+  count_launch();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int c = cls[i];
@@ -437,6 +819,7 @@ __global__ void k_node_weight(int n, const uint8_t* cls, const int* gidx, const 
 // res = sum_i w[node(i)] x_i y_i over a local-layout vector (single block, fixed order)
 __global__ void k_dot_w(long long nnodes, int P, const double* w, const double* x, const double* y,
                         double* res) {
+  count_launch();
   double s = 0.0;
   for (long long i = threadIdx.x; i < nnodes * P; i += blockDim.x) s += w[i / P] * x[i] * y[i];
   __shared__ double sh[32];
@@ -456,11 +839,13 @@ __global__ void k_dot_w(long long nnodes, int P, const double* w, const double* 
 // ------------------------------------------------------------------------------------------
 // z_loc on the local interface of each subdomain (R = 1):
 //   corner node: u_c[cidx][k];  remaining node: v + sum_{lc,m} Phi[sub][lc*P+m][gam][k] u_c[corner(lc)][m]
+template <typename TV>
 __global__ void k_coarse_extend(int nsub, int nl, int P, int nGam, int maxc, const uint8_t* cls,
                                 const int* cidx, const int* gam_ln, const int* n_gam, const int* loc_corner,
                                 const int* n_loc_corner, const double* __restrict__ Phi,
-                                const double* __restrict__ uc, const double* __restrict__ v,
+                                const double* __restrict__ uc, const TV* __restrict__ v,
                                 double* __restrict__ zloc) {
+  count_launch();
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nsub * nGam * P) return;
   const int k = (int)(idx % P);
@@ -473,7 +858,7 @@ __global__ void k_coarse_extend(int nsub, int nl, int P, int nGam, int maxc, con
   if (cls[so] == COR) {
     val = uc[(long long)cidx[so] * P + k];
   } else {
-    val = v[so * P + k];
+    val = (double)v[so * P + k];
     const int nc = n_loc_corner[sub];
     const int ncolmax = maxc * P;
     for (int lc = 0; lc < nc; ++lc) {
@@ -488,15 +873,17 @@ __global__ void k_coarse_extend(int nsub, int nl, int P, int nGam, int maxc, con
 }
 
 // d[c][k] = sum over owners o of (wc - y)[o][k]
+template <typename TY>
 __global__ void k_corner_rhs(int nC, int P, const int* cowners, const double* __restrict__ wc,
-                             const double* __restrict__ y, double* __restrict__ d) {
+                             const TY* __restrict__ y, double* __restrict__ d) {
+  count_launch();
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nC * P) return;
   const int k = (int)(idx % P), c = (int)(idx / P);
   double s = 0.0;
   for (int q = 0; q < 4; ++q) {
     const int o = cowners[c * 4 + q];
-    if (o >= 0) s += wc[(long long)o * P + k] - y[(long long)o * P + k];
+    if (o >= 0) s += wc[(long long)o * P + k] - (double)y[(long long)o * P + k];
   }
   d[idx] = s;
 }
@@ -504,6 +891,7 @@ __global__ void k_corner_rhs(int nC, int P, const int* cowners, const double* __
 // y = A x for a dense n x n row-major matrix (one warp per row)
 __global__ void k_gemv(int n, const double* __restrict__ A, const double* __restrict__ x,
                        double* __restrict__ y) {
+  count_launch();
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int l = threadIdx.x & 31;
   if (row >= n) return;
@@ -517,9 +905,9 @@ __global__ void k_gemv(int n, const double* __restrict__ A, const double* __rest
 // unit vectors of the coarse basis problems: problem b = sub * R + (lc * P + m)
 __global__ void k_coarse_units(int nsub, int R, int nl, int P, int sub0, const int* loc_corner,
                                const int* n_loc_corner, double* e) {
+  count_launch();
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int nsc = nsub;
-  if (idx >= (long long)nsc * R) return;
+  if (idx >= (long long)nsub * R) return;
   const int col = (int)(idx % R), sl = (int)(idx / R);
   const int sub = sub0 + sl;
   const int lc = col / P, m = col % P;
@@ -532,6 +920,7 @@ __global__ void k_coarse_units(int nsub, int R, int nl, int P, int sub0, const i
 __global__ void k_coarse_phi(int nsub_chunk, int sub0, int R, int nl, int P, int nGam, const uint8_t* cls,
                              const int* gam_ln, const int* n_gam, const double* __restrict__ v,
                              double* __restrict__ Phi) {
+  count_launch();
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nsub_chunk * R * nGam * P) return;
   const int k = (int)(idx % P);
@@ -551,6 +940,7 @@ __global__ void k_coarse_phi(int nsub_chunk, int sub0, int R, int nl, int P, int
 // local coarse matrix entries: Fs[sub][row = lc'*P+m'][col] = y[b(col)][loc_corner[lc']][m']
 __global__ void k_coarse_fs(int nsub_chunk, int sub0, int R, int nl, int P, const int* loc_corner,
                             const int* n_loc_corner, const double* __restrict__ y, double* __restrict__ Fs) {
+  count_launch();
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nsub_chunk * R * R) return;
   const int col = (int)(idx % R);
@@ -570,10 +960,11 @@ __global__ void k_coarse_fs(int nsub_chunk, int sub0, int R, int nl, int P, cons
 // Newmark and loads.
 // ------------------------------------------------------------------------------------------
 // um = (U + dt V)/(zeta dt^2) + (1 - 2 zeta) A/(2 zeta); uc = gamma dt um - V - (1-gamma) dt A
-// xm = um + alpha0 uc (mass input of the effective load), all on free nodes (Eqs. UmCm)
+// xm = um + alpha0 uc (mass input of the effective load), on every node (Eqs. UmCm)
 __global__ void k_newmark_pre(long long n, double dt, double alpha0, const double* __restrict__ U,
                               const double* __restrict__ V, const double* __restrict__ A,
                               double* __restrict__ um, double* __restrict__ uc, double* __restrict__ xm) {
+  count_launch();
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double zeta = 0.25, gamma = 0.5;
@@ -588,6 +979,7 @@ __global__ void k_newmark_pre(long long n, double dt, double alpha0, const doubl
 __global__ void k_newmark_post(long long n, double dt, const double* __restrict__ Un,
                                const double* __restrict__ um, double* __restrict__ U,
                                double* __restrict__ V, double* __restrict__ A) {
+  count_launch();
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double zeta = 0.25, gamma = 0.5;
@@ -597,11 +989,14 @@ __global__ void k_newmark_post(long long n, double dt, const double* __restrict_
   U[i] = Un[i];
 }
 
-// point source: f[node][0] += w * amp * ricker(t)  (amp folded into w)
-__global__ void k_point_load(int n, const int* node, const double* w, double t, double freq, int P,
-                             double* f) {
+// point source: f[node][0] += w * ricker(t), t = (step + 1 + toff) dt read from the device step
+// counter (amp folded into w)
+__global__ void k_point_load(int n, const int* node, const double* w, const long long* stepctr, double dt,
+                             double toff, double freq, int P, double* f) {
+  count_launch();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const double t = stepctr ? ((double)(*stepctr) + toff) * dt : toff * dt;
   const double pi = 3.14159265358979323846;
   const double tau = t - 1.0 / freq;
   const double a = (pi * freq * tau) * (pi * freq * tau);
@@ -612,6 +1007,7 @@ __global__ void k_point_load(int n, const int* node, const double* w, double t, 
 __global__ void k_ext_load(long long nloc, int P, const int* free_of_local, const uint8_t* cls,
                            const int* gidx, const double* D, const double* __restrict__ fext,
                            double* __restrict__ f) {
+  count_launch();
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nloc) return;
   const int fi = free_of_local[i];
@@ -623,6 +1019,7 @@ __global__ void k_ext_load(long long nloc, int P, const int* free_of_local, cons
 // out[f][k] = src[owner(f)][k] (mode < 0: all modes; else one mode into out[f])
 __global__ void k_gather_free(int nfree, int P, int mode, const int* owner, const double* __restrict__ src,
                               double* __restrict__ out) {
+  count_launch();
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (mode < 0) {
     if (idx >= (long long)nfree * P) return;
@@ -636,6 +1033,7 @@ __global__ void k_gather_free(int nfree, int P, int mode, const int* owner, cons
 
 __global__ void k_moments(int nfree, int P, const int* owner, const double* __restrict__ src,
                           double* mean, double* var) {
+  count_launch();
   int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= nfree) return;
   const double* u = src + (long long)owner[f] * P;
@@ -650,6 +1048,7 @@ __global__ void k_moments(int nfree, int P, const int* owner, const double* __re
 // local[sub][ln][k] = src[free_of_local][k] for free nodes (checkpoint restore)
 __global__ void k_scatter_free(long long nloc, int P, const int* free_of_local, const double* __restrict__ src,
                                double* __restrict__ dst) {
+  count_launch();
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nloc * P) return;
   const int k = (int)(idx % P);
@@ -664,31 +1063,38 @@ __global__ void k_scatter_free(long long nloc, int P, const int* free_of_local, 
 template <typename T>
 __global__ void k_axpby(long long n, T a, const T* __restrict__ x, T b, const T* __restrict__ y,
                         T* __restrict__ out) {
+  count_launch();
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = a * x[i] + b * y[i];
 }
 
-template <typename T, typename U>
-__global__ void k_convert(long long n, const T* __restrict__ x, U* __restrict__ y) {
+// plain type conversion y = (TO) x
+template <typename TI, typename TO>
+__global__ void k_cvt(long long n, const TI* __restrict__ x, TO* __restrict__ y) {
+  count_launch();
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = (U)x[i];
+  if (i < n) y[i] = (TO)x[i];
 }
 
-// keep values on nodes whose class is in mask, zero elsewhere (R right-hand sides per subdomain)
-template <typename T>
-__global__ void k_mask(int nb, int R, int nl, int P, const uint8_t* cls, const T* __restrict__ x,
-                       T* __restrict__ y, int mask) {
+// out = (double) xa + ya  (mixed-type sum of a converted vector and an FP64 vector)
+template <typename TA>
+__global__ void k_add_conv(long long n, const TA* __restrict__ xa, const double* __restrict__ ya,
+                           double* __restrict__ out) {
+  count_launch();
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (double)xa[i] + ya[i];
+}
+
+// out = convert(s * x) on nodes whose class is in mask (else 0)
+template <typename TI, typename TO>
+__global__ void k_conv_mask(int nb, int R, int nl, int P, const uint8_t* cls, const TI* __restrict__ x,
+                            TO* __restrict__ y, int mask, double s) {
+  count_launch();
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nb * nl * P) return;
   const long long t = idx / P;
   const int ln = (int)(t % nl), b = (int)(t / nl);
-  y[idx] = ((mask >> cls[(long long)(b / R) * nl + ln]) & 1) ? x[idx] : T(0);
-}
-
-template <typename T>
-__global__ void k_finite(long long n, const T* __restrict__ x, int* bad) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && !isfinite((double)x[i])) *bad = 1;
+  y[idx] = ((mask >> cls[(long long)(b / R) * nl + ln]) & 1) ? (TO)(s * (double)x[idx]) : TO(0);
 }
 
 }  // namespace sgk
