@@ -54,6 +54,7 @@ struct LineFactor {
   T* Sinv = nullptr;  // [sub][L][L][L]
   T* Bd = nullptr;    // [sub][L][L]
   T* Bu = nullptr;
+  T* Spad = nullptr;  // [sub][L][L][LS] rows zero-padded to a multiple of 4 (FP32 staged kernel)
 };
 
 struct Ctx {
@@ -145,6 +146,8 @@ struct sg_handle_s {
     o.kapN += (size_t)s0 * pr.nl * pr.PI;
     o.gk_ptr = gk_ptr; o.gk_i = gk_i; o.gk_j = gk_j;
     o.L = pr.L; o.nl = pr.nl; o.P = pr.P; o.PI = pr.PI; o.mass_h = (T)(pr.h * pr.h / 24.0);
+    o.fP = sgk::make_fd(pr.P); o.fPI = sgk::make_fd(pr.PI); o.fL = sgk::make_fd(pr.L);
+    o.fLm1 = sgk::make_fd(pr.L - 1); o.fLP = sgk::make_fd(pr.L * pr.P);
     return o;
   }
   long long nloc() const { return (long long)pr.nsub * pr.nl; }
@@ -280,17 +283,19 @@ const LineFactor<float>& lfT<float>(sg_handle h, int pat) { return h->lf32[pat];
 template <typename T>
 static void apply_cfg(const sgh::Problem& pr, int nb, int* TL, int* NT, size_t* sm, int* stage) {
   const int L = pr.L, P = pr.P, PI = pr.PI;
+  const int PS = P | 1, PIS = PI | 1;
   const size_t nnz = pr.gk_v.size();
+  auto edges = [&](int t) { return (size_t)t * (L - 1) + (size_t)(t + 1) * L; };
   auto base = [&](int t) {
-    return sizeof(T) * ((size_t)P * ((size_t)(t + 2) * L + 2 * ((size_t)t * (L - 1) + (size_t)(t + 1) * L)) + nnz) +
-           sizeof(unsigned) * nnz + sizeof(int) * (P + 1) + 16;
+    return sizeof(T) * ((size_t)(t + 2) * L * P + 2 * edges(t) * PS + nnz) + sizeof(unsigned) * nnz +
+           sizeof(int) * (P + 1) + 16;
   };
-  auto kap = [&](int t) { return sizeof(T) * (size_t)PI * ((size_t)t * (L - 1) + (size_t)(t + 1) * L); };
+  auto kap = [&](int t) { return sizeof(T) * edges(t) * PIS; };
   int best = 1;
   for (int t : {8, 4, 2, 1}) {
     if (t > L) continue;
     const long long blocks = (long long)nb * ((L + t - 1) / t);
-    if (base(t) + kap(t) <= 110 * 1024 && (blocks >= 256 || t == 1)) { best = t; break; }
+    if (base(t) + kap(t) <= 110 * 1024 && (blocks >= 128 || t == 1)) { best = t; break; }
   }
   while (best > 1 && base(best) > 200 * 1024) best /= 2;
   *TL = best;
@@ -320,20 +325,59 @@ template <typename T>
 static size_t line_smem(int L, int G) {
   return sizeof(T) * (2 * (size_t)L * L + 2 * (size_t)L * L * G + (size_t)L * G);
 }
-
-// line-solve block: G modes (fast thread index) x Lp rows, G * Lp a multiple of 32; the residual
-// and solution slices of the block live in shared memory (budget 200 KB).  FP32 covers the
-// modes of a problem with about two blocks, FP64 spreads them over more blocks.
+static int pad4(int L) { return (L + 3) & ~3; }
 template <typename T>
-static void line_cfg(const sgh::Problem& pr, int* G, int* Lp) {
+static size_t team_smem(int L, int G) {
+  const size_t LL = (size_t)L * L, LS = pad4(L);
+  const size_t tstride = LS + 2 * LL + ((4 - ((2 * LL) & 3)) & 3);
+  return sizeof(T) * (LL * LS + ((2 * LL + 3) & ~(size_t)3) + (size_t)G * tstride);
+}
+constexpr int TEAM_LS_MAX = 40;  // padded row length of the largest staged factor
+constexpr size_t SMEM_MAX = 232448 - 1024;  // opt-in dynamic shared memory per block (static use below 1 KB)
+
+struct LineCfg {
+  bool team;      // warp-team kernel with the factor staged in shared memory
+  int G, NG;      // modes per block, blocks per problem
+  dim3 block;
+  size_t smem;
+};
+
+// line-solve launch shape: FP32 uses the warp-team kernel when the whole factor fits in shared
+// memory; otherwise the block-synchronous kernel with a double-buffered factor (G modes x Lp
+// rows, G * Lp a multiple of 32, FP64 spreads the modes over more blocks).
+template <typename T>
+static LineCfg line_cfg(const sgh::Problem& pr, int nb_hint) {
   const int L = pr.L, P = pr.P;
+  LineCfg c{};
+  if (sizeof(T) == 4) {
+    int gmax = 0;
+    for (int g = 1; g <= std::min(P, 15); ++g)
+      if (pad4(L) <= TEAM_LS_MAX && team_smem<T>(L, g) <= SMEM_MAX && 32 * ((L + 31) / 32) * g <= 1024) gmax = g;
+    if (gmax >= 1) {
+      // one block per SM (the staged factor fills shared memory): pick the fewest modes per block
+      // that keep the (problem, mode group) blocks within one wave of 152 SMs
+      const int nbp = std::max(1, nb_hint);
+      int g = std::max(1, (P * nbp + 151) / 152);
+      g = std::min(g, gmax);
+      c.team = true;
+      c.NG = (P + g - 1) / g;
+      c.G = (P + c.NG - 1) / c.NG;
+      c.block = dim3(32 * ((L + 31) / 32) * c.G);
+      c.smem = team_smem<T>(L, c.G);
+      return c;
+    }
+  }
   int g = sizeof(T) == 8 ? 2 : (P + 1) / 2;
   g = std::max(1, std::min(g, 1024 / L));
   while (g > 1 && line_smem<T>(L, g) > 200 * 1024) --g;
   int lp = L;
   while ((g * lp) % 32) ++lp;
-  *G = g;
-  *Lp = lp;
+  c.team = false;
+  c.G = g;
+  c.NG = (P + g - 1) / g;
+  c.block = dim3(g, lp);
+  c.smem = line_smem<T>(L, g);
+  return c;
 }
 
 static int ensure_ctl(sg_handle h, int nb, int nt, int ng) {
@@ -366,9 +410,9 @@ static int ensure_ws(sg_handle h, int nb) {
   int TL, NT, stage;
   size_t sm;
   apply_cfg<T>(h->pr, nb, &TL, &NT, &sm, &stage);
-  int G, Lp;
-  line_cfg<T>(h->pr, &G, &Lp);
-  return ensure_ctl(h, nb, NT, (h->pr.P + G - 1) / G);
+  int ng = 1;
+  for (int nbh : {1, nb, h->pr.nsub}) ng = std::max(ng, line_cfg<T>(h->pr, nbh).NG);
+  return ensure_ctl(h, nb, NT, ng);
 }
 
 // CUDA-event timing of one kernel launch on its stream (host-driven enqueue only)
@@ -396,9 +440,8 @@ static int enq_inner(sg_handle h, Ctx& cx, int pat, int nb, int R, int s0, const
   const Op<T> op = h->op<T>(s0);
   const int mask = pat == 0 ? sgk::MASK_I : sgk::MASK_N;
   const int L = pr.L;
-  int G, Lp;
-  line_cfg<T>(pr, &G, &Lp);
-  const int NG = (pr.P + G - 1) / G;
+  const LineCfg lc = line_cfg<T>(pr, nb);
+  const int NG = lc.NG;
   int TL, NT, stage;
   size_t asm_;
   apply_cfg<T>(pr, nb, &TL, &NT, &asm_, &stage);
@@ -412,15 +455,33 @@ static int enq_inner(sg_handle h, Ctx& cx, int pat, int nb, int R, int s0, const
   // right-hand sides whose squared norm is at the underflow level of T are left at x = 0
   const double bb_min = sizeof(T) == 8 ? 1e-280 : 1e-60;
   const int imax = sizeof(T) == 8 ? h->inner_max : std::min(h->inner_max, 120);
-  const dim3 lb(G, Lp);
   const unsigned lg = (unsigned)nb * NG;
-  const size_t lsm = line_smem<T>(L, G);
+  const int LSp = pad4(L);
+  const long long pstride_pad = (long long)L * L * LSp;
+  const T* Sinv_pad = lf.Spad ? lf.Spad + (size_t)s0 * pstride_pad : nullptr;
+  auto line = [&](cudaStream_t s, int init, cudaGraphConditionalHandle hh, int use) {
+    if (lc.team) {
+#define SG_TEAM(LSV)                                                                                              \
+  case LSV:                                                                                                       \
+    sgk::k_line_team<T, LSV><<<lg, lc.block, lc.smem, s>>>(L, pr.nl, pr.P, R, NG, NT, lc.G, pstride_pad, Sinv_pad, \
+                                                           Bd, Bu, nb, w.x, w.r, w.z, w.p0, w.p1, w.q, h->ctl, init, \
+                                                           tol2, bb_min, imax, hh, use);                         \
+    break;
+      switch (LSp) {
+        SG_TEAM(4) SG_TEAM(8) SG_TEAM(12) SG_TEAM(16) SG_TEAM(20) SG_TEAM(24) SG_TEAM(28) SG_TEAM(32) SG_TEAM(36)
+        SG_TEAM(40)
+        default: break;
+      }
+#undef SG_TEAM
+    } else
+      sgk::k_line<T><<<lg, lc.block, lc.smem, s>>>(L, pr.nl, pr.P, R, NG, NT, pstride, Sinv, Bd, Bu, nb, w.x, w.r,
+                                                   w.z, w.p0, w.p1, w.q, h->ctl, init, tol2, bb_min, imax, hh, use);
+  };
   CK(cudaMemcpyAsync(w.r, rhs, sizeof(T) * n, cudaMemcpyDeviceToDevice, cx.st));
   CK(cudaMemsetAsync(w.x, 0, sizeof(T) * n, cx.st));
   cudaGraphConditionalHandle hnd;
   RET(make_handle(h, cx, &hnd));
-  sgk::k_line<T><<<lg, lb, lsm, cx.st>>>(L, pr.nl, pr.P, R, NG, NT, pstride, Sinv, Bd, Bu, nb, w.x, w.r, w.z, w.p0,
-                                         w.p1, w.q, h->ctl, 1, tol2, bb_min, imax, hnd, cx.capture ? 1 : 0);
+  line(cx.st, 1, hnd, cx.capture ? 1 : 0);
   CKL();
   return cond_node(h, cx, hnd, true, h->ctl.cond, [&](Ctx& c2) -> int {
     RET(kprof_begin(h, c2, 2));
@@ -428,8 +489,7 @@ static int enq_inner(sg_handle h, Ctx& cx, int pat, int nb, int R, int s0, const
                                         w.p0, w.p1, w.z)));
     RET(kprof_end(h, c2, 2));
     RET(kprof_begin(h, c2, 1));
-    sgk::k_line<T><<<lg, lb, lsm, c2.st>>>(L, pr.nl, pr.P, R, NG, NT, pstride, Sinv, Bd, Bu, nb, w.x, w.r, w.z, w.p0,
-                                           w.p1, w.q, h->ctl, 0, tol2, bb_min, imax, hnd, c2.capture ? 1 : 0);
+    line(c2.st, 0, hnd, c2.capture ? 1 : 0);
     CKL();
     RET(kprof_end(h, c2, 1));
     return SG_OK;
@@ -708,6 +768,11 @@ static int build_line_factors(sg_handle h) {
     RET(dalloc(h, &h->lf32[pat].Bd, (long long)nsub * L * L));
     RET(dalloc(h, &h->lf32[pat].Bu, (long long)nsub * L * L));
     sgk::k_cvt<double, float><<<nblk(ns), 256, 0, h->st>>>(ns, h->lf[pat].Sinv, h->lf32[pat].Sinv);
+    if (pad4(L) <= TEAM_LS_MAX) {
+      const long long nrows = (long long)nsub * L * L;
+      RET(dalloc(h, &h->lf32[pat].Spad, nrows * pad4(L)));
+      sgk::k_pad_factor<<<nblk(nrows * pad4(L)), 256, 0, h->st>>>(nrows, L, pad4(L), h->lf[pat].Sinv, h->lf32[pat].Spad);
+    }
     sgk::k_cvt<double, float><<<nblk((long long)nsub * L * L), 256, 0, h->st>>>((long long)nsub * L * L, h->lf[pat].Bd,
                                                                                h->lf32[pat].Bd);
     sgk::k_cvt<double, float><<<nblk((long long)nsub * L * L), 256, 0, h->st>>>((long long)nsub * L * L, h->lf[pat].Bu,
@@ -998,6 +1063,10 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
     CK(cudaFuncSetAttribute(sgk::k_apply<float, double, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     CK(cudaFuncSetAttribute(sgk::k_line<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     CK(cudaFuncSetAttribute(sgk::k_line<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+#define SG_ATTR(LSV) \
+  CK(cudaFuncSetAttribute(sgk::k_line_team<float, LSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX));
+    SG_ATTR(4) SG_ATTR(8) SG_ATTR(12) SG_ATTR(16) SG_ATTR(20) SG_ATTR(24) SG_ATTR(28) SG_ATTR(32) SG_ATTR(36) SG_ATTR(40)
+#undef SG_ATTR
   }
   // problem data (FP64 and FP32 copies of the operator coefficients)
   RET(upload(h, &h->cls, pr.cls)); RET(upload(h, &h->cells, pr.cells));

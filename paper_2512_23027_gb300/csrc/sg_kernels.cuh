@@ -18,9 +18,43 @@ constexpr int MASK_G = MASK_R | MASK_C, MASK_FREE = MASK_I | MASK_R | MASK_C, MA
 
 __device__ unsigned long long* g_nlaunch;  // set once per context by the host (may stay null)
 
+// Optional per-phase cycle marks of block 0 (only when a profiling build defines SG_PHASE_TIMING).
+#ifdef SG_PHASE_TIMING
+__device__ long long g_phase[16];
+#define SG_MARK(i)                                                          \
+  do {                                                                      \
+    if (blockIdx.x == 0 && threadIdx.x == 0) g_phase[i] = clock64();        \
+  } while (0)
+#else
+#define SG_MARK(i) \
+  do {             \
+  } while (0)
+#endif
+
 __device__ __forceinline__ void count_launch() {
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0 && g_nlaunch)
     atomicAdd(g_nlaunch, 1ULL);
+}
+
+// Division by a runtime constant d >= 1 for 0 <= x < 2^31 without a divide instruction:
+// q = floor(x * m / 2^(31+s)) with s = ceil(log2 d) and m = ceil(2^(31+s) / d) < 2^32, which is
+// exact for every x < 2^31 (round-up multiplier method for 31-bit dividends).
+struct FD {
+  unsigned m;
+  int s;
+  unsigned d;
+};
+__host__ __device__ inline FD make_fd(unsigned d) {
+  FD f;
+  int s = 0;
+  while ((1u << s) < d) ++s;
+  f.s = s;
+  f.d = d;
+  f.m = (unsigned)((((unsigned long long)1 << (31 + s)) + d - 1) / d);
+  return f;
+}
+__device__ __forceinline__ int fdiv(int x, const FD& f) {
+  return (int)(((unsigned long long)(unsigned)x * f.m) >> (31 + f.s));
 }
 
 // Geometry and Galerkin data of one problem family (shared by every right-hand side).
@@ -36,6 +70,7 @@ struct Op {
   const T* gk_v;
   int L, nl, P, PI;
   T mass_h;              // h^2 / 24: unit entry of the consistent P1 mass on a right triangle
+  FD fP, fPI, fL, fLm1, fLP;  // fast division by P, PI, L, L-1, L*P
 };
 
 // Inner-CG control block (device memory), one per batched solve.
@@ -71,31 +106,31 @@ struct CgCtl {
 // ------------------------------------------------------------------------------------------
 template <typename T, typename TO, bool FUSEDP, bool DOT>
 __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, int NT, int nnz, int stage_kap,
-                                               const T* __restrict__ xm,
-                                               const T* __restrict__ xk, TO* y,
+                                               const T* __restrict__ xm, const T* __restrict__ xk, TO* y,
                                                const TO* add, T cm, T ck, int out_mask,
                                                // fused-CG inputs
                                                T* pbuf0, T* pbuf1, const T* __restrict__ zin, const int* parity,
                                                const double* beta, const int* active, double* part_pq) {
   count_launch();
-  extern __shared__ unsigned char smem_raw[];
-  const int P = op.P, L = op.L, nl = op.nl;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int P = op.P, L = op.L, nl = op.nl, PI = op.PI;
+  const int PS = P | 1, PIS = PI | 1;               // odd row strides: conflict-free per-edge rows
   const int b = blockIdx.x / NT, tile = blockIdx.x % NT;
   const int lj0 = tile * TL;
   const int nlin = min(TL, L - lj0);  // owned lines
   if (FUSEDP && !active[b]) return;
   const int sub = b / R;
-  T* xs = reinterpret_cast<T*>(smem_raw);            // [(TL+2)][L][P]
-  T* dE = xs + (size_t)(TL + 2) * L * P;            // [TL][L-1][P]
-  T* dN = dE + (size_t)TL * (L - 1) * P;            // [TL+1][L][P]
-  T* zE = dN + (size_t)(TL + 1) * L * P;
-  T* zN = zE + (size_t)TL * (L - 1) * P;
-  T* gv_s = zN + (size_t)(TL + 1) * L * P;                 // [nnz] G values
-  T* kE_s = gv_s + nnz;                                    // [TL][L-1][PI] (when staged)
-  T* kN_s = kE_s + (size_t)TL * (L - 1) * op.PI;           // [TL+1][L][PI]
-  unsigned* gpk_s = reinterpret_cast<unsigned*>(stage_kap ? kN_s + (size_t)(TL + 1) * L * op.PI : kE_s);
-  int* gptr_s = reinterpret_cast<int*>(gpk_s + nnz);        // [P+1]
+  const int nE = nlin * (L - 1), nNr = nlin + 1;
+  const int nEd = nE + nNr * L;                     // edges of the block: horizontal then vertical
+  T* xs = reinterpret_cast<T*>(smem_raw);           // [(TL+2)][L][P]
+  T* ds = xs + (size_t)(TL + 2) * L * P;            // [edges][PS] differences
+  T* zs = ds + (size_t)(TL * (L - 1) + (TL + 1) * L) * PS;   // [edges][PS] fluxes
+  T* gv_s = zs + (size_t)(TL * (L - 1) + (TL + 1) * L) * PS; // [nnz]
+  T* ks = gv_s + nnz;                               // [edges][PIS] edge weights (when staged)
+  unsigned* gpk_s = reinterpret_cast<unsigned*>(stage_kap ? ks + (size_t)(TL * (L - 1) + (TL + 1) * L) * PIS : ks);
+  int* gptr_s = reinterpret_cast<int*>(gpk_s + nnz);  // [P+1]
   const long long pb = (long long)b * nl * P;
+  const long long so0 = (long long)sub * nl;
   const int nt = blockDim.x;
   const T* pold = nullptr;
   T* pnew = nullptr;
@@ -106,33 +141,34 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
     pnew = par ? pbuf0 : pbuf1;
     bet = (T)beta[b];
   }
-  // phase 0: triple products (values, packed (i, j) and per-k ranges) and edge weights
+  SG_MARK(0);
+  // phase 0: triple products (values, packed (i, j), per-k ranges) and the block's edge weights
   for (int e = threadIdx.x; e < nnz; e += nt) {
     gv_s[e] = op.gk_v[e];
     gpk_s[e] = (unsigned)op.gk_i[e] | ((unsigned)op.gk_j[e] << 16);
   }
   for (int e = threadIdx.x; e <= P; e += nt) gptr_s[e] = op.gk_ptr[e];
   if (stage_kap) {
-    const long long so0 = (long long)sub * nl;
-    const int PI = op.PI;
-    for (int e = threadIdx.x; e < nlin * (L - 1) * PI; e += nt) {
-      const int t = e / ((L - 1) * PI), rem = e % ((L - 1) * PI);
-      kE_s[e] = op.kapE[(so0 + (long long)(lj0 + t) * L) * PI + rem];
+    for (int e = threadIdx.x; e < nE * PI; e += nt) {
+      const int ed = fdiv(e, op.fPI), i = e - ed * PI;
+      const int t = fdiv(ed, op.fLm1), c = ed - t * (L - 1);
+      ks[(size_t)ed * PIS + i] = op.kapE[(so0 + (long long)(lj0 + t) * L + c) * PI + i];
     }
-    for (int e = threadIdx.x; e < (nlin + 1) * L * PI; e += nt) {
-      const int t = e / (L * PI), rem = e % (L * PI);
+    for (int e = threadIdx.x; e < nNr * L * PI; e += nt) {
+      const int ed = fdiv(e, op.fPI), i = e - ed * PI;
+      const int t = fdiv(ed, op.fL), c = ed - t * L;
       const int jb = lj0 - 1 + t;
-      kN_s[e] = (jb >= 0 && jb + 1 < L) ? op.kapN[(so0 + (long long)jb * L) * PI + rem] : T(0);
+      ks[(size_t)(nE + ed) * PIS + i] = (jb >= 0 && jb + 1 < L) ? op.kapN[(so0 + (long long)jb * L + c) * PI + i] : T(0);
     }
   }
   // phase 1: input lines lj0-1 .. lj0+nlin (zeros outside the grid)
   const int nin = (nlin + 2) * L * P;
   for (int e = threadIdx.x; e < nin; e += nt) {
-    const int t = e / (L * P);
+    const int t = fdiv(e, op.fLP);
     const int jl = lj0 - 1 + t;
     T v = T(0);
     if (jl >= 0 && jl < L) {
-      const long long g = pb + (long long)jl * L * P + (e % (L * P));
+      const long long g = pb + (long long)jl * L * P + (e - t * L * P);
       if (FUSEDP) {
         v = zin[g];
         if (bet != T(0)) v += bet * pold[g];
@@ -144,61 +180,104 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
     xs[e] = v;
   }
   __syncthreads();
-  // phase 2a: differences of the block's edges
-  const int nE = nlin * (L - 1), nNr = nlin + 1;
-  for (int e = threadIdx.x; e < nE * P; e += nt) {
-    const int j = e % P, ed = e / P;
-    const int t = ed / (L - 1), i = ed % (L - 1);
-    const T* xr = xs + ((size_t)(t + 1) * L + i) * P;
-    dE[e] = xr[j] - xr[P + j];
-  }
-  for (int e = threadIdx.x; e < nNr * L * P; e += nt) {
-    const int j = e % P, ed = e / P;
-    const int t = ed / L, i = ed % L;
-    const T* xb = xs + ((size_t)t * L + i) * P;
-    dN[e] = xb[j] - xb[(size_t)L * P + j];
+  SG_MARK(1);
+  // phase 2a: differences d_e = x_a - x_b of every edge (a = left / bottom end)
+  for (int e = threadIdx.x; e < nEd * P; e += nt) {
+    const int ed = fdiv(e, op.fP), j = e - ed * P;
+    T dv;
+    if (ed < nE) {
+      const int t = fdiv(ed, op.fLm1), i = ed - t * (L - 1);
+      const T* xr = xs + ((size_t)(t + 1) * L + i) * P;
+      dv = xr[j] - xr[P + j];
+    } else {
+      const int v = ed - nE, t = fdiv(v, op.fL), i = v - t * L;
+      const T* xb = xs + ((size_t)t * L + i) * P;
+      dv = xb[j] - xb[(size_t)L * P + j];
+    }
+    ds[(size_t)ed * PS + j] = dv;
   }
   __syncthreads();
-  // phase 2b: fluxes z_e[k]
+  SG_MARK(2);
+  // phase 2b: fluxes.  A work item is (pair of edges, range of output modes); the G entries are
+  // warp-uniform (broadcast) and each is applied to both edges of the pair.
   if (ck != T(0)) {
-    const long long so0 = (long long)sub * nl;
-    const int PI = op.PI;
-    for (int e = threadIdx.x; e < nE * P; e += nt) {
-      const int k = e % P, ed = e / P;
-      const int t = ed / (L - 1), i = ed % (L - 1);
-      const T* kap = stage_kap ? kE_s + (size_t)ed * PI : op.kapE + (so0 + (long long)(lj0 + t) * L + i) * PI;
-      const T* d = dE + (size_t)ed * P;
-      T s = T(0);
-      for (int q = gptr_s[k]; q < gptr_s[k + 1]; ++q) {
-        const unsigned pk = gpk_s[q];
-        s += kap[pk & 0xffffu] * gv_s[q] * d[pk >> 16];
-      }
-      zE[e] = s;
-    }
-    for (int e = threadIdx.x; e < nNr * L * P; e += nt) {
-      const int k = e % P, ed = e / P;
-      const int t = ed / L, i = ed % L;
-      const int jb = lj0 - 1 + t;  // bottom line of the edge row
-      T s = T(0);
-      if (jb >= 0 && jb + 1 < L) {
-        const T* kap = stage_kap ? kN_s + (size_t)ed * PI : op.kapN + (so0 + (long long)jb * L + i) * PI;
-        const T* d = dN + (size_t)ed * P;
-        for (int q = gptr_s[k]; q < gptr_s[k + 1]; ++q) {
-          const unsigned pk = gpk_s[q];
-          s += kap[pk & 0xffffu] * gv_s[q] * d[pk >> 16];
+    const int npair = (nEd + 1) >> 1;
+    const int KS = max(1, min(P, (2 * nt + npair - 1) / npair));   // mode ranges per pair
+    const int kchunk = (P + KS - 1) / KS;
+    const FD fpair = make_fd((unsigned)npair);
+    for (int it = threadIdx.x; it < npair * KS; it += nt) {
+      const int krg = fdiv(it, fpair), pr = it - krg * npair;
+      const int e0 = pr, e1 = pr + npair;
+      const bool has1 = e1 < nEd;
+      const T* kap0;
+      const T* kap1;
+      bool live0 = true, live1 = has1;
+      auto kap_of = [&](int ed, bool& live) -> const T* {
+        if (stage_kap) {
+          if (ed >= nE) {
+            const int v = ed - nE, t = fdiv(v, op.fL);
+            const int jb = lj0 - 1 + t;
+            live = live && jb >= 0 && jb + 1 < L;
+          }
+          return (const T*)(ks + (size_t)ed * PIS);
         }
+        if (ed < nE) {
+          const int t = fdiv(ed, op.fLm1), c = ed - t * (L - 1);
+          return op.kapE + (so0 + (long long)(lj0 + t) * L + c) * PI;
+        }
+        const int v = ed - nE, t = fdiv(v, op.fL), c = v - t * L;
+        const int jb = lj0 - 1 + t;
+        live = live && jb >= 0 && jb + 1 < L;
+        return op.kapN + (so0 + (long long)max(jb, 0) * L + c) * PI;
+      };
+      kap0 = kap_of(e0, live0);
+      kap1 = has1 ? kap_of(e1, live1) : kap0;
+      const T* d0 = ds + (size_t)e0 * PS;
+      const T* d1 = ds + (size_t)(has1 ? e1 : e0) * PS;
+      T* z0 = zs + (size_t)e0 * PS;
+      T* z1 = zs + (size_t)(has1 ? e1 : e0) * PS;
+      const int k0 = krg * kchunk, k1 = min(P, k0 + kchunk);
+      for (int kk = k0; kk < k1; ++kk) {
+        T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0);
+        const int q1 = gptr_s[kk + 1];
+        int q = gptr_s[kk];
+        for (; q + 3 < q1; q += 4) {  // four entries per round: loads issue together
+          const unsigned p0 = gpk_s[q], p1 = gpk_s[q + 1], p2 = gpk_s[q + 2], p3 = gpk_s[q + 3];
+          const T g0 = gv_s[q], g1 = gv_s[q + 1], g2 = gv_s[q + 2], g3 = gv_s[q + 3];
+          const unsigned i0 = p0 & 0xffffu, i1 = p1 & 0xffffu, i2 = p2 & 0xffffu, i3 = p3 & 0xffffu;
+          const unsigned j0 = p0 >> 16, j1 = p1 >> 16, j2 = p2 >> 16, j3 = p3 >> 16;
+          a0 += (kap0[i0] * g0) * d0[j0];
+          a1 += (kap1[i0] * g0) * d1[j0];
+          b0 += (kap0[i1] * g1) * d0[j1];
+          b1 += (kap1[i1] * g1) * d1[j1];
+          a0 += (kap0[i2] * g2) * d0[j2];
+          a1 += (kap1[i2] * g2) * d1[j2];
+          b0 += (kap0[i3] * g3) * d0[j3];
+          b1 += (kap1[i3] * g3) * d1[j3];
+        }
+        for (; q < q1; ++q) {
+          const unsigned pk = gpk_s[q];
+          const T g = gv_s[q];
+          const unsigned i = pk & 0xffffu, j = pk >> 16;
+          a0 += (kap0[i] * g) * d0[j];
+          a1 += (kap1[i] * g) * d1[j];
+        }
+        a0 += b0;
+        a1 += b1;
+        z0[kk] = live0 ? a0 : T(0);
+        if (has1) z1[kk] = live1 ? a1 : T(0);
       }
-      zN[e] = s;
     }
   }
   __syncthreads();
+  SG_MARK(3);
   // phase 3: outputs of the owned lines
   double dsum = 0.0;
   for (int e = threadIdx.x; e < nlin * L * P; e += nt) {
-    const int k = e % P, nd = e / P;
-    const int t = nd / L, i = nd % L;
+    const int nd = fdiv(e, op.fP), k = e - nd * P;
+    const int t = fdiv(nd, op.fL), i = nd - t * L;
     const int lj = lj0 + t;
-    const long long so = (long long)sub * nl + (long long)lj * L + i;
+    const long long so = so0 + (long long)lj * L + i;
     const long long g = pb + ((long long)lj * L + i) * P + k;
     const int c = op.cls[so];
     TO out = TO(0);
@@ -206,32 +285,22 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
       T acc = T(0);
       if (ck != T(0)) {
         T s = T(0);
-        if (i < L - 1) s += zE[((size_t)t * (L - 1) + i) * P + k];
-        if (i > 0) s -= zE[((size_t)t * (L - 1) + i - 1) * P + k];
-        s += zN[((size_t)(t + 1) * L + i) * P + k];
-        s -= zN[((size_t)t * L + i) * P + k];
+        if (i < L - 1) s += zs[((size_t)t * (L - 1) + i) * PS + k];
+        if (i > 0) s -= zs[((size_t)t * (L - 1) + i - 1) * PS + k];
+        s += zs[((size_t)nE + (size_t)(t + 1) * L + i) * PS + k];
+        s -= zs[((size_t)nE + (size_t)t * L + i) * PS + k];
         acc += ck * s;
       }
       if (cm != T(0)) {
         const int cb = op.cells[so];
         T self = T(0), nbs = T(0);
-        if (FUSEDP || xm == xk) {
-          const T* xa = xs + ((size_t)(t + 1) * L + i) * P + k;
-          const long long dN_ = (long long)L * P;
-          if (cb & 1) { self += T(4); nbs += T(2) * xa[-dN_ - P] + xa[-dN_] + xa[-P]; }
-          if (cb & 2) { self += T(2); nbs += xa[-dN_] + xa[P]; }
-          if (cb & 4) { self += T(2); nbs += xa[-P] + xa[dN_]; }
-          if (cb & 8) { self += T(4); nbs += xa[P] + T(2) * xa[dN_ + P] + xa[dN_]; }
-          acc += cm * op.mass_h * (self * xa[0] + nbs);
-        } else {
-          const T* xa = xm + g;
-          const long long dN_ = (long long)L * P;
-          if (cb & 1) { self += T(4); nbs += T(2) * xa[-dN_ - P] + xa[-dN_] + xa[-P]; }
-          if (cb & 2) { self += T(2); nbs += xa[-dN_] + xa[P]; }
-          if (cb & 4) { self += T(2); nbs += xa[-P] + xa[dN_]; }
-          if (cb & 8) { self += T(4); nbs += xa[P] + T(2) * xa[dN_ + P] + xa[dN_]; }
-          acc += cm * op.mass_h * (self * xa[0] + nbs);
-        }
+        const long long dN_ = (long long)L * P;
+        const T* xa = (FUSEDP || xm == xk) ? xs + ((size_t)(t + 1) * L + i) * P + k : xm + g;
+        if (cb & 1) { self += T(4); nbs += T(2) * xa[-dN_ - P] + xa[-dN_] + xa[-P]; }
+        if (cb & 2) { self += T(2); nbs += xa[-dN_] + xa[P]; }
+        if (cb & 4) { self += T(2); nbs += xa[-P] + xa[dN_]; }
+        if (cb & 8) { self += T(4); nbs += xa[P] + T(2) * xa[dN_ + P] + xa[dN_]; }
+        acc += cm * op.mass_h * (self * xa[0] + nbs);
       }
       out = (TO)acc;
       if (add) out += add[g];
@@ -239,6 +308,7 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
     }
     y[g] = out;
   }
+  SG_MARK(4);
   if (DOT) {
     __shared__ double red[32];
     for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
@@ -279,6 +349,84 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// Partials of r.z and r.r for block (b, grp), then the last block to finish reduces the
+// partials of every problem (fixed order), updates the per-problem scalars and convergence flags
+// and sets the loop condition.  Every block of the launch must call this exactly once.
+__device__ __forceinline__ void line_control(double s_rz, double s_rr, int b, int grp, int NG, int NT, int nb,
+                                             const CgCtl& ctl, int init, double tol2, double bb_min, int max_it,
+                                             cudaGraphConditionalHandle cond_handle, int use_handle) {
+  __shared__ double red_rz[32], red_rr[32];
+  __shared__ int am_last;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y;
+  for (int o = 16; o > 0; o >>= 1) {
+    s_rz += __shfl_down_sync(0xffffffffu, s_rz, o);
+    s_rr += __shfl_down_sync(0xffffffffu, s_rr, o);
+  }
+  if ((tid & 31) == 0) { red_rz[tid >> 5] = s_rz; red_rr[tid >> 5] = s_rr; }
+  __syncthreads();
+  if (tid == 0) {
+    double a1 = 0.0, a2 = 0.0;
+    for (int wdx = 0; wdx < (nthr + 31) / 32; ++wdx) { a1 += red_rz[wdx]; a2 += red_rr[wdx]; }
+    ctl.part_rz[(long long)b * NG + grp] = a1;
+    ctl.part_rr[(long long)b * NG + grp] = a2;
+    __threadfence();
+    const unsigned prev = atomicAdd(ctl.counter, 1u);
+    am_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  // control (last block): per-problem scalars, convergence, loop condition
+  __shared__ int n_act;
+  if (tid == 0) n_act = 0;
+  __syncthreads();
+  for (int bb = tid; bb < nb; bb += nthr) {
+    double rz = 0.0, rr = 0.0;
+    for (int g = 0; g < NG; ++g) {
+      rz += ctl.part_rz[(long long)bb * NG + g];
+      rr += ctl.part_rr[(long long)bb * NG + g];
+    }
+    if (init) {
+      ctl.bb[bb] = rr;
+      ctl.rz[bb] = rz;
+      ctl.beta[bb] = 0.0;
+      if (!isfinite(rr) || !isfinite(rz)) ctl.breakdown[0] = 1;
+      const int ac = rr > bb_min && isfinite(rr) && rz > 0.0;
+      ctl.active[bb] = ac;
+      if (ac) atomicAdd(&n_act, 1);
+    } else if (ctl.active[bb]) {
+      double pq = 0.0;
+      for (int t = 0; t < NT; ++t) pq += ctl.part_pq[(long long)bb * NT + t];
+      if (!isfinite(rr) || !isfinite(rz)) ctl.breakdown[0] = 1;
+      const bool stop = !(pq > 0.0) || !isfinite(pq) || !isfinite(rr) || !(rz > 0.0);
+      const bool conv = stop || !(rr > tol2 * ctl.bb[bb]);
+      if (conv) {
+        ctl.active[bb] = 0;
+      } else {
+        ctl.beta[bb] = rz / ctl.rz[bb];
+        ctl.rz[bb] = rz;
+        atomicAdd(&n_act, 1);
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int itn = init ? 0 : (*ctl.it + 1);
+    *ctl.it = itn;
+    if (!init) {
+      *ctl.it_total += 1;
+      *ctl.parity ^= 1;
+    } else {
+      *ctl.parity = 0;
+    }
+    const int cond = (n_act > 0) && (itn < max_it);
+    *ctl.cond = cond;
+    *ctl.counter = 0u;
+    if (use_handle) cudaGraphSetConditional(cond_handle, cond ? 1u : 0u);
+  }
+}
+
 template <typename T>
 __global__ void k_line(int L, int nl, int P, int R, int NG, int NT, long long pat_stride,
                        const T* __restrict__ Sinv, const T* __restrict__ Bd, const T* __restrict__ Bu, int nb,
@@ -286,15 +434,13 @@ __global__ void k_line(int L, int nl, int P, int R, int NG, int NT, long long pa
                        const T* __restrict__ q, CgCtl ctl, int init, double tol2, double bb_min, int max_it,
                        cudaGraphConditionalHandle cond_handle, int use_handle) {
   count_launch();
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int G = blockDim.x;                      // modes of the block (fast index)
   const int LL = L * L;
   T* Sb = reinterpret_cast<T*>(smem_raw);        // [2][L][L] double-buffered S_j^{-1}
   T* rs = Sb + 2 * LL;                           // [L lines][L][G] residual slice
   T* ys = rs + (size_t)LL * G;                   // [L lines][L][G] solution slice
   T* w = ys + (size_t)LL * G;                    // [L][G]
-  __shared__ double red_rz[32], red_rr[32];
-  __shared__ int am_last;
   const int b = blockIdx.x / NG, grp = blockIdx.x % NG;
   const int m = threadIdx.x, a = threadIdx.y;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -326,8 +472,9 @@ __global__ void k_line(int L, int nl, int P, int R, int NG, int NT, long long pa
       alpha = isfinite(al) ? (T)al : T(0);
       pc = (*ctl.parity) ? pbuf0 : pbuf1;  // p_new written by the apply kernel
     }
+    const FD fgl = make_fd((unsigned)gl);
     for (int e = tid; e < LL * gl; e += nthr) {
-      const int mm = e % gl, node = e / gl;
+      const int node = fdiv(e, fgl), mm = e - node * gl;
       const long long o = base + (long long)node * P + kb + mm;
       T rv = r[o];
       if (!init) {
@@ -413,7 +560,7 @@ __global__ void k_line(int L, int nl, int P, int R, int NG, int NT, long long pa
     cp_async_wait0();
     // phase D (parallel): write z, partial r.z and r.r
     for (int e = tid; e < LL * gl; e += nthr) {
-      const int mm = e % gl, node = e / gl;
+      const int node = fdiv(e, fgl), mm = e - node * gl;
       const T zv = ys[(size_t)node * G + mm];
       const double rv = (double)rs[(size_t)node * G + mm];
       z[base + (long long)node * P + kb + mm] = zv;
@@ -421,73 +568,157 @@ __global__ void k_line(int L, int nl, int P, int R, int NG, int NT, long long pa
       s_rr += rv * rv;
     }
   }
-  // block partials (every block, active or not, writes and counts)
-  for (int o = 16; o > 0; o >>= 1) {
-    s_rz += __shfl_down_sync(0xffffffffu, s_rz, o);
-    s_rr += __shfl_down_sync(0xffffffffu, s_rr, o);
-  }
-  if ((tid & 31) == 0) { red_rz[tid >> 5] = s_rz; red_rr[tid >> 5] = s_rr; }
-  __syncthreads();
-  if (tid == 0) {
-    double a1 = 0.0, a2 = 0.0;
-    for (int wdx = 0; wdx < (nthr + 31) / 32; ++wdx) { a1 += red_rz[wdx]; a2 += red_rr[wdx]; }
-    ctl.part_rz[(long long)b * NG + grp] = a1;
-    ctl.part_rr[(long long)b * NG + grp] = a2;
-    __threadfence();
-    const unsigned prev = atomicAdd(ctl.counter, 1u);
-    am_last = (prev == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-  // control (last block): per-problem scalars, convergence, loop condition
-  __shared__ int n_act;
-  if (tid == 0) n_act = 0;
-  __syncthreads();
-  for (int bb = tid; bb < nb; bb += nthr) {
-    double rz = 0.0, rr = 0.0;
-    for (int g = 0; g < NG; ++g) {
-      rz += ctl.part_rz[(long long)bb * NG + g];
-      rr += ctl.part_rr[(long long)bb * NG + g];
+  line_control(s_rz, s_rr, b, grp, NG, NT, nb, ctl, init, tol2, bb_min, max_it, cond_handle, use_handle);
+}
+
+// Mean-operator line solve fused with the inner CG update, warp-team form (FP32, small L):
+// the whole factor {S_j^{-1}} of the subdomain (L^3 values) and the coupling coefficients are
+// staged in shared memory once; each PCE mode is swept by its own team of ceil(L/32) warps that
+// synchronises with a named barrier (or __syncwarp), so the 2L sequential line steps of
+// different modes never wait on one another.
+// 16-byte async copy global -> shared (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc));
+}
+
+// Fully unrolled dot of a zero-padded row (length LS, 16-byte aligned) with a broadcast vector.
+template <typename T, int LS>
+__device__ __forceinline__ T row_dot(const T* __restrict__ row, const T* __restrict__ w) {
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  if constexpr (sizeof(T) == 4) {
+    const float4* r4 = reinterpret_cast<const float4*>(row);
+    const float4* w4 = reinterpret_cast<const float4*>(w);
+#pragma unroll
+    for (int c = 0; c < LS / 4; ++c) {
+      const float4 a = r4[c], b = w4[c];
+      s0 += a.x * b.x;
+      s1 += a.y * b.y;
+      s2 += a.z * b.z;
+      s3 += a.w * b.w;
     }
-    if (init) {
-      ctl.bb[bb] = rr;
-      ctl.rz[bb] = rz;
-      ctl.beta[bb] = 0.0;
-      if (!isfinite(rr) || !isfinite(rz)) ctl.breakdown[0] = 1;
-      const int ac = rr > bb_min && isfinite(rr) && rz > 0.0;
-      ctl.active[bb] = ac;
-      if (ac) atomicAdd(&n_act, 1);
-    } else if (ctl.active[bb]) {
+  } else {
+#pragma unroll
+    for (int c = 0; c < LS; c += 4) {
+      s0 += row[c] * w[c];
+      s1 += row[c + 1] * w[c + 1];
+      s2 += row[c + 2] * w[c + 2];
+      s3 += row[c + 3] * w[c + 3];
+    }
+  }
+  return (s0 + s1) + (s2 + s3);
+}
+
+template <typename T, int LS>
+__global__ void k_line_team(int L, int nl, int P, int R, int NG, int NT, int G, long long pat_stride,
+                            const T* __restrict__ Sinv, const T* __restrict__ Bd, const T* __restrict__ Bu, int nb,
+                            T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, T* pbuf0, T* pbuf1,
+                            const T* __restrict__ q, CgCtl ctl, int init, double tol2, double bb_min, int max_it,
+                            cudaGraphConditionalHandle cond_handle, int use_handle) {
+  count_launch();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int LL = L * L;
+  const int W = (L + 31) >> 5;                   // warps per team
+  T* Ss = reinterpret_cast<T*>(smem_raw);        // [L][L][LS] rows zero-padded to LS
+  T* bds = Ss + (size_t)LL * LS;                 // [L][L]
+  T* bus = bds + LL;                             // [L][L]
+  T* team_base = Ss + (size_t)LL * LS + ((2 * LL + 3) & ~3);  // per team: w [LS], rs [LL], ys [LL]
+  const int tstride = LS + 2 * LL + ((4 - ((2 * LL) & 3)) & 3);  // keeps every w 16-byte aligned
+  const int b = blockIdx.x / NG, grp = blockIdx.x % NG;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int team = warp / W;
+  const int a = (warp % W) * 32 + lane;          // row (node along the line)
+  const int nthr = blockDim.x;
+  const int tid = threadIdx.x;
+  const int kb = grp * G;
+  const int gl = min(G, P - kb);
+  const int k = kb + team;
+  const bool tok = team < gl;
+  const bool act = init ? true : (ctl.active[b] != 0);
+  double s_rz = 0.0, s_rr = 0.0;
+  if (act) {
+    const int sub = b / R;
+    const T* S = Sinv + (long long)sub * pat_stride;  // padded layout [L][L][LS]
+    const T* bd = Bd + (long long)sub * LL;
+    const T* bu = Bu + (long long)sub * LL;
+    const long long base = (long long)b * nl * P;
+    for (int e = tid; e < LL * LS / 4; e += nthr) cp_async16(Ss + 4 * e, S + 4 * e);
+    for (int e = tid; e < LL; e += nthr) {
+      cp_async_elem(bds + e, bd + e);
+      cp_async_elem(bus + e, bu + e);
+    }
+    cp_async_commit();
+    // phase A: CG update of the block's modes, residual staged per team
+    T alpha = T(0);
+    const T* pc = nullptr;
+    if (!init) {
       double pq = 0.0;
-      for (int t = 0; t < NT; ++t) pq += ctl.part_pq[(long long)bb * NT + t];
-      if (!isfinite(rr) || !isfinite(rz)) ctl.breakdown[0] = 1;
-      const bool stop = !(pq > 0.0) || !isfinite(pq) || !isfinite(rr) || !(rz > 0.0);
-      const bool conv = stop || !(rr > tol2 * ctl.bb[bb]);
-      if (conv) {
-        ctl.active[bb] = 0;
-      } else {
-        ctl.beta[bb] = rz / ctl.rz[bb];
-        ctl.rz[bb] = rz;
-        atomicAdd(&n_act, 1);
+      for (int t = 0; t < NT; ++t) pq += ctl.part_pq[(long long)b * NT + t];
+      const double al = (pq > 0.0 && isfinite(pq)) ? ctl.rz[b] / pq : 0.0;
+      alpha = isfinite(al) ? (T)al : T(0);
+      pc = (*ctl.parity) ? pbuf0 : pbuf1;
+    }
+    const FD fgl = make_fd((unsigned)gl);
+    for (int e = tid; e < LL * gl; e += nthr) {
+      const int node = fdiv(e, fgl), mm = e - node * gl;
+      const long long o = base + (long long)node * P + kb + mm;
+      T rv = r[o];
+      if (!init) {
+        x[o] += alpha * pc[o];
+        rv -= alpha * q[o];
+        r[o] = rv;
+      }
+      team_base[(size_t)mm * tstride + LS + node] = rv;
+    }
+    cp_async_wait0();
+    __syncthreads();
+    if (tok) {
+      T* w = team_base + (size_t)team * tstride;
+      T* rs = w + LS;
+      T* ys = rs + LL;
+      if (a < LS && a >= L) w[a] = T(0);
+      auto tsync = [&]() {
+        if (W == 1) __syncwarp();
+        else asm volatile("bar.sync %0, %1;\n" ::"r"(team + 1), "r"(W * 32) : "memory");
+      };
+      const bool ok = a < L;
+      for (int j = 0; j < L; ++j) {
+        if (ok) {
+          T rhs = rs[j * L + a];
+          if (j > 0) {
+            rhs -= bds[(j - 1) * L + a] * ys[(j - 1) * L + a];
+            if (a > 0) rhs -= bus[(j - 1) * L + a - 1] * ys[(j - 1) * L + a - 1];
+          }
+          w[a] = rhs;
+        }
+        tsync();
+        if (ok) ys[j * L + a] = row_dot<T, LS>(Ss + ((size_t)j * L + a) * LS, w);
+        tsync();
+      }
+      for (int j = L - 2; j >= 0; --j) {
+        if (ok) {
+          T tv = bds[j * L + a] * ys[(j + 1) * L + a];
+          if (a + 1 < L) tv += bus[j * L + a] * ys[(j + 1) * L + a + 1];
+          w[a] = tv;
+        }
+        tsync();
+        if (ok) ys[j * L + a] -= row_dot<T, LS>(Ss + ((size_t)j * L + a) * LS, w);
+        tsync();
       }
     }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    int itn = init ? 0 : (*ctl.it + 1);
-    *ctl.it = itn;
-    if (!init) {
-      *ctl.it_total += 1;
-      *ctl.parity ^= 1;
-    } else {
-      *ctl.parity = 0;
+    __syncthreads();
+    // phase D: write z, partial r.z and r.r
+    for (int e = tid; e < LL * gl; e += nthr) {
+      const int node = fdiv(e, fgl), mm = e - node * gl;
+      const T* rs = team_base + (size_t)mm * tstride + LS;
+      const T zv = rs[LL + node];
+      const double rv = (double)rs[node];
+      z[base + (long long)node * P + kb + mm] = zv;
+      s_rz += rv * (double)zv;
+      s_rr += rv * rv;
     }
-    const int cond = (n_act > 0) && (itn < max_it);
-    *ctl.cond = cond;
-    *ctl.counter = 0u;
-    if (use_handle) cudaGraphSetConditional(cond_handle, cond ? 1u : 0u);
   }
+  line_control(s_rz, s_rr, b, grp, NG, NT, nb, ctl, init, tol2, bb_min, max_it, cond_handle, use_handle);
 }
 
 // Line factorisation, FP64: one block per (subdomain, pattern).  D (within-line tridiagonal)
@@ -1066,6 +1297,16 @@ __global__ void k_axpby(long long n, T a, const T* __restrict__ x, T b, const T*
   count_launch();
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = a * x[i] + b * y[i];
+}
+
+// FP64 line factor [sub][j][a][c] -> FP32 copy with rows zero-padded to LS columns
+__global__ void k_pad_factor(long long nrows, int L, int LS, const double* __restrict__ src, float* __restrict__ dst) {
+  count_launch();
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrows * LS) return;
+  const long long row = i / LS;
+  const int c = (int)(i - row * LS);
+  dst[i] = c < L ? (float)src[row * L + c] : 0.0f;
 }
 
 // plain type conversion y = (TO) x
