@@ -29,6 +29,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "SG-DD time-steps/sec & PCG iters vs plain FP64 DD-PCG at rel resid 1e-8"
+
+# DRAM traffic (read + write bytes per launch) of the dominant kernel from one ncu capture, keyed by
+# the sha256 prefix of the kernel source it was taken on; any other source reports null.
+LINE_TRAFFIC = {"c1127b40a78c48ec": 8290816}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -174,6 +178,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--enqueue", default="graph", choices=["graph", "eager"],
+                    help="graph: one CUDA graph per step (default); eager: host-driven enqueue of the same "
+                         "kernels (per-kernel profilers cannot see inside graphs with conditional nodes)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -217,14 +224,24 @@ def main():
             inner += st["inner_total"]
         return ms, its, inner
 
+    eager = args.enqueue == "eager"
+
+    def make(p, precision):
+        sv = Solver(p, precision=precision, stream=stream)
+        if eager:
+            sv.set_eager(True)
+        return sv
+
     # ---- optimised solver (mixed precision, graph per step) ----
-    s = Solver(prob, precision=SG_MIXED, stream=stream)
+    s = make(prob, SG_MIXED)
     s.step(W)
     sampler = ClockSampler(bus_id_of(torch, local))
     barrier()
     l0 = s.launch_count()
     sampler.start()
+    torch.cuda.nvtx.range_push("timed")
     ms, its, inner = timed(s, K)
+    torch.cuda.nvtx.range_pop()
     barrier()
     clocks = sampler.stop()
     launches = s.launch_count() - l0
@@ -243,14 +260,17 @@ def main():
         flush.fill_(float(k))
         s.step(1)
     kms, kn = s.kernel_timing(0)
-    s.set_eager(False)
+    s.set_eager(eager)
     peaks = read_peaks()
     hbm = peaks.get("hbm_gbs")
     kbytes = line_kernel_bytes(prob, 4)
     achieved = kbytes / (kms / kn / 1e3) / 1e9 if kn else None
-    roofline = {"kernel": "k_line<float> (mean-operator line solve fused with the CG update)",
+    import hashlib
+    ksha = hashlib.sha256(open(os.path.join(ROOT, "paper_2512_23027_gb300", "csrc", "sg_kernels.cuh"), "rb").read()
+                          ).hexdigest()[:16]
+    roofline = {"kernel": "k_line_team<float> (FP32 mean-operator line solve fused with the inner CG update)",
                 "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": (achieved / hbm) if (achieved and hbm) else None, "traffic": None,
+                "frac": (achieved / hbm) if (achieved and hbm) else None, "traffic": LINE_TRAFFIC.get(ksha),
                 "launches_timed": kn, "avg_launch_us": 1e3 * kms / kn if kn else None,
                 "bytes_per_launch": kbytes, "peak_source": "measured" if hbm else "fallback"}
     if not hbm:
@@ -262,7 +282,7 @@ def main():
     if True:  # every rank measures its own replica end to end
         src0 = prob.source
         pe = prob.replace(source=w.Source())
-        se = Solver(pe, precision=SG_MIXED, stream=stream)
+        se = make(pe, SG_MIXED)
         nf = se.n_free
         N, h = prob.N, 1.0 / prob.N
         i = min(int(math.floor(src0.x0 / h)), N - 1)
@@ -294,7 +314,7 @@ def main():
         se.close()
 
     # ---- plain FP64 DD-PCG on the same GPU ----
-    s64 = Solver(prob, precision=SG_FP64, stream=stream)
+    s64 = make(prob, SG_FP64)
     s64.step(3)
     barrier()
     K64 = max(1, min(args.fp64_steps, K))
@@ -315,7 +335,7 @@ def main():
                            "steps": K64},
             "speedup_vs_plain_fp64": (value / (world * K64 / (ms64 / 1e3))),
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
-            "gpu_launches": launches}
+            "gpu_launches": launches, "enqueue": args.enqueue}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
