@@ -206,6 +206,19 @@ static int upload(sg_handle h, T** p, const std::vector<T>& v) {
   return SG_OK;
 }
 
+// release one allocation made by dalloc (set-up scratch)
+template <typename T>
+static void dfree(sg_handle h, T** p) {
+  if (!*p) return;
+  for (size_t i = 0; i < h->allocs.size(); ++i)
+    if (h->allocs[i] == (void*)*p) {
+      h->allocs.erase(h->allocs.begin() + i);
+      break;
+    }
+  cudaFree(*p);
+  *p = nullptr;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Graph helpers: a conditional handle and a conditional node whose body is captured on the next
 // capture stream.  In eager mode the same code runs the body as a host loop driven by a device
@@ -821,26 +834,26 @@ static bool spd_inverse(std::vector<double>& A, int n) {
 }
 
 // Coarse basis Phi_s = -S_rr^{-1} S_rc (per local corner dof) and F_cc (Eq. Fcc_2), from one
-// FP64 Neumann solve per local corner dof: v = -N^{-1} K_[ir],c e, F^s e = (K~ (v + e))_c.
-static int build_coarse(sg_handle h) {
+// Neumann solve per local corner dof: v = -N^{-1} K_[ir],c e, F^s e = (K~ (v + e))_c.  The right-hand
+// sides and F^s are formed in FP64; the Neumann solves run in T (FP64 in FP64 mode, FP32 in mixed
+// mode, where the coarse space only enters the preconditioner).  The batched-solve workspace is
+// set-up scratch and is released afterwards.
+template <typename T>
+static int build_coarse_t(sg_handle h) {
   const auto& pr = h->pr;
   const int P = pr.P, nl = pr.nl, nsub = pr.nsub;
-  h->Rc = pr.max_corner * P;
-  h->nCd = pr.nC * P;
   const int R = h->Rc;
-  RET(dalloc(h, &h->Phi, (long long)nsub * std::max(R, 1) * pr.nGam * P));
-  RET(dalloc(h, &h->dC, std::max(h->nCd, 1)));
-  RET(dalloc(h, &h->uC, std::max(h->nCd, 1)));
-  if (pr.nC == 0 || R == 0) return SG_OK;
-  const int chunk = std::max(1, std::min(nsub, 2048 / R));
+  const int chunk = std::max(1, std::min(nsub, 1024 / R));
   const long long len = (long long)nl * P;
-  RET(ensure_ws<double>(h, chunk * R));
+  RET(ensure_ws<T>(h, chunk * R));
   double *e, *rhs, *ve, *y, *Fs;
+  T* rhsT = nullptr;
   RET(dalloc(h, &e, len * chunk * R));
   RET(dalloc(h, &rhs, len * chunk * R));
   RET(dalloc(h, &ve, len * chunk * R));
   RET(dalloc(h, &y, len * chunk * R));
   RET(dalloc(h, &Fs, (long long)nsub * R * R));
+  if (sizeof(T) != 8) RET(dalloc(h, &rhsT, len * chunk * R));
   Ctx cx{h->st, 0, false};
   cudaStream_t st = h->st;
   for (int s0 = 0; s0 < nsub; s0 += chunk) {
@@ -851,10 +864,16 @@ static int build_coarse(sg_handle h) {
     CK(cudaMemsetAsync(e, 0, sizeof(double) * n, st));
     sgk::k_coarse_units<<<nblk((long long)nb), 256, 0, st>>>(ns, R, nl, P, s0, h->loc_corner, h->n_loc_corner, e);
     RET((launch_apply<double, double, false, false>(h, st, op, nb, R, e, e, rhs, nullptr, -h->am, -h->bk, sgk::MASK_N)));
-    RET(enq_inner<double>(h, cx, 1, nb, R, s0, rhs));
-    sgk::k_coarse_phi<<<nblk((long long)nb * pr.nGam * P), 256, 0, st>>>(ns, s0, R, nl, P, pr.nGam, h->cls, h->gam_ln,
-                                                                         h->n_gam, h->ws.x, h->Phi);
-    sgk::k_axpby<double><<<nblk(n), 256, 0, st>>>(n, 1.0, h->ws.x, 1.0, e, ve);
+    const T* rhs_in = reinterpret_cast<const T*>(rhs);
+    if (sizeof(T) != 8) {
+      sgk::k_cvt<double, float><<<nblk(n), 256, 0, st>>>(n, rhs, reinterpret_cast<float*>(rhsT));
+      rhs_in = rhsT;
+    }
+    RET(enq_inner<T>(h, cx, 1, nb, R, s0, rhs_in));
+    const T* v = wsT<T>(h).x;
+    sgk::k_coarse_phi<T><<<nblk((long long)nb * pr.nGam * P), 256, 0, st>>>(ns, s0, R, nl, P, pr.nGam, h->cls,
+                                                                            h->gam_ln, h->n_gam, v, h->Phi);
+    sgk::k_add_conv<T><<<nblk(n), 256, 0, st>>>(n, v, e, ve);
     RET((launch_apply<double, double, false, false>(h, st, op, nb, R, ve, ve, y, nullptr, h->am, h->bk, sgk::MASK_C)));
     sgk::k_coarse_fs<<<nblk((long long)nb * R), 256, 0, st>>>(ns, s0, R, nl, P, h->loc_corner, h->n_loc_corner, y, Fs);
     CKL();
@@ -862,6 +881,13 @@ static int build_coarse(sg_handle h) {
   std::vector<double> hFs((size_t)nsub * R * R);
   CK(cudaMemcpyAsync(hFs.data(), Fs, sizeof(double) * hFs.size(), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  dfree(h, &e); dfree(h, &rhs); dfree(h, &ve); dfree(h, &y); dfree(h, &Fs);
+  if (rhsT) dfree(h, &rhsT);
+  // shrink the batched workspace back to one problem per subdomain
+  auto& w = wsT<T>(h);
+  dfree(h, &w.x); dfree(h, &w.r); dfree(h, &w.z); dfree(h, &w.p0); dfree(h, &w.p1); dfree(h, &w.q);
+  w.cap_nb = 0;
+  RET(ensure_ws<T>(h, nsub));
   const int nCd = h->nCd;
   std::vector<double> F((size_t)nCd * nCd, 0.0);
   for (int s = 0; s < nsub; ++s) {
@@ -884,6 +910,17 @@ static int build_coarse(sg_handle h) {
   if (!spd_inverse(F, nCd)) { h->err = "coarse matrix F_cc not positive definite"; return SG_ENUMERIC; }
   RET(upload(h, &h->Finv, F));
   return SG_OK;
+}
+
+static int build_coarse(sg_handle h) {
+  const auto& pr = h->pr;
+  h->Rc = pr.max_corner * pr.P;
+  h->nCd = pr.nC * pr.P;
+  RET(dalloc(h, &h->Phi, (long long)pr.nsub * std::max(h->Rc, 1) * pr.nGam * pr.P));
+  RET(dalloc(h, &h->dC, std::max(h->nCd, 1)));
+  RET(dalloc(h, &h->uC, std::max(h->nCd, 1)));
+  if (pr.nC == 0 || h->Rc == 0) return SG_OK;
+  return h->precision == SG_FP64 ? build_coarse_t<double>(h) : build_coarse_t<float>(h);
 }
 
 static int ldot_w(sg_handle h, const double* x, const double* y, double* out) {
@@ -1170,15 +1207,116 @@ int sg_step_host(sg_handle h, int nsteps, const double* f_host, double* u_host, 
   return step_common(h, nsteps, f_host, u_host, stats);
 }
 
-int sg_solve_batch(sg_handle* hs, int n, int nsteps, sg_stats* out_n) {
-  if (!hs || n < 0) return SG_EINVAL;
+// Batched run: one CUDA graph holds one time step of EVERY handle as concurrent branches (fork from
+// a private stream to each handle's own capture stream, join back); the graph is launched once per
+// time step, so a step of the whole batch is a single launch.  Each handle's step keeps its own
+// conditional WHILE/IF loops (same nesting depth as the single-handle graph).
+static int batch_impl(sg_handle* hs, int n, int nsteps, sg_stats* out_n) {
+  sg_handle h = hs[0];  // errors are reported on the first handle
+  for (int i = 1; i < n; ++i)
+    for (int j = 0; j < i; ++j)
+      if (hs[i] == hs[j]) { h->err = "sg_solve_batch: duplicate handle"; return SG_EINVAL; }
+  std::vector<cudaEvent_t> ev(n + 1, nullptr);
+  for (auto& e : ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaStream_t root;
+  CK(cudaStreamCreateWithFlags(&root, cudaStreamNonBlocking));
+  for (int i = 0; i < n; ++i) CK(cudaStreamSynchronize(hs[i]->st));
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
   int rc = SG_OK;
-  for (int i = 0; i < n; ++i) {
-    int r = sg_step(hs[i], nsteps, out_n ? &out_n[i] : nullptr);
-    if (r == SG_ENOTCONV) rc = r;
-    else if (r != SG_OK) return r;
+  std::string why;
+  if (cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    h->err = "batch: begin capture failed";
+    rc = SG_ECUDA;
+  } else {
+    cudaEventRecord(ev[n], root);  // fork point
+    int joined = 0;
+    for (int i = 0; i < n; ++i) {
+      sg_handle hi = hs[i];
+      if (cudaStreamWaitEvent(hi->cs[0], ev[n], 0) != cudaSuccess) { why = "fork"; rc = SG_ECUDA; break; }
+      ++joined;
+      Ctx ci{hi->cs[0], 0, true};
+      const int r = enq_step(hi, ci, false);
+      cudaEventRecord(ev[i], hi->cs[0]);
+      cudaStreamWaitEvent(root, ev[i], 0);  // join (also after a failure, so the capture can end)
+      if (r != SG_OK) {
+        why = hi->err;
+        rc = r;
+        break;
+      }
+    }
+    (void)joined;
+    const cudaError_t e = cudaStreamEndCapture(root, &g);
+    if (rc == SG_OK && e != cudaSuccess) { why = std::string("end capture: ") + cudaGetErrorString(e); rc = SG_ECUDA; }
+    if (rc != SG_OK) h->err = "sg_solve_batch: " + why;
   }
-  return rc;
+  if (rc == SG_OK && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+    h->err = "sg_solve_batch: graph instantiation failed";
+    rc = SG_ECUDA;
+  }
+  std::vector<long long> first(n);
+  float ms = 0.f;
+  if (rc == SG_OK) {
+    for (int i = 0; i < n; ++i) {
+      first[i] = hs[i]->step;
+      hs[i]->iters.clear();
+      hs[i]->relres.clear();
+      CK(cudaMemsetAsync(hs[i]->rec_flags, 0, sizeof(int), root));
+    }
+    CK(cudaEventRecord(h->ev0, root));
+    for (int s = 0; s < nsteps && rc == SG_OK; ++s)
+      if (cudaGraphLaunch(ex, root) != cudaSuccess) { h->err = "sg_solve_batch: graph launch failed"; rc = SG_ECUDA; }
+    CK(cudaEventRecord(h->ev1, root));
+    if (cudaStreamSynchronize(root) != cudaSuccess) { h->err = "sg_solve_batch: run failed"; rc = SG_ECUDA; }
+    if (rc == SG_OK) cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  }
+  if (ex) cudaGraphExecDestroy(ex);
+  if (g) cudaGraphDestroy(g);
+  for (auto& e : ev) cudaEventDestroy(e);
+  cudaStreamDestroy(root);
+  if (rc != SG_OK) return rc;
+  int worst = SG_OK;
+  for (int i = 0; i < n; ++i) {
+    sg_handle hi = hs[i];
+    const long long cnt = std::min<long long>(nsteps, REC_CAP);
+    std::vector<int> it((size_t)cnt);
+    std::vector<double> rl((size_t)cnt);
+    const long long s0 = (first[i] + nsteps - cnt) % REC_CAP;
+    for (long long k = 0; k < cnt; ++k) {
+      CK(cudaMemcpy(&it[k], hi->rec_iters + (s0 + k) % REC_CAP, sizeof(int), cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(&rl[k], hi->rec_rel + (s0 + k) % REC_CAP, sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    hi->iters = it;
+    hi->relres = rl;
+    hi->step += nsteps;
+    int flags = 0, brk = 0;
+    CK(cudaMemcpy(&flags, hi->rec_flags, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&brk, hi->ctl.breakdown, sizeof(int), cudaMemcpyDeviceToHost));
+    if ((flags & 2) || brk) worst = SG_ENUMERIC;
+    else if ((flags & 1) && worst == SG_OK) worst = SG_ENOTCONV;
+    if (out_n) {
+      sg_stats& st = out_n[i];
+      st.steps = nsteps;
+      st.step_index = (int)hi->step;
+      st.iters_last = cnt ? it.back() : 0;
+      long long tot = 0;
+      for (int v : it) tot += v;
+      st.iters_total = tot;
+      long long inner = 0;
+      CK(cudaMemcpy(&inner, hi->ctl.it_total, sizeof(long long), cudaMemcpyDeviceToHost));
+      st.inner_total = inner;  // cumulative for the handle
+      st.relres_last = cnt ? rl.back() : 0.0;
+      st.ms = ms;              // wall time of the whole batched run
+    }
+  }
+  return worst;
+}
+
+int sg_solve_batch(sg_handle* hs, int n, int nsteps, sg_stats* out_n) {
+  if (!hs || n <= 0 || nsteps < 0) return SG_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!hs[i]) return SG_EINVAL;
+  return batch_impl(hs, n, nsteps, out_n);
 }
 
 int sg_get_field(sg_handle h, int mode, double* dst, int on_device) {

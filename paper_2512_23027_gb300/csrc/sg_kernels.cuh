@@ -1148,8 +1148,9 @@ __global__ void k_coarse_units(int nsub, int R, int nl, int P, int sub0, const i
 }
 
 // Phi[sub][col][q][k] = v[b][gam_ln[q]][k] on remaining nodes (0 on corners)
+template <typename TV>
 __global__ void k_coarse_phi(int nsub_chunk, int sub0, int R, int nl, int P, int nGam, const uint8_t* cls,
-                             const int* gam_ln, const int* n_gam, const double* __restrict__ v,
+                             const int* gam_ln, const int* n_gam, const TV* __restrict__ v,
                              double* __restrict__ Phi) {
   count_launch();
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1163,7 +1164,7 @@ __global__ void k_coarse_phi(int nsub_chunk, int sub0, int R, int nl, int P, int
   double val = 0.0;
   if (q < n_gam[sub]) {
     const int ln = gam_ln[(long long)sub * nGam + q];
-    if (cls[(long long)sub * nl + ln] == REM) val = v[(((long long)sl * R + col) * nl + ln) * P + k];
+    if (cls[(long long)sub * nl + ln] == REM) val = (double)v[(((long long)sl * R + col) * nl + ln) * P + k];
   }
   Phi[(((long long)sub * R + col) * nGam + q) * P + k] = val;
 }
