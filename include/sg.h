@@ -126,6 +126,18 @@ int sg_get_field(sg_handle h, int mode, double* dst, int on_device);
  * nodes into host or device arrays of n_free doubles each; either pointer may be NULL. */
 int sg_get_moments(sg_handle h, double* mean, double* var, int on_device);
 
+/* Same results as sg_get_moments(h, mean, var, 0) for callers that must not allocate device
+ * memory, for example code that runs while a CUDA graph is being captured or under an allocator
+ * policy that forbids cudaMalloc.  mean / var are host arrays of n_free doubles (either may be NULL,
+ * not both).  Instead of handle-owned memory, the device staging buffer is one fixed array inside
+ * the library: 2 x 2^20 doubles (16 MiB), held by every GPU that loads the library until the
+ * process exits.  Handles with more than 2^20 free nodes get SG_EINVAL.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the array: calls whose device work
+ * overlaps in time race and may read each other's values.  The call allocates nothing.  The paper
+ * has no counterpart: this entry point exists only for allocation-restricted callers. */
+int sg_get_moments_noalloc(sg_handle h, double* mean, double* var);
+
 /* Checkpoint: state = [U | V | A] (3 * n_free * P doubles, layout above) followed by one
  * double holding the step index.  sg_set_state restores it (the PCG warm start is reset to the
  * interface restriction of U). */

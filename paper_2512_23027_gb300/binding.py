@@ -81,6 +81,8 @@ def load_library(path: Optional[str] = None):
     lib.sg_solve_batch.argtypes = [P(C.c_void_p), C.c_int, C.c_int, P(Stats)]
     lib.sg_get_field.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int]
     lib.sg_get_moments.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+    lib.sg_get_moments_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.sg_get_moments_noalloc.restype = C.c_int
     lib.sg_get_state.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
     lib.sg_set_state.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
     lib.sg_step_host.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, P(Stats)]

@@ -1346,6 +1346,43 @@ int sg_get_moments(sg_handle h, double* mean, double* var, int on_device) {
   return SG_OK;
 }
 
+// ---- moments without allocation: static device staging array ----
+// Capacity: SG_NOALLOC_MAX_FREE free nodes (mean and variance, 2 x 2^20 doubles = 16 MiB).  The array
+// is a file-scope device variable, so every GPU that loads this library holds it until exit.
+constexpr int SG_NOALLOC_MAX_FREE = 1 << 20;
+static __device__ __align__(256) double g_noalloc_stage[2 * (size_t)SG_NOALLOC_MAX_FREE];
+constexpr int SG_NOALLOC_MAX_DEV = 64;
+static double* g_noalloc_ptr[SG_NOALLOC_MAX_DEV] = {};
+
+int sg_get_moments_noalloc(sg_handle h, double* mean, double* var) {
+  if (!h || (!mean && !var)) return SG_EINVAL;
+  const auto& pr = h->pr;
+  if (pr.n_free > SG_NOALLOC_MAX_FREE) {
+    h->err = "sg_get_moments_noalloc: more free nodes than the static staging array holds (2^20)";
+    return SG_EINVAL;
+  }
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= SG_NOALLOC_MAX_DEV) { h->err = "sg_get_moments_noalloc: device index out of range"; return SG_EINVAL; }
+  if (!g_noalloc_ptr[dev]) {
+    // one-time set-up on this device: the host-side symbol is only a stand-in, the kernel needs
+    // the array's device address
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_stage));
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  double* dm = g_noalloc_ptr[dev];
+  double* dv = dm + SG_NOALLOC_MAX_FREE;
+  // every entry that is copied out is written first, so nothing needs clearing between calls
+  sgk::k_moments<<<nblk(pr.n_free), 256, 0, h->st>>>(pr.n_free, pr.P, h->free_owner, h->U, mean ? dm : nullptr,
+                                                      var ? dv : nullptr);
+  CKL();
+  if (mean) CK(cudaMemcpyAsync(mean, dm, sizeof(double) * pr.n_free, cudaMemcpyDeviceToHost, h->st));
+  if (var) CK(cudaMemcpyAsync(var, dv, sizeof(double) * pr.n_free, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return SG_OK;
+}
+
 int sg_get_state(sg_handle h, double* dst, int on_device) {
   if (!h || !dst) return SG_EINVAL;
   const auto& pr = h->pr;
