@@ -168,6 +168,47 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """Batched workload: independent problems of uneven size advanced together, one graph launch per
+    time step for the whole batch (mixed precision, autotuned tiles)."""
+    import torch
+    import sg_workloads as w
+    from paper_2512_23027_gb300 import Solver, solve_batch
+    from paper_2512_23027_gb300.binding import SG_MIXED
+    from paper_2512_23027_gb300.binding import SGError
+    drawn = w.batch_problems(256)[: args.batch]
+    t0 = time.perf_counter()
+    probs, solvers, skipped = [], [], []
+    for p in drawn:
+        try:
+            solvers.append(Solver(p, precision=SG_MIXED, autotune=True))
+            probs.append(p)
+        except SGError as e:  # reported, never silently replaced
+            if e.code != -7:
+                raise
+            skipped.append(f"{p.name}: {p.N}^2 grid, {p.s}x{p.s} subdomains")
+    setup = time.perf_counter() - t0
+    solve_batch(solvers, max(3, args.warmup))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = solve_batch(solvers, args.steps)
+    wall = time.perf_counter() - t0
+    ms = st[0]["ms"]
+    dofs = sum((p.N - 1) ** 2 * p.P for p in probs)
+    line = {"metric": "batched SG-DD problem-steps/sec (uneven problems, one graph launch per step)",
+            "value": len(probs) * args.steps / (ms / 1e3), "unit": "problem-steps/s", "problems": len(probs),
+            "steps": args.steps, "ms_per_batch_step": ms / args.steps, "wall_s": wall, "setup_s": setup,
+            "total_sg_dofs": dofs, "pcg_iters_per_step": sum(s["iters_total"] for s in st) / (len(st) * args.steps),
+            "max_iters_last": max(s["iters_last"] for s in st), "dtype": "f32+f64", "data": "synthetic",
+            "skipped": skipped,
+            "config": {"workload": "batch (seed 20251227)", "grids": sorted({p.N for p in probs}),
+                       "subdomains": sorted({p.s for p in probs}), "pce_terms": sorted({p.P for p in probs})}}
+    print(json.dumps(line), flush=True)
+    for s in solvers:
+        s.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -178,12 +219,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--batch", type=int, default=0,
+                    help="instead of the default line, run the first BATCH problems of the batched workload "
+                         "(64^2..256^2 grids, uneven sizes) with sg_solve_batch and report problem-steps/s")
     ap.add_argument("--enqueue", default="graph", choices=["graph", "eager"],
                     help="graph: one CUDA graph per step (default); eager: host-driven enqueue of the same "
                          "kernels (per-kernel profilers cannot see inside graphs with conditional nodes)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch:
+        return run_batch(args)
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

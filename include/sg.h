@@ -77,6 +77,8 @@ typedef struct {
   int    warm;        /* SG_WARM_PREV or SG_WARM_LEARNED                                    */
   double inner_tol;   /* subdomain solves: relative residual target (0 = automatic)         */
   int    inner_max_iter; /* subdomain solves: iteration cap (0 = automatic)                 */
+  int    autotune;    /* 1: time candidate tile shapes of the hot kernels at set-up and keep the
+                         fastest per problem shape (process-wide table); 0: built-in heuristics */
 } sg_params;
 
 typedef struct { int kind; double x0, y0, width, freq, amp; } sg_source;

@@ -35,7 +35,7 @@ class PCE(C.Structure):
 class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("tol", C.c_double), ("alpha0", C.c_double), ("alpha1", C.c_double),
                 ("max_iter", C.c_int), ("precision", C.c_int), ("warm", C.c_int),
-                ("inner_tol", C.c_double), ("inner_max_iter", C.c_int)]
+                ("inner_tol", C.c_double), ("inner_max_iter", C.c_int), ("autotune", C.c_int)]
 
 
 class Source(C.Structure):
@@ -122,7 +122,7 @@ class Solver:
 
     def __init__(self, prob, precision: int = SG_FP64, warm: int = SG_WARM_PREV, stream=None,
                  tol: Optional[float] = None, inner_tol: float = 0.0, inner_max_iter: int = 0,
-                 max_iter: Optional[int] = None):
+                 max_iter: Optional[int] = None, autotune: bool = False):
         self.lib = load_library()
         self.prob = prob
         s = prob.source
@@ -131,7 +131,7 @@ class Solver:
         self._pce = PCE(prob.p, prob.p_in)
         self._prm = Params(prob.dt, prob.tol if tol is None else tol, prob.alpha0, prob.alpha1,
                            prob.max_iter if max_iter is None else max_iter, precision, warm, inner_tol,
-                           inner_max_iter)
+                           inner_max_iter, int(bool(autotune)))
         self._src = Source(s.kind, s.x0, s.y0, s.width, s.freq, s.amp)
         st = 0
         if stream is not None:

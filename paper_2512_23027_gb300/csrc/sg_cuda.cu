@@ -25,6 +25,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <map>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -292,6 +294,20 @@ const LineFactor<double>& lfT<double>(sg_handle h, int pat) { return h->lf[pat];
 template <>
 const LineFactor<float>& lfT<float>(sg_handle h, int pat) { return h->lf32[pat]; }
 
+// ---- autotuned tile shapes (process-wide, keyed by the problem shape) ----
+struct TuneKey {
+  int kind, tsize, L, P, PI, nnz, nb;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(kind, tsize, L, P, PI, nnz, nb) < std::tie(o.kind, o.tsize, o.L, o.P, o.PI, o.nnz, o.nb);
+  }
+};
+static std::map<TuneKey, int> g_tune;  // kind 0: apply lines per block; 1: line-solve modes per block
+
+static int tuned(int kind, size_t tsize, const sgh::Problem& pr, int nb) {
+  auto it = g_tune.find(TuneKey{kind, (int)tsize, pr.L, pr.P, pr.PI, (int)pr.gk_v.size(), nb});
+  return it == g_tune.end() ? 0 : it->second;
+}
+
 // apply tile configuration: lines per block, dynamic shared memory, kappa staging
 template <typename T>
 static void apply_cfg(const sgh::Problem& pr, int nb, int* TL, int* NT, size_t* sm, int* stage) {
@@ -311,6 +327,7 @@ static void apply_cfg(const sgh::Problem& pr, int nb, int* TL, int* NT, size_t* 
     if (base(t) + kap(t) <= 110 * 1024 && (blocks >= 128 || t == 1)) { best = t; break; }
   }
   while (best > 1 && base(best) > 200 * 1024) best /= 2;
+  if (const int t = tuned(0, sizeof(T), pr, nb)) best = t;
   *TL = best;
   *NT = (L + best - 1) / best;
   *stage = base(best) + kap(best) <= 200 * 1024 ? 1 : 0;
@@ -372,6 +389,7 @@ static LineCfg line_cfg(const sgh::Problem& pr, int nb_hint) {
       const int nbp = std::max(1, nb_hint);
       int g = std::max(1, (P * nbp + 151) / 152);
       g = std::min(g, gmax);
+      if (const int t = tuned(1, sizeof(T), pr, nb_hint)) g = std::min(t, gmax);
       c.team = true;
       c.NG = (P + g - 1) / g;
       c.G = (P + c.NG - 1) / c.NG;
@@ -381,6 +399,7 @@ static LineCfg line_cfg(const sgh::Problem& pr, int nb_hint) {
     }
   }
   int g = sizeof(T) == 8 ? 2 : (P + 1) / 2;
+  if (const int t = tuned(1, sizeof(T), pr, nb_hint)) g = t;
   g = std::max(1, std::min(g, 1024 / L));
   while (g > 1 && line_smem<T>(L, g) > 200 * 1024) --g;
   int lp = L;
@@ -423,9 +442,9 @@ static int ensure_ws(sg_handle h, int nb) {
   int TL, NT, stage;
   size_t sm;
   apply_cfg<T>(h->pr, nb, &TL, &NT, &sm, &stage);
-  int ng = 1;
-  for (int nbh : {1, nb, h->pr.nsub}) ng = std::max(ng, line_cfg<T>(h->pr, nbh).NG);
-  return ensure_ctl(h, nb, NT, ng);
+  // capacities cover every tile shape the tuner may pick: NT <= L, NG <= P
+  (void)NT;
+  return ensure_ctl(h, nb, h->pr.L, h->pr.P);
 }
 
 // CUDA-event timing of one kernel launch on its stream (host-driven enqueue only)
@@ -1045,6 +1064,106 @@ static void free_all(sg_handle h) {
   if (h->own_st && h->st) cudaStreamDestroy(h->st);
 }
 
+// Autotuner: times the candidate tile shapes of the two hot kernels of the inner solve on this
+// handle's own workspace (results discarded) and records the fastest per problem shape.  Candidates:
+// fused apply with 1, 2, 4 or 8 grid lines per block (shared memory permitting); line solve with
+// 1..gmax modes per block (warp-team kernel) or 1, 2, 4, 8 (block kernel).
+template <typename T>
+static int autotune_t(sg_handle h, int nb) {
+  const auto& pr = h->pr;
+  cudaStream_t st = h->st;
+  auto& w = wsT<T>(h);
+  const Op<T> op = h->op<T>();
+  auto time_it = [&](auto&& launch, float* best_ms) -> int {
+    for (int i = 0; i < 2; ++i) launch();
+    CK(cudaEventRecord(h->kev0, st));
+    for (int i = 0; i < 6; ++i) launch();
+    CK(cudaEventRecord(h->kev1, st));
+    CK(cudaEventSynchronize(h->kev1));
+    CKL();
+    CK(cudaEventElapsedTime(best_ms, h->kev0, h->kev1));
+    return SG_OK;
+  };
+  // apply: lines per block
+  {
+    const TuneKey key{0, (int)sizeof(T), pr.L, pr.P, pr.PI, (int)pr.gk_v.size(), nb};
+    if (!g_tune.count(key)) {
+      int best_t = 0;
+      float best = 1e30f;
+      for (int t : {1, 2, 4, 8}) {
+        if (t > pr.L) continue;
+        g_tune[key] = t;
+        int TL, NT, stage;
+        size_t sm;
+        apply_cfg<T>(pr, nb, &TL, &NT, &sm, &stage);
+        if (TL != t || sm > 200 * 1024) continue;
+        float ms = 0.f;
+        auto launch_ap = [&]() {
+          launch_apply<T, T, true, true>(h, st, op, nb, 1, nullptr, nullptr, w.q, nullptr, h->am, h->bk, sgk::MASK_N,
+                                         w.p0, w.p1, w.z);
+        };
+        RET(time_it(launch_ap, &ms));
+        if (ms < best) { best = ms; best_t = t; }
+      }
+      if (best_t) g_tune[key] = best_t;
+      else g_tune.erase(key);
+    }
+  }
+  // line solve: modes per block
+  {
+    const TuneKey key{1, (int)sizeof(T), pr.L, pr.P, pr.PI, (int)pr.gk_v.size(), nb};
+    if (!g_tune.count(key)) {
+      const int L = pr.L;
+      const long long pstride = (long long)L * L * L;
+      const auto& lf = lfT<T>(h, 1);
+      const long long pstride_pad = (long long)L * L * pad4(L);
+      int best_g = 0;
+      float best = 1e30f;
+      for (int g = 1; g <= std::min(pr.P, 15); ++g) {
+        g_tune[key] = g;
+        const LineCfg lc = line_cfg<T>(pr, nb);
+        if (lc.G != g && !(lc.team && lc.G == (pr.P + lc.NG - 1) / lc.NG && lc.G <= g)) continue;
+        int TL, NT, stage;
+        size_t sm;
+        apply_cfg<T>(pr, nb, &TL, &NT, &sm, &stage);
+        const unsigned lg = (unsigned)nb * lc.NG;
+        float ms = 0.f;
+        auto launch_line = [&]() {
+          if (lc.team) {
+#define SG_TEAM_T(LSV)                                                                                           \
+  case LSV:                                                                                                      \
+    sgk::k_line_team<T, LSV><<<lg, lc.block, lc.smem, st>>>(L, pr.nl, pr.P, 1, lc.NG, NT, lc.G, pstride_pad,     \
+                                                            lf.Spad, lf.Bd, lf.Bu, nb, w.x, w.r, w.z, w.p0, w.p1, \
+                                                            w.q, h->ctl, 1, 1e-30, 1e300, 1, 0, 0);              \
+    break;
+            switch (pad4(L)) {
+              SG_TEAM_T(4) SG_TEAM_T(8) SG_TEAM_T(12) SG_TEAM_T(16) SG_TEAM_T(20) SG_TEAM_T(24) SG_TEAM_T(28)
+              SG_TEAM_T(32) SG_TEAM_T(36) SG_TEAM_T(40)
+              default: break;
+            }
+#undef SG_TEAM_T
+          } else {
+            sgk::k_line<T><<<lg, lc.block, lc.smem, st>>>(L, pr.nl, pr.P, 1, lc.NG, NT, pstride, lf.Sinv, lf.Bd, lf.Bu,
+                                                          nb, w.x, w.r, w.z, w.p0, w.p1, w.q, h->ctl, 1, 1e-30, 1e300,
+                                                          1, 0, 0);
+          }
+        };
+        RET(time_it(launch_line, &ms));
+        if (ms < best) { best = ms; best_g = g; }
+      }
+      if (best_g) g_tune[key] = best_g;
+      else g_tune.erase(key);
+    }
+  }
+  return SG_OK;
+}
+
+static int autotune(sg_handle h) {
+  RET(autotune_t<float>(h, h->pr.nsub));
+  if (h->precision == SG_FP64) RET(autotune_t<double>(h, h->pr.nsub));
+  return SG_OK;
+}
+
 static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const sg_pce* pce,
                       const sg_params* prm, const sg_source* src) {
   sgh::SourceDesc sd{src ? src->kind : 0, src ? src->x0 : 0.5, src ? src->y0 : 0.5,
@@ -1139,7 +1258,29 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   RET(ensure_ws<double>(h, pr.nsub));
   RET(ensure_ws<float>(h, pr.nsub));
   CKL();
+  // shared-memory fit of the hot kernels at this subdomain size (per precision in use)
+  {
+    auto fits_apply = [&](auto tag) {
+      using T = decltype(tag);
+      int TL, NT, stage;
+      size_t sm;
+      apply_cfg<T>(pr, pr.nsub, &TL, &NT, &sm, &stage);
+      return sm <= 200 * 1024;
+    };
+    auto fits_line = [&](auto tag) {
+      using T = decltype(tag);
+      const LineCfg lc = line_cfg<T>(pr, pr.nsub);
+      return lc.smem <= (lc.team ? SMEM_MAX : 200 * 1024);
+    };
+    const bool ok = fits_apply(double{}) && (h->precision == SG_MIXED ? (fits_apply(float{}) && fits_line(float{}))
+                                                                        : fits_line(double{}));
+    if (!ok) {
+      h->err = "subdomain too large for the shared-memory tiles of this build (H = " + std::to_string(pr.H) + " cells)";
+      return SG_ENOTSUP;
+    }
+  }
   RET(build_line_factors(h));
+  if (prm->autotune) RET(autotune(h));
   RET(build_coarse(h));
   RET(initial_state(h));
   CK(cudaStreamSynchronize(h->st));

@@ -54,3 +54,16 @@ def test_batch_workload_draw_is_reproducible():
     assert a == b
     assert all(p.N % p.s == 0 and 64 <= p.N <= 256 and p.s in (2, 4, 8) for p in a)
     assert {p.M for p in a} == {2, 3, 4} and {p.p for p in a} == {2, 3}
+
+
+def test_autotuned_tiles_match_heuristic_tiles(Solver):
+    """Tile shapes chosen by the set-up autotuner change only summation order."""
+    prob = w.config("small")
+    a = Solver(prob, tol=1e-13)
+    a.step(3)
+    b = Solver(prob, tol=1e-13, autotune=True)
+    b.step(3)
+    ua, ub = a.field(), b.field()
+    assert np.linalg.norm(ua - ub) <= 1e-10 * np.linalg.norm(ua)
+    a.close()
+    b.close()
