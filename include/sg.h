@@ -79,6 +79,8 @@ typedef struct {
   int    inner_max_iter; /* subdomain solves: iteration cap (0 = automatic)                 */
   int    autotune;    /* 1: time candidate tile shapes of the hot kernels at set-up and keep the
                          fastest per problem shape (process-wide table); 0: built-in heuristics */
+  int    warm_train_steps; /* SG_WARM_LEARNED: steps of online training (0 = 20)              */
+  double warm_lr;          /* SG_WARM_LEARNED: Adam learning rate (0 = 1e-3)                  */
 } sg_params;
 
 typedef struct { int kind; double x0, y0, width, freq, amp; } sg_source;
@@ -158,6 +160,24 @@ int sg_get_sizes(sg_handle h, sg_sizes* out);
 /* Per-step outer iteration counts of the last sg_step call (up to cap entries); returns the
  * number written or a negative code. */
 int sg_get_iters(sg_handle h, int* iters, double* relres, int cap);
+
+/* Learned warm start (extension of the paper's method; with warm = SG_WARM_LEARNED).  Per interface
+ * (dof, mode) row a 4-32-32-1 tanh MLP (BF16 weights, FP32 arithmetic) maps the normalised history
+ * [u^n, u^{n-1}, u^{n-2}, p] / s, p = u^n + dt v^n + dt^2/2 a^n, to a correction c; the PCG starts
+ * from p + s c.  The network trains online (Adam, hand-written kernels) on the first
+ * warm_train_steps steps; until it has trained the previous-step guess is used.  The PCG still
+ * stops at the same relative residual.  Weights: NN_NP = 1249 floats, order W1 (32x4, row-major),
+ * b1 (32), W2 (32x32), b2 (32), W3 (32), b3 (1).
+ * sg_warm_weights copies the FP32 master weights out (get_host) and/or in (set_host, which also
+ * marks the network as trained and resets Adam); n must be 1249. */
+int sg_warm_weights(sg_handle h, float* get_host, const float* set_host, int n);
+int sg_warm_status(sg_handle h, int* trained, int* train_left, float* loss);
+
+/* Network evaluation on caller device buffers (for gradient checks): X rows x 4, t rows, theta the
+ * 1249 FP32 parameters (rounded to BF16 as in the solver).  Writes y (rows, optional) and, when t
+ * and grad are given, grad (1249 floats) of the mean squared error and the loss (host double).
+ * Allocates and frees its own scratch; synchronises the device. */
+int sg_mlp_eval(int rows, const float* X, const float* t, const float* theta, float* y, float* grad, double* loss);
 
 /* Enqueue mode of sg_step: 0 (default) launches one captured CUDA graph per step whose inner
  * and outer loops are conditional nodes; 1 enqueues the same kernels from the host with the

@@ -35,7 +35,8 @@ class PCE(C.Structure):
 class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("tol", C.c_double), ("alpha0", C.c_double), ("alpha1", C.c_double),
                 ("max_iter", C.c_int), ("precision", C.c_int), ("warm", C.c_int),
-                ("inner_tol", C.c_double), ("inner_max_iter", C.c_int), ("autotune", C.c_int)]
+                ("inner_tol", C.c_double), ("inner_max_iter", C.c_int), ("autotune", C.c_int),
+                ("warm_train_steps", C.c_int), ("warm_lr", C.c_double)]
 
 
 class Source(C.Structure):
@@ -93,6 +94,12 @@ def load_library(path: Optional[str] = None):
     lib.sg_set_enqueue_mode.restype = C.c_int
     lib.sg_kernel_timing.argtypes = [C.c_void_p, C.c_int, P(C.c_double), P(C.c_longlong)]
     lib.sg_kernel_timing.restype = C.c_int
+    lib.sg_warm_weights.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+    lib.sg_warm_weights.restype = C.c_int
+    lib.sg_warm_status.argtypes = [C.c_void_p, P(C.c_int), P(C.c_int), P(C.c_float)]
+    lib.sg_warm_status.restype = C.c_int
+    lib.sg_mlp_eval.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, P(C.c_double)]
+    lib.sg_mlp_eval.restype = C.c_int
     lib.sg_launch_count.argtypes = [C.c_void_p]
     lib.sg_launch_count.restype = C.c_longlong
     lib.sg_strerror.argtypes = [C.c_int]
@@ -122,7 +129,8 @@ class Solver:
 
     def __init__(self, prob, precision: int = SG_FP64, warm: int = SG_WARM_PREV, stream=None,
                  tol: Optional[float] = None, inner_tol: float = 0.0, inner_max_iter: int = 0,
-                 max_iter: Optional[int] = None, autotune: bool = False):
+                 max_iter: Optional[int] = None, autotune: bool = False, warm_train_steps: int = 0,
+                 warm_lr: float = 0.0):
         self.lib = load_library()
         self.prob = prob
         s = prob.source
@@ -131,7 +139,7 @@ class Solver:
         self._pce = PCE(prob.p, prob.p_in)
         self._prm = Params(prob.dt, prob.tol if tol is None else tol, prob.alpha0, prob.alpha1,
                            prob.max_iter if max_iter is None else max_iter, precision, warm, inner_tol,
-                           inner_max_iter, int(bool(autotune)))
+                           inner_max_iter, int(bool(autotune)), warm_train_steps, warm_lr)
         self._src = Source(s.kind, s.x0, s.y0, s.width, s.freq, s.amp)
         st = 0
         if stream is not None:
@@ -210,6 +218,21 @@ class Solver:
         n = C.c_longlong()
         self._check(self.lib.sg_kernel_timing(self.h, which, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    def warm_weights(self, new=None):
+        """FP32 master weights of the warm-start network (copy); `new` replaces them."""
+        out = np.zeros(1249, dtype=np.float32)
+        setp = None
+        if new is not None:
+            new = np.ascontiguousarray(new, dtype=np.float32)
+            setp = C.c_void_p(new.ctypes.data)
+        self._check(self.lib.sg_warm_weights(self.h, C.c_void_p(out.ctypes.data), setp, 1249))
+        return out
+
+    def warm_status(self):
+        a, b, l = C.c_int(), C.c_int(), C.c_float()
+        self._check(self.lib.sg_warm_status(self.h, C.byref(a), C.byref(b), C.byref(l)))
+        return {"trained": a.value, "train_left": b.value, "loss": l.value}
 
     def launch_count(self) -> int:
         """Kernels launched by the library so far in this process (device-side count)."""

@@ -128,6 +128,12 @@ struct sg_handle_s {
   std::vector<int> iters;
   std::vector<double> relres;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // learned warm start
+  sgk::WarmCtl wctl{};
+  double *wU0 = nullptr, *wU1 = nullptr, *wU2 = nullptr, *vG = nullptr, *aG = nullptr, *wpred = nullptr, *wscale = nullptr;
+  float *wX = nullptr, *wy = nullptr, *wt = nullptr;
+  int warm_train = 20, warm_epochs = 4;
+  float warm_lr = 1e-3f;
   // per-kernel timing (host-driven enqueue only): 0 off, 1 line kernel, 2 fused apply kernel
   int kprof = 0;
   double kprof_ms = 0.0;
@@ -662,6 +668,92 @@ static int enq_outer(sg_handle h, Ctx& cx) {
   });
 }
 
+// ---------------------------------------------------------------------------------------------
+// Learned warm start (extension): guess before the PCG, online training after it
+// ---------------------------------------------------------------------------------------------
+static int enq_warm_guess(sg_handle h, Ctx& cx) {
+  const auto& pr = h->pr;
+  cudaStream_t st = cx.st;
+  const int nr = (int)h->nGd();
+  sgk::k_scatter<double><<<nblk(nr), 256, 0, st>>>(pr.nG, pr.P, h->owners, h->Dw, h->V, h->vG, 1);
+  sgk::k_scatter<double><<<nblk(nr), 256, 0, st>>>(pr.nG, pr.P, h->owners, h->Dw, h->A, h->aG, 1);
+  sgk::k_wfeat<<<nblk(nr), 256, 0, st>>>(nr, pr.dt, h->xG, h->wU1, h->wU2, h->vG, h->aG, h->wX, h->wpred, h->wscale);
+  CK(cudaMemcpyAsync(h->wU0, h->xG, sizeof(double) * nr, cudaMemcpyDeviceToDevice, st));
+  sgk::k_mlp<false><<<(nr + sgk::NN_ROWS - 1) / sgk::NN_ROWS, sgk::NN_ROWS, 0, st>>>(nr, h->wX, nullptr, h->wctl.wb, h->wy,
+                                                                                    nullptr, nullptr, nullptr);
+  sgk::k_wguess<<<nblk(nr), 256, 0, st>>>(nr, h->wctl.trained, h->wy, h->wpred, h->wscale, h->xG);
+  CKL();
+  return SG_OK;
+}
+
+static int enq_warm_train(sg_handle h, Ctx& cx) {
+  cudaStream_t st = cx.st;
+  const int nr = (int)h->nGd();
+  const int nb = (nr + sgk::NN_ROWS - 1) / sgk::NN_ROWS;
+  sgk::k_wtarget<<<nblk(nr), 256, 0, st>>>(nr, h->wctl.train_left, h->xG, h->wpred, h->wscale, h->wt);
+  for (int e = 0; e < h->warm_epochs; ++e) {
+    sgk::k_mlp<true><<<nb, sgk::NN_ROWS, 0, st>>>(nr, h->wX, h->wt, h->wctl.wb, nullptr, h->wctl.part, h->wctl.loss_part,
+                                                  h->wctl.train_left);
+    sgk::k_mlp_adam<<<1, 256, 0, st>>>(nb, nr, h->wctl, h->warm_lr, h->wctl.train_left);
+  }
+  sgk::k_wdone<<<1, 32, 0, st>>>(h->wctl);
+  sgk::k_wshift<<<nblk(nr), 256, 0, st>>>(nr, h->wU1, h->wU2, h->wU0);
+  CKL();
+  return SG_OK;
+}
+
+// initial weights: SplitMix64 stream (seed 1), uniform in +-sqrt(6 / (fan_in + fan_out)); the output
+// layer starts at 1/10 of that scale so the first guesses stay close to the predictor
+static std::vector<float> warm_init_weights() {
+  std::vector<float> th(sgk::NN_NP, 0.f);
+  unsigned long long s = 1ULL;
+  auto u01 = [&]() {
+    s += 0x9E3779B97F4A7C15ULL;
+    unsigned long long z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  };
+  auto fill = [&](int off, int n, int fin, int fout, double scale) {
+    const double a = scale * std::sqrt(6.0 / (fin + fout));
+    for (int i = 0; i < n; ++i) th[off + i] = (float)((2.0 * u01() - 1.0) * a);
+  };
+  fill(sgk::NN_OW1, sgk::NN_H * sgk::NN_F, sgk::NN_F, sgk::NN_H, 1.0);
+  fill(sgk::NN_OW2, sgk::NN_H * sgk::NN_H, sgk::NN_H, sgk::NN_H, 1.0);
+  fill(sgk::NN_OW3, sgk::NN_H, sgk::NN_H, 1, 0.1);
+  return th;
+}
+
+static int warm_setup(sg_handle h) {
+  const int nr = (int)h->nGd();
+  auto& wc = h->wctl;
+  RET(dalloc(h, &wc.theta, sgk::NN_NP)); RET(dalloc(h, &wc.m, sgk::NN_NP)); RET(dalloc(h, &wc.v, sgk::NN_NP));
+  RET(dalloc(h, &wc.wb, sgk::NN_NP));
+  const int nb = std::max(1, (nr + sgk::NN_ROWS - 1) / sgk::NN_ROWS);
+  RET(dalloc(h, &wc.part, (long long)nb * sgk::NN_NP)); RET(dalloc(h, &wc.loss_part, nb));
+  RET(dalloc(h, &wc.loss, 1)); RET(dalloc(h, &wc.train_left, 1)); RET(dalloc(h, &wc.trained, 1));
+  RET(dalloc(h, &wc.adam_it, 1));
+  for (double** p : {&h->wU0, &h->wU1, &h->wU2, &h->vG, &h->aG, &h->wpred, &h->wscale}) RET(dalloc(h, p, nr));
+  RET(dalloc(h, &h->wX, 4LL * nr)); RET(dalloc(h, &h->wy, nr)); RET(dalloc(h, &h->wt, nr));
+  const std::vector<float> th = warm_init_weights();
+  CK(cudaMemcpyAsync(wc.theta, th.data(), sizeof(float) * th.size(), cudaMemcpyHostToDevice, h->st));
+  sgk::k_to_bf16<<<nblk(sgk::NN_NP), 256, 0, h->st>>>(sgk::NN_NP, wc.theta, wc.wb);
+  CK(cudaMemcpyAsync(wc.train_left, &h->warm_train, sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  CKL();
+  return SG_OK;
+}
+
+// history of the interface solution starts from the current one
+static int warm_reset_history(sg_handle h) {
+  if (h->warm != SG_WARM_LEARNED) return SG_OK;
+  const size_t nb = sizeof(double) * (size_t)h->nGd();
+  CK(cudaMemcpyAsync(h->wU1, h->xG, nb, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(h->wU2, h->xG, nb, cudaMemcpyDeviceToDevice, h->st));
+  return SG_OK;
+}
+
 // One time step (a1 .. a7), enqueued on cx.
 static int enq_step(sg_handle h, Ctx& cx, bool ext) {
   const auto& pr = h->pr;
@@ -703,9 +795,12 @@ static int enq_step(sg_handle h, Ctx& cx, bool ext) {
   }
   sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, h->Dw, h->wc, h->gG, 0);
   CKL();
-  // a3-a5: PCG on the interface, warm-started from the previous solution in xG
+  // a3: initial guess -- previous solution in xG (Alg. 1), or the learned predictor
+  if (h->warm == SG_WARM_LEARNED) RET(enq_warm_guess(h, cx));
+  // a4-a5: PCG on the interface
   RET(enq_outer(h, cx));
   sgk::k_record<<<1, 32, 0, st>>>(h->octl, h->stepctr, REC_CAP, h->rec_iters, h->rec_rel, h->rec_flags);
+  if (h->warm == SG_WARM_LEARNED) RET(enq_warm_train(h, cx));
   // a6: interior recovery u_I = K_II^{-1} (f~_I - K_IG u_G)
   sgk::k_gather<double><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->gidx, h->Dw, h->xG, h->wa, sgk::MASK_G, 0);
   RET((launch_apply<double, double, false, false>(h, st, op, nsub, 1, h->wa, h->wa, h->wb, h->ft, -h->am, -h->bk,
@@ -1189,6 +1284,10 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   h->inner_tol32 = prm->inner_tol > 0 ? std::max(prm->inner_tol, 1e-7) : 1e-6;
   h->inner_max = prm->inner_max_iter > 0 ? prm->inner_max_iter : 400;
   h->eager = std::getenv("SG_EAGER") != nullptr;
+  if (prm->warm != SG_WARM_PREV && prm->warm != SG_WARM_LEARNED) { h->err = "warm"; return SG_EINVAL; }
+  if (prm->warm_train_steps < 0 || prm->warm_lr < 0) { h->err = "warm-start training parameters"; return SG_EINVAL; }
+  h->warm_train = prm->warm_train_steps > 0 ? prm->warm_train_steps : 20;
+  h->warm_lr = prm->warm_lr > 0 ? (float)prm->warm_lr : 1e-3f;
   h->am = 1.0 / (ZETA * pr.dt * pr.dt) + pr.alpha0 * GAMMA / (ZETA * pr.dt);
   h->bk = 1.0 + pr.alpha1 * GAMMA / (ZETA * pr.dt);
   if (!h->st) {  // private stream when the caller passes none
@@ -1282,7 +1381,9 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   RET(build_line_factors(h));
   if (prm->autotune) RET(autotune(h));
   RET(build_coarse(h));
+  if (h->warm == SG_WARM_LEARNED) RET(warm_setup(h));
   RET(initial_state(h));
+  RET(warm_reset_history(h));
   CK(cudaStreamSynchronize(h->st));
   return SG_OK;
 }
@@ -1559,6 +1660,7 @@ int sg_set_state(sg_handle h, const double* src, int on_device) {
   CK(cudaMemcpyAsync(h->stepctr, &h->step, sizeof(long long), cudaMemcpyHostToDevice, h->st));
   sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, h->st>>>(pr.nG, pr.P, h->owners, h->Dw, h->U, h->xG, 1);
   CKL();
+  RET(warm_reset_history(h));
   CK(cudaStreamSynchronize(h->st));
   return SG_OK;
 }
@@ -1586,6 +1688,68 @@ long long sg_launch_count(sg_handle h) {
   unsigned long long v = 0;
   if (cudaMemcpy(&v, h->nlaunch, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return SG_ECUDA;
   return (long long)v;
+}
+
+int sg_warm_weights(sg_handle h, float* get_host, const float* set_host, int n) {
+  if (!h || h->warm != SG_WARM_LEARNED || n != sgk::NN_NP) return SG_EINVAL;
+  if (get_host) {
+    CK(cudaMemcpyAsync(get_host, h->wctl.theta, sizeof(float) * n, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+  }
+  if (set_host) {
+    CK(cudaMemcpyAsync(h->wctl.theta, set_host, sizeof(float) * n, cudaMemcpyHostToDevice, h->st));
+    sgk::k_to_bf16<<<nblk(n), 256, 0, h->st>>>(n, h->wctl.theta, h->wctl.wb);
+    CKL();
+    const int one = 1;
+    CK(cudaMemcpyAsync(h->wctl.trained, &one, sizeof(int), cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemsetAsync(h->wctl.m, 0, sizeof(float) * n, h->st));
+    CK(cudaMemsetAsync(h->wctl.v, 0, sizeof(float) * n, h->st));
+    CK(cudaMemsetAsync(h->wctl.adam_it, 0, sizeof(int), h->st));
+    CK(cudaStreamSynchronize(h->st));
+  }
+  return SG_OK;
+}
+
+int sg_warm_status(sg_handle h, int* trained, int* train_left, float* loss) {
+  if (!h || h->warm != SG_WARM_LEARNED) return SG_EINVAL;
+  int a = 0, b = 0;
+  float l = 0.f;
+  CK(cudaMemcpy(&a, h->wctl.trained, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&b, h->wctl.train_left, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&l, h->wctl.loss, sizeof(float), cudaMemcpyDeviceToHost));
+  if (trained) *trained = a;
+  if (train_left) *train_left = b;
+  if (loss) *loss = l;
+  return SG_OK;
+}
+
+int sg_mlp_eval(int rows, const float* X, const float* t, const float* theta, float* y, float* grad, double* loss) {
+  if (rows <= 0 || !X || !theta) return SG_EINVAL;
+  const int nb = (rows + sgk::NN_ROWS - 1) / sgk::NN_ROWS;
+  __nv_bfloat16* wb = nullptr;
+  float* part = nullptr;
+  double *lp = nullptr, *ld = nullptr;
+  int rc = SG_OK;
+  if (cudaMalloc(&wb, sizeof(__nv_bfloat16) * sgk::NN_NP) != cudaSuccess ||
+      cudaMalloc(&part, sizeof(float) * (size_t)nb * sgk::NN_NP) != cudaSuccess ||
+      cudaMalloc(&lp, sizeof(double) * nb) != cudaSuccess || cudaMalloc(&ld, sizeof(double)) != cudaSuccess)
+    rc = SG_ENOMEM;
+  if (rc == SG_OK) {
+    sgk::k_to_bf16<<<nblk(sgk::NN_NP), 256>>>(sgk::NN_NP, theta, wb);
+    if (y) sgk::k_mlp<false><<<nb, sgk::NN_ROWS>>>(rows, X, nullptr, wb, y, nullptr, nullptr, nullptr);
+    if (grad && t) {
+      sgk::k_mlp<true><<<nb, sgk::NN_ROWS>>>(rows, X, t, wb, nullptr, part, lp, nullptr);
+      sgk::k_mlp_reduce<<<1, 256>>>(nb, rows, part, lp, grad, ld);
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) rc = SG_ECUDA;
+    if (rc == SG_OK && loss && grad && t && cudaMemcpy(loss, ld, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = SG_ECUDA;
+  }
+  cudaFree(wb);
+  cudaFree(part);
+  cudaFree(lp);
+  cudaFree(ld);
+  return rc;
 }
 
 int sg_set_enqueue_mode(sg_handle h, int eager) {

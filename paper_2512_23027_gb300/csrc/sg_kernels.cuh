@@ -8,6 +8,7 @@
 #pragma once
 #include <cmath>
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace sgk {
@@ -1337,6 +1338,219 @@ __global__ void k_conv_mask(int nb, int R, int nl, int P, const uint8_t* cls, co
   const long long t = idx / P;
   const int ln = (int)(t % nl), b = (int)(t / nl);
   y[idx] = ((mask >> cls[(long long)(b / R) * nl + ln]) & 1) ? (TO)(s * (double)x[idx]) : TO(0);
+}
+
+
+// ------------------------------------------------------------------------------------------
+// Learned PCG warm start (an extension of the method): per interface (dof, mode) row a small
+// MLP maps normalised features [u^n, u^{n-1}, u^{n-2}, predictor] / s to a correction c of the
+// Newmark predictor, guess = predictor + s c.  BF16 weights, FP32 arithmetic and accumulation;
+// FP32 master weights with Adam.  Parameter order: W1 (H x F), b1, W2 (H x H), b2, W3 (H), b3.
+// ------------------------------------------------------------------------------------------
+constexpr int NN_F = 4, NN_H = 32;
+constexpr int NN_OW1 = 0, NN_OB1 = NN_OW1 + NN_H * NN_F, NN_OW2 = NN_OB1 + NN_H, NN_OB2 = NN_OW2 + NN_H * NN_H;
+constexpr int NN_OW3 = NN_OB2 + NN_H, NN_OB3 = NN_OW3 + NN_H, NN_NP = NN_OB3 + 1;
+constexpr int NN_ROWS = 64;   // rows per block of the network kernels (static shared memory < 48 KB)
+
+struct WarmCtl {
+  float* theta;           // [NP] FP32 master weights
+  float* m;               // [NP] Adam first moment
+  float* v;               // [NP] Adam second moment
+  __nv_bfloat16* wb;      // [NP] BF16 weights used by the network kernels
+  float* part;            // [blocks][NP] gradient partials
+  double* loss_part;      // [blocks] loss partials
+  float* loss;            // last training loss (mean squared error)
+  int* train_left;        // online training steps still to do
+  int* trained;           // training steps done (the guess is used once > 0)
+  int* adam_it;           // Adam iteration counter
+};
+
+// features and predictor per row: pred = u + dt v + dt^2/2 a (second-order Taylor of u^{n+1})
+__global__ void k_wfeat(int nrows, double dt, const double* __restrict__ u0, const double* __restrict__ u1,
+                        const double* __restrict__ u2, const double* __restrict__ vG, const double* __restrict__ aG,
+                        float* __restrict__ X, double* __restrict__ pred, double* __restrict__ scale) {
+  count_launch();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  const double p = u0[r] + dt * vG[r] + 0.5 * dt * dt * aG[r];
+  const double f[4] = {u0[r], u1[r], u2[r], p};
+  double s = 0.0;
+  for (int i = 0; i < 4; ++i) s += f[i] * f[i];
+  s = sqrt(0.25 * s);
+  const bool z = !(s > 0.0);
+  for (int i = 0; i < 4; ++i) X[(long long)r * 4 + i] = z ? 0.f : (float)(f[i] / s);
+  pred[r] = p;
+  scale[r] = z ? 1.0 : s;
+}
+
+// Network forward (and, with TRAIN, backward to block-partial gradients and loss).  One thread per
+// row; activations of the block's rows live in shared memory for the weight-gradient sums.
+template <bool TRAIN>
+__global__ void __launch_bounds__(NN_ROWS) k_mlp(int nrows, const float* __restrict__ X, const float* __restrict__ t,
+                                                 const __nv_bfloat16* __restrict__ wb, float* __restrict__ y_out,
+                                                 float* __restrict__ part, double* __restrict__ loss_part,
+                                                 const int* gate) {
+  count_launch();
+  if (TRAIN && gate && *gate <= 0) return;
+  __shared__ float w[NN_NP];
+  __shared__ float xs[NN_ROWS][NN_F];
+  __shared__ float h1s[NN_ROWS][NN_H + 1];
+  __shared__ float h2s[NN_ROWS][NN_H + 1];
+  __shared__ float d2s[NN_ROWS][NN_H + 1];
+  __shared__ float d1s[NN_ROWS][NN_H + 1];
+  __shared__ float dys[NN_ROWS];
+  __shared__ double red[NN_ROWS / 32];
+  for (int i = threadIdx.x; i < NN_NP; i += blockDim.x) w[i] = __bfloat162float(wb[i]);
+  const int lr = threadIdx.x;
+  const int r = blockIdx.x * NN_ROWS + lr;
+  const bool live = r < nrows;
+  for (int f = 0; f < NN_F; ++f) xs[lr][f] = live ? X[(long long)r * NN_F + f] : 0.f;
+  __syncthreads();
+  for (int j = 0; j < NN_H; ++j) {
+    float a = w[NN_OB1 + j];
+    for (int f = 0; f < NN_F; ++f) a += w[NN_OW1 + j * NN_F + f] * xs[lr][f];
+    h1s[lr][j] = tanhf(a);
+  }
+  float y = w[NN_OB3];
+  for (int j = 0; j < NN_H; ++j) {
+    float a = w[NN_OB2 + j];
+    for (int q = 0; q < NN_H; ++q) a += w[NN_OW2 + j * NN_H + q] * h1s[lr][q];
+    const float hv = tanhf(a);
+    h2s[lr][j] = hv;
+    y += w[NN_OW3 + j] * hv;
+  }
+  if (!TRAIN) {
+    if (live) y_out[r] = y;
+    return;
+  }
+  const float res = live ? y - t[r] : 0.f;
+  const float dy = live ? 2.f * res / (float)nrows : 0.f;
+  dys[lr] = dy;
+  for (int j = 0; j < NN_H; ++j) d2s[lr][j] = dy * w[NN_OW3 + j] * (1.f - h2s[lr][j] * h2s[lr][j]);
+  for (int q = 0; q < NN_H; ++q) {
+    float a = 0.f;
+    for (int j = 0; j < NN_H; ++j) a += d2s[lr][j] * w[NN_OW2 + j * NN_H + q];
+    d1s[lr][q] = a * (1.f - h1s[lr][q] * h1s[lr][q]);
+  }
+  double l = (double)res * (double)res;
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+  if ((lr & 31) == 0) red[lr >> 5] = l;
+  __syncthreads();
+  // block-partial weight gradients: sums over the block's rows in a fixed order
+  float* pb = part + (long long)blockIdx.x * NN_NP;
+  for (int i = threadIdx.x; i < NN_NP; i += blockDim.x) {
+    float s = 0.f;
+    if (i < NN_OB1) {
+      const int j = (i - NN_OW1) / NN_F, f = (i - NN_OW1) % NN_F;
+      for (int q = 0; q < NN_ROWS; ++q) s += d1s[q][j] * xs[q][f];
+    } else if (i < NN_OW2) {
+      const int j = i - NN_OB1;
+      for (int q = 0; q < NN_ROWS; ++q) s += d1s[q][j];
+    } else if (i < NN_OB2) {
+      const int j = (i - NN_OW2) / NN_H, c = (i - NN_OW2) % NN_H;
+      for (int q = 0; q < NN_ROWS; ++q) s += d2s[q][j] * h1s[q][c];
+    } else if (i < NN_OW3) {
+      const int j = i - NN_OB2;
+      for (int q = 0; q < NN_ROWS; ++q) s += d2s[q][j];
+    } else if (i < NN_OB3) {
+      const int j = i - NN_OW3;
+      for (int q = 0; q < NN_ROWS; ++q) s += dys[q] * h2s[q][j];
+    } else {
+      for (int q = 0; q < NN_ROWS; ++q) s += dys[q];
+    }
+    pb[i] = s;
+  }
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int q = 0; q < NN_ROWS / 32; ++q) a += red[q];
+    loss_part[blockIdx.x] = a;
+  }
+}
+
+// Reduce the gradient partials (fixed order) and take one Adam step; refresh the BF16 copy.
+__global__ void k_mlp_adam(int nblk, int nrows, WarmCtl c, float lr, const int* gate) {
+  count_launch();
+  if (gate && *gate <= 0) return;
+  __shared__ int it_s;
+  if (threadIdx.x == 0) it_s = *c.adam_it + 1;
+  __syncthreads();
+  const int it = it_s;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float c1 = 1.f - powf(b1, (float)it), c2 = 1.f - powf(b2, (float)it);
+  for (int i = threadIdx.x; i < NN_NP; i += blockDim.x) {
+    float g = 0.f;
+    for (int b = 0; b < nblk; ++b) g += c.part[(long long)b * NN_NP + i];
+    const float m = b1 * c.m[i] + (1.f - b1) * g;
+    const float v = b2 * c.v[i] + (1.f - b2) * g * g;
+    c.m[i] = m;
+    c.v[i] = v;
+    const float th = c.theta[i] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+    c.theta[i] = th;
+    c.wb[i] = __float2bfloat16_rn(th);
+  }
+  if (threadIdx.x == 0) {
+    *c.adam_it = it;
+    double l = 0.0;
+    for (int b = 0; b < nblk; ++b) l += c.loss_part[b];
+    *c.loss = (float)(l / (double)max(nrows, 1));
+  }
+}
+
+// guess = pred + s y once the network has been trained; otherwise keep the previous solution
+__global__ void k_wguess(int nrows, const int* trained, const float* __restrict__ y, const double* __restrict__ pred,
+                         const double* __restrict__ scale, double* __restrict__ xG) {
+  count_launch();
+  if (*trained <= 0) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nrows) xG[r] = pred[r] + scale[r] * (double)y[r];
+}
+
+// training target t = (u^{n+1} - pred) / s
+__global__ void k_wtarget(int nrows, const int* gate, const double* __restrict__ xG, const double* __restrict__ pred,
+                          const double* __restrict__ scale, float* __restrict__ t) {
+  count_launch();
+  if (*gate <= 0) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nrows) t[r] = (float)((xG[r] - pred[r]) / scale[r]);
+}
+
+// FP32 -> BF16 copy of the parameters
+__global__ void k_to_bf16(int n, const float* __restrict__ a, __nv_bfloat16* __restrict__ b) {
+  count_launch();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __float2bfloat16_rn(a[i]);
+}
+
+// sum of the gradient partials into one vector (fixed order), mean-squared-error loss
+__global__ void k_mlp_reduce(int nblk, int nrows, const float* __restrict__ part, const double* __restrict__ loss_part,
+                             float* __restrict__ grad, double* __restrict__ loss) {
+  count_launch();
+  for (int i = threadIdx.x; i < NN_NP; i += blockDim.x) {
+    float g = 0.f;
+    for (int b = 0; b < nblk; ++b) g += part[(long long)b * NN_NP + i];
+    grad[i] = g;
+  }
+  if (threadIdx.x == 0) {
+    double l = 0.0;
+    for (int b = 0; b < nblk; ++b) l += loss_part[b];
+    *loss = l / (double)max(nrows, 1);
+  }
+}
+
+// end of a step: history shift (u^{n-2} <- u^{n-1} <- u^n) and training bookkeeping
+__global__ void k_wshift(int nrows, double* __restrict__ u1, double* __restrict__ u2, const double* __restrict__ u0) {
+  count_launch();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  u2[r] = u1[r];
+  u1[r] = u0[r];
+}
+__global__ void k_wdone(WarmCtl c) {
+  count_launch();
+  if (threadIdx.x == 0 && *c.train_left > 0) {
+    *c.train_left -= 1;
+    *c.trained += 1;
+  }
 }
 
 }  // namespace sgk

@@ -1,0 +1,92 @@
+"""Learned PCG warm start: gradients of the hand-written network kernels against the FP64 CPU
+reference, and the gain of the trained network over the previous-step guess of the paper.
+
+Gradient bar: the GPU evaluates the network with BF16 weights and FP32 arithmetic; the reference
+uses the same BF16-rounded weights in FP64, so the remaining difference is FP32 rounding:
+max |g_gpu - g_ref| <= 1e-4 max |g_ref| + 1e-7."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import sg_workloads as w
+from oracle import mlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    from paper_2512_23027_gb300 import build as b
+    b.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_23027_gb300 import Solver
+    from paper_2512_23027_gb300.binding import load_library
+    return torch, Solver, load_library()
+
+
+def test_network_gradients_match_reference(env):
+    torch, _, lib = env
+    H = 32
+    g = w.SplitMix64(11)
+    rows = 1000
+    X = np.array(w.normal_samples(rows, 4, seed=5), dtype=np.float32)
+    t = np.array([0.3 * g.uniform() - 0.15 for _ in range(rows)], dtype=np.float32)
+    theta = np.array([(2 * g.uniform() - 1) * 0.4 for _ in range(mlp.n_params(H))], dtype=np.float32)
+    dX, dt_, dth = (torch.from_numpy(a).cuda() for a in (X, t, theta))
+    y = torch.zeros(rows, dtype=torch.float32, device="cuda")
+    gr = torch.zeros(mlp.n_params(H), dtype=torch.float32, device="cuda")
+    loss = ctypes.c_double()
+    rc = lib.sg_mlp_eval(rows, ctypes.c_void_p(dX.data_ptr()), ctypes.c_void_p(dt_.data_ptr()),
+                         ctypes.c_void_p(dth.data_ptr()), ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(gr.data_ptr()),
+                         ctypes.byref(loss))
+    assert rc == 0
+    th_ref = mlp.bf16_round(theta).astype(np.float64)
+    l_ref, g_ref = mlp.loss_and_grad(th_ref, X.astype(np.float64), t.astype(np.float64), H)
+    y_ref, _ = mlp.forward(th_ref, X.astype(np.float64), H)
+    assert np.abs(y.cpu().numpy() - y_ref).max() <= 1e-5 * max(1.0, np.abs(y_ref).max())
+    gg = gr.cpu().numpy()
+    assert np.abs(gg - g_ref).max() <= 1e-4 * np.abs(g_ref).max() + 1e-7
+    assert abs(loss.value - l_ref) <= 1e-5 * l_ref
+
+
+def test_learned_warm_start_reduces_pcg_iterations(env):
+    _, Solver, _ = env
+    from paper_2512_23027_gb300.binding import SG_MIXED, SG_WARM_LEARNED, SG_WARM_PREV
+    prob = w.config("small").replace(steps=60)
+    train, total = 15, 45
+    a = Solver(prob, precision=SG_MIXED, warm=SG_WARM_PREV)
+    b = Solver(prob, precision=SG_MIXED, warm=SG_WARM_LEARNED, warm_train_steps=train)
+    a.step(train)
+    b.step(train)
+    st = b.warm_status()
+    assert st["trained"] == train and st["train_left"] == 0 and st["loss"] >= 0.0
+    a.step(total - train)
+    b.step(total - train)
+    ia, ra = a.iters()
+    ib, rb = b.iters()
+    assert all(r <= prob.tol for r in ra + rb)
+    # same converged solution up to the stopping tolerance
+    ua, ub = a.field(), b.field()
+    assert np.linalg.norm(ua - ub) <= 1e3 * prob.tol * np.linalg.norm(ua)
+    print(f"outer iterations per step after training: previous-step guess {np.mean(ia):.2f}, "
+          f"learned {np.mean(ib):.2f}")
+    assert np.mean(ib) < np.mean(ia)
+    a.close()
+    b.close()
+
+
+def test_weights_round_trip(env):
+    _, Solver, _ = env
+    from paper_2512_23027_gb300.binding import SG_WARM_LEARNED
+    s = Solver(w.config("tiny"), warm=SG_WARM_LEARNED, warm_train_steps=3)
+    s.step(4)
+    th = s.warm_weights()
+    s2 = Solver(w.config("tiny"), warm=SG_WARM_LEARNED, warm_train_steps=1)
+    s2.warm_weights(th)
+    assert np.array_equal(s2.warm_weights(), th)
+    assert s2.warm_status()["trained"] >= 1
+    s.close()
+    s2.close()
