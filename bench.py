@@ -31,8 +31,9 @@ sys.path.insert(0, ROOT)
 METRIC = "SG-DD time-steps/sec & PCG iters vs plain FP64 DD-PCG at rel resid 1e-8"
 
 # DRAM traffic (read + write bytes per launch) of the dominant kernel from one ncu capture, keyed by
-# the sha256 prefix of the kernel source it was taken on; any other source reports null.
-LINE_TRAFFIC = {"c1127b40a78c48ec": 8290816}
+# the sha256 prefix of the kernel sources it was taken on; any other source reports null.
+KERNEL_TRAFFIC = {"39d0c564768ed2ea": 46277376}
+KERNEL_SOURCES = ("sg_kernels.cuh", "sg_mma.cuh", "sg_gfix.cuh")
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -125,6 +126,27 @@ def finish_cpu_baseline(proc, cfg, steps, timeout):
     except Exception as e:  # a missing baseline is reported, never invented
         proc.kill()
         return {"value": None, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+
+def tc_product_shape(prob):
+    L = prob.N // prob.s + 1
+    Kp = -(-L * L // 128) * 128
+    NB = 16 if prob.P <= 16 else 32
+    return L, prob.s * prob.s, Kp, NB
+
+
+def tc_product_bytes(prob):
+    """Algorithmic bytes of one tensor-core preconditioner launch over all subdomains: the BF16
+    dense inverse of the mean operator (nsub x Kp^2 x 2 B, read once), the packed residual image
+    (nsub x Kp rows x [hi; lo] NB modes x 2 B) and z written + r read (2 FP32 vector passes)."""
+    L, nsub, Kp, NB = tc_product_shape(prob)
+    return nsub * Kp * Kp * 2 + nsub * Kp * 2 * NB * 2 + 2 * nsub * L * L * prob.P * 4
+
+
+def tc_product_flops(prob):
+    """Tensor-core flops of one launch: D[Kp x 2 NB] = Ainv[Kp x Kp] [r_hi; r_lo]^T per subdomain."""
+    L, nsub, Kp, NB = tc_product_shape(prob)
+    return 2 * nsub * Kp * Kp * 2 * NB
 
 
 def line_kernel_bytes(prob, tsize):
@@ -298,9 +320,10 @@ def main():
         tmax = float(t.item())
     value = world * K / (tmax / 1e3)
 
-    # ---- dominant kernel: CUDA-event timing of every line-solve launch (host-driven enqueue) ----
+    # ---- dominant kernel: CUDA-event timing of each of its launches (host-driven enqueue) ----
+    tc = s.sizes.get("fp32_precond", 0) == 1
     s.set_eager(True)
-    s.kernel_timing(1)
+    s.kernel_timing(3 if tc else 1)
     kr = min(K, 5)
     for k in range(kr):
         flush.fill_(float(k))
@@ -309,16 +332,27 @@ def main():
     s.set_eager(eager)
     peaks = read_peaks()
     hbm = peaks.get("hbm_gbs")
-    kbytes = line_kernel_bytes(prob, 4)
-    achieved = kbytes / (kms / kn / 1e3) / 1e9 if kn else None
+    kbytes = tc_product_bytes(prob) if tc else line_kernel_bytes(prob, 4)
+    kdur = (kms / kn / 1e3) if kn else None
+    achieved = kbytes / kdur / 1e9 if kdur else None
     import hashlib
-    ksha = hashlib.sha256(open(os.path.join(ROOT, "paper_2512_23027_gb300", "csrc", "sg_kernels.cuh"), "rb").read()
-                          ).hexdigest()[:16]
-    roofline = {"kernel": "k_line_team<float> (FP32 mean-operator line solve fused with the inner CG update)",
-                "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": (achieved / hbm) if (achieved and hbm) else None, "traffic": LINE_TRAFFIC.get(ksha),
+    hsh = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        hsh.update(open(os.path.join(ROOT, "paper_2512_23027_gb300", "csrc", f), "rb").read())
+    ksha = hsh.hexdigest()[:16]
+    kname = ("k_pre_mma<32> (BF16 dense inverse of the mean operator x [r_hi; r_lo] on tcgen05, TMA-fed, "
+             "FP32 accumulation in TMEM)" if tc else
+             "k_line_team<float> (FP32 mean-operator line solve fused with the inner CG update)")
+    roofline = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": (achieved / hbm) if (achieved and hbm) else None, "traffic": KERNEL_TRAFFIC.get(ksha),
                 "launches_timed": kn, "avg_launch_us": 1e3 * kms / kn if kn else None,
-                "bytes_per_launch": kbytes, "peak_source": "measured" if hbm else "fallback"}
+                "bytes_per_launch": kbytes, "peak_source": "measured" if hbm else "fallback",
+                "source_sha": ksha}
+    if tc and kdur:
+        bf16 = peaks.get("bf16_tflops")
+        tfl = tc_product_flops(prob) / kdur / 1e12
+        roofline["tensor"] = {"achieved": tfl, "peak": bf16, "unit": "TFLOP/s",
+                              "frac": tfl / bf16 if bf16 else None, "flops_per_launch": tc_product_flops(prob)}
     if not hbm:
         roofline["peak"] = 6800.0
         roofline["frac"] = achieved / 6800.0 if achieved else None

@@ -100,6 +100,10 @@ typedef struct {
 typedef struct {
   int N, nsub, P, P_in, n_free, n_gamma, n_corner, n_sub_nodes;
   long long device_bytes;  /* device memory owned by the handle                              */
+  int fp32_precond;        /* FP32 subdomain-CG preconditioner: 0 line sweeps of the mean
+                              operator, 1 its dense BF16 inverse on the tensor cores            */
+  int compiled_apply;      /* 1 when the triple-product table of (M, p, p_in) is compiled into
+                              the FP32 operator apply, 0 for the runtime-table kernel          */
 } sg_sizes;
 
 /* Build the solver: KL eigenpairs (analytic, separable exponential kernel), log-normal PCE of
@@ -186,8 +190,10 @@ int sg_set_enqueue_mode(sg_handle h, int eager);
 
 /* Per-kernel CUDA-event timing in the host-driven mode: returns the accumulated device time and
  * launch count of the kernel class selected by the previous call, then selects `which` and
- * resets the totals.  which: 0 none, 1 mean-operator line solve (fused CG update), 2 fused SG
- * operator apply.  Events are recorded on the stream the kernel is launched on. */
+ * resets the totals.  which: 0 none, 1 preconditioner step of the FP32/FP64 subdomain CG (line
+ * sweeps with the fused CG update, or CG update + residual pack + tensor-core product), 2 fused
+ * SG operator apply, 3 the tensor-core product kernel alone.  Events are recorded on the stream
+ * the kernel is launched on. */
 int sg_kernel_timing(sg_handle h, int which, double* total_ms, long long* launches);
 
 /* Kernels launched by this library in this process so far (all handles), counted on the device

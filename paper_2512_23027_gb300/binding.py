@@ -56,7 +56,7 @@ class Stats(C.Structure):
 class Sizes(C.Structure):
     _fields_ = [("N", C.c_int), ("nsub", C.c_int), ("P", C.c_int), ("P_in", C.c_int), ("n_free", C.c_int),
                 ("n_gamma", C.c_int), ("n_corner", C.c_int), ("n_sub_nodes", C.c_int),
-                ("device_bytes", C.c_longlong)]
+                ("device_bytes", C.c_longlong), ("fp32_precond", C.c_int), ("compiled_apply", C.c_int)]
 
 
 _LIB = None
@@ -213,7 +213,8 @@ class Solver:
 
     def kernel_timing(self, which: int):
         """Return (ms, launches) accumulated for the previously selected kernel class and
-        select `which` (0 none, 1 line solve, 2 fused apply) for the following eager steps."""
+        select `which` (0 none, 1 preconditioner step, 2 fused apply, 3 tensor-core product) for the
+        following eager steps."""
         ms = C.c_double()
         n = C.c_longlong()
         self._check(self.lib.sg_kernel_timing(self.h, which, C.byref(ms), C.byref(n)))

@@ -18,6 +18,7 @@
 // The whole step is one CUDA graph: the inner and outer loops are conditional WHILE nodes whose
 // conditions are set on the device, so a step needs no host synchronisation.
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -93,6 +94,14 @@ struct sg_handle_s {
   int nload = 0;
   LineFactor<double> lf[2];  // 0: Dirichlet (interior free), 1: Neumann (interior + remaining free)
   LineFactor<float> lf32[2];
+  // tensor-core mean preconditioner of the FP32 inner solves (mixed precision, small subdomains)
+  bool mma = false;
+  int mma_nb = 32;                 // N of the product: PCE modes padded to 16 or 32
+  int Kp = 0, NC = 0, MT = 0;      // padded local node count, 64-node chunks, 128-row tiles
+  __nv_bfloat16* ainv = nullptr;   // [pattern][subdomain][Kp][Kp] BF16 copy of A0^{-1}
+  unsigned char* bimg = nullptr;   // [problem][chunk][hi, lo][NB x 64 swizzled] residual image
+  int bimg_cap = 0;
+  CUtensorMap tmA;                 // TMA map over ainv (64 x 128 boxes, 128-byte swizzle)
   // coarse space
   double *Phi = nullptr, *Finv = nullptr;
   int nCd = 0, Rc = 0;
@@ -314,6 +323,59 @@ static int tuned(int kind, size_t tsize, const sgh::Problem& pr, int nb) {
   return it == g_tune.end() ? 0 : it->second;
 }
 
+// ---- compile-time triple-product tables (sg_gfix.cuh) ----
+// Calls f(C{}) with the compiled size of index id; returns f's result (or r0 for an unknown id).
+template <class R, class F>
+static R with_gfix(int id, R r0, F&& f) {
+  namespace gf = sgk::gfix;
+  switch (id) {
+    case 0: return f(gf::C0{});
+    case 1: return f(gf::C1{});
+    case 2: return f(gf::C2{});
+    case 3: return f(gf::C3{});
+    case 4: return f(gf::C4{});
+    case 5: return f(gf::C5{});
+    case 6: return f(gf::C6{});
+    default: return r0;
+  }
+}
+
+// the compiled table must list exactly the host's nonzero triples, in the host's order
+template <class C>
+static bool gfix_matches(const sgh::Problem& pr) {
+  if (pr.M != C::M || pr.p != C::p || pr.p_in != C::pin) return false;
+  if (pr.P != C::P || pr.PI != C::PI || (int)pr.gk_v.size() != C::NNZ) return false;
+  for (int k = 0; k <= pr.P; ++k)
+    if (pr.gk_ptr[k] != C::kptr(k)) return false;
+  for (int e = 0; e < C::NNZ; ++e)
+    if (pr.gk_i[e] != C::ti(e) || pr.gk_j[e] != C::tj(e)) return false;
+  return true;
+}
+
+// FP64 applies keep the runtime-table kernel: FP64 arithmetic runs at about 1/60 of the FP32 rate on
+// this part, so the FP64 flux is bound by the DP pipe either way, and the register-resident variant
+// (about 200 registers, one block per SM) measured 3x slower (348 vs 104 us at 128^2, P = 20).
+template <class C>
+constexpr bool gfix_fp64_ok() { return false; }
+
+// compiled table usable for element type T (-1: runtime-table kernel)
+template <typename T>
+static int gfix_for(const sgh::Problem& pr) {
+  if (pr.gfix < 0) return -1;
+  if (sizeof(T) == 8) return -1;
+  return pr.gfix;
+}
+
+// Dynamic shared-memory opt-in plus the maximum shared-memory carveout.  Every kernel of the inner
+// loop asks for the same L1 / shared split, so consecutive launches never wait for the SM to drain
+// and repartition its on-chip memory.
+template <typename... A>
+static int smem_attr(sg_handle h, void (*f)(A...), int lim) {
+  CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  CK(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared));
+  return SG_OK;
+}
+
 // apply tile configuration: lines per block, dynamic shared memory, kappa staging
 template <typename T>
 static void apply_cfg(const sgh::Problem& pr, int nb, int* TL, int* NT, size_t* sm, int* stage) {
@@ -321,6 +383,23 @@ static void apply_cfg(const sgh::Problem& pr, int nb, int* TL, int* NT, size_t* 
   const int PS = P | 1, PIS = PI | 1;
   const size_t nnz = pr.gk_v.size();
   auto edges = [&](int t) { return (size_t)t * (L - 1) + (size_t)(t + 1) * L; };
+  if (gfix_for<T>(pr) >= 0) {
+    // compiled-table variant: input lines and fluxes only; the largest tile that still gives
+    // about two blocks per SM
+    auto bytes = [&](int t) { return sizeof(T) * ((size_t)(t + 2) * L * P + edges(t) * PS) + 16; };
+    int best = 1;
+    for (int t : {8, 4, 2, 1}) {
+      if (t > L) continue;
+      const long long blocks = (long long)nb * ((L + t - 1) / t);
+      if (bytes(t) <= 100 * 1024 && blocks >= 256) { best = t; break; }
+    }
+    if (const int t = tuned(0, sizeof(T), pr, nb)) best = t;
+    *TL = best;
+    *NT = (L + best - 1) / best;
+    *stage = 0;
+    *sm = bytes(best);
+    return;
+  }
   auto base = [&](int t) {
     return sizeof(T) * ((size_t)(t + 2) * L * P + 2 * edges(t) * PS + nnz) + sizeof(unsigned) * nnz +
            sizeof(int) * (P + 1) + 16;
@@ -347,10 +426,25 @@ static int launch_apply(sg_handle h, cudaStream_t st, const Op<T>& op, int nb, i
   int TL, NT, stage;
   size_t sm;
   apply_cfg<T>(h->pr, nb, &TL, &NT, &sm, &stage);
-  auto kern = sgk::k_apply<T, TO, FUSEDP, DOT>;
-  kern<<<(unsigned)((long long)nb * NT), 256, sm, st>>>(op, nb, R, TL, NT, (int)h->pr.gk_v.size(), stage, xm, xk, y, add,
-                                                        (T)cm, (T)ck, mask, p0, p1, z,
-                                                        h->ctl.parity, h->ctl.beta, h->ctl.active, h->ctl.part_pq);
+  const int fx = gfix_for<T>(h->pr);
+  const unsigned grid = (unsigned)((long long)nb * NT);
+  const int nnz = (int)h->pr.gk_v.size();
+  const bool done = with_gfix(fx, false, [&](auto c) -> bool {
+    using C = decltype(c);
+    if constexpr (sizeof(T) == 4 || gfix_fp64_ok<C>()) {
+      sgk::k_apply<T, TO, FUSEDP, DOT, C><<<grid, 256, sm, st>>>(op, nb, R, TL, NT, nnz, stage, xm, xk, y, add, (T)cm,
+                                                                 (T)ck, mask, p0, p1, z, h->ctl.parity, h->ctl.beta,
+                                                                 h->ctl.active, h->ctl.part_pq);
+      return true;
+    } else {
+      return false;
+    }
+  });
+  if (!done) {
+    auto kern = sgk::k_apply<T, TO, FUSEDP, DOT>;
+    kern<<<grid, 256, sm, st>>>(op, nb, R, TL, NT, nnz, stage, xm, xk, y, add, (T)cm, (T)ck, mask, p0, p1, z,
+                                h->ctl.parity, h->ctl.beta, h->ctl.active, h->ctl.part_pq);
+  }
   CKL();
   return SG_OK;
 }
@@ -436,9 +530,18 @@ static int ensure_ctl(sg_handle h, int nb, int nt, int ng) {
   return SG_OK;
 }
 
+// residual image of the tensor-core preconditioner for nb right-hand sides
+static int ensure_bimg(sg_handle h, int nb) {
+  if (!h->mma || h->bimg_cap >= nb) return SG_OK;
+  RET(dalloc(h, &h->bimg, (long long)nb * h->NC * 2 * h->mma_nb * 128));
+  h->bimg_cap = nb;
+  return SG_OK;
+}
+
 template <typename T>
 static int ensure_ws(sg_handle h, int nb) {
   auto& w = wsT<T>(h);
+  if (sizeof(T) == 4) RET(ensure_bimg(h, nb));
   if (w.cap_nb < nb) {
     const long long len = (long long)h->pr.nl * h->pr.P * nb;
     RET(dalloc(h, &w.x, len)); RET(dalloc(h, &w.r, len)); RET(dalloc(h, &w.z, len));
@@ -448,9 +551,9 @@ static int ensure_ws(sg_handle h, int nb) {
   int TL, NT, stage;
   size_t sm;
   apply_cfg<T>(h->pr, nb, &TL, &NT, &sm, &stage);
-  // capacities cover every tile shape the tuner may pick: NT <= L, NG <= P
+  // capacities cover every tile shape the tuner may pick: NT <= L, NG <= max(P, row tiles)
   (void)NT;
-  return ensure_ctl(h, nb, h->pr.L, h->pr.P);
+  return ensure_ctl(h, nb, h->pr.L, std::max(h->pr.P, h->MT));
 }
 
 // CUDA-event timing of one kernel launch on its stream (host-driven enqueue only)
@@ -515,10 +618,58 @@ static int enq_inner(sg_handle h, Ctx& cx, int pat, int nb, int R, int s0, const
       sgk::k_line<T><<<lg, lc.block, lc.smem, s>>>(L, pr.nl, pr.P, R, NG, NT, pstride, Sinv, Bd, Bu, nb, w.x, w.r,
                                                    w.z, w.p0, w.p1, w.q, h->ctl, init, tol2, bb_min, imax, hh, use);
   };
+  // tensor-core preconditioner (FP32 solves of small subdomains): CG update + residual image, then
+  // the dense product with the inner-CG control
+  const bool use_mma = sizeof(T) == 4 && h->mma;
+  const int row0 = (pat * pr.nsub + s0) * h->Kp;
+  auto pre_mma = [&](Ctx& cc, int init, cudaGraphConditionalHandle hh, int use) -> int {
+    cudaStream_t s = cc.st;
+    float* wx = (float*)w.x;
+    float* wr = (float*)w.r;
+    float* wz = (float*)w.z;
+    const float* p0 = (const float*)w.p0;
+    const float* p1 = (const float*)w.p1;
+    const float* wq = (const float*)w.q;
+    const unsigned gp = (unsigned)nb * h->NC, gm = (unsigned)nb * h->MT;
+    if (h->mma_nb == 32)
+      sgk::k_cg_pack<32><<<gp, 256, 0, s>>>(L, pr.nl, pr.P, h->NC, NT, wx, wr, p0, p1, wq, h->ctl, init, h->bimg);
+    else
+      sgk::k_cg_pack<16><<<gp, 256, 0, s>>>(L, pr.nl, pr.P, h->NC, NT, wx, wr, p0, p1, wq, h->ctl, init, h->bimg);
+    RET(kprof_begin(h, cc, 3));
+    if (h->mma_nb == 32)
+      sgk::k_pre_mma<32><<<gm, 256, sgk::PreShape<32>::SMEM, s>>>(
+          h->tmA, L, pr.nl, pr.P, R, h->MT, h->NC, NT, h->Kp, row0, nb, h->bimg, wr, wz, h->ctl, init, tol2, bb_min,
+          imax, hh, use, h->ctl.breakdown);
+    else
+      sgk::k_pre_mma<16><<<gm, 256, sgk::PreShape<16>::SMEM, s>>>(
+          h->tmA, L, pr.nl, pr.P, R, h->MT, h->NC, NT, h->Kp, row0, nb, h->bimg, wr, wz, h->ctl, init, tol2, bb_min,
+          imax, hh, use, h->ctl.breakdown);
+    RET(kprof_end(h, cc, 3));
+    return SG_OK;
+  };
+  if (use_mma && h->bimg_cap < nb) {
+    h->err = "residual image smaller than the batch of inner solves";
+    return SG_EINVAL;
+  }
   CK(cudaMemcpyAsync(w.r, rhs, sizeof(T) * n, cudaMemcpyDeviceToDevice, cx.st));
   CK(cudaMemsetAsync(w.x, 0, sizeof(T) * n, cx.st));
   cudaGraphConditionalHandle hnd;
   RET(make_handle(h, cx, &hnd));
+  if (use_mma) {
+    RET(pre_mma(cx, 1, hnd, cx.capture ? 1 : 0));
+    CKL();
+    return cond_node(h, cx, hnd, true, h->ctl.cond, [&](Ctx& c2) -> int {
+      RET(kprof_begin(h, c2, 2));
+      RET((launch_apply<T, T, true, true>(h, c2.st, op, nb, R, nullptr, nullptr, w.q, nullptr, h->am, h->bk, mask,
+                                          w.p0, w.p1, w.z)));
+      RET(kprof_end(h, c2, 2));
+      RET(kprof_begin(h, c2, 1));
+      RET(pre_mma(c2, 0, hnd, c2.capture ? 1 : 0));
+      CKL();
+      RET(kprof_end(h, c2, 1));
+      return SG_OK;
+    });
+  }
   line(cx.st, 1, hnd, cx.capture ? 1 : 0);
   CKL();
   return cond_node(h, cx, hnd, true, h->ctl.cond, [&](Ctx& c2) -> int {
@@ -914,6 +1065,55 @@ static int build_line_factors(sg_handle h) {
   return SG_OK;
 }
 
+// Tensor-core mean preconditioner (mixed precision): A0^{-1} of both patterns in BF16 and its TMA
+// map.  Used when the subdomains have at most MMA_LMAX nodes per side and P <= 32; larger subdomains
+// keep the line-sweep preconditioner (a dense inverse would grow as L^4).
+constexpr int MMA_LMAX = 40;
+static int build_mma_precond(sg_handle h) {
+  const auto& pr = h->pr;
+  if (h->precision != SG_MIXED || pr.L > MMA_LMAX || pr.P > 32 || std::getenv("SG_NO_MMA")) return SG_OK;
+  const int L = pr.L, LL = L * L;
+  h->Kp = (LL + sgk::MMA_M - 1) / sgk::MMA_M * sgk::MMA_M;
+  h->NC = h->Kp / sgk::MMA_KC;
+  h->MT = h->Kp / sgk::MMA_M;
+  h->mma_nb = pr.P <= 16 ? 16 : 32;
+  const long long per = (long long)pr.nsub * h->Kp * h->Kp;
+  RET(dalloc(h, &h->ainv, 2 * per));
+  const size_t sm = sizeof(double) * ((size_t)sgk::INV_CB * LL + sgk::INV_CB * 64);
+  RET(smem_attr(h, sgk::k_inv_cols, (int)sm));
+  const int ngrp = (LL + sgk::INV_CB - 1) / sgk::INV_CB;
+  for (int pat = 0; pat < 2; ++pat) {
+    const int mask = pat == 0 ? sgk::MASK_I : sgk::MASK_N;
+    sgk::k_inv_cols<<<(unsigned)(pr.nsub * ngrp), dim3(64, sgk::INV_CB), sm, h->st>>>(
+        L, pr.nl, h->Kp, mask, h->cls, h->lf[pat].Sinv, h->lf[pat].Bd, h->lf[pat].Bu, h->ainv + pat * per);
+    CKL();
+  }
+  PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  cudaDriverEntryPointQueryResult qr;
+  CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&enc, 12000, cudaEnableDefault, &qr));
+  if (!enc || qr != cudaDriverEntryPointSuccess) {
+    h->err = "cuTensorMapEncodeTiled is not available from the driver";
+    return SG_ECUDA;
+  }
+  // rows [pattern][subdomain][Kp] x Kp BF16 columns; 64 x 128 boxes with the 128-byte swizzle
+  const cuuint64_t dims[2] = {(cuuint64_t)h->Kp, (cuuint64_t)(2LL * pr.nsub * h->Kp)};
+  const cuuint64_t strides[1] = {(cuuint64_t)h->Kp * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)sgk::MMA_KC, (cuuint32_t)sgk::MMA_M};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult cr = enc(&h->tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, h->ainv, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) {
+    h->err = "tensor map encoding of the mean-operator inverse failed";
+    return SG_ECUDA;
+  }
+  RET(smem_attr(h, sgk::k_pre_mma<32>, sgk::PreShape<32>::SMEM));
+  RET(smem_attr(h, sgk::k_pre_mma<16>, sgk::PreShape<16>::SMEM));
+  h->mma = true;
+  RET(ensure_bimg(h, pr.nsub));
+  return ensure_ctl(h, pr.nsub, pr.L, std::max(pr.P, h->MT));
+}
+
 // Host inverse of a small SPD matrix by Cholesky (set-up only).
 static bool spd_inverse(std::vector<double>& A, int n) {
   std::vector<double> Lm((size_t)n * n, 0.0);
@@ -1135,6 +1335,11 @@ static int run_steps(sg_handle h, int nsteps, const double* f_host, double* u_ho
   *rc_out = SG_OK;
   if (h->hint[0] & 1) *rc_out = SG_ENOTCONV;
   if ((h->hint[0] & 2) || h->hint[1]) { h->err = "numerical breakdown in PCG"; *rc_out = SG_ENUMERIC; }
+  if (h->hint[1] >= 16) {
+    h->err = "a bounded wait of the tensor-core preconditioner expired (pipeline stage " +
+             std::to_string(h->hint[1] - 16) + ")";
+    *rc_out = SG_ETIMEOUT;
+  }
   return SG_OK;
 }
 
@@ -1311,17 +1516,43 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   // shared-memory opt-in of the apply variants
   {
     const int lim = 200 * 1024;
-    CK(cudaFuncSetAttribute(sgk::k_apply<double, double, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    CK(cudaFuncSetAttribute(sgk::k_apply<double, double, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    CK(cudaFuncSetAttribute(sgk::k_apply<float, float, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    CK(cudaFuncSetAttribute(sgk::k_apply<float, float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    CK(cudaFuncSetAttribute(sgk::k_apply<float, double, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    CK(cudaFuncSetAttribute(sgk::k_line<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    CK(cudaFuncSetAttribute(sgk::k_line<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    RET(smem_attr(h, sgk::k_apply<double, double, false, false>, lim));
+    RET(smem_attr(h, sgk::k_apply<double, double, true, true>, lim));
+    RET(smem_attr(h, sgk::k_apply<float, float, false, false>, lim));
+    RET(smem_attr(h, sgk::k_apply<float, float, true, true>, lim));
+    RET(smem_attr(h, sgk::k_apply<float, double, false, false>, lim));
+    RET(smem_attr(h, sgk::k_line<double>, lim));
+    RET(smem_attr(h, sgk::k_line<float>, lim));
 #define SG_ATTR(LSV) \
-  CK(cudaFuncSetAttribute(sgk::k_line_team<float, LSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX));
+  RET(smem_attr(h, sgk::k_line_team<float, LSV>, (int)SMEM_MAX));
     SG_ATTR(4) SG_ATTR(8) SG_ATTR(12) SG_ATTR(16) SG_ATTR(20) SG_ATTR(24) SG_ATTR(28) SG_ATTR(32) SG_ATTR(36) SG_ATTR(40)
 #undef SG_ATTR
+  }
+  // compiled triple-product table for this PCE size (values into constant memory; the same
+  // values for every handle of that size, so concurrent handles may share the slot)
+  {
+    pr.gfix = -1;
+    for (int id = 0; id < sgk::gfix::NCFG && pr.gfix < 0; ++id)
+      if (with_gfix(id, false, [&](auto c) { return gfix_matches<decltype(c)>(pr); })) pr.gfix = id;
+    if (std::getenv("SG_NO_GFIX")) pr.gfix = -1;
+    if (pr.gfix >= 0) {
+      const int rc = with_gfix(pr.gfix, (int)SG_EINVAL, [&](auto c) -> int {
+        using C = decltype(c);
+        std::vector<float> f(pr.gk_v.begin(), pr.gk_v.end());
+        CK(cudaMemcpyToSymbol(sgk::c_gvf, f.data(), sizeof(float) * C::NNZ, sizeof(float) * C::OFF));
+        CK(cudaMemcpyToSymbol(sgk::c_gvd, pr.gk_v.data(), sizeof(double) * C::NNZ, sizeof(double) * C::OFF));
+        const int lim = 200 * 1024;
+        RET(smem_attr(h, sgk::k_apply<float, float, false, false, C>, lim));
+        RET(smem_attr(h, sgk::k_apply<float, float, true, true, C>, lim));
+        RET(smem_attr(h, sgk::k_apply<float, double, false, false, C>, lim));
+        if constexpr (gfix_fp64_ok<C>()) {
+          RET(smem_attr(h, sgk::k_apply<double, double, false, false, C>, lim));
+          RET(smem_attr(h, sgk::k_apply<double, double, true, true, C>, lim));
+        }
+        return SG_OK;
+      });
+      RET(rc);
+    }
   }
   // problem data (FP64 and FP32 copies of the operator coefficients)
   RET(upload(h, &h->cls, pr.cls)); RET(upload(h, &h->cells, pr.cells));
@@ -1379,6 +1610,7 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
     }
   }
   RET(build_line_factors(h));
+  RET(build_mma_precond(h));
   if (prm->autotune) RET(autotune(h));
   RET(build_coarse(h));
   if (h->warm == SG_WARM_LEARNED) RET(warm_setup(h));
@@ -1534,7 +1766,8 @@ static int batch_impl(sg_handle* hs, int n, int nsteps, sg_stats* out_n) {
     int flags = 0, brk = 0;
     CK(cudaMemcpy(&flags, hi->rec_flags, sizeof(int), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(&brk, hi->ctl.breakdown, sizeof(int), cudaMemcpyDeviceToHost));
-    if ((flags & 2) || brk) worst = SG_ENUMERIC;
+    if (brk >= 16) worst = SG_ETIMEOUT;
+    else if ((flags & 2) || brk) worst = SG_ENUMERIC;
     else if ((flags & 1) && worst == SG_OK) worst = SG_ENOTCONV;
     if (out_n) {
       sg_stats& st = out_n[i];
@@ -1670,6 +1903,8 @@ int sg_get_sizes(sg_handle h, sg_sizes* out) {
   const auto& pr = h->pr;
   out->N = pr.N; out->nsub = pr.nsub; out->P = pr.P; out->P_in = pr.PI; out->n_free = pr.n_free;
   out->n_gamma = pr.nG; out->n_corner = pr.nC; out->n_sub_nodes = pr.nl; out->device_bytes = h->bytes;
+  out->fp32_precond = h->mma ? 1 : 0;
+  out->compiled_apply = gfix_for<float>(pr) >= 0 ? 1 : 0;
   return SG_OK;
 }
 
@@ -1759,7 +1994,7 @@ int sg_set_enqueue_mode(sg_handle h, int eager) {
 }
 
 int sg_kernel_timing(sg_handle h, int which, double* total_ms, long long* launches) {
-  if (!h || which < 0 || which > 2) return SG_EINVAL;
+  if (!h || which < 0 || which > 3) return SG_EINVAL;
   if (total_ms) *total_ms = h->kprof_ms;
   if (launches) *launches = h->kprof_n;
   h->kprof = which;

@@ -20,6 +20,7 @@ struct Problem {
   // sizes
   int N = 0, s = 0, H = 0, L = 0, nl = 0, nsub = 0;
   int M = 0, p = 0, p_in = 0, P = 0, PI = 0;
+  int gfix = -1;  // compiled triple-product table matching (M, p, p_in), or -1 (set by the CUDA set-up)
   double sigma = 0, bx = 0, by = 0, g0 = 0;
   double dt = 0, alpha0 = 0, alpha1 = 0;
   double h = 0;

@@ -10,6 +10,8 @@
 #include <cstdint>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include "sg_gfix.cuh"
+#include "sg_mma.cuh"
 
 namespace sgk {
 
@@ -105,7 +107,11 @@ struct CgCtl {
 // FUSEDP: the input is the CG direction p_new = z + beta p_old, formed on the fly (halo
 // included) and written back for the owned lines; DOT: per-block partial of p_new . y.
 // ------------------------------------------------------------------------------------------
-template <typename T, typename TO, bool FUSEDP, bool DOT>
+// C = GDyn: runtime triple-product table staged in shared memory (any PCE size).  C = gfix::Cfg<...>:
+// the table is a compile-time constant (sg_gfix.cuh); each work item (edge, output-mode group) keeps
+// kappa_e and d_e in registers and the values come from constant memory, so the flux phase issues two
+// instructions per triple product and needs neither the difference nor the staging buffers.
+template <typename T, typename TO, bool FUSEDP, bool DOT, class C = GDyn>
 __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, int NT, int nnz, int stage_kap,
                                                const T* __restrict__ xm, const T* __restrict__ xk, TO* y,
                                                const TO* add, T cm, T ck, int out_mask,
@@ -124,8 +130,8 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
   const int nE = nlin * (L - 1), nNr = nlin + 1;
   const int nEd = nE + nNr * L;                     // edges of the block: horizontal then vertical
   T* xs = reinterpret_cast<T*>(smem_raw);           // [(TL+2)][L][P]
-  T* ds = xs + (size_t)(TL + 2) * L * P;            // [edges][PS] differences
-  T* zs = ds + (size_t)(TL * (L - 1) + (TL + 1) * L) * PS;   // [edges][PS] fluxes
+  T* ds = xs + (size_t)(TL + 2) * L * P;            // [edges][PS] differences (runtime table only)
+  T* zs = C::fixed ? ds : ds + (size_t)(TL * (L - 1) + (TL + 1) * L) * PS;   // [edges][PS] fluxes
   T* gv_s = zs + (size_t)(TL * (L - 1) + (TL + 1) * L) * PS; // [nnz]
   T* ks = gv_s + nnz;                               // [edges][PIS] edge weights (when staged)
   unsigned* gpk_s = reinterpret_cast<unsigned*>(stage_kap ? ks + (size_t)(TL * (L - 1) + (TL + 1) * L) * PIS : ks);
@@ -144,6 +150,7 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
   }
   SG_MARK(0);
   // phase 0: triple products (values, packed (i, j), per-k ranges) and the block's edge weights
+  if constexpr (!C::fixed) {
   for (int e = threadIdx.x; e < nnz; e += nt) {
     gv_s[e] = op.gk_v[e];
     gpk_s[e] = (unsigned)op.gk_i[e] | ((unsigned)op.gk_j[e] << 16);
@@ -161,6 +168,7 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
       const int jb = lj0 - 1 + t;
       ks[(size_t)(nE + ed) * PIS + i] = (jb >= 0 && jb + 1 < L) ? op.kapN[(so0 + (long long)jb * L + c) * PI + i] : T(0);
     }
+  }
   }
   // phase 1: input lines lj0-1 .. lj0+nlin (zeros outside the grid)
   const int nin = (nlin + 2) * L * P;
@@ -182,6 +190,32 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
   }
   __syncthreads();
   SG_MARK(1);
+  if constexpr (C::fixed) {
+    // phase 2 (compile-time table): one work item per (edge, output-mode group)
+    if (ck != T(0)) {
+      for (int it = threadIdx.x; it < nEd * C::KG; it += nt) {
+        const int ed = it / C::KG, g = it - ed * C::KG;
+        const T* xa;
+        const T* xb;
+        const T* kp;
+        bool live = true;
+        if (ed < nE) {
+          const int t = fdiv(ed, op.fLm1), c = ed - t * (L - 1);
+          xa = xs + ((size_t)(t + 1) * L + c) * P;
+          xb = xa + P;
+          kp = op.kapE + (so0 + (long long)(lj0 + t) * L + c) * PI;
+        } else {
+          const int v = ed - nE, t = fdiv(v, op.fL), c = v - t * L;
+          const int jb = lj0 - 1 + t;
+          live = jb >= 0 && jb + 1 < L;
+          xa = xs + ((size_t)t * L + c) * P;
+          xb = xa + (size_t)L * P;
+          kp = op.kapN + (so0 + (long long)max(jb, 0) * L + c) * PI;
+        }
+        gflux<C, T>(g, kp, xa, xb, zs + (size_t)ed * PS, live);
+      }
+    }
+  } else {
   // phase 2a: differences d_e = x_a - x_b of every edge (a = left / bottom end)
   for (int e = threadIdx.x; e < nEd * P; e += nt) {
     const int ed = fdiv(e, op.fP), j = e - ed * P;
@@ -269,6 +303,7 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
         if (has1) z1[kk] = live1 ? a1 : T(0);
       }
     }
+  }
   }
   __syncthreads();
   SG_MARK(3);
@@ -1551,6 +1586,206 @@ __global__ void k_wdone(WarmCtl c) {
     *c.train_left -= 1;
     *c.trained += 1;
   }
+}
+
+// ------------------------------------------------------------------------------------------
+// Dense inverse of the mean operator A0 of one pattern (set-up, FP64).  Column c of A0^{-1} is the
+// block-tridiagonal solve with right-hand side e_c, by the forward / backward line sweeps of the
+// line preconditioner with the stored S_j^{-1}.  A0^{-1} is symmetric, so column c is stored as row c
+// of the BF16 copy Ainv[sub][c][node] (row length Kp); rows and columns of nodes outside the
+// pattern's free set (class bit not in pat_mask) are zero.  Block (64, INV_CB): x = position along
+// a grid line, y = column; grid nsub x ceil(L^2 / INV_CB).
+// ------------------------------------------------------------------------------------------
+constexpr int INV_CB = 4;
+__global__ void __launch_bounds__(256) k_inv_cols(int L, int nl, int Kp, int pat_mask, const uint8_t* __restrict__ cls,
+                                                  const double* __restrict__ Sinv, const double* __restrict__ Bd,
+                                                  const double* __restrict__ Bu, __nv_bfloat16* __restrict__ out) {
+  count_launch();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int LL = L * L;
+  double* ys = reinterpret_cast<double*>(smem_raw);  // [INV_CB][LL]
+  double* ws = ys + (size_t)INV_CB * LL;              // [INV_CB][64]
+  const int ngrp = (LL + INV_CB - 1) / INV_CB;
+  const int s = blockIdx.x / ngrp;
+  const int col = (blockIdx.x % ngrp) * INV_CB + threadIdx.y;
+  const int a = threadIdx.x;
+  const bool colok = col < LL && ((pat_mask >> cls[(size_t)s * nl + col]) & 1);
+  const double* S = Sinv + (size_t)s * LL * L;
+  const double* bd = Bd + (size_t)s * LL;
+  const double* bu = Bu + (size_t)s * LL;
+  double* y = ys + (size_t)threadIdx.y * LL;
+  double* w = ws + threadIdx.y * 64;
+  const bool ok = a < L;
+  for (int j = 0; j < L; ++j) {
+    if (ok) {
+      double rhs = (colok && col == j * L + a) ? 1.0 : 0.0;
+      if (j > 0) {
+        rhs -= bd[(j - 1) * L + a] * y[(j - 1) * L + a];
+        if (a > 0) rhs -= bu[(j - 1) * L + a - 1] * y[(j - 1) * L + a - 1];
+      }
+      w[a] = rhs;
+    }
+    __syncthreads();
+    if (ok) {
+      const double* row = S + ((size_t)j * L + a) * L;
+      double acc = 0.0;
+      for (int c2 = 0; c2 < L; ++c2) acc += row[c2] * w[c2];
+      y[j * L + a] = acc;
+    }
+    __syncthreads();
+  }
+  for (int j = L - 2; j >= 0; --j) {
+    if (ok) {
+      double t = bd[j * L + a] * y[(j + 1) * L + a];
+      if (a + 1 < L) t += bu[j * L + a] * y[(j + 1) * L + a + 1];
+      w[a] = t;
+    }
+    __syncthreads();
+    if (ok) {
+      const double* row = S + ((size_t)j * L + a) * L;
+      double acc = 0.0;
+      for (int c2 = 0; c2 < L; ++c2) acc += row[c2] * w[c2];
+      y[j * L + a] -= acc;
+    }
+    __syncthreads();
+  }
+  if (col < LL) {
+    __nv_bfloat16* o = out + ((size_t)s * Kp + col) * Kp;
+    for (int nd = a; nd < LL; nd += 64) {
+      const bool nok = (pat_mask >> cls[(size_t)s * nl + nd]) & 1;
+      o[nd] = __float2bfloat16_rn(colok && nok ? (float)y[nd] : 0.f);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Inner CG update (x += alpha p, r -= alpha q, alpha = r.z / p.q, on all modes of 64 nodes) and
+// packing of the updated residual into the image read by k_pre_mma: per right-hand side b and
+// 64-node chunk c, the BF16 terms r_hi = bf16(r) and r_lo = bf16(r - r_hi), each a K-major
+// 128-byte-swizzled block of NB rows (PCE modes, zero beyond P) x 64 nodes.  Grid: nb x NC blocks.
+// init: first call of a solve (x = 0, pack r only).
+// ------------------------------------------------------------------------------------------
+template <int NB>
+__global__ void __launch_bounds__(256) k_cg_pack(int L, int nl, int P, int NC, int NT, float* __restrict__ x,
+                                                 float* __restrict__ r, const float* pbuf0, const float* pbuf1,
+                                                 const float* __restrict__ q, CgCtl ctl, int init,
+                                                 unsigned char* __restrict__ bimg) {
+  count_launch();
+  __shared__ float rs[64][NB + 1];
+  const int b = blockIdx.x / NC, c = blockIdx.x % NC;
+  if (!init && !ctl.active[b]) return;
+  const int LL = L * L;
+  float alpha = 0.f;
+  const float* pc = nullptr;
+  if (!init) {
+    double pq = 0.0;
+    for (int t = 0; t < NT; ++t) pq += ctl.part_pq[(long long)b * NT + t];
+    const double al = (pq > 0.0 && isfinite(pq)) ? ctl.rz[b] / pq : 0.0;
+    alpha = isfinite(al) ? (float)al : 0.f;
+    pc = (*ctl.parity) ? pbuf0 : pbuf1;
+  }
+  const long long base = (long long)b * nl * P;
+  const int n0 = c * 64;
+  for (int e = threadIdx.x; e < 64 * P; e += blockDim.x) {
+    const int i = e / P, k = e - i * P;
+    float rv = 0.f;
+    if (n0 + i < LL) {
+      const long long o = base + (long long)n0 * P + e;
+      rv = r[o];
+      if (!init) {
+        x[o] += alpha * pc[o];
+        rv -= alpha * q[o];
+        r[o] = rv;
+      }
+    }
+    rs[i][k] = rv;
+  }
+  if (NB > P)
+    for (int e = threadIdx.x; e < 64 * (NB - P); e += blockDim.x) rs[e / (NB - P)][P + e % (NB - P)] = 0.f;
+  __syncthreads();
+  unsigned char* dst = bimg + ((size_t)b * NC + c) * 2 * (NB * 128);
+  for (int t = threadIdx.x; t < 2 * NB * 8; t += blockDim.x) {
+    const int hl = t / (NB * 8), rem = t - hl * NB * 8, n = rem >> 3, j = rem & 7;
+    unsigned h[8];
+#pragma unroll
+    for (int i2 = 0; i2 < 8; ++i2) {
+      const float f = rs[j * 8 + i2][n];
+      const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+      const __nv_bfloat16 v = hl ? __float2bfloat16_rn(f - __bfloat162float(hi)) : hi;
+      h[i2] = (unsigned)__bfloat16_as_ushort(v);
+    }
+    uint4 pk;
+    pk.x = h[0] | (h[1] << 16);
+    pk.y = h[2] | (h[3] << 16);
+    pk.z = h[4] | (h[5] << 16);
+    pk.w = h[6] | (h[7] << 16);
+    *reinterpret_cast<uint4*>(dst + hl * NB * 128 + sw128_offset(n, j * 8)) = pk;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// z = A0^{-1} r on the tensor cores (mma_tile) for every mode of every right-hand side; the image
+// holds r, packed by k_cg_pack after the CG update.  The accumulator tile (128 nodes x NB modes) is
+// staged through shared memory so that z is stored, and r read back for the partials r.z, r.r, with
+// coalesced accesses (the tile's 128 nodes x P modes are contiguous in the [node][mode] layout).
+// Then the loop control (line_control, NG = MT row tiles).  Grid: nb x MT CTAs of 256 threads;
+// rows of A for (pattern, subdomain) start at row0 + sub * Kp.  err: set to 16 + stage when a
+// bounded wait of the pipeline ran out.
+// ------------------------------------------------------------------------------------------
+constexpr int PRE_NST = 4, PRE_CPS = 2;  // pipeline of the preconditioner product: 4 stages of 2 chunks
+template <int NB>
+using PreShape = MmaShape<NB, PRE_NST, PRE_CPS>;
+
+template <int NB>
+__global__ void __launch_bounds__(256, 1) k_pre_mma(const __grid_constant__ CUtensorMap tmA, int L, int nl, int P,
+                                                    int R, int MT, int NC, int NT, int Kp, int row0, int nb,
+                                                    const unsigned char* __restrict__ bimg,
+                                                    const float* __restrict__ r, float* __restrict__ z, CgCtl ctl,
+                                                    int init, double tol2, double bb_min, int max_it,
+                                                    cudaGraphConditionalHandle cond_handle, int use_handle,
+                                                    int* err) {
+  count_launch();
+  extern __shared__ unsigned char smem_mma_raw[];
+  __shared__ __align__(8) unsigned long long bars[2 * PRE_NST + 1];
+  __shared__ unsigned tmem_slot;
+  __shared__ int s_flags[2];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_mma_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int b = blockIdx.x / MT, tile = blockIdx.x % MT;
+  const bool act = init ? true : (ctl.active[b] != 0);
+  double s_rz = 0.0, s_rr = 0.0;
+  if (act) {
+    const int sub = b / R;
+    const int y0 = row0 + sub * Kp + tile * MMA_M;
+    const unsigned char* bb = bimg + (size_t)b * NC * PreShape<NB>::BCHUNK;
+    const unsigned tmem = mma_tile<NB, PRE_NST, PRE_CPS>(&tmA, y0, bb, NC, smem, bars, &tmem_slot, s_flags, err);
+    // every stage has been consumed: stage 0 is free for the accumulator tile [128][NB + 1]
+    float* zt = reinterpret_cast<float*>(smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp >= 4) {
+      float v[NB];
+      mma_row<NB>(tmem, warp - 4, v);
+      float* zr = zt + ((warp - 4) * 32 + lane) * (NB + 1);
+#pragma unroll
+      for (int k = 0; k < NB; ++k) zr[k] = v[k];
+    }
+    mma_tile_end<NB, PRE_NST>(bars, tmem, s_flags);  // contains __syncthreads
+    const int m0 = tile * MMA_M;
+    const int rows = min(MMA_M, L * L - m0);
+    if (rows > 0) {
+      const long long o = (long long)b * nl * P + (long long)m0 * P;
+      const int cnt = rows * P;
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int rr_ = e / P, k = e - rr_ * P;
+        const float zv = zt[rr_ * (NB + 1) + k];
+        z[o + e] = zv;
+        const double rv = (double)r[o + e];
+        s_rz += rv * (double)zv;
+        s_rr += rv * rv;
+      }
+    }
+  }
+  line_control(s_rz, s_rr, b, tile, MT, NT, nb, ctl, init, tol2, bb_min, max_it, cond_handle, use_handle);
 }
 
 }  // namespace sgk

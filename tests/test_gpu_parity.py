@@ -129,3 +129,36 @@ def test_graph_equals_eager(lib):
     finally:
         del os.environ["SG_EAGER"]
     assert np.array_equal(ua, ub)
+
+
+def test_tensor_core_preconditioner_matches_line_sweeps(lib):
+    """Mixed precision on the 128^2 / P = 20 workload: the FP32 subdomain CG preconditioned by the
+    dense BF16 inverse of the mean operator on the tensor cores (with the compiled triple-product
+    apply) and by the exact line sweeps (runtime-table apply) converge to the same fields.  Both runs
+    stop at the outer tolerance, so they agree to a small multiple of it; outer iteration counts
+    agree within one."""
+    import os
+    from paper_2512_23027_gb300.binding import SG_MIXED
+    prob = w.config("ricker128")
+    steps = 6
+    a = lib(prob, precision=SG_MIXED)
+    assert a.sizes["fp32_precond"] == 1 and a.sizes["compiled_apply"] == 1
+    a.step(steps)
+    ua, (ia, ra) = a.field(), a.iters()
+    a.close()
+    os.environ["SG_NO_MMA"] = "1"
+    os.environ["SG_NO_GFIX"] = "1"
+    try:
+        b = lib(prob, precision=SG_MIXED)
+    finally:
+        del os.environ["SG_NO_MMA"]
+        del os.environ["SG_NO_GFIX"]
+    assert b.sizes["fp32_precond"] == 0 and b.sizes["compiled_apply"] == 0
+    b.step(steps)
+    ub, (ib, rb) = b.field(), b.iters()
+    b.close()
+    err = rel(ua, ub)
+    print(f"tensor-core vs line-sweep preconditioner: rel diff {err:.3e}, iters {ia} vs {ib}")
+    assert err <= 1e2 * prob.tol, err
+    assert all(r <= prob.tol for r in ra) and all(r <= prob.tol for r in rb)
+    assert all(abs(x - y) <= 1 for x, y in zip(ia, ib))
