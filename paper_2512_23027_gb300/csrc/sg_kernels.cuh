@@ -125,6 +125,8 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
   const int b = blockIdx.x / NT, tile = blockIdx.x % NT;
   const int lj0 = tile * TL;
   const int nlin = min(TL, L - lj0);  // owned lines
+  pdl_trigger();
+  pdl_wait();
   if (FUSEDP && !active[b]) return;
   const int sub = b / R;
   const int nE = nlin * (L - 1), nNr = nlin + 1;
@@ -172,6 +174,37 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
   }
   // phase 1: input lines lj0-1 .. lj0+nlin (zeros outside the grid)
   const int nin = (nlin + 2) * L * P;
+  const bool vec16 = sizeof(T) == 4 && ((L * P) & 3) == 0 &&
+                     ((FUSEDP ? ((reinterpret_cast<uintptr_t>(zin) | reinterpret_cast<uintptr_t>(pold) |
+                                  reinterpret_cast<uintptr_t>(pnew)) & 15)
+                              : (reinterpret_cast<uintptr_t>(xk) & 15)) == 0);
+  if (vec16) {
+    // 16-byte vectors: a line of L x P values starts on a 16-byte boundary and holds whole vectors
+    const int LP4 = (L * P) >> 2;
+    const FD fLP4 = make_fd((unsigned)LP4);
+    for (int e4 = threadIdx.x; e4 < (nin >> 2); e4 += nt) {
+      const int t = fdiv(e4, fLP4);
+      const int jl = lj0 - 1 + t;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (jl >= 0 && jl < L) {
+        const long long g = pb + (long long)jl * L * P + 4LL * (e4 - t * LP4);
+        if (FUSEDP) {
+          v = *reinterpret_cast<const float4*>(zin + g);
+          if (bet != T(0)) {
+            const float4 o = *reinterpret_cast<const float4*>(pold + g);
+            v.x += (float)bet * o.x;
+            v.y += (float)bet * o.y;
+            v.z += (float)bet * o.z;
+            v.w += (float)bet * o.w;
+          }
+          if (t >= 1 && t <= nlin) *reinterpret_cast<float4*>(pnew + g) = v;
+        } else {
+          v = *reinterpret_cast<const float4*>(xk + g);
+        }
+      }
+      *reinterpret_cast<float4*>(xs + 4 * e4) = v;
+    }
+  } else
   for (int e = threadIdx.x; e < nin; e += nt) {
     const int t = fdiv(e, op.fLP);
     const int jl = lj0 - 1 + t;
@@ -191,10 +224,14 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
   __syncthreads();
   SG_MARK(1);
   if constexpr (C::fixed) {
-    // phase 2 (compile-time table): one work item per (edge, output-mode group)
+    // phase 2 (compile-time table): one work item per (edge, output-mode group); the group is
+    // uniform across a warp (32 consecutive edges), so the unrolled group code never diverges
     if (ck != T(0)) {
-      for (int it = threadIdx.x; it < nEd * C::KG; it += nt) {
-        const int ed = it / C::KG, g = it - ed * C::KG;
+      const int nEd32 = (nEd + 31) & ~31;
+      for (int it = threadIdx.x; it < nEd32 * C::KG; it += nt) {
+        const int wi = it >> 5, g = wi % C::KG;
+        const int ed = ((wi / C::KG) << 5) + (it & 31);
+        if (ed >= nEd) continue;
         const T* xa;
         const T* xb;
         const T* kp;
@@ -307,7 +344,8 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
   }
   __syncthreads();
   SG_MARK(3);
-  // phase 3: outputs of the owned lines
+  // phase 3: outputs of the owned lines (p.q partial in FP64: the FP32 products of a correction
+  // solve can be far below the FP32 normal range)
   double dsum = 0.0;
   for (int e = threadIdx.x; e < nlin * L * P; e += nt) {
     const int nd = fdiv(e, op.fP), k = e - nd * P;
@@ -1673,6 +1711,8 @@ __global__ void __launch_bounds__(256) k_cg_pack(int L, int nl, int P, int NC, i
   count_launch();
   __shared__ float rs[64][NB + 1];
   const int b = blockIdx.x / NC, c = blockIdx.x % NC;
+  pdl_trigger();
+  pdl_wait();
   if (!init && !ctl.active[b]) return;
   const int LL = L * L;
   float alpha = 0.f;
@@ -1686,19 +1726,78 @@ __global__ void __launch_bounds__(256) k_cg_pack(int L, int nl, int P, int NC, i
   }
   const long long base = (long long)b * nl * P;
   const int n0 = c * 64;
-  for (int e = threadIdx.x; e < 64 * P; e += blockDim.x) {
-    const int i = e / P, k = e - i * P;
-    float rv = 0.f;
-    if (n0 + i < LL) {
-      const long long o = base + (long long)n0 * P + e;
-      rv = r[o];
-      if (!init) {
-        x[o] += alpha * pc[o];
-        rv -= alpha * q[o];
-        r[o] = rv;
+  const int nv = min(64, LL - n0) * P;  // values of the chunk's nodes (contiguous)
+  const long long o0 = base + (long long)n0 * P;
+  const bool vec = ((nl * P) & 3) == 0 && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(r) |
+                                            reinterpret_cast<uintptr_t>(q) | reinterpret_cast<uintptr_t>(pbuf0) |
+                                            reinterpret_cast<uintptr_t>(pbuf1)) & 15) == 0;
+  if (vec) {
+    // 16-byte vectors; every load of a thread is issued before its stores (pc may alias nothing,
+    // but the compiler cannot know)
+    const int n4 = nv >> 2;
+    constexpr int U = 2;
+    float4 rv[U], xv[U], pv[U], qv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e4 = threadIdx.x + u * 256;
+      if (e4 < n4) {
+        rv[u] = reinterpret_cast<const float4*>(r + o0)[e4];
+        if (!init) {
+          xv[u] = reinterpret_cast<const float4*>(x + o0)[e4];
+          pv[u] = reinterpret_cast<const float4*>(pc + o0)[e4];
+          qv[u] = reinterpret_cast<const float4*>(q + o0)[e4];
+        }
       }
     }
-    rs[i][k] = rv;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e4 = threadIdx.x + u * 256;
+      if (e4 < n4) {
+        if (!init) {
+          xv[u].x += alpha * pv[u].x; xv[u].y += alpha * pv[u].y;
+          xv[u].z += alpha * pv[u].z; xv[u].w += alpha * pv[u].w;
+          rv[u].x -= alpha * qv[u].x; rv[u].y -= alpha * qv[u].y;
+          rv[u].z -= alpha * qv[u].z; rv[u].w -= alpha * qv[u].w;
+          reinterpret_cast<float4*>(x + o0)[e4] = xv[u];
+          reinterpret_cast<float4*>(r + o0)[e4] = rv[u];
+        }
+        const float vv[4] = {rv[u].x, rv[u].y, rv[u].z, rv[u].w};
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int e = 4 * e4 + m, i = e / P;
+          rs[i][e - i * P] = vv[m];
+        }
+      }
+    }
+    for (int e = nv + threadIdx.x; e < 64 * P; e += blockDim.x) rs[e / P][e % P] = 0.f;
+    for (int e4 = threadIdx.x + U * 256; e4 < n4; e4 += blockDim.x) {  // chunks beyond U x 256 vectors
+      for (int m = 0; m < 4; ++m) {
+        const int e = 4 * e4 + m, i = e / P;
+        const long long o = o0 + e;
+        float v = r[o];
+        if (!init) {
+          x[o] += alpha * pc[o];
+          v -= alpha * q[o];
+          r[o] = v;
+        }
+        rs[i][e - i * P] = v;
+      }
+    }
+  } else {
+    for (int e = threadIdx.x; e < 64 * P; e += blockDim.x) {
+      const int i = e / P, k = e - i * P;
+      float v = 0.f;
+      if (e < nv) {
+        const long long o = o0 + e;
+        v = r[o];
+        if (!init) {
+          x[o] += alpha * pc[o];
+          v -= alpha * q[o];
+          r[o] = v;
+        }
+      }
+      rs[i][k] = v;
+    }
   }
   if (NB > P)
     for (int e = threadIdx.x; e < 64 * (NB - P); e += blockDim.x) rs[e / (NB - P)][P + e % (NB - P)] = 0.f;
@@ -1752,13 +1851,20 @@ __global__ void __launch_bounds__(256, 1) k_pre_mma(const __grid_constant__ CUte
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_mma_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int b = blockIdx.x / MT, tile = blockIdx.x % MT;
+  pdl_trigger();
+  // prologue before the predecessor has finished: mbarriers, TMEM, the tensor-map descriptor
+  const unsigned tmem = mma_begin<NB, PRE_NST>(bars, &tmem_slot, s_flags);
+  if (threadIdx.x == 32)
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&tmA)) : "memory");
+  pdl_wait();
   const bool act = init ? true : (ctl.active[b] != 0);
   double s_rz = 0.0, s_rr = 0.0;
+  if (!act) mma_tile_end<NB, PRE_NST>(bars, tmem, s_flags);
   if (act) {
     const int sub = b / R;
     const int y0 = row0 + sub * Kp + tile * MMA_M;
     const unsigned char* bb = bimg + (size_t)b * NC * PreShape<NB>::BCHUNK;
-    const unsigned tmem = mma_tile<NB, PRE_NST, PRE_CPS>(&tmA, y0, bb, NC, smem, bars, &tmem_slot, s_flags, err);
+    mma_run<NB, PRE_NST, PRE_CPS>(&tmA, y0, bb, NC, smem, bars, tmem, s_flags, err);
     // every stage has been consumed: stage 0 is free for the accumulator tile [128][NB + 1]
     float* zt = reinterpret_cast<float*>(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

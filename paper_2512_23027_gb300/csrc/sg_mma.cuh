@@ -39,6 +39,11 @@ struct MmaShape {
   static constexpr unsigned TX = STAGE;                        // bytes landing per stage
 };
 
+// Programmatic dependent launch: let the next kernel of the stream start its prologue, and wait
+// until every predecessor grid has completed and its memory is visible (no-ops without PDL).
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -155,16 +160,13 @@ __host__ __device__ constexpr unsigned sw128_offset(int n, int k) {
 // MMAs; on return (all threads) the accumulator is complete, or *err is set.  smem: 1024-aligned
 // stage area; bars: 2 NST + 1 mbarriers.  NC must be a multiple of CPS.  Returns the TMEM base.
 // ------------------------------------------------------------------------------------------
-template <int NB, int NST = MMA_NST, int CPS = 1, bool MMA = true>
-__device__ __forceinline__ unsigned mma_tile(const CUtensorMap* tmA, int y0, const unsigned char* __restrict__ bimg,
-                                             int NC, unsigned char* smem, unsigned long long* bars,
-                                             unsigned* tmem_slot, volatile int* s_flags, int* err) {
-  using S = MmaShape<NB, NST, CPS>;
-  constexpr unsigned NCOL = 2 * NB;  // TMEM columns (32 or 64)
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const unsigned full0 = smem_u32(bars), empty0 = smem_u32(bars + NST), done = smem_u32(bars + 2 * NST);
-  const int NS = NC / CPS;  // stages to stream
+// Prologue (all threads): mbarriers and the TMEM accumulator (2 NB columns).  Needs no input data,
+// so it may run before the wait on the predecessor grid.  Returns the TMEM base address.
+template <int NB, int NST = MMA_NST>
+__device__ __forceinline__ unsigned mma_begin(unsigned long long* bars, unsigned* tmem_slot, volatile int* s_flags) {
+  const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
+    const unsigned full0 = smem_u32(bars), empty0 = smem_u32(bars + NST), done = smem_u32(bars + 2 * NST);
     for (int s = 0; s < NST; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
@@ -176,14 +178,29 @@ __device__ __forceinline__ unsigned mma_tile(const CUtensorMap* tmA, int y0, con
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(NCOL)
+                 "r"((unsigned)(2 * NB))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const unsigned tmem = *tmem_slot;
+  return *tmem_slot;
+}
+
+// Main loop (all threads; call after mma_begin): accumulates
+//   D[128 x 2NB] = sum_c A[y0 .. y0+127][64c .. 64c+63] * [Bhi_c; Blo_c]^T
+// into TMEM (columns 0..NB-1: hi term, NB..2NB-1: lo term).  Warp 0 lane 0 produces (TMA for A, one
+// bulk copy for the B chunks of a stage), warp 1 lane 0 issues the MMAs; on return the accumulator
+// is complete, or *err is set.  smem: 1024-aligned stage area.  NC must be a multiple of CPS.
+template <int NB, int NST = MMA_NST, int CPS = 1, bool MMA = true>
+__device__ __forceinline__ void mma_run(const CUtensorMap* tmA, int y0, const unsigned char* __restrict__ bimg, int NC,
+                                        unsigned char* smem, unsigned long long* bars, unsigned tmem,
+                                        volatile int* s_flags, int* err) {
+  using S = MmaShape<NB, NST, CPS>;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned full0 = smem_u32(bars), empty0 = smem_u32(bars + NST), done = smem_u32(bars + 2 * NST);
+  const int NS = NC / CPS;  // stages to stream
   const unsigned sbase = smem_u32(smem);
   if (warp == 0 && lane == 0) {
     // producer
@@ -236,6 +253,15 @@ __device__ __forceinline__ unsigned mma_tile(const CUtensorMap* tmA, int y0, con
   if (!mbar_wait(done, 0u)) atomicExch(err, 19);
   __syncwarp();
   tc_fence_after();
+}
+
+// mma_begin + mma_run
+template <int NB, int NST = MMA_NST, int CPS = 1, bool MMA = true>
+__device__ __forceinline__ unsigned mma_tile(const CUtensorMap* tmA, int y0, const unsigned char* __restrict__ bimg,
+                                             int NC, unsigned char* smem, unsigned long long* bars,
+                                             unsigned* tmem_slot, volatile int* s_flags, int* err) {
+  const unsigned tmem = mma_begin<NB, NST>(bars, tmem_slot, s_flags);
+  mma_run<NB, NST, CPS, MMA>(tmA, y0, bimg, NC, smem, bars, tmem, s_flags, err);
   return tmem;
 }
 
