@@ -110,6 +110,10 @@ struct sg_handle_s {
   double *U = nullptr, *V = nullptr, *A = nullptr, *um = nullptr, *uc = nullptr, *xm = nullptr;
   double *ft = nullptr, *Unew = nullptr, *wa = nullptr, *wb = nullptr, *wc = nullptr, *wd = nullptr, *we = nullptr;
   float *fa = nullptr, *fb = nullptr;
+  // mixed precision: interior solution accumulated from the Schur matvecs, W_I = K_II^{-1} f~_I +
+  // sum of the PCG steps' Dirichlet extensions (replaces the two interior-recovery solves)
+  double* Wrec = nullptr;
+  bool a6_rec = false;
   double* fext = nullptr;  // n_free
   double* outbuf = nullptr;
   // interface vectors and outer control
@@ -655,20 +659,19 @@ static int enq_inner(sg_handle h, Ctx& cx, int pat, int nb, int R, int s0, const
     const bool pdl_pack = h->pdl && !init && h->kprof == 0;
     const bool pdl_mma = h->pdl && h->kprof == 0;
     if (h->mma_nb == 32)
-      CK(launch_k(pdl_pack, sgk::k_cg_pack<32>, dim3(gp), dim3(256), 0, s, L, pr.nl, pr.P, h->NC, NT, wx, wr, p0, p1,
-                  wq, h->ctl, init, h->bimg));
+      CK(launch_k(pdl_pack, sgk::k_cg_pack<32, 2>, dim3(gp), dim3(256), 0, s, L, pr.nl, pr.P, h->NC, NT, wx, wr, p0,
+                  p1, wq, h->ctl, init, h->bimg));
     else
-      CK(launch_k(pdl_pack, sgk::k_cg_pack<16>, dim3(gp), dim3(256), 0, s, L, pr.nl, pr.P, h->NC, NT, wx, wr, p0, p1,
-                  wq, h->ctl, init, h->bimg));
+      CK(launch_k(pdl_pack, sgk::k_cg_pack<16, 2>, dim3(gp), dim3(256), 0, s, L, pr.nl, pr.P, h->NC, NT, wx, wr, p0,
+                  p1, wq, h->ctl, init, h->bimg));
     RET(kprof_begin(h, cc, 3));
-    if (h->mma_nb == 32)
-      CK(launch_k(pdl_mma, sgk::k_pre_mma<32>, dim3(gm), dim3(256), (size_t)sgk::PreShape<32>::SMEM, s, h->tmA, L,
-                  pr.nl, pr.P, R, h->MT, h->NC, NT, h->Kp, row0, nb, (const unsigned char*)h->bimg, (const float*)wr,
-                  wz, h->ctl, init, tol2, bb_min, imax, hh, use, h->ctl.breakdown));
-    else
-      CK(launch_k(pdl_mma, sgk::k_pre_mma<16>, dim3(gm), dim3(256), (size_t)sgk::PreShape<16>::SMEM, s, h->tmA, L,
-                  pr.nl, pr.P, R, h->MT, h->NC, NT, h->Kp, row0, nb, (const unsigned char*)h->bimg, (const float*)wr,
-                  wz, h->ctl, init, tol2, bb_min, imax, hh, use, h->ctl.breakdown));
+#define SG_PRE(NBV, SMEMV)                                                                                      \
+  CK(launch_k(pdl_mma, sgk::k_pre_mma<NBV>, dim3(gm), dim3(256), (size_t)SMEMV, s, h->tmA, L, pr.nl, pr.P, R,     \
+              h->MT, h->NC, NT, h->Kp, row0, nb, (const unsigned char*)h->bimg, (const float*)wr, wz, h->ctl, init, \
+              tol2, bb_min, imax, hh, use, h->ctl.breakdown))
+    if (h->mma_nb == 32) SG_PRE(32, (sgk::PreShape<32, 2>::SMEM));
+    else SG_PRE(16, (sgk::PreShape<16, 2>::SMEM));
+#undef SG_PRE
     RET(kprof_end(h, cc, 3));
     return SG_OK;
   };
@@ -798,6 +801,9 @@ static int enq_outer(sg_handle h, Ctx& cx) {
   sgk::k_ozero_if<<<nbo, 256, 0, st>>>(n, h->octl, h->xG);
   CKL();
   RET(enq_schur(h, cx, h->xG, h->qG));
+  const long long nl_all = h->nvec();
+  if (h->a6_rec)  // W_I += K_II^{-1}(-K_IG x0): interior part of the extension just computed
+    sgk::k_wacc<<<nblk(nl_all), 256, 0, st>>>(nl_all, h->pr.P, h->cls, nullptr, 0, h->wd, h->ws32.x, h->Wrec);
   sgk::k_ores0<<<nbo, 256, 0, st>>>(n, h->gG, h->qG, h->rG, h->opart);
   cudaGraphConditionalHandle hw, hif;
   RET(make_handle(h, cx, &hw));
@@ -821,6 +827,8 @@ static int enq_outer(sg_handle h, Ctx& cx) {
                                     h->omirror);
     if (flex) CK(cudaMemcpyAsync(h->roG, h->rG, sizeof(double) * n, cudaMemcpyDeviceToDevice, c.st));
     sgk::k_oupd<<<nbo, 256, 0, c.st>>>(n, h->octl, h->pG, h->qG, h->xG, h->rG, h->opart);
+    if (h->a6_rec)  // W_I += alpha K_II^{-1}(-K_IG p), with the alpha that just updated x
+      sgk::k_wacc<<<nblk(nl_all), 256, 0, c.st>>>(nl_all, h->pr.P, h->cls, h->octl, 0, h->wd, h->ws32.x, h->Wrec);
     cudaGraphConditionalHandle hif2;
     RET(make_handle(h, c, &hif2));
     sgk::k_octl<<<1, 32, 0, c.st>>>(sgk::OP_CHECK, nbo, h->opart, nullptr, h->octl, h->tol, h->max_iter, hw, hif2,
@@ -968,6 +976,9 @@ static int enq_step(sg_handle h, Ctx& cx, bool ext) {
     // g_s = f~_G - K_GI (w0 + e) = wa_G - (K32 [e; 0])_G
     RET((launch_apply<float, double, false, false>(h, st, o32, nsub, 1, h->ws32.x, h->ws32.x, h->wc, h->wa, -h->am,
                                                    -h->bk, sgk::MASK_G)));
+    // interior accumulator: W_I = K_II^{-1} f~_I = w0 + e
+    if (h->a6_rec)
+      sgk::k_wacc<<<nblk(n), 256, 0, st>>>(n, P, h->cls, nullptr, 1, h->wd, h->ws32.x, h->Wrec);
   }
   sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, h->Dw, h->wc, h->gG, 0);
   CKL();
@@ -979,11 +990,15 @@ static int enq_step(sg_handle h, Ctx& cx, bool ext) {
   if (h->warm == SG_WARM_LEARNED) RET(enq_warm_train(h, cx));
   // a6: interior recovery u_I = K_II^{-1} (f~_I - K_IG u_G)
   sgk::k_gather<double><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->gidx, h->Dw, h->xG, h->wa, sgk::MASK_G, 0);
-  RET((launch_apply<double, double, false, false>(h, st, op, nsub, 1, h->wa, h->wa, h->wb, h->ft, -h->am, -h->bk,
-                                                  sgk::MASK_I)));
+  if (!h->a6_rec)
+    RET((launch_apply<double, double, false, false>(h, st, op, nsub, 1, h->wa, h->wa, h->wb, h->ft, -h->am, -h->bk,
+                                                    sgk::MASK_I)));
   if (h->precision == SG_FP64) {
     RET(enq_inner<double>(h, cx, 0, nsub, 1, 0, h->wb));
     sgk::k_axpby<double><<<nblk(n), 256, 0, st>>>(n, 1.0, h->ws.x, 1.0, h->wa, h->Unew);
+  } else if (h->a6_rec) {
+    // u = [W_I; u_G]: the interior part was accumulated along the PCG (k_wacc)
+    sgk::k_axpby<double><<<nblk(n), 256, 0, st>>>(n, 1.0, h->Wrec, 1.0, h->wa, h->Unew);
   } else {
     sgk::k_conv_mask<double, float><<<nblk(n), 256, 0, st>>>(nsub, 1, nl, P, h->cls, h->wb, h->fb, sgk::MASK_I, 1.0);
     RET(enq_inner<float>(h, cx, 0, nsub, 1, 0, h->fb));
@@ -1132,8 +1147,8 @@ static int build_mma_precond(sg_handle h) {
     h->err = "tensor map encoding of the mean-operator inverse failed";
     return SG_ECUDA;
   }
-  RET(smem_attr(h, sgk::k_pre_mma<32>, sgk::PreShape<32>::SMEM));
-  RET(smem_attr(h, sgk::k_pre_mma<16>, sgk::PreShape<16>::SMEM));
+  RET(smem_attr(h, sgk::k_pre_mma<32>, sgk::PreShape<32, 2>::SMEM));
+  RET(smem_attr(h, sgk::k_pre_mma<16>, sgk::PreShape<16, 2>::SMEM));
   h->mma = true;
   RET(ensure_bimg(h, pr.nsub));
   return ensure_ctl(h, pr.nsub, pr.L, std::max(pr.P, h->MT));
@@ -1603,6 +1618,8 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   const long long n = h->nvec();
   for (double** p : {&h->U, &h->V, &h->A, &h->um, &h->uc, &h->xm, &h->ft, &h->Unew, &h->wa, &h->wb, &h->wc, &h->wd, &h->we})
     RET(dalloc(h, p, n));
+  h->a6_rec = h->precision == SG_MIXED && std::getenv("SG_A6_SOLVE") == nullptr;
+  if (h->a6_rec) RET(dalloc(h, &h->Wrec, n));
   RET(dalloc(h, &h->fa, n)); RET(dalloc(h, &h->fb, n));
   RET(dalloc(h, &h->fext, pr.n_free));
   RET(dalloc(h, &h->outbuf, 2LL * pr.n_free * pr.P));

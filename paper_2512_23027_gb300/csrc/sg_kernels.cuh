@@ -93,6 +93,18 @@ struct CgCtl {
   int* breakdown;    // set when p.q <= 0 or non-finite values appear
 };
 
+// BF16 terms of an FP32 value, f = t0 + t1 (+ t2) up to the last term's rounding: each remainder
+// is exact in FP32.  Two terms keep about 17 significant bits, three about 25.
+template <int TERMS>
+__device__ __forceinline__ void bf16_split(float f, __nv_bfloat16 (&t)[TERMS]) {
+  float rem = f;
+#pragma unroll
+  for (int i = 0; i < TERMS; ++i) {
+    t[i] = __float2bfloat16_rn(rem);
+    rem -= __bfloat162float(t[i]);
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // SG operator apply, tile form.
 //   y = add + cm (M (x) I) xm + ck (sum_i K_i (x) G_i) xk      on nodes with class in out_mask
@@ -886,6 +898,26 @@ struct OuterCtl {
 };
 
 enum : int { OP_INIT_G = 0, OP_RES0 = 1, OP_RZ0 = 2, OP_ALPHA = 3, OP_CHECK = 4, OP_BETA = 5, OP_BETA_FLEX = 6 };
+
+// Interior accumulator of the mixed-precision step: on interior nodes (class INT),
+//   W = v + e          (init, the interior solution K_II^{-1} f~_I of the condensed right-hand side)
+//   W += a (v + e)     (otherwise; a = c->alpha of the outer PCG, or 1 when c is null),
+// where v holds the FP32 solve widened to FP64 (plus interface values, ignored) and e the FP32
+// correction.  By linearity u_I = K_II^{-1} (f~_I - K_IG u_G) is then W_I once u_G = x0 + sum a p.
+__global__ void k_wacc(long long n, int P, const uint8_t* __restrict__ cls, const OuterCtl* c, int init,
+                       const double* __restrict__ v, const float* __restrict__ e, double* __restrict__ W) {
+  count_launch();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool interior = cls[i / P] == INT;
+  if (init) {
+    W[i] = interior ? v[i] + (double)e[i] : 0.0;
+    return;
+  }
+  if (!interior) return;
+  const double a = c ? c->alpha : 1.0;
+  W[i] += a * (v[i] + (double)e[i]);
+}
 
 // partial sums of up to two dot products: part[blk] = x.y, part2[blk] = u.v
 __global__ void k_odot(long long n, const double* __restrict__ x, const double* __restrict__ y,
@@ -1699,11 +1731,11 @@ __global__ void __launch_bounds__(256) k_inv_cols(int L, int nl, int Kp, int pat
 // ------------------------------------------------------------------------------------------
 // Inner CG update (x += alpha p, r -= alpha q, alpha = r.z / p.q, on all modes of 64 nodes) and
 // packing of the updated residual into the image read by k_pre_mma: per right-hand side b and
-// 64-node chunk c, the BF16 terms r_hi = bf16(r) and r_lo = bf16(r - r_hi), each a K-major
-// 128-byte-swizzled block of NB rows (PCE modes, zero beyond P) x 64 nodes.  Grid: nb x NC blocks.
+// 64-node chunk c, the TERMS BF16 terms of r (bf16_split), each a K-major 128-byte-swizzled block
+// of NB rows (PCE modes, zero beyond P) x 64 nodes.  Grid: nb x NC blocks.
 // init: first call of a solve (x = 0, pack r only).
 // ------------------------------------------------------------------------------------------
-template <int NB>
+template <int NB, int TERMS>
 __global__ void __launch_bounds__(256) k_cg_pack(int L, int nl, int P, int NC, int NT, float* __restrict__ x,
                                                  float* __restrict__ r, const float* pbuf0, const float* pbuf1,
                                                  const float* __restrict__ q, CgCtl ctl, int init,
@@ -1802,15 +1834,18 @@ __global__ void __launch_bounds__(256) k_cg_pack(int L, int nl, int P, int NC, i
   if (NB > P)
     for (int e = threadIdx.x; e < 64 * (NB - P); e += blockDim.x) rs[e / (NB - P)][P + e % (NB - P)] = 0.f;
   __syncthreads();
-  unsigned char* dst = bimg + ((size_t)b * NC + c) * 2 * (NB * 128);
-  for (int t = threadIdx.x; t < 2 * NB * 8; t += blockDim.x) {
+  unsigned char* dst = bimg + ((size_t)b * NC + c) * TERMS * (NB * 128);
+  for (int t = threadIdx.x; t < TERMS * NB * 8; t += blockDim.x) {
     const int hl = t / (NB * 8), rem = t - hl * NB * 8, n = rem >> 3, j = rem & 7;
     unsigned h[8];
 #pragma unroll
     for (int i2 = 0; i2 < 8; ++i2) {
-      const float f = rs[j * 8 + i2][n];
-      const __nv_bfloat16 hi = __float2bfloat16_rn(f);
-      const __nv_bfloat16 v = hl ? __float2bfloat16_rn(f - __bfloat162float(hi)) : hi;
+      __nv_bfloat16 tt[TERMS];
+      bf16_split<TERMS>(rs[j * 8 + i2][n], tt);
+      __nv_bfloat16 v = tt[0];
+#pragma unroll
+      for (int q2 = 1; q2 < TERMS; ++q2)
+        if (hl == q2) v = tt[q2];
       h[i2] = (unsigned)__bfloat16_as_ushort(v);
     }
     uint4 pk;
@@ -1831,9 +1866,16 @@ __global__ void __launch_bounds__(256) k_cg_pack(int L, int nl, int P, int NC, i
 // rows of A for (pattern, subdomain) start at row0 + sub * Kp.  err: set to 16 + stage when a
 // bounded wait of the pipeline ran out.
 // ------------------------------------------------------------------------------------------
-constexpr int PRE_NST = 4, PRE_CPS = 2;  // pipeline of the preconditioner product: 4 stages of 2 chunks
-template <int NB>
-using PreShape = MmaShape<NB, PRE_NST, PRE_CPS>;
+// Pipeline of the preconditioner product: 2 chunks per stage; 4 stages with two terms, 3 with three.
+// (A recurrence z -= alpha A0^{-1} q on a three-term image of q, which would skip k_cg_pack, was
+// measured: 44% more inner iterations on the 128^2 workload and no faster per iteration.)
+constexpr int PRE_CPS = 2;
+template <int TERMS>
+struct PreNst {
+  static constexpr int v = TERMS == 3 ? 3 : 4;
+};
+template <int NB, int TERMS>
+using PreShape = MmaShape<NB, TERMS, PreNst<TERMS>::v, PRE_CPS>;
 
 template <int NB>
 __global__ void __launch_bounds__(256, 1) k_pre_mma(const __grid_constant__ CUtensorMap tmA, int L, int nl, int P,
@@ -1843,9 +1885,11 @@ __global__ void __launch_bounds__(256, 1) k_pre_mma(const __grid_constant__ CUte
                                                     int init, double tol2, double bb_min, int max_it,
                                                     cudaGraphConditionalHandle cond_handle, int use_handle,
                                                     int* err) {
+  constexpr int TERMS = 2;
+  constexpr int NST = PreNst<TERMS>::v;
   count_launch();
   extern __shared__ unsigned char smem_mma_raw[];
-  __shared__ __align__(8) unsigned long long bars[2 * PRE_NST + 1];
+  __shared__ __align__(8) unsigned long long bars[2 * NST + 1];
   __shared__ unsigned tmem_slot;
   __shared__ int s_flags[2];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -1853,29 +1897,29 @@ __global__ void __launch_bounds__(256, 1) k_pre_mma(const __grid_constant__ CUte
   const int b = blockIdx.x / MT, tile = blockIdx.x % MT;
   pdl_trigger();
   // prologue before the predecessor has finished: mbarriers, TMEM, the tensor-map descriptor
-  const unsigned tmem = mma_begin<NB, PRE_NST>(bars, &tmem_slot, s_flags);
+  const unsigned tmem = mma_begin<NB, TERMS, NST>(bars, &tmem_slot, s_flags);
   if (threadIdx.x == 32)
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&tmA)) : "memory");
   pdl_wait();
   const bool act = init ? true : (ctl.active[b] != 0);
   double s_rz = 0.0, s_rr = 0.0;
-  if (!act) mma_tile_end<NB, PRE_NST>(bars, tmem, s_flags);
+  if (!act) mma_tile_end<NB, TERMS, NST>(bars, tmem, s_flags);
   if (act) {
     const int sub = b / R;
     const int y0 = row0 + sub * Kp + tile * MMA_M;
-    const unsigned char* bb = bimg + (size_t)b * NC * PreShape<NB>::BCHUNK;
-    mma_run<NB, PRE_NST, PRE_CPS>(&tmA, y0, bb, NC, smem, bars, tmem, s_flags, err);
+    const unsigned char* bb = bimg + (size_t)b * NC * PreShape<NB, TERMS>::BCHUNK;
+    mma_run<NB, TERMS, NST, PRE_CPS>(&tmA, y0, bb, NC, smem, bars, tmem, s_flags, err);
     // every stage has been consumed: stage 0 is free for the accumulator tile [128][NB + 1]
     float* zt = reinterpret_cast<float*>(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp >= 4) {
       float v[NB];
-      mma_row<NB>(tmem, warp - 4, v);
+      mma_row<NB, TERMS>(tmem, warp - 4, v);
       float* zr = zt + ((warp - 4) * 32 + lane) * (NB + 1);
 #pragma unroll
       for (int k = 0; k < NB; ++k) zr[k] = v[k];
     }
-    mma_tile_end<NB, PRE_NST>(bars, tmem, s_flags);  // contains __syncthreads
+    mma_tile_end<NB, TERMS, NST>(bars, tmem, s_flags);  // contains __syncthreads
     const int m0 = tile * MMA_M;
     const int rows = min(MMA_M, L * L - m0);
     if (rows > 0) {

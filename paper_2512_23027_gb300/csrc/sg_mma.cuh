@@ -27,16 +27,19 @@ constexpr int MMA_ABYTES = MMA_M * MMA_KC * 2;  // 16 KB of A per stage
 constexpr int MMA_NST = 6;                    // pipeline stages
 constexpr unsigned long long MMA_WAIT_NS = 1000000000ull;  // bound of every wait
 
-// NB: PCE modes padded to 16 or 32; the B operand of one chunk is [r_hi; r_lo] = 2 NB rows, so one
-// MMA of N = 2 NB per K step covers both terms (the epilogue adds the two column halves).
-// CPS: 64-column chunks per pipeline stage.
-template <int NB, int NST = MMA_NST, int CPS = 1>
+// NB: PCE modes padded to 16 or 32; TERMS: BF16 terms of the right-hand side (2: r = hi + lo, about
+// 17 significant bits; 3: hi + mid + lo, about 25).  The B operand of one chunk is the TERMS x NB
+// rows [term 0; term 1; ...], so one MMA of N = TERMS x NB per K step covers all terms (the
+// epilogue adds the column blocks).  CPS: 64-column chunks per pipeline stage.
+template <int NB, int TERMS = 2, int NST = MMA_NST, int CPS = 1>
 struct MmaShape {
   static constexpr int BBYTES = NB * 128;                      // one term of one chunk (NB rows)
-  static constexpr int BCHUNK = 2 * BBYTES;                    // [hi; lo] of one chunk
+  static constexpr int BCHUNK = TERMS * BBYTES;                // all terms of one chunk
   static constexpr int STAGE = CPS * (MMA_ABYTES + BCHUNK);    // A chunks, then B chunks (x 1024)
   static constexpr int SMEM = NST * STAGE + 1024;              // + alignment slack
   static constexpr unsigned TX = STAGE;                        // bytes landing per stage
+  static constexpr int N = TERMS * NB;                         // MMA N
+  static constexpr unsigned TCOLS = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;  // TMEM alloc
 };
 
 // Programmatic dependent launch: let the next kernel of the stream start its prologue, and wait
@@ -160,9 +163,10 @@ __host__ __device__ constexpr unsigned sw128_offset(int n, int k) {
 // MMAs; on return (all threads) the accumulator is complete, or *err is set.  smem: 1024-aligned
 // stage area; bars: 2 NST + 1 mbarriers.  NC must be a multiple of CPS.  Returns the TMEM base.
 // ------------------------------------------------------------------------------------------
-// Prologue (all threads): mbarriers and the TMEM accumulator (2 NB columns).  Needs no input data,
+// Prologue (all threads): mbarriers and the TMEM accumulator (TERMS x NB columns, allocated as a
+// power of two).  Needs no input data,
 // so it may run before the wait on the predecessor grid.  Returns the TMEM base address.
-template <int NB, int NST = MMA_NST>
+template <int NB, int TERMS = 2, int NST = MMA_NST>
 __device__ __forceinline__ unsigned mma_begin(unsigned long long* bars, unsigned* tmem_slot, volatile int* s_flags) {
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
@@ -178,7 +182,7 @@ __device__ __forceinline__ unsigned mma_begin(unsigned long long* bars, unsigned
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"((unsigned)(2 * NB))
+                 "r"(MmaShape<NB, TERMS, NST>::TCOLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -189,15 +193,15 @@ __device__ __forceinline__ unsigned mma_begin(unsigned long long* bars, unsigned
 }
 
 // Main loop (all threads; call after mma_begin): accumulates
-//   D[128 x 2NB] = sum_c A[y0 .. y0+127][64c .. 64c+63] * [Bhi_c; Blo_c]^T
-// into TMEM (columns 0..NB-1: hi term, NB..2NB-1: lo term).  Warp 0 lane 0 produces (TMA for A, one
+//   D[128 x TERMS NB] = sum_c A[y0 .. y0+127][64c .. 64c+63] * [B_c,0; B_c,1; ...]^T
+// into TMEM (column block t: term t).  Warp 0 lane 0 produces (TMA for A, one
 // bulk copy for the B chunks of a stage), warp 1 lane 0 issues the MMAs; on return the accumulator
 // is complete, or *err is set.  smem: 1024-aligned stage area.  NC must be a multiple of CPS.
-template <int NB, int NST = MMA_NST, int CPS = 1, bool MMA = true>
+template <int NB, int TERMS = 2, int NST = MMA_NST, int CPS = 1, bool MMA = true>
 __device__ __forceinline__ void mma_run(const CUtensorMap* tmA, int y0, const unsigned char* __restrict__ bimg, int NC,
                                         unsigned char* smem, unsigned long long* bars, unsigned tmem,
                                         volatile int* s_flags, int* err) {
-  using S = MmaShape<NB, NST, CPS>;
+  using S = MmaShape<NB, TERMS, NST, CPS>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned full0 = smem_u32(bars), empty0 = smem_u32(bars + NST), done = smem_u32(bars + 2 * NST);
   const int NS = NC / CPS;  // stages to stream
@@ -219,7 +223,7 @@ __device__ __forceinline__ void mma_run(const CUtensorMap* tmA, int y0, const un
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    constexpr unsigned idesc = idesc_bf16(MMA_M, 2 * NB);
+    constexpr unsigned idesc = idesc_bf16(MMA_M, S::N);
     for (int g = 0; g < NS; ++g) {
       const int s = g % NST, u = g / NST;
       if (!mbar_wait(full0 + 8 * s, (unsigned)(u & 1))) {
@@ -256,29 +260,33 @@ __device__ __forceinline__ void mma_run(const CUtensorMap* tmA, int y0, const un
 }
 
 // mma_begin + mma_run
-template <int NB, int NST = MMA_NST, int CPS = 1, bool MMA = true>
+template <int NB, int TERMS = 2, int NST = MMA_NST, int CPS = 1, bool MMA = true>
 __device__ __forceinline__ unsigned mma_tile(const CUtensorMap* tmA, int y0, const unsigned char* __restrict__ bimg,
                                              int NC, unsigned char* smem, unsigned long long* bars,
                                              unsigned* tmem_slot, volatile int* s_flags, int* err) {
-  const unsigned tmem = mma_begin<NB, NST>(bars, tmem_slot, s_flags);
-  mma_run<NB, NST, CPS, MMA>(tmA, y0, bimg, NC, smem, bars, tmem, s_flags, err);
+  const unsigned tmem = mma_begin<NB, TERMS, NST>(bars, tmem_slot, s_flags);
+  mma_run<NB, TERMS, NST, CPS, MMA>(tmA, y0, bimg, NC, smem, bars, tmem, s_flags, err);
   return tmem;
 }
 
-// Row of the accumulator for this thread's lane (warps 4..7 own lanes 0..127): hi + lo columns.
-template <int NB>
+// Row of the accumulator for this thread's lane (warp quarter wq owns lanes 32 wq ...): the sum of
+// the TERMS column blocks.
+template <int NB, int TERMS = 2>
 __device__ __forceinline__ void mma_row(unsigned tmem, int wq, float (&v)[NB]) {
-  float lo[NB];
   const unsigned t = tmem + ((unsigned)(wq * 32) << 16);
   tmem_ld<NB>(t, v);
-  tmem_ld<NB>(t + NB, lo);
 #pragma unroll
-  for (int i = 0; i < NB; ++i) v[i] += lo[i];
+  for (int term = 1; term < TERMS; ++term) {
+    float w[NB];
+    tmem_ld<NB>(t + term * NB, w);
+#pragma unroll
+    for (int i = 0; i < NB; ++i) v[i] += w[i];
+  }
 }
 
 // After the accumulator has been read: drain copies that were issued but never consumed (error
 // path only), then free TMEM.  All threads call this.
-template <int NB, int NST = MMA_NST>
+template <int NB, int TERMS = 2, int NST = MMA_NST>
 __device__ __forceinline__ void mma_tile_end(unsigned long long* bars, unsigned tmem, volatile int* s_flags) {
   tc_fence_before();
   __syncthreads();
@@ -291,7 +299,8 @@ __device__ __forceinline__ void mma_tile_end(unsigned long long* bars, unsigned 
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((unsigned)(2 * NB))
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(MmaShape<NB, TERMS, NST>::TCOLS)
                  : "memory");
   }
 }
