@@ -1526,7 +1526,11 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   h->tol = prm->tol > 0 ? prm->tol : 1e-8;
   h->max_iter = prm->max_iter > 0 ? prm->max_iter : 500;
   h->inner_tol = prm->inner_tol > 0 ? prm->inner_tol : 1e-14;
-  h->inner_tol32 = prm->inner_tol > 0 ? std::max(prm->inner_tol, 1e-7) : 1e-6;
+  // FP32 solves: a corrected Dirichlet solve is two FP32 solves (the second on the FP64 residual of
+  // the first), so its accuracy is about the product of their tolerances; automatic choice: each
+  // sqrt(1e-2 tol), i.e. the product 100x below the outer tolerance, within [1e-6, 1e-4]
+  h->inner_tol32 = prm->inner_tol > 0 ? std::max(prm->inner_tol, 1e-7)
+                                      : std::min(1e-4, std::max(1e-6, std::sqrt(1e-2 * h->tol)));
   h->inner_max = prm->inner_max_iter > 0 ? prm->inner_max_iter : 400;
   h->eager = std::getenv("SG_EAGER") != nullptr;
   // measured on the 128^2 workload: 7.87 ms per step without, 7.96 with; opt-in only

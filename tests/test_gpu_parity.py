@@ -162,3 +162,27 @@ def test_tensor_core_preconditioner_matches_line_sweeps(lib):
     assert err <= 1e2 * prob.tol, err
     assert all(r <= prob.tol for r in ra) and all(r <= prob.tol for r in rb)
     assert all(abs(x - y) <= 1 for x, y in zip(ia, ib))
+
+
+@pytest.mark.slow
+def test_bench_workload_mixed_matches_oracle(lib):
+    """The timed workload itself (128^2 grid, 4 x 4 subdomains, P = 20, workload tolerance 1e-8) in
+    the configuration bench.py times (mixed precision, tensor-core preconditioner, CUDA graph), two
+    steps against the oracle's DD-PCG at the same tolerance.  Both stop at ||r|| / ||G|| <= 1e-8, so
+    the fields agree to a small multiple of it; every step converges and the outer iteration counts
+    agree within one."""
+    from paper_2512_23027_gb300.binding import SG_MIXED
+    prob = w.config("ricker128")
+    steps = 2
+    s = lib(prob, precision=SG_MIXED)
+    assert s.sizes["fp32_precond"] == 1
+    s.step(steps)
+    U = s.field()
+    its, rr = s.iters()
+    s.close()
+    Ur, _, _, its_ref = oracle_run(prob, steps, prob.tol)
+    err = rel(U, Ur)
+    print(f"ricker128 (bench workload): mixed vs oracle rel err {err:.3e}, iters {its} vs {its_ref}")
+    assert err <= 1e3 * prob.tol, err
+    assert all(r <= prob.tol for r in rr)
+    assert all(abs(a - b) <= 1 for a, b in zip(its, its_ref))
