@@ -76,7 +76,7 @@ typedef struct {
   int    precision;   /* SG_FP64 or SG_MIXED                                                */
   int    warm;        /* SG_WARM_PREV or SG_WARM_LEARNED                                    */
   double inner_tol;   /* subdomain solves: relative residual target (0 = automatic: 1e-14 in
-                         FP64; in FP32 sqrt(1e-2 tol) within [1e-6, 1e-4], since a corrected
+                         FP64; in FP32 sqrt(0.1 tol) within [1e-6, 1e-4], since a corrected
                          solve is two FP32 solves whose tolerances multiply)                  */
   int    inner_max_iter; /* subdomain solves: iteration cap (0 = automatic)                 */
   int    autotune;    /* 1: time candidate tile shapes of the hot kernels at set-up and keep the

@@ -1528,9 +1528,11 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   h->inner_tol = prm->inner_tol > 0 ? prm->inner_tol : 1e-14;
   // FP32 solves: a corrected Dirichlet solve is two FP32 solves (the second on the FP64 residual of
   // the first), so its accuracy is about the product of their tolerances; automatic choice: each
-  // sqrt(1e-2 tol), i.e. the product 100x below the outer tolerance, within [1e-6, 1e-4]
+  // sqrt(0.1 tol), i.e. the product 10x below the outer tolerance, within [1e-6, 1e-4] (measured on
+  // the 128^2 workload against 1e-2 tol and 1e-3 tol: 87.8 / 94.0 / 101.4 inner iterations per step,
+  // the same 3 outer iterations)
   h->inner_tol32 = prm->inner_tol > 0 ? std::max(prm->inner_tol, 1e-7)
-                                      : std::min(1e-4, std::max(1e-6, std::sqrt(1e-2 * h->tol)));
+                                      : std::min(1e-4, std::max(1e-6, std::sqrt(0.1 * h->tol)));
   h->inner_max = prm->inner_max_iter > 0 ? prm->inner_max_iter : 400;
   h->eager = std::getenv("SG_EAGER") != nullptr;
   // measured on the 128^2 workload: 7.87 ms per step without, 7.96 with; opt-in only
