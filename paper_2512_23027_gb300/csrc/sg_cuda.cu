@@ -401,7 +401,8 @@ static int smem_attr(sg_handle h, void (*f)(A...), int lim) {
 
 // apply tile configuration: lines per block, dynamic shared memory, kappa staging
 template <typename T>
-static void apply_cfg(const sgh::Problem& pr, int nb, int* TL, int* NT, size_t* sm, int* stage) {
+static void apply_cfg(const sgh::Problem& pr, int nb, int* TL, int* NT, size_t* sm, int* stage, int* nods = nullptr) {
+  if (nods) *nods = 0;
   const int L = pr.L, P = pr.P, PI = pr.PI;
   const int PS = P | 1, PIS = PI | 1;
   const size_t nnz = pr.gk_v.size();
@@ -428,6 +429,22 @@ static void apply_cfg(const sgh::Problem& pr, int nb, int* TL, int* NT, size_t* 
            sizeof(int) * (P + 1) + 16;
   };
   auto kap = [&](int t) { return sizeof(T) * edges(t) * PIS; };
+  if (base(1) > 200 * 1024 || std::getenv("SG_FORCE_NODS")) {
+    // widest subdomains: no staged edge differences (formed on the fly), no staged weights
+    auto bytes = [&](int t) {
+      return sizeof(T) * ((size_t)(t + 2) * L * P + edges(t) * PS + nnz) + sizeof(unsigned) * nnz +
+             sizeof(int) * (P + 1) + 16;
+    };
+    int best = 1;
+    for (int t : {4, 2, 1})
+      if (t <= L && bytes(t) <= 200 * 1024 && (long long)nb * ((L + t - 1) / t) >= 128) { best = t; break; }
+    *TL = best;
+    *NT = (L + best - 1) / best;
+    *stage = 0;
+    *sm = bytes(best);
+    if (nods) *nods = 1;
+    return;
+  }
   int best = 1;
   for (int t : {8, 4, 2, 1}) {
     if (t > L) continue;
@@ -446,13 +463,13 @@ template <typename T, typename TO, bool FUSEDP, bool DOT>
 static int launch_apply(sg_handle h, cudaStream_t st, const Op<T>& op, int nb, int R, const T* xm, const T* xk, TO* y,
                         const TO* add, double cm, double ck, int mask, T* p0 = nullptr, T* p1 = nullptr,
                         const T* z = nullptr) {
-  int TL, NT, stage;
+  int TL, NT, stage, nods;
   size_t sm;
-  apply_cfg<T>(h->pr, nb, &TL, &NT, &sm, &stage);
+  apply_cfg<T>(h->pr, nb, &TL, &NT, &sm, &stage, &nods);
   const int fx = gfix_for<T>(h->pr);
   const unsigned grid = (unsigned)((long long)nb * NT);
   const int nnz = (int)h->pr.gk_v.size();
-  const bool done = with_gfix(fx, false, [&](auto c) -> bool {
+  bool done = with_gfix(fx, false, [&](auto c) -> bool {
     using C = decltype(c);
     if constexpr (sizeof(T) == 4 || gfix_fp64_ok<C>()) {
       sgk::k_apply<T, TO, FUSEDP, DOT, C><<<grid, 256, sm, st>>>(op, nb, R, TL, NT, nnz, stage, xm, xk, y, add, (T)cm,
@@ -463,6 +480,12 @@ static int launch_apply(sg_handle h, cudaStream_t st, const Op<T>& op, int nb, i
       return false;
     }
   });
+  if (!done && nods) {
+    sgk::k_apply<T, TO, FUSEDP, DOT, sgk::GDynNoDS><<<grid, 256, sm, st>>>(
+        op, nb, R, TL, NT, nnz, stage, xm, xk, y, add, (T)cm, (T)ck, mask, p0, p1, z, h->ctl.parity, h->ctl.beta,
+        h->ctl.active, h->ctl.part_pq);
+    done = true;
+  }
   if (!done) {
     auto kern = sgk::k_apply<T, TO, FUSEDP, DOT>;
     kern<<<grid, 256, sm, st>>>(op, nb, R, TL, NT, nnz, stage, xm, xk, y, add, (T)cm, (T)ck, mask, p0, p1, z,
@@ -490,6 +513,7 @@ constexpr size_t SMEM_MAX = 232448 - 1024;  // opt-in dynamic shared memory per 
 
 struct LineCfg {
   bool team;      // warp-team kernel with the factor staged in shared memory
+  bool gs;        // block kernel reading the factor from global memory (widest subdomains)
   int G, NG;      // modes per block, blocks per problem
   dim3 block;
   size_t smem;
@@ -525,13 +549,19 @@ static LineCfg line_cfg(const sgh::Problem& pr, int nb_hint) {
   if (const int t = tuned(1, sizeof(T), pr, nb_hint)) g = t;
   g = std::max(1, std::min(g, 1024 / L));
   while (g > 1 && line_smem<T>(L, g) > 200 * 1024) --g;
+  c.gs = line_smem<T>(L, g) > 200 * 1024 || std::getenv("SG_FORCE_GLINE");
+  if (c.gs) {  // factor and residual from global memory: solution slice only
+    auto gsm = [&](int gg) { return sizeof(T) * ((size_t)L * L * gg + (size_t)L * gg); };
+    g = std::max(1, std::min(g, 1024 / L));
+    while (g > 1 && gsm(g) > 200 * 1024) --g;
+  }
   int lp = L;
   while ((g * lp) % 32) ++lp;
   c.team = false;
   c.G = g;
   c.NG = (P + g - 1) / g;
   c.block = dim3(g, lp);
-  c.smem = line_smem<T>(L, g);
+  c.smem = c.gs ? sizeof(T) * ((size_t)L * L * g + (size_t)L * g) : line_smem<T>(L, g);
   return c;
 }
 
@@ -637,7 +667,11 @@ static int enq_inner(sg_handle h, Ctx& cx, int pat, int nb, int R, int s0, const
         default: break;
       }
 #undef SG_TEAM
-    } else
+    } else if (lc.gs)
+      sgk::k_line<T, true><<<lg, lc.block, lc.smem, s>>>(L, pr.nl, pr.P, R, NG, NT, pstride, Sinv, Bd, Bu, nb, w.x,
+                                                         w.r, w.z, w.p0, w.p1, w.q, h->ctl, init, tol2, bb_min, imax,
+                                                         hh, use);
+    else
       sgk::k_line<T><<<lg, lc.block, lc.smem, s>>>(L, pr.nl, pr.P, R, NG, NT, pstride, Sinv, Bd, Bu, nb, w.x, w.r,
                                                    w.z, w.p0, w.p1, w.q, h->ctl, init, tol2, bb_min, imax, hh, use);
   };
@@ -1482,6 +1516,10 @@ static int autotune_t(sg_handle h, int nb) {
               default: break;
             }
 #undef SG_TEAM_T
+          } else if (lc.gs) {
+            sgk::k_line<T, true><<<lg, lc.block, lc.smem, st>>>(L, pr.nl, pr.P, 1, lc.NG, NT, pstride, lf.Sinv, lf.Bd,
+                                                                lf.Bu, nb, w.x, w.r, w.z, w.p0, w.p1, w.q, h->ctl, 1,
+                                                                1e-30, 1e300, 1, 0, 0);
           } else {
             sgk::k_line<T><<<lg, lc.block, lc.smem, st>>>(L, pr.nl, pr.P, 1, lc.NG, NT, pstride, lf.Sinv, lf.Bd, lf.Bu,
                                                           nb, w.x, w.r, w.z, w.p0, w.p1, w.q, h->ctl, 1, 1e-30, 1e300,
@@ -1571,6 +1609,13 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
     RET(smem_attr(h, sgk::k_apply<float, double, false, false>, lim));
     RET(smem_attr(h, sgk::k_line<double>, lim));
     RET(smem_attr(h, sgk::k_line<float>, lim));
+    RET(smem_attr(h, sgk::k_line<double, true>, lim));
+    RET(smem_attr(h, sgk::k_line<float, true>, lim));
+    RET(smem_attr(h, sgk::k_apply<double, double, false, false, sgk::GDynNoDS>, lim));
+    RET(smem_attr(h, sgk::k_apply<double, double, true, true, sgk::GDynNoDS>, lim));
+    RET(smem_attr(h, sgk::k_apply<float, float, false, false, sgk::GDynNoDS>, lim));
+    RET(smem_attr(h, sgk::k_apply<float, float, true, true, sgk::GDynNoDS>, lim));
+    RET(smem_attr(h, sgk::k_apply<float, double, false, false, sgk::GDynNoDS>, lim));
 #define SG_ATTR(LSV) \
   RET(smem_attr(h, sgk::k_line_team<float, LSV>, (int)SMEM_MAX));
     SG_ATTR(4) SG_ATTR(8) SG_ATTR(12) SG_ATTR(16) SG_ATTR(20) SG_ATTR(24) SG_ATTR(28) SG_ATTR(32) SG_ATTR(36) SG_ATTR(40)

@@ -99,6 +99,7 @@ constexpr Tab<N> table(int M, int p, int pin) {
 template <int M_, int P_ORD, int PIN, int OFF_>
 struct Cfg {
   static constexpr bool fixed = true;
+  static constexpr bool nods = false;
   static constexpr int M = M_, p = P_ORD, pin = PIN, OFF = OFF_;
   static constexpr int P = multi(M_, P_ORD).n, PI = multi(M_, PIN).n;
   static constexpr int NNZ = count(M_, P_ORD, PIN);
@@ -201,6 +202,13 @@ __device__ __forceinline__ void gflux(int g, const T* __restrict__ kp, const T* 
 // the generic (runtime-G) variant of the apply kernel
 struct GDyn {
   static constexpr bool fixed = false;
+  static constexpr bool nods = false;
+  static constexpr int KG = 1;
+};
+// runtime table without the staged edge differences (subdomains too wide for the staging tiles)
+struct GDynNoDS {
+  static constexpr bool fixed = false;
+  static constexpr bool nods = true;
   static constexpr int KG = 1;
 };
 

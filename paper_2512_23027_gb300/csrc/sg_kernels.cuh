@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
   const int nEd = nE + nNr * L;                     // edges of the block: horizontal then vertical
   T* xs = reinterpret_cast<T*>(smem_raw);           // [(TL+2)][L][P]
   T* ds = xs + (size_t)(TL + 2) * L * P;            // [edges][PS] differences (runtime table only)
-  T* zs = C::fixed ? ds : ds + (size_t)(TL * (L - 1) + (TL + 1) * L) * PS;   // [edges][PS] fluxes
+  T* zs = (C::fixed || C::nods) ? ds : ds + (size_t)(TL * (L - 1) + (TL + 1) * L) * PS;   // [edges][PS] fluxes
   T* gv_s = zs + (size_t)(TL * (L - 1) + (TL + 1) * L) * PS; // [nnz]
   T* ks = gv_s + nnz;                               // [edges][PIS] edge weights (when staged)
   unsigned* gpk_s = reinterpret_cast<unsigned*>(stage_kap ? ks + (size_t)(TL * (L - 1) + (TL + 1) * L) * PIS : ks);
@@ -265,7 +265,9 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
       }
     }
   } else {
-  // phase 2a: differences d_e = x_a - x_b of every edge (a = left / bottom end)
+  // phase 2a: differences d_e = x_a - x_b of every edge (a = left / bottom end); the no-staging
+  // variant (nods, for the widest subdomains) forms them on the fly in phase 2b
+  if constexpr (!C::nods)
   for (int e = threadIdx.x; e < nEd * P; e += nt) {
     const int ed = fdiv(e, op.fP), j = e - ed * P;
     T dv;
@@ -316,8 +318,32 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
       };
       kap0 = kap_of(e0, live0);
       kap1 = has1 ? kap_of(e1, live1) : kap0;
+      auto ends = [&](int ed, const T*& xa, const T*& xb) {
+        if (ed < nE) {
+          const int t = fdiv(ed, op.fLm1), c = ed - t * (L - 1);
+          xa = xs + ((size_t)(t + 1) * L + c) * P;
+          xb = xa + P;
+        } else {
+          const int v = ed - nE, t = fdiv(v, op.fL), c = v - t * L;
+          xa = xs + ((size_t)t * L + c) * P;
+          xb = xa + (size_t)L * P;
+        }
+      };
+      const T *xa0 = nullptr, *xb0 = nullptr, *xa1 = nullptr, *xb1 = nullptr;
+      if constexpr (C::nods) {
+        ends(e0, xa0, xb0);
+        ends(has1 ? e1 : e0, xa1, xb1);
+      }
       const T* d0 = ds + (size_t)e0 * PS;
       const T* d1 = ds + (size_t)(has1 ? e1 : e0) * PS;
+      auto D0 = [&](unsigned j) -> T {
+        if constexpr (C::nods) return xa0[j] - xb0[j];
+        else return d0[j];
+      };
+      auto D1 = [&](unsigned j) -> T {
+        if constexpr (C::nods) return xa1[j] - xb1[j];
+        else return d1[j];
+      };
       T* z0 = zs + (size_t)e0 * PS;
       T* z1 = zs + (size_t)(has1 ? e1 : e0) * PS;
       const int k0 = krg * kchunk, k1 = min(P, k0 + kchunk);
@@ -330,21 +356,21 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
           const T g0 = gv_s[q], g1 = gv_s[q + 1], g2 = gv_s[q + 2], g3 = gv_s[q + 3];
           const unsigned i0 = p0 & 0xffffu, i1 = p1 & 0xffffu, i2 = p2 & 0xffffu, i3 = p3 & 0xffffu;
           const unsigned j0 = p0 >> 16, j1 = p1 >> 16, j2 = p2 >> 16, j3 = p3 >> 16;
-          a0 += (kap0[i0] * g0) * d0[j0];
-          a1 += (kap1[i0] * g0) * d1[j0];
-          b0 += (kap0[i1] * g1) * d0[j1];
-          b1 += (kap1[i1] * g1) * d1[j1];
-          a0 += (kap0[i2] * g2) * d0[j2];
-          a1 += (kap1[i2] * g2) * d1[j2];
-          b0 += (kap0[i3] * g3) * d0[j3];
-          b1 += (kap1[i3] * g3) * d1[j3];
+          a0 += (kap0[i0] * g0) * D0(j0);
+          a1 += (kap1[i0] * g0) * D1(j0);
+          b0 += (kap0[i1] * g1) * D0(j1);
+          b1 += (kap1[i1] * g1) * D1(j1);
+          a0 += (kap0[i2] * g2) * D0(j2);
+          a1 += (kap1[i2] * g2) * D1(j2);
+          b0 += (kap0[i3] * g3) * D0(j3);
+          b1 += (kap1[i3] * g3) * D1(j3);
         }
         for (; q < q1; ++q) {
           const unsigned pk = gpk_s[q];
           const T g = gv_s[q];
           const unsigned i = pk & 0xffffu, j = pk >> 16;
-          a0 += (kap0[i] * g) * d0[j];
-          a1 += (kap1[i] * g) * d1[j];
+          a0 += (kap0[i] * g) * D0(j);
+          a1 += (kap1[i] * g) * D1(j);
         }
         a0 += b0;
         a1 += b1;
@@ -513,7 +539,11 @@ __device__ __forceinline__ void line_control(double s_rz, double s_rr, int b, in
   }
 }
 
-template <typename T>
+// GS: the factor is read from global memory instead of being staged, and so is the residual
+// (subdomains too wide for the factor buffers and both slices); only the solution slice stays in
+// shared memory.  S_j^{-1} is symmetric, so row a is read as column a, which makes the accesses of
+// consecutive threads (consecutive a) contiguous.
+template <typename T, bool GS = false>
 __global__ void k_line(int L, int nl, int P, int R, int NG, int NT, long long pat_stride,
                        const T* __restrict__ Sinv, const T* __restrict__ Bd, const T* __restrict__ Bu, int nb,
                        T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, T* pbuf0, T* pbuf1,
@@ -523,9 +553,9 @@ __global__ void k_line(int L, int nl, int P, int R, int NG, int NT, long long pa
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int G = blockDim.x;                      // modes of the block (fast index)
   const int LL = L * L;
-  T* Sb = reinterpret_cast<T*>(smem_raw);        // [2][L][L] double-buffered S_j^{-1}
-  T* rs = Sb + 2 * LL;                           // [L lines][L][G] residual slice
-  T* ys = rs + (size_t)LL * G;                   // [L lines][L][G] solution slice
+  T* Sb = reinterpret_cast<T*>(smem_raw);        // [2][L][L] double-buffered S_j^{-1} (not with GS)
+  T* rs = GS ? Sb : Sb + 2 * LL;                 // [L lines][L][G] residual slice (not with GS)
+  T* ys = GS ? rs : rs + (size_t)LL * G;         // [L lines][L][G] solution slice
   T* w = ys + (size_t)LL * G;                    // [L][G]
   const int b = blockIdx.x / NG, grp = blockIdx.x % NG;
   const int m = threadIdx.x, a = threadIdx.y;
@@ -544,8 +574,10 @@ __global__ void k_line(int L, int nl, int P, int R, int NG, int NT, long long pa
     const int kb = grp * G;
     const int gl = min(G, P - kb);  // modes of this block
     // prefetch S_0^{-1} while the CG update runs
-    for (int e = tid; e < LL; e += nthr) cp_async_elem(Sb + e, S + e);
-    cp_async_commit();
+    if (!GS) {
+      for (int e = tid; e < LL; e += nthr) cp_async_elem(Sb + e, S + e);
+      cp_async_commit();
+    }
     // phase A (parallel over the block's slice): x += alpha p, r -= alpha q, stage r
     T alpha = T(0);
     const T* pc = nullptr;
@@ -568,19 +600,26 @@ __global__ void k_line(int L, int nl, int P, int R, int NG, int NT, long long pa
         rv -= alpha * q[o];
         r[o] = rv;
       }
-      rs[(size_t)node * G + mm] = rv;
+      if (!GS) rs[(size_t)node * G + mm] = rv;
     }
     __syncthreads();
+    // residual of line j, position a, mode m of the block (shared slice, or global with GS)
+    auto rval = [&](int node, int mm) -> T {
+      if (GS) return r[base + (long long)node * P + kb + mm];
+      return rs[(size_t)node * G + mm];
+    };
     // phase B: forward sweep y_j = S_j^{-1} (r_j - B_{j-1}^T y_{j-1}) in shared memory
     for (int j = 0; j < L; ++j) {
-      if (j + 1 < L) {
-        const T* src = S + (long long)(j + 1) * LL;
-        T* dst = Sb + ((j + 1) & 1) * LL;
-        for (int e = tid; e < LL; e += nthr) cp_async_elem(dst + e, src + e);
+      if (!GS) {
+        if (j + 1 < L) {
+          const T* src = S + (long long)(j + 1) * LL;
+          T* dst = Sb + ((j + 1) & 1) * LL;
+          for (int e = tid; e < LL; e += nthr) cp_async_elem(dst + e, src + e);
+        }
+        cp_async_commit();
       }
-      cp_async_commit();
       if (ok) {
-        T rhs = rs[((size_t)j * L + a) * G + m];
+        T rhs = rval(j * L + a, m);
         if (j > 0) {
           const T* yp = ys + (size_t)(j - 1) * L * G;
           rhs -= bd[(j - 1) * L + a] * yp[a * G + m];
@@ -588,67 +627,95 @@ __global__ void k_line(int L, int nl, int P, int R, int NG, int NT, long long pa
         }
         w[a * G + m] = rhs;
       }
-      cp_async_wait1();   // S_j^{-1} has landed (the newest group may still be in flight)
+      if (!GS) cp_async_wait1();   // S_j^{-1} has landed (the newest group may still be in flight)
       __syncthreads();
       if (ok) {
-        const T* Sj = Sb + (j & 1) * LL + a * L;
         T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-        int c = 0;
-        for (; c + 3 < L; c += 4) {
-          s0 += Sj[c] * w[c * G + m];
-          s1 += Sj[c + 1] * w[(c + 1) * G + m];
-          s2 += Sj[c + 2] * w[(c + 2) * G + m];
-          s3 += Sj[c + 3] * w[(c + 3) * G + m];
+        if (GS) {
+          const T* Sj = S + (long long)j * LL + a;  // column a of the symmetric S_j^{-1}
+          int c = 0;
+          for (; c + 3 < L; c += 4) {
+            s0 += Sj[(size_t)c * L] * w[c * G + m];
+            s1 += Sj[(size_t)(c + 1) * L] * w[(c + 1) * G + m];
+            s2 += Sj[(size_t)(c + 2) * L] * w[(c + 2) * G + m];
+            s3 += Sj[(size_t)(c + 3) * L] * w[(c + 3) * G + m];
+          }
+          for (; c < L; ++c) s0 += Sj[(size_t)c * L] * w[c * G + m];
+        } else {
+          const T* Sj = Sb + (j & 1) * LL + a * L;
+          int c = 0;
+          for (; c + 3 < L; c += 4) {
+            s0 += Sj[c] * w[c * G + m];
+            s1 += Sj[c + 1] * w[(c + 1) * G + m];
+            s2 += Sj[c + 2] * w[(c + 2) * G + m];
+            s3 += Sj[c + 3] * w[(c + 3) * G + m];
+          }
+          for (; c < L; ++c) s0 += Sj[c] * w[c * G + m];
         }
-        for (; c < L; ++c) s0 += Sj[c] * w[c * G + m];
         ys[((size_t)j * L + a) * G + m] = (s0 + s1) + (s2 + s3);
       }
       __syncthreads();
     }
-    cp_async_wait0();
+    if (!GS) cp_async_wait0();
     __syncthreads();
     // phase C: backward sweep x_j = y_j - S_j^{-1} B_j x_{j+1} in place in ys
-    if (L >= 2) {
-      const T* src = S + (long long)(L - 2) * LL;
-      for (int e = tid; e < LL; e += nthr) cp_async_elem(Sb + ((L - 2) & 1) * LL + e, src + e);
-    }
-    cp_async_commit();
-    for (int j = L - 2; j >= 0; --j) {
-      if (j - 1 >= 0) {
-        const T* src = S + (long long)(j - 1) * LL;
-        T* dst = Sb + ((j - 1) & 1) * LL;
-        for (int e = tid; e < LL; e += nthr) cp_async_elem(dst + e, src + e);
+    if (!GS) {
+      if (L >= 2) {
+        const T* src = S + (long long)(L - 2) * LL;
+        for (int e = tid; e < LL; e += nthr) cp_async_elem(Sb + ((L - 2) & 1) * LL + e, src + e);
       }
       cp_async_commit();
+    }
+    for (int j = L - 2; j >= 0; --j) {
+      if (!GS) {
+        if (j - 1 >= 0) {
+          const T* src = S + (long long)(j - 1) * LL;
+          T* dst = Sb + ((j - 1) & 1) * LL;
+          for (int e = tid; e < LL; e += nthr) cp_async_elem(dst + e, src + e);
+        }
+        cp_async_commit();
+      }
       if (ok) {
         const T* xn = ys + (size_t)(j + 1) * L * G;
         T tv = bd[j * L + a] * xn[a * G + m];
         if (a + 1 < L) tv += bu[j * L + a] * xn[(a + 1) * G + m];
         w[a * G + m] = tv;
       }
-      cp_async_wait1();
+      if (!GS) cp_async_wait1();
       __syncthreads();
       if (ok) {
-        const T* Sj = Sb + (j & 1) * LL + a * L;
         T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-        int c = 0;
-        for (; c + 3 < L; c += 4) {
-          s0 += Sj[c] * w[c * G + m];
-          s1 += Sj[c + 1] * w[(c + 1) * G + m];
-          s2 += Sj[c + 2] * w[(c + 2) * G + m];
-          s3 += Sj[c + 3] * w[(c + 3) * G + m];
+        if (GS) {
+          const T* Sj = S + (long long)j * LL + a;
+          int c = 0;
+          for (; c + 3 < L; c += 4) {
+            s0 += Sj[(size_t)c * L] * w[c * G + m];
+            s1 += Sj[(size_t)(c + 1) * L] * w[(c + 1) * G + m];
+            s2 += Sj[(size_t)(c + 2) * L] * w[(c + 2) * G + m];
+            s3 += Sj[(size_t)(c + 3) * L] * w[(c + 3) * G + m];
+          }
+          for (; c < L; ++c) s0 += Sj[(size_t)c * L] * w[c * G + m];
+        } else {
+          const T* Sj = Sb + (j & 1) * LL + a * L;
+          int c = 0;
+          for (; c + 3 < L; c += 4) {
+            s0 += Sj[c] * w[c * G + m];
+            s1 += Sj[c + 1] * w[(c + 1) * G + m];
+            s2 += Sj[c + 2] * w[(c + 2) * G + m];
+            s3 += Sj[c + 3] * w[(c + 3) * G + m];
+          }
+          for (; c < L; ++c) s0 += Sj[c] * w[c * G + m];
         }
-        for (; c < L; ++c) s0 += Sj[c] * w[c * G + m];
         ys[((size_t)j * L + a) * G + m] -= (s0 + s1) + (s2 + s3);
       }
       __syncthreads();
     }
-    cp_async_wait0();
+    if (!GS) cp_async_wait0();
     // phase D (parallel): write z, partial r.z and r.r
     for (int e = tid; e < LL * gl; e += nthr) {
       const int node = fdiv(e, fgl), mm = e - node * gl;
       const T zv = ys[(size_t)node * G + mm];
-      const double rv = (double)rs[(size_t)node * G + mm];
+      const double rv = (double)rval(node, mm);
       z[base + (long long)node * P + kb + mm] = zv;
       s_rz += rv * (double)zv;
       s_rr += rv * rv;

@@ -186,3 +186,52 @@ def test_bench_workload_mixed_matches_oracle(lib):
     assert err <= 1e3 * prob.tol, err
     assert all(r <= prob.tol for r in rr)
     assert all(abs(a - b) <= 1 for a, b in zip(its, its_ref))
+
+
+def _run_env(lib, prob, precision, steps, env):
+    import os
+    for k, v in env.items():
+        os.environ[k] = v
+    try:
+        s = lib(prob, precision=precision)
+    finally:
+        for k in env:
+            del os.environ[k]
+    s.step(steps)
+    u, (its, rr) = s.field(), s.iters()
+    s.close()
+    return u, its, rr
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_wide_subdomain_kernel_variants(lib, precision):
+    """The kernel variants for subdomains too wide for the shared-memory tiles (runtime-table apply
+    that forms the edge differences on the fly; line sweep reading the symmetric factor from global
+    memory, column-wise) forced on a small problem give the fields of the default kernels: bitwise
+    up to the summation order of the factor rows, i.e. within 1e-12 in FP64 and within the solver
+    tolerance in mixed precision."""
+    prob = w.config("small")
+    ua, ia, _ = _run_env(lib, prob, precision, 3, {})
+    ub, ib, rb = _run_env(lib, prob, precision, 3, {"SG_FORCE_NODS": "1", "SG_FORCE_GLINE": "1",
+                                                    "SG_NO_MMA": "1", "SG_NO_GFIX": "1"})
+    err = rel(ub, ua)
+    print(f"precision {precision}: forced wide-subdomain variants vs default rel diff {err:.3e}")
+    assert err <= (1e-12 if precision == 0 else 1e2 * prob.tol), err
+    assert all(r <= prob.tol for r in rb)
+    assert all(abs(x - y) <= 1 for x, y in zip(ia, ib))
+
+
+@pytest.mark.slow
+def test_widest_batch_subdomains_converge(lib):
+    """Batch instances whose 121 x 121-node subdomains exceed the shared-memory tiles (240^2 grid,
+    2 x 2 subdomains) run with the wide-subdomain variants: mixed precision converges every step and
+    agrees with the FP64 solver on the same GPU to a small multiple of the tolerance."""
+    from paper_2512_23027_gb300.binding import SG_FP64, SG_MIXED
+    prob = [p for p in w.batch_problems(8) if p.N // p.s + 1 > 81][0]
+    um, im, rm = _run_env(lib, prob, SG_MIXED, 2, {})
+    ud, idd, rd = _run_env(lib, prob, SG_FP64, 2, {})
+    err = rel(um, ud)
+    print(f"{prob.name} ({prob.N}^2, {prob.s}x{prob.s}, P={prob.P}): mixed vs FP64 rel diff {err:.3e}, "
+          f"iters {im} vs {idd}")
+    assert all(r <= prob.tol for r in rm + rd)
+    assert err <= 1e2 * prob.tol, err
