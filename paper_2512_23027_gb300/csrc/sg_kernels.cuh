@@ -785,7 +785,6 @@ __global__ void k_line_team(int L, int nl, int P, int R, int NG, int NT, int G, 
   const int tid = threadIdx.x;
   const int kb = grp * G;
   const int gl = min(G, P - kb);
-  const int k = kb + team;
   const bool tok = team < gl;
   const bool act = init ? true : (ctl.active[b] != 0);
   double s_rz = 0.0, s_rr = 0.0;
