@@ -180,7 +180,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
             "steps": steps, "warmup": warm, "ms_per_step": 1e3 * sec / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(prob, "fp64 (CPU oracle)"),
+            "config": dict(workload_config(prob, "fp64 (CPU oracle)"), l2="not applicable (host CPU)"),
             "pcg_iters_per_step": sum(i for i, _ in it) / len(it),
             "cpu_baseline": {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
                              "sample": f"{steps} time steps after {warm} warm-up step(s); FP64 numpy/scipy oracle "
