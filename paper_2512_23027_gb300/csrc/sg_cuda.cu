@@ -555,8 +555,14 @@ static LineCfg line_cfg(const sgh::Problem& pr, int nb_hint) {
     g = std::max(1, std::min(g, 1024 / L));
     while (g > 1 && gsm(g) > 200 * 1024) --g;
   }
-  int lp = L;
-  while ((g * lp) % 32) ++lp;
+  // rows padded so that the block is whole warps; keep the block within 1024 threads
+  auto rows_for = [&](int gg) {
+    int lp = L;
+    while ((gg * lp) % 32) ++lp;
+    return lp;
+  };
+  while (g > 1 && g * rows_for(g) > 1024) --g;
+  const int lp = rows_for(g);
   c.team = false;
   c.G = g;
   c.NG = (P + g - 1) / g;

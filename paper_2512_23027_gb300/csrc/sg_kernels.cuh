@@ -1824,7 +1824,8 @@ __global__ void __launch_bounds__(256) k_cg_pack(int L, int nl, int P, int NC, i
   }
   const long long base = (long long)b * nl * P;
   const int n0 = c * 64;
-  const int nv = min(64, LL - n0) * P;  // values of the chunk's nodes (contiguous)
+  // values of the chunk's nodes (contiguous); the last chunks of the padded Kp rows may hold none
+  const int nv = max(0, min(64, LL - n0)) * P;
   const long long o0 = base + (long long)n0 * P;
   const bool vec = ((nl * P) & 3) == 0 && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(r) |
                                             reinterpret_cast<uintptr_t>(q) | reinterpret_cast<uintptr_t>(pbuf0) |

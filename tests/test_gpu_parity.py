@@ -164,6 +164,33 @@ def test_tensor_core_preconditioner_matches_line_sweeps(lib):
     assert all(abs(x - y) <= 1 for x, y in zip(ia, ib))
 
 
+@pytest.mark.parametrize("N,M,p", [(38, 4, 2), (22, 3, 2), (24, 3, 3)])
+def test_tensor_core_preconditioner_empty_trailing_chunk(lib, N, M, p):
+    """Subdomain sizes whose L^2 nodes leave the last 64-node chunk of the 128-padded rows of the
+    dense inverse empty (L = 20, 12, 13) with nl * P a multiple of four, so that the residual image
+    is packed with 16-byte vectors: P = 15 and 10 (16 image rows) and P = 20 (32 rows).  Mixed
+    precision with the tensor-core preconditioner against the oracle's DD-PCG at the same
+    tolerance."""
+    from paper_2512_23027_gb300.binding import SG_MIXED
+    base = w.config("ricker128")
+    prob = base.replace(name=f"chunk{N}", N=N, s=2, M=M, p=p, p_in=p, dt=w.cfl_dt(N))
+    L = N // 2 + 1
+    assert (L * L) % 128 <= 64 and (L * L * prob.P) % 4 == 0
+    steps = 4
+    s = lib(prob, precision=SG_MIXED)
+    assert s.sizes["fp32_precond"] == 1
+    s.step(steps)
+    U = s.field()
+    its, rr = s.iters()
+    s.close()
+    Ur, _, _, its_ref = oracle_run(prob, steps, prob.tol)
+    err = rel(U, Ur)
+    print(f"L={L} P={prob.P}: tensor-core mixed vs oracle rel err {err:.3e}, iters {its} vs {its_ref}")
+    assert err <= 1e3 * prob.tol, err
+    assert all(r <= prob.tol for r in rr)
+    assert all(a <= b + 2 for a, b in zip(its, its_ref))
+
+
 @pytest.mark.slow
 def test_bench_workload_mixed_matches_oracle(lib):
     """The timed workload itself (128^2 grid, 4 x 4 subdomains, P = 20, workload tolerance 1e-8) in
