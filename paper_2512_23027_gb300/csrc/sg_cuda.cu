@@ -85,6 +85,7 @@ struct sg_handle_s {
   double *kapE = nullptr, *kapN = nullptr, *gk_v = nullptr;
   float *kapE32 = nullptr, *kapN32 = nullptr, *gk_v32 = nullptr;
   int *gk_ptr = nullptr, *gk_i = nullptr, *gk_j = nullptr;
+  unsigned* gk_pk = nullptr;  // gk_i | gk_j << 16
   int *gidx = nullptr, *cidx = nullptr, *owners = nullptr, *cowners = nullptr, *gam_ln = nullptr;
   int *n_gam = nullptr, *loc_corner = nullptr, *n_loc_corner = nullptr, *free_owner = nullptr;
   int *free_of_local = nullptr;
@@ -166,7 +167,7 @@ struct sg_handle_s {
     }
     o.kapE += (size_t)s0 * pr.nl * pr.PI;
     o.kapN += (size_t)s0 * pr.nl * pr.PI;
-    o.gk_ptr = gk_ptr; o.gk_i = gk_i; o.gk_j = gk_j;
+    o.gk_ptr = gk_ptr; o.gk_i = gk_i; o.gk_j = gk_j; o.gk_pk = gk_pk;
     o.L = pr.L; o.nl = pr.nl; o.P = pr.P; o.PI = pr.PI; o.mass_h = (T)(pr.h * pr.h / 24.0);
     o.fP = sgk::make_fd(pr.P); o.fPI = sgk::make_fd(pr.PI); o.fL = sgk::make_fd(pr.L);
     o.fLm1 = sgk::make_fd(pr.L - 1); o.fLP = sgk::make_fd(pr.L * pr.P);
@@ -400,6 +401,8 @@ static int smem_attr(sg_handle h, void (*f)(A...), int lim) {
 }
 
 // apply tile configuration: lines per block, dynamic shared memory, kappa staging
+constexpr size_t SMEM_MAX = 232448 - 1024;  // opt-in dynamic shared memory per block (static use below 1 KB)
+
 template <typename T>
 static void apply_cfg(const sgh::Problem& pr, int nb, int* TL, int* NT, size_t* sm, int* stage, int* nods = nullptr) {
   if (nods) *nods = 0;
@@ -429,20 +432,26 @@ static void apply_cfg(const sgh::Problem& pr, int nb, int* TL, int* NT, size_t* 
            sizeof(int) * (P + 1) + 16;
   };
   auto kap = [&](int t) { return sizeof(T) * edges(t) * PIS; };
-  if (base(1) > 200 * 1024 || std::getenv("SG_FORCE_NODS")) {
-    // widest subdomains: no staged edge differences (formed on the fly), no staged weights
-    auto bytes = [&](int t) {
-      return sizeof(T) * ((size_t)(t + 2) * L * P + edges(t) * PS + nnz) + sizeof(unsigned) * nnz +
-             sizeof(int) * (P + 1) + 16;
+  const char* force = std::getenv("SG_FORCE_NODS");
+  if (base(1) > 200 * 1024 || force) {
+    // widest subdomains: no staged edge differences (formed on the fly), no staged weights; when
+    // even a one-line tile with the staged table exceeds 200 KB, the table is read from global
+    // memory and the tile may use the whole opt-in shared memory (SG_FORCE_NODS=2 forces this)
+    const bool gtab_forced = force && force[0] == '2';
+    auto bytes = [&](int t, bool gtab) {
+      return sizeof(T) * ((size_t)(t + 2) * L * P + edges(t) * PS) + 16 +
+             (gtab ? 0 : sizeof(T) * nnz + sizeof(unsigned) * nnz + sizeof(int) * (P + 1));
     };
+    const bool gtab = gtab_forced || bytes(1, false) > 200 * 1024;
+    const size_t cap = gtab ? SMEM_MAX : 200 * 1024;
     int best = 1;
     for (int t : {4, 2, 1})
-      if (t <= L && bytes(t) <= 200 * 1024 && (long long)nb * ((L + t - 1) / t) >= 128) { best = t; break; }
+      if (t <= L && bytes(t, gtab) <= cap && (long long)nb * ((L + t - 1) / t) >= 128) { best = t; break; }
     *TL = best;
     *NT = (L + best - 1) / best;
     *stage = 0;
-    *sm = bytes(best);
-    if (nods) *nods = 1;
+    *sm = bytes(best, gtab);
+    if (nods) *nods = gtab ? 2 : 1;
     return;
   }
   int best = 1;
@@ -480,6 +489,12 @@ static int launch_apply(sg_handle h, cudaStream_t st, const Op<T>& op, int nb, i
       return false;
     }
   });
+  if (!done && nods == 2) {
+    sgk::k_apply<T, TO, FUSEDP, DOT, sgk::GDynNoDSG><<<grid, 256, sm, st>>>(
+        op, nb, R, TL, NT, nnz, stage, xm, xk, y, add, (T)cm, (T)ck, mask, p0, p1, z, h->ctl.parity, h->ctl.beta,
+        h->ctl.active, h->ctl.part_pq);
+    done = true;
+  }
   if (!done && nods) {
     sgk::k_apply<T, TO, FUSEDP, DOT, sgk::GDynNoDS><<<grid, 256, sm, st>>>(
         op, nb, R, TL, NT, nnz, stage, xm, xk, y, add, (T)cm, (T)ck, mask, p0, p1, z, h->ctl.parity, h->ctl.beta,
@@ -509,7 +524,6 @@ static size_t team_smem(int L, int G) {
   return sizeof(T) * (LL * LS + ((2 * LL + 3) & ~(size_t)3) + (size_t)G * tstride);
 }
 constexpr int TEAM_LS_MAX = 40;  // padded row length of the largest staged factor
-constexpr size_t SMEM_MAX = 232448 - 1024;  // opt-in dynamic shared memory per block (static use below 1 KB)
 
 struct LineCfg {
   bool team;      // warp-team kernel with the factor staged in shared memory
@@ -1622,6 +1636,11 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
     RET(smem_attr(h, sgk::k_apply<float, float, false, false, sgk::GDynNoDS>, lim));
     RET(smem_attr(h, sgk::k_apply<float, float, true, true, sgk::GDynNoDS>, lim));
     RET(smem_attr(h, sgk::k_apply<float, double, false, false, sgk::GDynNoDS>, lim));
+    RET(smem_attr(h, sgk::k_apply<double, double, false, false, sgk::GDynNoDSG>, (int)SMEM_MAX));
+    RET(smem_attr(h, sgk::k_apply<double, double, true, true, sgk::GDynNoDSG>, (int)SMEM_MAX));
+    RET(smem_attr(h, sgk::k_apply<float, float, false, false, sgk::GDynNoDSG>, (int)SMEM_MAX));
+    RET(smem_attr(h, sgk::k_apply<float, float, true, true, sgk::GDynNoDSG>, (int)SMEM_MAX));
+    RET(smem_attr(h, sgk::k_apply<float, double, false, false, sgk::GDynNoDSG>, (int)SMEM_MAX));
 #define SG_ATTR(LSV) \
   RET(smem_attr(h, sgk::k_line_team<float, LSV>, (int)SMEM_MAX));
     SG_ATTR(4) SG_ATTR(8) SG_ATTR(12) SG_ATTR(16) SG_ATTR(20) SG_ATTR(24) SG_ATTR(28) SG_ATTR(32) SG_ATTR(36) SG_ATTR(40)
@@ -1662,6 +1681,11 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
     RET(upload(h, &h->kapE32, e32)); RET(upload(h, &h->kapN32, n32)); RET(upload(h, &h->gk_v32, g32));
   }
   RET(upload(h, &h->gk_ptr, pr.gk_ptr)); RET(upload(h, &h->gk_i, pr.gk_i)); RET(upload(h, &h->gk_j, pr.gk_j));
+  {
+    std::vector<unsigned> pk(pr.gk_i.size());
+    for (size_t e = 0; e < pk.size(); ++e) pk[e] = (unsigned)pr.gk_i[e] | ((unsigned)pr.gk_j[e] << 16);
+    RET(upload(h, &h->gk_pk, pk));
+  }
   RET(upload(h, &h->gk_v, pr.gk_v));
   RET(upload(h, &h->gidx, pr.gidx)); RET(upload(h, &h->cidx, pr.cidx));
   RET(upload(h, &h->owners, pr.owners)); RET(upload(h, &h->cowners, pr.cowners));
@@ -1693,10 +1717,10 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   {
     auto fits_apply = [&](auto tag) {
       using T = decltype(tag);
-      int TL, NT, stage;
+      int TL, NT, stage, nods;
       size_t sm;
-      apply_cfg<T>(pr, pr.nsub, &TL, &NT, &sm, &stage);
-      return sm <= 200 * 1024;
+      apply_cfg<T>(pr, pr.nsub, &TL, &NT, &sm, &stage, &nods);
+      return sm <= (nods == 2 ? SMEM_MAX : 200 * 1024);
     };
     auto fits_line = [&](auto tag) {
       using T = decltype(tag);

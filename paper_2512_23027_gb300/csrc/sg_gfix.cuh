@@ -100,6 +100,7 @@ template <int M_, int P_ORD, int PIN, int OFF_>
 struct Cfg {
   static constexpr bool fixed = true;
   static constexpr bool nods = false;
+  static constexpr bool gglob = false;
   static constexpr int M = M_, p = P_ORD, pin = PIN, OFF = OFF_;
   static constexpr int P = multi(M_, P_ORD).n, PI = multi(M_, PIN).n;
   static constexpr int NNZ = count(M_, P_ORD, PIN);
@@ -203,12 +204,22 @@ __device__ __forceinline__ void gflux(int g, const T* __restrict__ kp, const T* 
 struct GDyn {
   static constexpr bool fixed = false;
   static constexpr bool nods = false;
+  static constexpr bool gglob = false;
   static constexpr int KG = 1;
 };
 // runtime table without the staged edge differences (subdomains too wide for the staging tiles)
 struct GDynNoDS {
   static constexpr bool fixed = false;
   static constexpr bool nods = true;
+  static constexpr bool gglob = false;
+  static constexpr int KG = 1;
+};
+// the same with the triple-product table read from global memory (through L1) instead of staged:
+// input lines and fluxes of a one-line tile of the widest FP64 subdomains fill shared memory alone
+struct GDynNoDSG {
+  static constexpr bool fixed = false;
+  static constexpr bool nods = true;
+  static constexpr bool gglob = true;
   static constexpr int KG = 1;
 };
 

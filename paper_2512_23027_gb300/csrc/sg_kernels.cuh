@@ -71,6 +71,7 @@ struct Op {
   const int* gk_i;
   const int* gk_j;
   const T* gk_v;
+  const unsigned* gk_pk;  // gk_i | gk_j << 16
   int L, nl, P, PI;
   T mass_h;              // h^2 / 24: unit entry of the consistent P1 mass on a right triangle
   FD fP, fPI, fL, fLm1, fLP;  // fast division by P, PI, L, L-1, L*P
@@ -146,10 +147,10 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
   T* xs = reinterpret_cast<T*>(smem_raw);           // [(TL+2)][L][P]
   T* ds = xs + (size_t)(TL + 2) * L * P;            // [edges][PS] differences (runtime table only)
   T* zs = (C::fixed || C::nods) ? ds : ds + (size_t)(TL * (L - 1) + (TL + 1) * L) * PS;   // [edges][PS] fluxes
-  T* gv_s = zs + (size_t)(TL * (L - 1) + (TL + 1) * L) * PS; // [nnz]
-  T* ks = gv_s + nnz;                               // [edges][PIS] edge weights (when staged)
+  T* gv_s = zs + (size_t)(TL * (L - 1) + (TL + 1) * L) * PS; // [nnz] (staged table only)
+  T* ks = gv_s + (C::gglob ? 0 : nnz);              // [edges][PIS] edge weights (when staged)
   unsigned* gpk_s = reinterpret_cast<unsigned*>(stage_kap ? ks + (size_t)(TL * (L - 1) + (TL + 1) * L) * PIS : ks);
-  int* gptr_s = reinterpret_cast<int*>(gpk_s + nnz);  // [P+1]
+  int* gptr_s = reinterpret_cast<int*>(gpk_s + (C::gglob ? 0 : nnz));  // [P+1]
   const long long pb = (long long)b * nl * P;
   const long long so0 = (long long)sub * nl;
   const int nt = blockDim.x;
@@ -165,11 +166,13 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
   SG_MARK(0);
   // phase 0: triple products (values, packed (i, j), per-k ranges) and the block's edge weights
   if constexpr (!C::fixed) {
-  for (int e = threadIdx.x; e < nnz; e += nt) {
-    gv_s[e] = op.gk_v[e];
-    gpk_s[e] = (unsigned)op.gk_i[e] | ((unsigned)op.gk_j[e] << 16);
+  if constexpr (!C::gglob) {
+    for (int e = threadIdx.x; e < nnz; e += nt) {
+      gv_s[e] = op.gk_v[e];
+      gpk_s[e] = op.gk_pk[e];
+    }
+    for (int e = threadIdx.x; e <= P; e += nt) gptr_s[e] = op.gk_ptr[e];
   }
-  for (int e = threadIdx.x; e <= P; e += nt) gptr_s[e] = op.gk_ptr[e];
   if (stage_kap) {
     for (int e = threadIdx.x; e < nE * PI; e += nt) {
       const int ed = fdiv(e, op.fPI), i = e - ed * PI;
@@ -287,6 +290,9 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
   // phase 2b: fluxes.  A work item is (pair of edges, range of output modes); the G entries are
   // warp-uniform (broadcast) and each is applied to both edges of the pair.
   if (ck != T(0)) {
+    const T* gv_t = C::gglob ? op.gk_v : gv_s;
+    const unsigned* gpk_t = C::gglob ? op.gk_pk : gpk_s;
+    const int* gptr_t = C::gglob ? op.gk_ptr : gptr_s;
     const int npair = (nEd + 1) >> 1;
     const int KS = max(1, min(P, (2 * nt + npair - 1) / npair));   // mode ranges per pair
     const int kchunk = (P + KS - 1) / KS;
@@ -349,11 +355,11 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
       const int k0 = krg * kchunk, k1 = min(P, k0 + kchunk);
       for (int kk = k0; kk < k1; ++kk) {
         T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0);
-        const int q1 = gptr_s[kk + 1];
-        int q = gptr_s[kk];
+        const int q1 = gptr_t[kk + 1];
+        int q = gptr_t[kk];
         for (; q + 3 < q1; q += 4) {  // four entries per round: loads issue together
-          const unsigned p0 = gpk_s[q], p1 = gpk_s[q + 1], p2 = gpk_s[q + 2], p3 = gpk_s[q + 3];
-          const T g0 = gv_s[q], g1 = gv_s[q + 1], g2 = gv_s[q + 2], g3 = gv_s[q + 3];
+          const unsigned p0 = gpk_t[q], p1 = gpk_t[q + 1], p2 = gpk_t[q + 2], p3 = gpk_t[q + 3];
+          const T g0 = gv_t[q], g1 = gv_t[q + 1], g2 = gv_t[q + 2], g3 = gv_t[q + 3];
           const unsigned i0 = p0 & 0xffffu, i1 = p1 & 0xffffu, i2 = p2 & 0xffffu, i3 = p3 & 0xffffu;
           const unsigned j0 = p0 >> 16, j1 = p1 >> 16, j2 = p2 >> 16, j3 = p3 >> 16;
           a0 += (kap0[i0] * g0) * D0(j0);
@@ -366,8 +372,8 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
           b1 += (kap1[i3] * g3) * D1(j3);
         }
         for (; q < q1; ++q) {
-          const unsigned pk = gpk_s[q];
-          const T g = gv_s[q];
+          const unsigned pk = gpk_t[q];
+          const T g = gv_t[q];
           const unsigned i = pk & 0xffffu, j = pk >> 16;
           a0 += (kap0[i] * g) * D0(j);
           a1 += (kap1[i] * g) * D1(j);

@@ -231,15 +231,17 @@ def _run_env(lib, prob, precision, steps, env):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_wide_subdomain_kernel_variants(lib, precision):
+@pytest.mark.parametrize("nods", ["1", "2"])
+def test_wide_subdomain_kernel_variants(lib, precision, nods):
     """The kernel variants for subdomains too wide for the shared-memory tiles (runtime-table apply
-    that forms the edge differences on the fly; line sweep reading the symmetric factor from global
-    memory, column-wise) forced on a small problem give the fields of the default kernels: bitwise
-    up to the summation order of the factor rows, i.e. within 1e-12 in FP64 and within the solver
+    that forms the edge differences on the fly, with the triple-product table staged (1) or read
+    from global memory (2); line sweep reading the symmetric factor from global memory,
+    column-wise) forced on a small problem give the fields of the default kernels: bitwise up to
+    the summation order of the factor rows, i.e. within 1e-12 in FP64 and within the solver
     tolerance in mixed precision."""
     prob = w.config("small")
     ua, ia, _ = _run_env(lib, prob, precision, 3, {})
-    ub, ib, rb = _run_env(lib, prob, precision, 3, {"SG_FORCE_NODS": "1", "SG_FORCE_GLINE": "1",
+    ub, ib, rb = _run_env(lib, prob, precision, 3, {"SG_FORCE_NODS": nods, "SG_FORCE_GLINE": "1",
                                                     "SG_NO_MMA": "1", "SG_NO_GFIX": "1"})
     err = rel(ub, ua)
     print(f"precision {precision}: forced wide-subdomain variants vs default rel diff {err:.3e}")
@@ -249,12 +251,18 @@ def test_wide_subdomain_kernel_variants(lib, precision):
 
 
 @pytest.mark.slow
-def test_widest_batch_subdomains_converge(lib):
-    """Batch instances whose 121 x 121-node subdomains exceed the shared-memory tiles (240^2 grid,
-    2 x 2 subdomains) run with the wide-subdomain variants: mixed precision converges every step and
-    agrees with the FP64 solver on the same GPU to a small multiple of the tolerance."""
+@pytest.mark.parametrize("which", ["240^2 P=10", "256^2 P=35"])
+def test_widest_batch_subdomains_converge(lib, which):
+    """Batch instances whose subdomains exceed the shared-memory tiles (240^2 grid, 2 x 2
+    subdomains of 121 x 121 nodes, P = 10; 256^2 grid, 2 x 2 subdomains of 129 x 129 nodes, P = 35,
+    where the FP64 apply reads the triple-product table from global memory) run with the
+    wide-subdomain variants: mixed precision converges every step and agrees with the FP64 solver
+    on the same GPU to a small multiple of the tolerance."""
     from paper_2512_23027_gb300.binding import SG_FP64, SG_MIXED
-    prob = [p for p in w.batch_problems(8) if p.N // p.s + 1 > 81][0]
+    if which == "240^2 P=10":
+        prob = [p for p in w.batch_problems(8) if p.N // p.s + 1 > 81][0]
+    else:
+        prob = [p for p in w.batch_problems(256) if p.N == 256 and p.s == 2 and p.P == 35][0]
     um, im, rm = _run_env(lib, prob, SG_MIXED, 2, {})
     ud, idd, rd = _run_env(lib, prob, SG_FP64, 2, {})
     err = rel(um, ud)
