@@ -140,7 +140,15 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
   const int nlin = min(TL, L - lj0);  // owned lines
   pdl_trigger();
   pdl_wait();
-  if (FUSEDP && !active[b]) return;
+  // the fused-CG scalars in one round trip
+  int act_b = 1, par = 0;
+  double bet_d = 0.0;
+  if (FUSEDP) {
+    act_b = active[b];
+    par = *parity;
+    bet_d = beta[b];
+  }
+  if (FUSEDP && !act_b) return;
   const int sub = b / R;
   const int nE = nlin * (L - 1), nNr = nlin + 1;
   const int nEd = nE + nNr * L;                     // edges of the block: horizontal then vertical
@@ -158,10 +166,9 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
   T* pnew = nullptr;
   T bet = T(0);
   if (FUSEDP) {
-    const int par = *parity;
     pold = par ? pbuf1 : pbuf0;
     pnew = par ? pbuf0 : pbuf1;
-    bet = (T)beta[b];
+    bet = (T)bet_d;
   }
   SG_MARK(0);
   // phase 0: triple products (values, packed (i, j), per-k ranges) and the block's edge weights
@@ -1817,17 +1824,19 @@ __global__ void __launch_bounds__(256) k_cg_pack(int L, int nl, int P, int NC, i
   const int b = blockIdx.x / NC, c = blockIdx.x % NC;
   pdl_trigger();
   pdl_wait();
-  if (!init && !ctl.active[b]) return;
-  const int LL = L * L;
-  float alpha = 0.f;
-  const float* pc = nullptr;
+  // control scalars and the p.q partials of the problem in one round trip (each warp sums the
+  // partials in index order from shuffles, as a sequential loop would); the chunk's data loads
+  // that do not depend on them are issued before the activity test
+  const int lane = threadIdx.x & 31;
+  int actv = 1, par = 0;
+  double rzb = 0.0, vq = 0.0;
   if (!init) {
-    double pq = 0.0;
-    for (int t = 0; t < NT; ++t) pq += ctl.part_pq[(long long)b * NT + t];
-    const double al = (pq > 0.0 && isfinite(pq)) ? ctl.rz[b] / pq : 0.0;
-    alpha = isfinite(al) ? (float)al : 0.f;
-    pc = (*ctl.parity) ? pbuf0 : pbuf1;
+    actv = ctl.active[b];
+    par = *ctl.parity;
+    rzb = ctl.rz[b];
+    vq = lane < NT ? ctl.part_pq[(long long)b * NT + lane] : 0.0;
   }
+  const int LL = L * L;
   const long long base = (long long)b * nl * P;
   const int n0 = c * 64;
   // values of the chunk's nodes (contiguous); the last chunks of the padded Kp rows may hold none
@@ -1836,24 +1845,42 @@ __global__ void __launch_bounds__(256) k_cg_pack(int L, int nl, int P, int NC, i
   const bool vec = ((nl * P) & 3) == 0 && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(r) |
                                             reinterpret_cast<uintptr_t>(q) | reinterpret_cast<uintptr_t>(pbuf0) |
                                             reinterpret_cast<uintptr_t>(pbuf1)) & 15) == 0;
-  if (vec) {
-    // 16-byte vectors; every load of a thread is issued before its stores (pc may alias nothing,
-    // but the compiler cannot know)
-    const int n4 = nv >> 2;
-    constexpr int U = 2;
-    float4 rv[U], xv[U], pv[U], qv[U];
+  constexpr int U = 2;
+  float4 rv[U], xv[U], pv[U], qv[U];
+  const int n4 = vec ? nv >> 2 : 0;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int e4 = threadIdx.x + u * 256;
+    if (e4 < n4) {
+      rv[u] = reinterpret_cast<const float4*>(r + o0)[e4];
+      if (!init) {
+        xv[u] = reinterpret_cast<const float4*>(x + o0)[e4];
+        qv[u] = reinterpret_cast<const float4*>(q + o0)[e4];
+      }
+    }
+  }
+  float alpha = 0.f;
+  const float* pc = nullptr;
+  if (!init) {
+    double pq = 0.0;
+    for (int t0 = 0; t0 < NT; t0 += 32) {
+      if (t0 > 0) vq = t0 + lane < NT ? ctl.part_pq[(long long)b * NT + t0 + lane] : 0.0;
+      const int n = min(32, NT - t0);
+      for (int t = 0; t < n; ++t) pq += __shfl_sync(0xffffffffu, vq, t);
+    }
+    const double al = (pq > 0.0 && isfinite(pq)) ? rzb / pq : 0.0;
+    alpha = isfinite(al) ? (float)al : 0.f;
+    pc = par ? pbuf0 : pbuf1;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int e4 = threadIdx.x + u * 256;
-      if (e4 < n4) {
-        rv[u] = reinterpret_cast<const float4*>(r + o0)[e4];
-        if (!init) {
-          xv[u] = reinterpret_cast<const float4*>(x + o0)[e4];
-          pv[u] = reinterpret_cast<const float4*>(pc + o0)[e4];
-          qv[u] = reinterpret_cast<const float4*>(q + o0)[e4];
-        }
-      }
+      if (e4 < n4) pv[u] = reinterpret_cast<const float4*>(pc + o0)[e4];
     }
+  }
+  if (!actv) return;
+  if (vec) {
+    // 16-byte vectors; every load of a thread is issued before its stores (pc may alias nothing,
+    // but the compiler cannot know)
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int e4 = threadIdx.x + u * 256;
@@ -1974,6 +2001,19 @@ __global__ void __launch_bounds__(256, 1) k_pre_mma(const __grid_constant__ CUte
   if (threadIdx.x == 32)
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&tmA)) : "memory");
   pdl_wait();
+  // the tile's residual (rows x P contiguous values, at most NB / 2 per thread) is loaded before the
+  // product, so that its latency overlaps the pipeline instead of following it
+  constexpr int EPT = MMA_M * NB / 256;
+  const int m0 = tile * MMA_M;
+  const int rows = min(MMA_M, L * L - m0);
+  const int cnt = rows > 0 ? rows * P : 0;
+  const long long o = (long long)b * nl * P + (long long)m0 * P;
+  float rpre[EPT];
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    const int e = threadIdx.x + u * 256;
+    rpre[u] = e < cnt ? r[o + e] : 0.f;
+  }
   const bool act = init ? true : (ctl.active[b] != 0);
   double s_rz = 0.0, s_rr = 0.0;
   if (!act) mma_tile_end<NB, TERMS, NST>(bars, tmem, s_flags);
@@ -1993,16 +2033,14 @@ __global__ void __launch_bounds__(256, 1) k_pre_mma(const __grid_constant__ CUte
       for (int k = 0; k < NB; ++k) zr[k] = v[k];
     }
     mma_tile_end<NB, TERMS, NST>(bars, tmem, s_flags);  // contains __syncthreads
-    const int m0 = tile * MMA_M;
-    const int rows = min(MMA_M, L * L - m0);
-    if (rows > 0) {
-      const long long o = (long long)b * nl * P + (long long)m0 * P;
-      const int cnt = rows * P;
-      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int e = threadIdx.x + u * 256;
+      if (e < cnt) {
         const int rr_ = e / P, k = e - rr_ * P;
         const float zv = zt[rr_ * (NB + 1) + k];
         z[o + e] = zv;
-        const double rv = (double)r[o + e];
+        const double rv = (double)rpre[u];
         s_rz += rv * (double)zv;
         s_rr += rv * rv;
       }
