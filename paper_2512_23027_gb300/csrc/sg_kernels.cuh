@@ -1824,17 +1824,21 @@ __global__ void __launch_bounds__(256) k_cg_pack(int L, int nl, int P, int NC, i
   const int b = blockIdx.x / NC, c = blockIdx.x % NC;
   pdl_trigger();
   pdl_wait();
-  // control scalars and the p.q partials of the problem in one round trip (each warp sums the
-  // partials in index order from shuffles, as a sequential loop would); the chunk's data loads
-  // that do not depend on them are issued before the activity test
-  const int lane = threadIdx.x & 31;
+  // control scalars and the p.q partials of the problem in one round trip; the chunk's data loads
+  // that do not depend on them are issued before the activity test.  alpha is formed in FP64 by
+  // warp 0 alone (partials summed in index order from shuffles, as a sequential loop would) and
+  // broadcast through shared memory: FP64 work is slow on this GPU.
+  __shared__ float s_alpha;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int actv = 1, par = 0;
   double rzb = 0.0, vq = 0.0;
   if (!init) {
     actv = ctl.active[b];
     par = *ctl.parity;
-    rzb = ctl.rz[b];
-    vq = lane < NT ? ctl.part_pq[(long long)b * NT + lane] : 0.0;
+    if (warp == 0) {
+      rzb = ctl.rz[b];
+      vq = lane < NT ? ctl.part_pq[(long long)b * NT + lane] : 0.0;
+    }
   }
   const int LL = L * L;
   const long long base = (long long)b * nl * P;
@@ -1862,22 +1866,28 @@ __global__ void __launch_bounds__(256) k_cg_pack(int L, int nl, int P, int NC, i
   float alpha = 0.f;
   const float* pc = nullptr;
   if (!init) {
-    double pq = 0.0;
-    for (int t0 = 0; t0 < NT; t0 += 32) {
-      if (t0 > 0) vq = t0 + lane < NT ? ctl.part_pq[(long long)b * NT + t0 + lane] : 0.0;
-      const int n = min(32, NT - t0);
-      for (int t = 0; t < n; ++t) pq += __shfl_sync(0xffffffffu, vq, t);
-    }
-    const double al = (pq > 0.0 && isfinite(pq)) ? rzb / pq : 0.0;
-    alpha = isfinite(al) ? (float)al : 0.f;
     pc = par ? pbuf0 : pbuf1;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int e4 = threadIdx.x + u * 256;
       if (e4 < n4) pv[u] = reinterpret_cast<const float4*>(pc + o0)[e4];
     }
+    if (warp == 0) {
+      double pq = 0.0;
+      for (int t0 = 0; t0 < NT; t0 += 32) {
+        if (t0 > 0) vq = t0 + lane < NT ? ctl.part_pq[(long long)b * NT + t0 + lane] : 0.0;
+        const int n = min(32, NT - t0);
+        for (int t = 0; t < n; ++t) pq += __shfl_sync(0xffffffffu, vq, t);
+      }
+      const double al = (pq > 0.0 && isfinite(pq)) ? rzb / pq : 0.0;
+      if (lane == 0) s_alpha = isfinite(al) ? (float)al : 0.f;
+    }
   }
-  if (!actv) return;
+  if (!actv) return;  // uniform over the block
+  if (!init) {
+    __syncthreads();
+    alpha = s_alpha;
+  }
   if (vec) {
     // 16-byte vectors; every load of a thread is issued before its stores (pc may alias nothing,
     // but the compiler cannot know)
