@@ -108,6 +108,40 @@ typedef struct {
                               the FP32 operator apply, 0 for the runtime-table kernel          */
 } sg_sizes;
 
+/* Launch plan of the per-step kernels for one problem, as sg_setup chooses it before any
+ * autotuning (sg_plan_query).  Index [0]: the FP64 kernels; [1]: the FP32 kernels (used by
+ * SG_MIXED). */
+typedef struct {
+  int L, P, P_in, nsub, nnz_G;  /* subdomain nodes per side, PCE terms, nonzero triple products */
+  int apply_variant[2];     /* SG operator apply (Sec. 4, Eq. stoksub): 0 triple-product table
+                               staged in shared memory, 1 the same without staged edge differences,
+                               2 table read from global memory, 3 table compiled into the kernel  */
+  int apply_lines[2];       /* grid lines per block                                               */
+  int apply_tiles[2];       /* blocks per subdomain problem                                       */
+  long long apply_smem[2];  /* dynamic shared memory per block, bytes                             */
+  int line_kind[2];         /* mean-operator line solve: 0 block kernel with the factor staged,
+                               1 warp-team kernel, 2 factor and residual read from global memory  */
+  int line_modes[2];        /* PCE modes per block                                                */
+  int line_groups[2];       /* blocks per subdomain problem                                       */
+  int line_block[2][3];     /* block shape                                                        */
+  long long line_smem[2];   /* dynamic shared memory per block, bytes                             */
+  int mma;                  /* 1: dense BF16 inverse of the mean operator on the tensor cores    */
+  int mma_kp;               /* rows of that inverse per subdomain, L^2 rounded up to 128          */
+  int mma_nc, mma_mt;       /* 64-node chunks and 128-row tiles per subdomain                     */
+  int mma_nb;               /* PCE rows of the residual image (16 or 32)                          */
+  long long mma_smem;       /* dynamic shared memory of the product kernel, bytes                 */
+  int fits;                 /* 1 when the kernels of this precision fit their shared-memory
+                               limits, i.e. sg_setup would not return SG_ENOTSUP for the size     */
+} sg_plan;
+
+/* Host-only query: builds the problem on the host (no device memory, no CUDA call; works without
+ * a GPU) and writes the launch plan sg_setup would use to *out.  params->precision selects the
+ * kernels that `fits` covers; the source is irrelevant to the plan and not taken.  Errors as
+ * sg_setup: SG_EINVAL for invalid sizes or parameters (message in sg_last_error(NULL)),
+ * SG_ENOTSUP for subdomains wider than 255 cells or fewer than 2 x 2 subdomains. */
+int sg_plan_query(const sg_grid* grid, const sg_kl* kl, const sg_pce* pce, const sg_params* params,
+                  sg_plan* out);
+
 /* Build the solver: KL eigenpairs (analytic, separable exponential kernel), log-normal PCE of
  * c_s at element centroids (Eqs. c0pce, LNL0), Hermite triple products G_ijk, subdomain
  * operators, mean-operator line factorisations, coarse basis and F_cc^{-1} (Eq. Fcc_2), and the

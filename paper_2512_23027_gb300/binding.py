@@ -59,6 +59,21 @@ class Sizes(C.Structure):
                 ("device_bytes", C.c_longlong), ("fp32_precond", C.c_int), ("compiled_apply", C.c_int)]
 
 
+class Plan(C.Structure):
+    _fields_ = [("L", C.c_int), ("P", C.c_int), ("P_in", C.c_int), ("nsub", C.c_int), ("nnz_G", C.c_int),
+                ("apply_variant", C.c_int * 2), ("apply_lines", C.c_int * 2), ("apply_tiles", C.c_int * 2),
+                ("apply_smem", C.c_longlong * 2), ("line_kind", C.c_int * 2), ("line_modes", C.c_int * 2),
+                ("line_groups", C.c_int * 2), ("line_block", (C.c_int * 3) * 2), ("line_smem", C.c_longlong * 2),
+                ("mma", C.c_int), ("mma_kp", C.c_int), ("mma_nc", C.c_int), ("mma_mt", C.c_int),
+                ("mma_nb", C.c_int), ("mma_smem", C.c_longlong), ("fits", C.c_int)]
+
+
+def _plain(v):
+    if isinstance(v, C.Array):
+        return [_plain(x) for x in v]
+    return v
+
+
 _LIB = None
 
 
@@ -88,6 +103,8 @@ def load_library(path: Optional[str] = None):
     lib.sg_set_state.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
     lib.sg_step_host.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, P(Stats)]
     lib.sg_get_sizes.argtypes = [C.c_void_p, P(Sizes)]
+    lib.sg_plan_query.argtypes = [P(Grid), P(KL), P(PCE), P(Params), P(Plan)]
+    lib.sg_plan_query.restype = C.c_int
     lib.sg_get_iters.argtypes = [C.c_void_p, P(C.c_int), D, C.c_int]
     lib.sg_destroy.argtypes = [C.c_void_p]
     lib.sg_set_enqueue_mode.argtypes = [C.c_void_p, C.c_int]
@@ -255,6 +272,19 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+def plan_query(prob, precision: int = SG_FP64) -> dict:
+    """Launch plan of the per-step kernels for `prob` (host-only; no GPU needed), as a dict of the
+    sg_plan fields; two-element lists are [FP64 kernels, FP32 kernels]."""
+    lib = load_library()
+    grid, kl, pce = Grid(prob.N, prob.s, prob.s), KL(prob.M, prob.sigma, prob.bx, prob.by, prob.g0), PCE(prob.p, prob.p_in)
+    prm = Params(prob.dt, prob.tol, prob.alpha0, prob.alpha1, prob.max_iter, precision, SG_WARM_PREV, 0.0, 0, 0, 0, 0.0)
+    out = Plan()
+    rc = lib.sg_plan_query(C.byref(grid), C.byref(kl), C.byref(pce), C.byref(prm), C.byref(out))
+    if rc != 0:
+        raise SGError(rc, lib.sg_last_error(None).decode())
+    return {f: _plain(getattr(out, f)) for f, _ in Plan._fields_}
 
 
 def solve_batch(solvers: Sequence[Solver], nsteps: int):

@@ -1163,9 +1163,13 @@ static int build_line_factors(sg_handle h) {
 // map.  Used when the subdomains have at most MMA_LMAX nodes per side and P <= 32; larger subdomains
 // keep the line-sweep preconditioner (a dense inverse would grow as L^4).
 constexpr int MMA_LMAX = 40;
+static bool mma_eligible(const sgh::Problem& pr, int precision) {
+  return precision == SG_MIXED && pr.L <= MMA_LMAX && pr.P <= 32 && !std::getenv("SG_NO_MMA");
+}
+
 static int build_mma_precond(sg_handle h) {
   const auto& pr = h->pr;
-  if (h->precision != SG_MIXED || pr.L > MMA_LMAX || pr.P > 32 || std::getenv("SG_NO_MMA")) return SG_OK;
+  if (!mma_eligible(pr, h->precision)) return SG_OK;
   const int L = pr.L, LL = L * L;
   h->Kp = (LL + sgk::MMA_M - 1) / sgk::MMA_M * sgk::MMA_M;
   h->NC = h->Kp / sgk::MMA_KC;
@@ -1562,6 +1566,46 @@ static int autotune(sg_handle h) {
   return SG_OK;
 }
 
+// Compiled triple-product table matching the problem's PCE sizes, or -1 (SG_NO_GFIX forces -1).
+static int select_gfix(const sgh::Problem& pr) {
+  int id = -1;
+  for (int i = 0; i < sgk::gfix::NCFG && id < 0; ++i)
+    if (with_gfix(i, false, [&](auto c) { return gfix_matches<decltype(c)>(pr); })) id = i;
+  return std::getenv("SG_NO_GFIX") ? -1 : id;
+}
+
+// Whether the per-step kernels of a precision fit their shared-memory limits at this subdomain size
+// (the FP64 apply always runs; the line kernel and the FP32 apply of the precision in use).
+static bool tiles_fit(const sgh::Problem& pr, int precision) {
+  auto fits_apply = [&](auto tag) {
+    using T = decltype(tag);
+    int TL, NT, stage, nods;
+    size_t sm;
+    apply_cfg<T>(pr, pr.nsub, &TL, &NT, &sm, &stage, &nods);
+    return sm <= (nods == 2 ? SMEM_MAX : 200 * 1024);
+  };
+  auto fits_line = [&](auto tag) {
+    using T = decltype(tag);
+    const LineCfg lc = line_cfg<T>(pr, pr.nsub);
+    return lc.smem <= (lc.team ? SMEM_MAX : 200 * 1024);
+  };
+  return fits_apply(double{}) &&
+         (precision == SG_MIXED ? (fits_apply(float{}) && fits_line(float{})) : fits_line(double{}));
+}
+
+// Problem construction and the size limits shared by sg_setup and sg_plan_query.
+static int build_checked(sgh::Problem& pr, std::string& err, const sg_grid* grid, const sg_kl* kl,
+                         const sg_pce* pce, const sg_params* prm, const sgh::SourceDesc& sd) {
+  if (prm->precision != SG_FP64 && prm->precision != SG_MIXED) { err = "precision"; return SG_EINVAL; }
+  std::string msg = sgh::build_problem(pr, grid->N, grid->nsub_x, grid->nsub_y, kl->M, kl->sigma, kl->bx,
+                                       kl->by, kl->g0, pce->p, pce->p_in, prm->dt, prm->alpha0, prm->alpha1, sd);
+  if (!msg.empty()) { err = msg; return SG_EINVAL; }
+  if (pr.L > 256 || pr.L * 2 > 1024) { err = "subdomains wider than 255 cells are not supported"; return SG_ENOTSUP; }
+  if (pr.nsub < 2) { err = "at least 2 x 2 subdomains are required"; return SG_ENOTSUP; }
+  pr.gfix = select_gfix(pr);
+  return SG_OK;
+}
+
 static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const sg_pce* pce,
                       const sg_params* prm, const sg_source* src) {
   sgh::SourceDesc sd{src ? src->kind : 0, src ? src->x0 : 0.5, src ? src->y0 : 0.5,
@@ -1572,13 +1616,8 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
     h->err = "ricker source outside the unit square or non-positive frequency";
     return SG_EINVAL;
   }
-  if (prm->precision != SG_FP64 && prm->precision != SG_MIXED) { h->err = "precision"; return SG_EINVAL; }
-  std::string msg = sgh::build_problem(h->pr, grid->N, grid->nsub_x, grid->nsub_y, kl->M, kl->sigma, kl->bx,
-                                       kl->by, kl->g0, pce->p, pce->p_in, prm->dt, prm->alpha0, prm->alpha1, sd);
-  if (!msg.empty()) { h->err = msg; return SG_EINVAL; }
+  RET(build_checked(h->pr, h->err, grid, kl, pce, prm, sd));
   auto& pr = h->pr;
-  if (pr.L > 256 || pr.L * 2 > 1024) { h->err = "subdomains wider than 255 cells are not supported"; return SG_ENOTSUP; }
-  if (pr.nsub < 2) { h->err = "at least 2 x 2 subdomains are required"; return SG_ENOTSUP; }
   h->precision = prm->precision;
   h->warm = prm->warm;
   h->tol = prm->tol > 0 ? prm->tol : 1e-8;
@@ -1649,10 +1688,6 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   // compiled triple-product table for this PCE size (values into constant memory; the same
   // values for every handle of that size, so concurrent handles may share the slot)
   {
-    pr.gfix = -1;
-    for (int id = 0; id < sgk::gfix::NCFG && pr.gfix < 0; ++id)
-      if (with_gfix(id, false, [&](auto c) { return gfix_matches<decltype(c)>(pr); })) pr.gfix = id;
-    if (std::getenv("SG_NO_GFIX")) pr.gfix = -1;
     if (pr.gfix >= 0) {
       const int rc = with_gfix(pr.gfix, (int)SG_EINVAL, [&](auto c) -> int {
         using C = decltype(c);
@@ -1714,25 +1749,9 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   RET(ensure_ws<float>(h, pr.nsub));
   CKL();
   // shared-memory fit of the hot kernels at this subdomain size (per precision in use)
-  {
-    auto fits_apply = [&](auto tag) {
-      using T = decltype(tag);
-      int TL, NT, stage, nods;
-      size_t sm;
-      apply_cfg<T>(pr, pr.nsub, &TL, &NT, &sm, &stage, &nods);
-      return sm <= (nods == 2 ? SMEM_MAX : 200 * 1024);
-    };
-    auto fits_line = [&](auto tag) {
-      using T = decltype(tag);
-      const LineCfg lc = line_cfg<T>(pr, pr.nsub);
-      return lc.smem <= (lc.team ? SMEM_MAX : 200 * 1024);
-    };
-    const bool ok = fits_apply(double{}) && (h->precision == SG_MIXED ? (fits_apply(float{}) && fits_line(float{}))
-                                                                        : fits_line(double{}));
-    if (!ok) {
-      h->err = "subdomain too large for the shared-memory tiles of this build (H = " + std::to_string(pr.H) + " cells)";
-      return SG_ENOTSUP;
-    }
+  if (!tiles_fit(pr, h->precision)) {
+    h->err = "subdomain too large for the shared-memory tiles of this build (H = " + std::to_string(pr.H) + " cells)";
+    return SG_ENOTSUP;
   }
   RET(build_line_factors(h));
   RET(build_mma_precond(h));
@@ -2030,6 +2049,45 @@ int sg_get_sizes(sg_handle h, sg_sizes* out) {
   out->n_gamma = pr.nG; out->n_corner = pr.nC; out->n_sub_nodes = pr.nl; out->device_bytes = h->bytes;
   out->fp32_precond = h->mma ? 1 : 0;
   out->compiled_apply = gfix_for<float>(pr) >= 0 ? 1 : 0;
+  return SG_OK;
+}
+
+int sg_plan_query(const sg_grid* grid, const sg_kl* kl, const sg_pce* pce, const sg_params* params, sg_plan* out) {
+  if (!grid || !kl || !pce || !params || !out) { g_setup_err = "null argument"; return SG_EINVAL; }
+  sgh::Problem pr;
+  const sgh::SourceDesc sd{0, 0.5, 0.5, 0.05, 10.0, 1.0};
+  const int rc = build_checked(pr, g_setup_err, grid, kl, pce, params, sd);
+  if (rc != SG_OK) return rc;
+  sg_plan p{};
+  p.L = pr.L; p.P = pr.P; p.P_in = pr.PI; p.nsub = pr.nsub; p.nnz_G = (int)pr.gk_v.size();
+  auto fill = [&](auto tag, int i) {
+    using T = decltype(tag);
+    int TL, NT, stage, nods;
+    size_t sm;
+    apply_cfg<T>(pr, pr.nsub, &TL, &NT, &sm, &stage, &nods);
+    p.apply_variant[i] = gfix_for<T>(pr) >= 0 ? 3 : nods;
+    p.apply_lines[i] = TL;
+    p.apply_tiles[i] = NT;
+    p.apply_smem[i] = (long long)sm;
+    const LineCfg lc = line_cfg<T>(pr, pr.nsub);
+    p.line_kind[i] = lc.team ? 1 : lc.gs ? 2 : 0;
+    p.line_modes[i] = lc.G;
+    p.line_groups[i] = lc.NG;
+    p.line_block[i][0] = (int)lc.block.x; p.line_block[i][1] = (int)lc.block.y; p.line_block[i][2] = (int)lc.block.z;
+    p.line_smem[i] = (long long)lc.smem;
+  };
+  fill(double{}, 0);
+  fill(float{}, 1);
+  if (mma_eligible(pr, params->precision)) {
+    p.mma = 1;
+    p.mma_kp = (pr.L * pr.L + sgk::MMA_M - 1) / sgk::MMA_M * sgk::MMA_M;
+    p.mma_nc = p.mma_kp / sgk::MMA_KC;
+    p.mma_mt = p.mma_kp / sgk::MMA_M;
+    p.mma_nb = pr.P <= 16 ? 16 : 32;
+    p.mma_smem = p.mma_nb == 16 ? sgk::PreShape<16, 2>::SMEM : sgk::PreShape<32, 2>::SMEM;
+  }
+  p.fits = tiles_fit(pr, params->precision) ? 1 : 0;
+  *out = p;
   return SG_OK;
 }
 
