@@ -108,9 +108,10 @@ typedef struct {
                               the FP32 operator apply, 0 for the runtime-table kernel          */
 } sg_sizes;
 
-/* Launch plan of the per-step kernels for one problem, as sg_setup chooses it before any
- * autotuning (sg_plan_query).  Index [0]: the FP64 kernels; [1]: the FP32 kernels (used by
- * SG_MIXED). */
+/* Launch plan of the per-step kernels for one problem, as sg_setup chooses it (sg_plan_query).
+ * Tile choices that an autotuned sg_setup earlier in the process recorded for the same sizes are
+ * taken into account, as sg_setup does.  Index [0]: the FP64 kernels; [1]: the FP32 kernels (used
+ * by SG_MIXED). */
 typedef struct {
   int L, P, P_in, nsub, nnz_G;  /* subdomain nodes per side, PCE terms, nonzero triple products */
   int apply_variant[2];     /* SG operator apply (Sec. 4, Eq. stoksub): 0 triple-product table
