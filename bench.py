@@ -37,6 +37,17 @@ KERNEL_SOURCES = ("sg_kernels.cuh", "sg_mma.cuh", "sg_gfix.cuh")
 L2_FLUSH_BYTES = 256 << 20
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """Largest value of x over the ranks of the default process group (x itself without one):
+    every replica-parallel duration is reported as the slowest rank's."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload_config(prob, precision):
     return {"workload": prob.name, "grid": f"{prob.N}x{prob.N}", "nodes": (prob.N + 1) ** 2,
             "subdomains": f"{prob.s}x{prob.s}", "kl_M": prob.M, "pce_order": prob.p, "pce_terms": prob.P,
@@ -313,11 +324,7 @@ def main():
     barrier()
     clocks = sampler.stop()
     launches = s.launch_count() - l0
-    tmax = ms
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax = float(t.item())
+    tmax = max_over_ranks(ms, dist, "cuda")
     value = world * K / (tmax / 1e3)
 
     # ---- dominant kernel: CUDA-event timing of each of its launches (host-driven enqueue) ----
@@ -387,7 +394,7 @@ def main():
             for fi, v in fidx:
                 fa[k, fi] = r * v
         se.step_host(K, fh, uh)
-        e2e_s = time.perf_counter() - t0
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         e2e = {"value": world * K / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": nf * 8,
                "d2h_bytes_per_step": nf * 8,
                "note": "sg_step_host: per step H2D of the nodal load, one SG-DD step, D2H of the mean field"}
@@ -400,10 +407,13 @@ def main():
     K64 = max(1, min(args.fp64_steps, K))
     ms64, its64, inner64 = timed(s64, K64)
     barrier()
+    ms64 = max_over_ranks(ms64, dist, "cuda")
     s64.close()
     s.close()
 
     if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
         return 0
     cpu = finish_cpu_baseline(cpu_proc, args.config, args.cpu_steps, timeout=900)
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": W,
