@@ -402,6 +402,7 @@ static int smem_attr(sg_handle h, void (*f)(A...), int lim) {
 
 // apply tile configuration: lines per block, dynamic shared memory, kappa staging
 constexpr size_t SMEM_MAX = 232448 - 1024;  // opt-in dynamic shared memory per block (static use below 1 KB)
+constexpr size_t SMEM_TILE = 200 * 1024;    // dynamic shared memory the tile kernels are opted into
 
 template <typename T>
 static void apply_cfg(const sgh::Problem& pr, int nb, int* TL, int* NT, size_t* sm, int* stage, int* nods = nullptr) {
@@ -433,7 +434,7 @@ static void apply_cfg(const sgh::Problem& pr, int nb, int* TL, int* NT, size_t* 
   };
   auto kap = [&](int t) { return sizeof(T) * edges(t) * PIS; };
   const char* force = std::getenv("SG_FORCE_NODS");
-  if (base(1) > 200 * 1024 || force) {
+  if (base(1) > SMEM_TILE || force) {
     // widest subdomains: no staged edge differences (formed on the fly), no staged weights; when
     // even a one-line tile with the staged table exceeds 200 KB, the table is read from global
     // memory and the tile may use the whole opt-in shared memory (SG_FORCE_NODS=2 forces this)
@@ -442,8 +443,8 @@ static void apply_cfg(const sgh::Problem& pr, int nb, int* TL, int* NT, size_t* 
       return sizeof(T) * ((size_t)(t + 2) * L * P + edges(t) * PS) + 16 +
              (gtab ? 0 : sizeof(T) * nnz + sizeof(unsigned) * nnz + sizeof(int) * (P + 1));
     };
-    const bool gtab = gtab_forced || bytes(1, false) > 200 * 1024;
-    const size_t cap = gtab ? SMEM_MAX : 200 * 1024;
+    const bool gtab = gtab_forced || bytes(1, false) > SMEM_TILE;
+    const size_t cap = gtab ? SMEM_MAX : SMEM_TILE;
     int best = 1;
     for (int t : {4, 2, 1})
       if (t <= L && bytes(t, gtab) <= cap && (long long)nb * ((L + t - 1) / t) >= 128) { best = t; break; }
@@ -460,11 +461,11 @@ static void apply_cfg(const sgh::Problem& pr, int nb, int* TL, int* NT, size_t* 
     const long long blocks = (long long)nb * ((L + t - 1) / t);
     if (base(t) + kap(t) <= 110 * 1024 && (blocks >= 128 || t == 1)) { best = t; break; }
   }
-  while (best > 1 && base(best) > 200 * 1024) best /= 2;
+  while (best > 1 && base(best) > SMEM_TILE) best /= 2;
   if (const int t = tuned(0, sizeof(T), pr, nb)) best = t;
   *TL = best;
   *NT = (L + best - 1) / best;
-  *stage = base(best) + kap(best) <= 200 * 1024 ? 1 : 0;
+  *stage = base(best) + kap(best) <= SMEM_TILE ? 1 : 0;
   *sm = base(best) + (*stage ? kap(best) : 0);
 }
 
@@ -562,12 +563,12 @@ static LineCfg line_cfg(const sgh::Problem& pr, int nb_hint) {
   int g = sizeof(T) == 8 ? 2 : (P + 1) / 2;
   if (const int t = tuned(1, sizeof(T), pr, nb_hint)) g = t;
   g = std::max(1, std::min(g, 1024 / L));
-  while (g > 1 && line_smem<T>(L, g) > 200 * 1024) --g;
-  c.gs = line_smem<T>(L, g) > 200 * 1024 || std::getenv("SG_FORCE_GLINE");
+  while (g > 1 && line_smem<T>(L, g) > SMEM_TILE) --g;
+  c.gs = line_smem<T>(L, g) > SMEM_TILE || std::getenv("SG_FORCE_GLINE");
   if (c.gs) {  // factor and residual from global memory: solution slice only
     auto gsm = [&](int gg) { return sizeof(T) * ((size_t)L * L * gg + (size_t)L * gg); };
     g = std::max(1, std::min(g, 1024 / L));
-    while (g > 1 && gsm(g) > 200 * 1024) --g;
+    while (g > 1 && gsm(g) > SMEM_TILE) --g;
   }
   // rows padded so that the block is whole warps; keep the block within 1024 threads
   auto rows_for = [&](int gg) {
@@ -1494,7 +1495,7 @@ static int autotune_t(sg_handle h, int nb) {
         int TL, NT, stage;
         size_t sm;
         apply_cfg<T>(pr, nb, &TL, &NT, &sm, &stage);
-        if (TL != t || sm > 200 * 1024) continue;
+        if (TL != t || sm > SMEM_TILE) continue;
         float ms = 0.f;
         auto launch_ap = [&]() {
           launch_apply<T, T, true, true>(h, st, op, nb, 1, nullptr, nullptr, w.q, nullptr, h->am, h->bk, sgk::MASK_N,
@@ -1582,12 +1583,12 @@ static bool tiles_fit(const sgh::Problem& pr, int precision) {
     int TL, NT, stage, nods;
     size_t sm;
     apply_cfg<T>(pr, pr.nsub, &TL, &NT, &sm, &stage, &nods);
-    return sm <= (nods == 2 ? SMEM_MAX : 200 * 1024);
+    return sm <= (nods == 2 ? SMEM_MAX : SMEM_TILE);
   };
   auto fits_line = [&](auto tag) {
     using T = decltype(tag);
     const LineCfg lc = line_cfg<T>(pr, pr.nsub);
-    return lc.smem <= (lc.team ? SMEM_MAX : 200 * 1024);
+    return lc.smem <= (lc.team ? SMEM_MAX : SMEM_TILE);
   };
   return fits_apply(double{}) &&
          (precision == SG_MIXED ? (fits_apply(float{}) && fits_line(float{})) : fits_line(double{}));
@@ -1660,7 +1661,7 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   h->nlaunch = g_nlaunch_dev;
   // shared-memory opt-in of the apply variants
   {
-    const int lim = 200 * 1024;
+    const int lim = (int)SMEM_TILE;
     RET(smem_attr(h, sgk::k_apply<double, double, false, false>, lim));
     RET(smem_attr(h, sgk::k_apply<double, double, true, true>, lim));
     RET(smem_attr(h, sgk::k_apply<float, float, false, false>, lim));
@@ -1694,7 +1695,7 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
         std::vector<float> f(pr.gk_v.begin(), pr.gk_v.end());
         CK(cudaMemcpyToSymbol(sgk::c_gvf, f.data(), sizeof(float) * C::NNZ, sizeof(float) * C::OFF));
         CK(cudaMemcpyToSymbol(sgk::c_gvd, pr.gk_v.data(), sizeof(double) * C::NNZ, sizeof(double) * C::OFF));
-        const int lim = 200 * 1024;
+        const int lim = (int)SMEM_TILE;
         RET(smem_attr(h, sgk::k_apply<float, float, false, false, C>, lim));
         RET(smem_attr(h, sgk::k_apply<float, float, true, true, C>, lim));
         RET(smem_attr(h, sgk::k_apply<float, double, false, false, C>, lim));
