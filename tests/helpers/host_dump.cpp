@@ -1,6 +1,6 @@
 // Prints the host set-up tables of one problem, built by the library's set-up code (sg_host.cpp),
 // for comparison with the oracle (tests/test_host_setup.py).  Plain C++17, no GPU.
-// Usage: host_dump N s M sigma bx by g0 p p_in dt
+// Usage: host_dump N s M sigma bx by g0 p p_in dt kind x0 y0 width freq amp
 // Output: one line per table, "name v0 v1 ...".
 #include <cstdio>
 #include <cstdlib>
@@ -21,8 +21,8 @@ static void row(const char* name, const std::vector<T>& v) {
 }
 
 int main(int argc, char** argv) {
-  if (argc != 11) {
-    std::fprintf(stderr, "usage: host_dump N s M sigma bx by g0 p p_in dt\n");
+  if (argc != 17) {
+    std::fprintf(stderr, "usage: host_dump N s M sigma bx by g0 p p_in dt kind x0 y0 width freq amp\n");
     return 2;
   }
   const int N = std::atoi(argv[1]), s = std::atoi(argv[2]), M = std::atoi(argv[3]);
@@ -30,7 +30,8 @@ int main(int argc, char** argv) {
   const double g0 = std::atof(argv[7]), dt = std::atof(argv[10]);
   const int p = std::atoi(argv[8]), p_in = std::atoi(argv[9]);
   sgh::Problem pr;
-  const sgh::SourceDesc sd{0, 0.5, 0.5, 0.05, 10.0, 1.0};
+  const sgh::SourceDesc sd{std::atoi(argv[11]), std::atof(argv[12]), std::atof(argv[13]), std::atof(argv[14]),
+                          std::atof(argv[15]), std::atof(argv[16])};
   const std::string msg = sgh::build_problem(pr, N, s, s, M, sigma, bx, by, g0, p, p_in, dt, 0.5445, 0.0174, sd);
   if (!msg.empty()) {
     std::fprintf(stderr, "%s\n", msg.c_str());
@@ -50,5 +51,8 @@ int main(int argc, char** argv) {
   row("Dw", pr.Dw);
   row("kapE", pr.kapE);
   row("kapN", pr.kapN);
+  row("load_node", pr.load_node);
+  row("load_w", pr.load_w);
+  row("u0_local", pr.u0_local);
   return 0;
 }

@@ -8,7 +8,9 @@ GPU) against the oracle, table by table:
 - the counting weights D_s;
 - the stiffness edge weights of every subdomain.  In the graph-Laplacian form of P1 on right
   triangles, the weight of edge (a, b) in subdomain s is -K_i^(s)[a, b], where K_i^(s) is the
-  stiffness the oracle assembles over that subdomain's elements (Sec. 4, Eq. stok)."""
+  stiffness the oracle assembles over that subdomain's elements (Sec. 4, Eq. stok);
+- the source terms: the point load's P1 weights, split over the subdomains that hold the node
+  (counting weights, Sec. 3), and the interpolated initial pulse (Sec. 6.2)."""
 import os
 import shutil
 import subprocess
@@ -40,7 +42,9 @@ def dump_exe(tmp_path_factory):
 
 
 def host_tables(exe, prob):
-    args = [prob.N, prob.s, prob.M, prob.sigma, prob.bx, prob.by, prob.g0, prob.p, prob.p_in, prob.dt]
+    src = prob.source
+    args = [prob.N, prob.s, prob.M, prob.sigma, prob.bx, prob.by, prob.g0, prob.p, prob.p_in, prob.dt,
+            src.kind, src.x0, src.y0, src.width, src.freq, src.amp]
     txt = subprocess.run([exe] + [repr(a) for a in args], check=True, capture_output=True, text=True).stdout
     t = {}
     for line in txt.splitlines():
@@ -128,3 +132,46 @@ def test_edge_weights_equal_minus_the_subdomain_stiffness(case):
             scale = max(np.abs(refE).max(), np.abs(refN).max(), 1e-300)
             assert np.allclose(kapE[sub_id, :, i], refE, rtol=0, atol=1e-13 * scale)
             assert np.allclose(kapN[sub_id, :, i], refN, rtol=0, atol=1e-13 * scale)
+
+
+def _global_of_local(prob, nl, L, o):
+    sub_id, ln = divmod(int(o), nl)
+    sy, sx = divmod(sub_id, prob.s)
+    lj, li = divmod(ln, L)
+    H = prob.N // prob.s
+    return fem.node_id(sx * H + li, sy * H + lj, prob.N)
+
+
+# Ricker point sources: inside a subdomain, on an interface line (node held by 2 subdomains) and on a
+# cross point (4 subdomains); 24^2 grid, 3 x 3 subdomains (interface lines at 8 and 16 cells)
+@pytest.mark.parametrize("x0,y0", [(0.3, 0.5), (1.0 / 3.0, 0.5 + 0.01), (1.0 / 3.0, 2.0 / 3.0)])
+def test_point_load_weights(dump_exe, x0, y0):
+    base = w.config("small")
+    prob = base.replace(source=base.source.__class__(2, x0, y0, 0.0, 10.0, 1.7))
+    t = host_tables(dump_exe, prob)
+    part = dd.Partition(prob.N, prob.s)
+    held = {}
+    for sub in part.subs:
+        for g in sub["nodes"].tolist():
+            held[g] = held.get(g, 0) + 1
+    ref = {g: prob.source.amp * v for g, v in fem.p1_values(prob.N, x0, y0).items() if g in part.free_index}
+    got = {}
+    for o, wgt in zip(t["load_node"], t["load_w"]):
+        g = _global_of_local(prob, t["nl"], t["L"], o)
+        assert np.isclose(wgt, ref[g] / held[g], rtol=1e-15, atol=0)
+        got[g] = got.get(g, 0.0) + wgt
+    assert set(got) == set(ref)
+    assert all(np.isclose(got[g], ref[g], rtol=1e-14, atol=0) for g in ref)
+    assert max(held[g] for g in ref) > 1 or (x0, y0) == (0.3, 0.5)
+
+
+def test_initial_pulse(dump_exe):
+    base = w.config("small")
+    prob = base.replace(source=base.source.__class__(1, 0.45, 0.55, 0.1, 0.0, 1.3))
+    t = host_tables(dump_exe, prob)
+    ref = fem.initial_displacement(prob.N, prob.source)
+    part = dd.Partition(prob.N, prob.s)
+    u0 = t["u0_local"]
+    for o in range(u0.size):
+        g = _global_of_local(prob, t["nl"], t["L"], o)
+        assert np.isclose(u0[o], ref[g] if g in part.free_index else 0.0, rtol=1e-14, atol=1e-300)
