@@ -22,6 +22,23 @@
  *     nodes (x index fastest, then y; node (i, j) for 1 <= i, j <= N-1), PCE mode fastest:
  *     value(i, j, k) is element ((j-1) (N-1) + (i-1)) * P + k.  PCE modes follow the graded
  *     multi-index order (total degree, then descending lexicographic), orthonormal basis.
+ *
+ * Environment switches.  They select between complete implementations of the same step and never
+ * skip work.  Set them before sg_setup; the tile choices also read them per launch.  Each is "on"
+ * when set, whatever its value (except SG_FORCE_NODS).
+ *   SG_EAGER        sg_step enqueues the step's kernels from the host instead of launching the
+ *                   captured graph: the same kernels, visible to profilers that cannot enter
+ *                   conditional graph nodes (same as sg_set_enqueue_mode(h, 1)).
+ *   SG_PDL          programmatic dependent launch between the FP32 inner-loop kernels.
+ *   SG_NO_MMA       FP32 subdomain CG preconditioned by the line sweeps of the mean operator
+ *                   instead of its dense BF16 inverse on the tensor cores.
+ *   SG_NO_GFIX      FP32 operator apply with the runtime triple-product table instead of the table
+ *                   compiled for (M, p, p_in).
+ *   SG_FORCE_NODS   apply without staged edge differences at every size; the value 2 also reads the
+ *                   triple-product table from global memory (the variants of the widest subdomains).
+ *   SG_FORCE_GLINE  line sweep reading the factor and residual from global memory at every size.
+ *   SG_A6_SOLVE     mixed precision recovers the interior unknowns by an explicit Dirichlet solve
+ *                   (Alg. 1) instead of accumulating them along the interface PCG.
  */
 #ifndef SG_H
 #define SG_H
