@@ -31,13 +31,18 @@ def check_plan(p, prob, precision):
     L = prob.N // prob.s + 1
     assert (p["L"], p["P"], p["nsub"]) == (L, prob.P, prob.s * prob.s)
     assert p["fits"] == 1
-    for i in (0, 1):  # FP64 kernels, FP32 kernels
+    # kernels the precision launches: the FP64 apply always (residual corrections in mixed mode),
+    # the FP32 apply and line sweep in mixed mode, the FP64 line sweep in FP64 mode
+    applies = (0, 1) if precision == SG_MIXED else (0,)
+    lines = (1,) if precision == SG_MIXED else (0,)
+    for i in applies:  # 0: FP64 kernels, 1: FP32 kernels
         tl, nt = p["apply_lines"][i], p["apply_tiles"][i]
         assert 1 <= tl <= L and nt == -(-L // tl)
         cap = SMEM_OPTIN if p["apply_variant"][i] == 2 else SMEM_DEFAULT
         assert 0 < p["apply_smem"][i] <= cap
         if i == 0:
             assert p["apply_variant"][i] != 3  # FP64 keeps the runtime-table kernel
+    for i in lines:
         threads = p["line_block"][i][0] * p["line_block"][i][1] * p["line_block"][i][2]
         assert 32 <= threads <= 1024 and threads % 32 == 0
         g, ng = p["line_modes"][i], p["line_groups"][i]
@@ -76,3 +81,31 @@ def test_plan_rejects_invalid_sizes(plan_query):
     with pytest.raises(SGError) as e:
         plan_query(prob, 7)  # unknown precision
     assert e.value.code == -1
+
+
+# subdomain widths around the thresholds where kernel variants switch (tensor-core preconditioner
+# and warp-team line kernel up to 40 nodes, the wide-subdomain variants near 81, 121 and 129 nodes)
+SWEEP_H = (3, 15, 19, 38, 39, 40, 41, 63, 64, 80, 81, 120, 128)
+SWEEP_MP = ((1, 3), (2, 4), (3, 3), (4, 3), (6, 2))   # P = 4, 15, 20, 35, 28
+
+
+def test_plans_at_size_thresholds(plan_query):
+    from paper_2512_23027_gb300.binding import SGError
+    base = w.config("ricker128")
+    n_fit = 0
+    for H in SWEEP_H:
+        for s in ((2, 4) if H <= 64 else (2,)):
+            for M, p in SWEEP_MP:
+                for precision in (SG_FP64, SG_MIXED):
+                    prob = base.replace(N=s * H, s=s, M=M, p=p, p_in=p, dt=w.cfl_dt(s * H))
+                    try:
+                        plan = plan_query(prob, precision)
+                    except SGError as e:
+                        assert e.code == -7  # SG_ENOTSUP: outside the build's sizes, never a bad plan
+                        continue
+                    if plan["fits"]:
+                        check_plan(plan, prob, precision)
+                        n_fit += 1
+                    else:
+                        assert precision == SG_FP64 or H > 128
+    assert n_fit >= 200
