@@ -139,31 +139,63 @@ std::string build_problem(Problem& pr, int N, int sx, int sy, int M, double sigm
   pr.kl_lambda.resize(M);
   for (int n = 0; n < M; ++n) pr.kl_lambda[n] = cand[n].lam;
 
-  // PCE coefficients of exp(g) at a point: c_alpha = exp(g0 + |g|^2/2) prod g_n^a_n / sqrt(a_n!)
-  auto coef_at = [&](double x, double y, double* c) {
-    std::vector<double> g(M);
-    double s2 = 0.0;
-    for (int n = 0; n < M; ++n) {
-      g[n] = sigma * std::sqrt(cand[n].lam) * phi1(x, ex[cand[n].ix]) * phi1(y, ey[cand[n].iy]);
-      s2 += g[n] * g[n];
+  // PCE coefficients of exp(g) at the element centroids (Eqs. c0pce, LNL0):
+  //   c_alpha = exp(g0 + |g|^2 / 2) prod_n g_n^{a_n} / sqrt(a_n!),  g_n = sigma sqrt(lambda_n) phi_n(x) psi_n(y).
+  // g_n is separable and the centroids of the T1 / T2 triangles lie on N column and N row positions,
+  // so the 1-D factors are tabulated once per position (O(N M) trigonometric evaluations instead of
+  // O(N^2 M)); the powers of g_n are formed by repeated products.
+  const double h = pr.h;
+  std::vector<double> fx1((size_t)M * N), fx2((size_t)M * N), fy1((size_t)M * N), fy2((size_t)M * N);
+  for (int n = 0; n < M; ++n) {
+    const double amp = sigma * std::sqrt(cand[n].lam);
+    const Eig1& exn = ex[cand[n].ix];
+    const Eig1& eyn = ey[cand[n].iy];
+    for (int q = 0; q < N; ++q) {
+      fx1[(size_t)n * N + q] = amp * phi1((q + 2.0 / 3.0) * h, exn);  // T1 centroid x
+      fx2[(size_t)n * N + q] = amp * phi1((q + 1.0 / 3.0) * h, exn);  // T2 centroid x
+      fy1[(size_t)n * N + q] = phi1((q + 1.0 / 3.0) * h, eyn);        // T1 centroid y
+      fy2[(size_t)n * N + q] = phi1((q + 2.0 / 3.0) * h, eyn);        // T2 centroid y
     }
-    double c0 = std::exp(g0 + 0.5 * s2);
-    for (int i = 0; i < PI; ++i) {
-      double v = c0;
-      for (int n = 0; n < M; ++n) {
-        int a = Ain[i][n];
-        if (a) v *= std::pow(g[n], a) / std::sqrt(fact(a));
+  }
+  // per input mode i: prod_n 1 / sqrt(a_n!) and its nonzero exponents as (variable, exponent) pairs
+  std::vector<double> kfac(PI);
+  std::vector<int> mi_off(PI + 1, 0), mi_n, mi_a;
+  for (int i = 0; i < PI; ++i) {
+    double v = 1.0;
+    for (int n = 0; n < M; ++n)
+      if (Ain[i][n]) {
+        v /= std::sqrt(fact(Ain[i][n]));
+        mi_n.push_back(n);
+        mi_a.push_back(Ain[i][n]);
       }
+    kfac[i] = v;
+    mi_off[i + 1] = (int)mi_n.size();
+  }
+  constexpr int MAXM = 12, MAXA = 20;  // limits checked above (M <= 12, p_in <= 20)
+  auto coef_from = [&](const double* g, double* c) {
+    double s2 = 0.0;
+    double pw[MAXM][MAXA + 1];
+    for (int n = 0; n < M; ++n) {
+      s2 += g[n] * g[n];
+      pw[n][0] = 1.0;
+      for (int a = 1; a <= p_in; ++a) pw[n][a] = pw[n][a - 1] * g[n];
+    }
+    const double c0 = std::exp(g0 + 0.5 * s2);
+    for (int i = 0; i < PI; ++i) {
+      double v = c0 * kfac[i];
+      for (int q = mi_off[i]; q < mi_off[i + 1]; ++q) v *= pw[mi_n[q]][mi_a[q]];
       c[i] = v;
     }
   };
-  const double h = pr.h;
   // element coefficients of the whole mesh: T1 centroid (i+2/3, j+1/3) h, T2 (i+1/3, j+2/3) h
   std::vector<double> cT1((size_t)N * N * PI), cT2((size_t)N * N * PI);
   for (int j = 0; j < N; ++j)
     for (int i = 0; i < N; ++i) {
-      coef_at((i + 2.0 / 3.0) * h, (j + 1.0 / 3.0) * h, &cT1[((size_t)j * N + i) * PI]);
-      coef_at((i + 1.0 / 3.0) * h, (j + 2.0 / 3.0) * h, &cT2[((size_t)j * N + i) * PI]);
+      double g[MAXM];
+      for (int n = 0; n < M; ++n) g[n] = fx1[(size_t)n * N + i] * fy1[(size_t)n * N + j];
+      coef_from(g, &cT1[((size_t)j * N + i) * PI]);
+      for (int n = 0; n < M; ++n) g[n] = fx2[(size_t)n * N + i] * fy2[(size_t)n * N + j];
+      coef_from(g, &cT2[((size_t)j * N + i) * PI]);
     }
 
   // node classes and maps
