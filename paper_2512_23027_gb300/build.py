@@ -25,7 +25,8 @@ def build(force=False, verbose=False):
         if all(os.path.getmtime(d) <= t for d in deps if os.path.exists(d)):
             return OUT
     cmd = [nvcc_path(), "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-           "-Xcompiler", "-fPIC", "-shared", "--threads", "2", "-o", OUT + ".tmp"] + SRC
+           "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-shared", "--threads", "2", "-o", OUT + ".tmp"] + SRC + [
+               "-lpthread"]
     if verbose:
         print(" ".join(cmd))
     subprocess.run(cmd, check=True)

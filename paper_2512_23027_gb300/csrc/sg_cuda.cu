@@ -1213,39 +1213,6 @@ static int build_mma_precond(sg_handle h) {
   return ensure_ctl(h, pr.nsub, pr.L, std::max(pr.P, h->MT));
 }
 
-// Host inverse of a small SPD matrix by Cholesky (set-up only).
-static bool spd_inverse(std::vector<double>& A, int n) {
-  std::vector<double> Lm((size_t)n * n, 0.0);
-  for (int j = 0; j < n; ++j) {
-    double d = A[(size_t)j * n + j];
-    for (int k = 0; k < j; ++k) d -= Lm[(size_t)j * n + k] * Lm[(size_t)j * n + k];
-    if (!(d > 0.0)) return false;
-    d = std::sqrt(d);
-    Lm[(size_t)j * n + j] = d;
-    for (int i = j + 1; i < n; ++i) {
-      double s = A[(size_t)i * n + j];
-      for (int k = 0; k < j; ++k) s -= Lm[(size_t)i * n + k] * Lm[(size_t)j * n + k];
-      Lm[(size_t)i * n + j] = s / d;
-    }
-  }
-  std::vector<double> Li((size_t)n * n, 0.0);
-  for (int c = 0; c < n; ++c) {
-    for (int i = c; i < n; ++i) {
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int k = c; k < i; ++k) s -= Lm[(size_t)i * n + k] * Li[(size_t)k * n + c];
-      Li[(size_t)i * n + c] = s / Lm[(size_t)i * n + i];
-    }
-  }
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j <= i; ++j) {
-      double s = 0.0;
-      for (int k = i; k < n; ++k) s += Li[(size_t)k * n + i] * Li[(size_t)k * n + j];
-      A[(size_t)i * n + j] = s;
-      A[(size_t)j * n + i] = s;
-    }
-  return true;
-}
-
 // Coarse basis Phi_s = -S_rr^{-1} S_rc (per local corner dof) and F_cc (Eq. Fcc_2), from one
 // Neumann solve per local corner dof: v = -N^{-1} K_[ir],c e, F^s e = (K~ (v + e))_c.  The right-hand
 // sides and F^s are formed in FP64; the Neumann solves run in T (FP64 in FP64 mode, FP32 in mixed
@@ -1320,7 +1287,7 @@ static int build_coarse_t(sg_handle h) {
       double v = 0.5 * (F[(size_t)i * nCd + j] + F[(size_t)j * nCd + i]);
       F[(size_t)i * nCd + j] = F[(size_t)j * nCd + i] = v;
     }
-  if (!spd_inverse(F, nCd)) { h->err = "coarse matrix F_cc not positive definite"; return SG_ENUMERIC; }
+  if (!sgh::spd_inverse(F, nCd)) { h->err = "coarse matrix F_cc not positive definite"; return SG_ENUMERIC; }
   RET(upload(h, &h->Finv, F));
   return SG_OK;
 }

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <functional>
 #include <map>
+#include <thread>
 
 namespace sgh {
 
@@ -337,6 +338,125 @@ std::string build_problem(Problem& pr, int N, int sx, int sy, int M, double sigm
     }
   }
   return "";
+}
+
+// Runs f(i) for i in [i0, i1) on up to 16 host threads, rows assigned cyclically (thread t takes
+// i0 + t, i0 + t + T, ...) so that triangular work stays balanced.
+template <class F>
+static void parallel_cyclic(int i0, int i1, F&& f) {
+  const int n = i1 - i0;
+  if (n <= 0) return;
+  int T = (int)std::thread::hardware_concurrency();
+  T = std::max(1, std::min({T, 16, n / 8}));
+  if (T <= 1) {
+    for (int i = i0; i < i1; ++i) f(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(T);
+  for (int t = 0; t < T; ++t)
+    th.emplace_back([&, t]() {
+      for (int i = i0 + t; i < i1; i += T) f(i);
+    });
+  for (auto& x : th) x.join();
+}
+
+bool spd_inverse(std::vector<double>& A, int n) {
+  if (n <= 0) return true;
+  if ((long long)A.size() < (long long)n * n) return false;
+  auto a = [&](int i, int j) -> double& { return A[(size_t)i * n + j]; };
+  // 1. Cholesky A = L L^T in place (lower triangle), blocked right-looking: factor the diagonal
+  //    block, solve the panel below it (inner products over contiguous row segments), update the
+  //    trailing lower triangle (row-parallel).
+  constexpr int B = 64;
+  bool spd = true;
+  for (int k0 = 0; k0 < n && spd; k0 += B) {
+    const int k1 = std::min(n, k0 + B);
+    for (int j = k0; j < k1; ++j) {
+      double d = a(j, j);
+      for (int k = k0; k < j; ++k) d -= a(j, k) * a(j, k);
+      if (!(d > 0.0)) { spd = false; break; }
+      d = std::sqrt(d);
+      a(j, j) = d;
+      for (int i = j + 1; i < k1; ++i) {
+        double s = a(i, j);
+        for (int k = k0; k < j; ++k) s -= a(i, k) * a(j, k);
+        a(i, j) = s / d;
+      }
+    }
+    if (!spd) break;
+    parallel_cyclic(k1, n, [&](int i) {
+      for (int j = k0; j < k1; ++j) {  // panel row i: L[i, k0:k1] = A[i, k0:k1] L_kk^{-T}
+        double s = a(i, j);
+        for (int k = k0; k < j; ++k) s -= a(i, k) * a(j, k);
+        a(i, j) = s / a(j, j);
+      }
+    });
+    // trailing update A[i][j] -= L[i, k0:k1] . L[j, k0:k1] (k1 <= j <= i), after the whole panel is
+    // known: with the panel transposed (Pt[k][j] = L[j][k0 + k]) row i is a sum of contiguous axpys
+    // over j, one per panel column k
+    const int nb = k1 - k0;
+    std::vector<double> Pt((size_t)nb * n);
+    for (int j = k1; j < n; ++j)
+      for (int k = 0; k < nb; ++k) Pt[(size_t)k * n + j] = a(j, k0 + k);
+    parallel_cyclic(k1, n, [&](int i) {
+      double* ri = &A[(size_t)i * n];
+      thread_local std::vector<double> acc;
+      acc.assign((size_t)(i + 1), 0.0);
+      for (int k = 0; k < nb; ++k) {
+        const double l = ri[k0 + k];
+        const double* pk = &Pt[(size_t)k * n];
+        for (int j = k1; j <= i; ++j) acc[j] += l * pk[j];
+      }
+      for (int j = k1; j <= i; ++j) ri[j] -= acc[j];
+    });
+  }
+  if (!spd) return false;
+  // 2. A^{-1} = L^{-T} L^{-1}, in groups of MG consecutive columns c = c0 + t: Y = L^{-1} E (E the
+  //    unit columns; rows above c0 are zero) and X = L^{-T} Y on rows c0..n-1, so that every row of
+  //    L (forward) and of L^T (backward, copied row-major) is read once per group and serves MG
+  //    right-hand sides (the inner loops run over the group's columns).  Only x[i] with i >= c is
+  //    kept (the lower triangle); it is written to row c of `inv` and mirrored at the end.
+  std::vector<double> U((size_t)n * n, 0.0);  // U = L^T, row-major
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k <= i; ++k) U[(size_t)k * n + i] = a(i, k);
+  std::vector<double> inv((size_t)n * n, 0.0);
+  constexpr int MG = 32;
+  parallel_cyclic(0, (n + MG - 1) / MG, [&](int gi) {
+    const int c0 = gi * MG, m = std::min(MG, n - c0), R = n - c0;
+    std::vector<double> Y((size_t)R * MG, 0.0), X((size_t)R * MG, 0.0);
+    double acc[MG];
+    for (int i = c0; i < n; ++i) {  // forward: L y = e_c for the group's columns
+      for (int t = 0; t < MG; ++t) acc[t] = 0.0;
+      const double* li = &A[(size_t)i * n + c0];
+      for (int k = 0; k < i - c0; ++k) {
+        const double l = li[k];
+        const double* yk = &Y[(size_t)k * MG];
+        for (int t = 0; t < MG; ++t) acc[t] += l * yk[t];
+      }
+      const double d = a(i, i);
+      double* yi = &Y[(size_t)(i - c0) * MG];
+      for (int t = 0; t < MG; ++t) yi[t] = ((i == c0 + t ? 1.0 : 0.0) - acc[t]) / d;
+    }
+    for (int i = n - 1; i >= c0; --i) {  // backward: L^T x = y
+      for (int t = 0; t < MG; ++t) acc[t] = 0.0;
+      const double* ui = &U[(size_t)i * n];
+      for (int k = i + 1; k < n; ++k) {
+        const double u = ui[k];
+        const double* xk = &X[(size_t)(k - c0) * MG];
+        for (int t = 0; t < MG; ++t) acc[t] += u * xk[t];
+      }
+      const double d = ui[i];
+      double* xi = &X[(size_t)(i - c0) * MG];
+      const double* yi = &Y[(size_t)(i - c0) * MG];
+      for (int t = 0; t < MG; ++t) xi[t] = (yi[t] - acc[t]) / d;
+    }
+    for (int t = 0; t < m; ++t)
+      for (int i = c0 + t; i < n; ++i) inv[(size_t)(c0 + t) * n + i] = X[(size_t)(i - c0) * MG + t];
+  });
+  for (int i = 0; i < n; ++i)
+    for (int j = i; j < n; ++j) A[(size_t)i * n + j] = A[(size_t)j * n + i] = inv[(size_t)i * n + j];
+  return true;
 }
 
 }  // namespace sgh

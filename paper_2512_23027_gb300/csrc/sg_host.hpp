@@ -67,4 +67,9 @@ std::vector<std::vector<int>> multi_indices(int M, int p);
 double hermite_triple(int a, int b, int c);
 double ricker(double t, double f);
 
+// In-place inverse of a symmetric positive definite n x n row-major matrix (the coarse matrix
+// F_cc, Eq. Fcc_2): blocked Cholesky A = L L^T, then A^{-1} = L^{-T} L^{-1} column by column, both
+// spread over up to 16 host threads.  Returns false (A then undefined) if a pivot is not positive.
+bool spd_inverse(std::vector<double>& A, int n);
+
 }  // namespace sgh
