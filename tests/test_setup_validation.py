@@ -1,0 +1,82 @@
+"""sg_setup rejects invalid and unsupported inputs before it touches the GPU (no device needed):
+every failure returns its status code (SG_EINVAL -1, SG_ENOTSUP -7) with a message in
+sg_last_error(NULL), leaves the output handle NULL, and issues no CUDA call (the checks run before
+the first one), so these tests run on a machine without a GPU."""
+import ctypes as C
+
+import pytest
+
+import sg_workloads as w
+
+SG_EINVAL, SG_ENOTSUP = -1, -7
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2512_23027_gb300 import build as b
+    b.build()
+    from paper_2512_23027_gb300 import binding
+    binding.load_library()
+    return binding
+
+
+def setup_rc(B, prob, precision=0, warm=0, warm_train_steps=0, grid=None, src_kind=None):
+    lib = B.load_library()
+    s = prob.source
+    g = grid or B.Grid(prob.N, prob.s, prob.s)
+    kl = B.KL(prob.M, prob.sigma, prob.bx, prob.by, prob.g0)
+    pce = B.PCE(prob.p, prob.p_in)
+    prm = B.Params(prob.dt, prob.tol, prob.alpha0, prob.alpha1, prob.max_iter, precision, warm, 0.0, 0, 0,
+                   warm_train_steps, 0.0)
+    src = B.Source(s.kind if src_kind is None else src_kind, s.x0, s.y0, s.width, s.freq, s.amp)
+    h = C.c_void_p(12345)
+    rc = lib.sg_setup(C.byref(g), C.byref(kl), C.byref(pce), C.byref(prm), C.byref(src), None, C.byref(h))
+    return rc, h.value, lib.sg_last_error(None).decode()
+
+
+CASES = [
+    ("source kind", dict(src_kind=5), SG_EINVAL, "source"),
+    ("precision", dict(precision=7), SG_EINVAL, "precision"),
+    ("warm-start mode", dict(warm=9), SG_EINVAL, "warm"),
+    ("warm-start training steps", dict(warm_train_steps=-1), SG_EINVAL, "warm"),
+]
+PROBS = [
+    ("N not divisible by s", dict(N=25), SG_EINVAL, "divisible"),
+    ("negative time step", dict(dt=-1e-3), SG_EINVAL, "dt"),
+    ("negative sigma", dict(sigma=-0.1), SG_EINVAL, "sigma"),
+    ("zero correlation length", dict(bx=0.0), SG_EINVAL, "correlation"),
+    ("too many random variables", dict(M=13), SG_EINVAL, "unsupported"),
+    ("single subdomain", dict(N=24, s=1), SG_ENOTSUP, "2 x 2"),
+    ("subdomains wider than 255 cells", dict(N=512, s=2), SG_ENOTSUP, "255"),
+    ("pulse of zero width", dict(source=w.Source(1, 0.5, 0.5, 0.0, 0.0, 1.0)), SG_EINVAL, "width"),
+    ("Ricker source outside the square", dict(source=w.Source(2, 1.5, 0.5, 0.0, 10.0, 1.0)), SG_EINVAL, "ricker"),
+]
+
+
+@pytest.mark.parametrize("what,kw,code,msg", CASES, ids=[c[0] for c in CASES])
+def test_invalid_parameters(B, what, kw, code, msg):
+    rc, h, err = setup_rc(B, w.config("small"), **kw)
+    assert rc == code and h is None, (what, rc, err)
+    assert msg in err.lower() or msg in err, err
+
+
+@pytest.mark.parametrize("what,kw,code,msg", PROBS, ids=[c[0] for c in PROBS])
+def test_invalid_or_unsupported_problems(B, what, kw, code, msg):
+    rc, h, err = setup_rc(B, w.config("small").replace(**kw))
+    assert rc == code and h is None, (what, rc, err)
+    assert msg.lower() in err.lower(), err
+
+
+def test_unequal_partition_and_null_arguments(B):
+    rc, h, err = setup_rc(B, w.config("small"), grid=B.Grid(24, 3, 2))
+    assert rc == SG_EINVAL and h is None and "nsub" in err
+    lib = B.load_library()
+    out = C.c_void_p(1)
+    assert lib.sg_setup(None, None, None, None, None, None, C.byref(out)) == SG_EINVAL
+    assert out.value is None
+
+
+def test_solver_raises_the_status(B):
+    with pytest.raises(B.SGError) as e:
+        B.Solver(w.config("small").replace(N=25))
+    assert e.value.code == SG_EINVAL
