@@ -94,6 +94,27 @@ static double phi1(double x, const Eig1& e) {
   return std::sin(e.w * u) / std::sqrt(0.5 - std::sin(e.w) / (2 * e.w));
 }
 
+// Runs f(i) for i in [i0, i1) on up to 16 host threads, rows assigned cyclically (thread t takes
+// i0 + t, i0 + t + T, ...) so that triangular work stays balanced.
+template <class F>
+static void parallel_cyclic(int i0, int i1, F&& f) {
+  const int n = i1 - i0;
+  if (n <= 0) return;
+  int T = (int)std::thread::hardware_concurrency();
+  T = std::max(1, std::min({T, 16, n / 8}));
+  if (T <= 1) {
+    for (int i = i0; i < i1; ++i) f(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(T);
+  for (int t = 0; t < T; ++t)
+    th.emplace_back([&, t]() {
+      for (int i = i0 + t; i < i1; i += T) f(i);
+    });
+  for (auto& x : th) x.join();
+}
+
 std::string build_problem(Problem& pr, int N, int sx, int sy, int M, double sigma, double bx,
                           double by, double g0, int p, int p_in, double dt, double alpha0,
                           double alpha1, const SourceDesc& src) {
@@ -190,7 +211,7 @@ std::string build_problem(Problem& pr, int N, int sx, int sy, int M, double sigm
   };
   // element coefficients of the whole mesh: T1 centroid (i+2/3, j+1/3) h, T2 (i+1/3, j+2/3) h
   std::vector<double> cT1((size_t)N * N * PI), cT2((size_t)N * N * PI);
-  for (int j = 0; j < N; ++j)
+  parallel_cyclic(0, N, [&](int j) {  // grid rows are independent
     for (int i = 0; i < N; ++i) {
       double g[MAXM];
       for (int n = 0; n < M; ++n) g[n] = fx1[(size_t)n * N + i] * fy1[(size_t)n * N + j];
@@ -198,6 +219,7 @@ std::string build_problem(Problem& pr, int N, int sx, int sy, int M, double sigm
       for (int n = 0; n < M; ++n) g[n] = fx2[(size_t)n * N + i] * fy2[(size_t)n * N + j];
       coef_from(g, &cT2[((size_t)j * N + i) * PI]);
     }
+  });
 
   // node classes and maps
   auto gfree = [&](int I, int J) { return I >= 1 && I <= N - 1 && J >= 1 && J <= N - 1; };
@@ -269,29 +291,32 @@ std::string build_problem(Problem& pr, int N, int sx, int sy, int M, double sigm
             pr.u0_local[o] = src.amp * std::exp(-(x * x + y * y) / (src.width * src.width));
           }
         }
-      // stiffness edge weights from the subdomain's own elements (graph-Laplacian form of the
-      // P1 stiffness on right triangles: each leg carries half the element coefficient, the
-      // hypotenuse none)
-      for (int lj = 0; lj <= H; ++lj)
-        for (int li = 0; li <= H; ++li) {
-          int I = sx_ * H + li, J = sy_ * H + lj, ln = lj * L + li;
-          double* kE = &pr.kapE[((size_t)sub * nl + ln) * PI];
-          double* kN = &pr.kapN[((size_t)sub * nl + ln) * PI];
-          for (int i = 0; i < PI; ++i) {
-            double e = 0.0, n = 0.0;
-            if (li < H) {
-              if (lj < H) e += 0.5 * cT1[((size_t)J * N + I) * PI + i];
-              if (lj > 0) e += 0.5 * cT2[((size_t)(J - 1) * N + I) * PI + i];
-            }
-            if (lj < H) {
-              if (li > 0) n += 0.5 * cT1[((size_t)J * N + (I - 1)) * PI + i];
-              if (li < H) n += 0.5 * cT2[((size_t)J * N + I) * PI + i];
-            }
-            kE[i] = e;
-            kN[i] = n;
-          }
-        }
     }
+  // stiffness edge weights from each subdomain's own elements (graph-Laplacian form of the P1
+  // stiffness on right triangles: each leg carries half the element coefficient, the hypotenuse
+  // none); subdomains write disjoint ranges and are filled in parallel
+  parallel_cyclic(0, nsub, [&](int sub) {
+    const int sy_ = sub / sx, sx_ = sub % sx;
+    for (int lj = 0; lj <= H; ++lj)
+      for (int li = 0; li <= H; ++li) {
+        const int I = sx_ * H + li, J = sy_ * H + lj, ln = lj * L + li;
+        double* kE = &pr.kapE[((size_t)sub * nl + ln) * PI];
+        double* kN = &pr.kapN[((size_t)sub * nl + ln) * PI];
+        for (int i = 0; i < PI; ++i) {
+          double e = 0.0, n = 0.0;
+          if (li < H) {
+            if (lj < H) e += 0.5 * cT1[((size_t)J * N + I) * PI + i];
+            if (lj > 0) e += 0.5 * cT2[((size_t)(J - 1) * N + I) * PI + i];
+          }
+          if (lj < H) {
+            if (li > 0) n += 0.5 * cT1[((size_t)J * N + (I - 1)) * PI + i];
+            if (li < H) n += 0.5 * cT2[((size_t)J * N + I) * PI + i];
+          }
+          kE[i] = e;
+          kN[i] = n;
+        }
+      }
+  });
   for (int g = 0; g < pr.nG; ++g) pr.Dw[g] = 1.0 / mult[g];
   pr.max_corner = 0;
   pr.nGam = 0;
@@ -338,27 +363,6 @@ std::string build_problem(Problem& pr, int N, int sx, int sy, int M, double sigm
     }
   }
   return "";
-}
-
-// Runs f(i) for i in [i0, i1) on up to 16 host threads, rows assigned cyclically (thread t takes
-// i0 + t, i0 + t + T, ...) so that triangular work stays balanced.
-template <class F>
-static void parallel_cyclic(int i0, int i1, F&& f) {
-  const int n = i1 - i0;
-  if (n <= 0) return;
-  int T = (int)std::thread::hardware_concurrency();
-  T = std::max(1, std::min({T, 16, n / 8}));
-  if (T <= 1) {
-    for (int i = i0; i < i1; ++i) f(i);
-    return;
-  }
-  std::vector<std::thread> th;
-  th.reserve(T);
-  for (int t = 0; t < T; ++t)
-    th.emplace_back([&, t]() {
-      for (int i = i0 + t; i < i1; i += T) f(i);
-    });
-  for (auto& x : th) x.join();
 }
 
 bool spd_inverse(std::vector<double>& A, int n) {
