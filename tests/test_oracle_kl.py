@@ -56,3 +56,53 @@ def test_isotropic_tie_order():
     assert idx[:3] == [(0, 0), (1, 0), (0, 1)]
     lam = [t[0] for t in m]
     assert lam == sorted(lam, reverse=True)
+
+
+def _cov_exact(sigma, bx, by, pts):
+    dx = np.abs(pts[:, None, 0] - pts[None, :, 0])
+    dy = np.abs(pts[:, None, 1] - pts[None, :, 1])
+    return sigma ** 2 * np.exp(-dx / bx - dy / by)
+
+
+def test_mercer_reconstruction_of_the_covariance():
+    """Mercer's theorem for the truncated expansion g = sum_n g_n xi_n: the covariance of the
+    truncated field, sum_n g_n(x) g_n(y), tends to sigma^2 exp(-|dx|/bx - |dy|/by) as M grows,
+    and the pointwise variance sum_n g_n(x)^2 rises monotonically towards sigma^2.  A slip in the
+    scaling g_n = sigma sqrt(lambda_n) phi_n (lambda for sqrt(lambda), sigma^2 for sigma) or in a
+    mode's pairing of 1-D factors fails this."""
+    pts = np.array([[0.2, 0.3], [0.5, 0.5], [0.8, 0.1], [0.45, 0.55], [0.52, 0.48], [0.05, 0.95]])
+    for sigma, bx, by, bar in ((0.3, 0.5, 0.3, 0.03), (0.4, 0.2, 0.2, 0.06)):
+        exact = _cov_exact(sigma, bx, by, pts)
+        prev_err, prev_var = None, None
+        for M in (10, 40, 160, 640):
+            g = kl.kl_fields(M, sigma, bx, by, pts[:, 0], pts[:, 1])
+            C = g.T @ g
+            var = np.diag(C)
+            assert np.all(var <= sigma ** 2 * (1 + 1e-12))
+            if prev_var is not None:
+                assert np.all(var >= prev_var - 1e-15)
+            err = np.abs(C - exact).max() / sigma ** 2
+            if prev_err is not None:
+                assert err < prev_err
+            prev_err, prev_var = err, var
+        assert prev_err < bar, (sigma, bx, by, prev_err)
+
+
+def test_modes_match_a_2d_nystrom_solve():
+    """Each field g_n against an independent 2-D Nystrom eigen-solve of the covariance operator
+    sigma^2 exp(-|dx|/bx - |dy|/by) on a midpoint grid: g_n = sigma sqrt(lambda_n) v_n sqrt(n_pts)
+    up to sign (anisotropic lengths, so no eigenvalue is tied)."""
+    n = 40
+    sigma, bx, by = 0.3, 0.5, 0.3
+    c = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(c, c, indexing="xy")
+    pts = np.stack([X.ravel(), Y.ravel()], axis=1)
+    Kmat = _cov_exact(1.0, bx, by, pts) / pts.shape[0]
+    ev, V = np.linalg.eigh(Kmat)
+    ev, V = ev[::-1], V[:, ::-1]
+    M = 6
+    g = kl.kl_fields(M, sigma, bx, by, pts[:, 0], pts[:, 1])
+    for m in range(M):
+        ref = sigma * math.sqrt(ev[m]) * V[:, m] * math.sqrt(pts.shape[0])
+        err = min(np.abs(g[m] - ref).max(), np.abs(g[m] + ref).max()) / np.abs(ref).max()
+        assert err < 2e-2, (m, err)
