@@ -188,16 +188,22 @@ int sg_get_field(sg_handle h, int mode, double* dst, int on_device);
  * nodes into host or device arrays of n_free doubles each; either pointer may be NULL. */
 int sg_get_moments(sg_handle h, double* mean, double* var, int on_device);
 
-/* Same results as sg_get_moments(h, mean, var, 0) for callers that must not allocate device
- * memory, for example code that runs while a CUDA graph is being captured or under an allocator
- * policy that forbids cudaMalloc.  mean / var are host arrays of n_free doubles (either may be NULL,
- * not both).  Instead of handle-owned memory, the device staging buffer is one fixed array inside
- * the library: 2 x 2^20 doubles (16 MiB), held by every GPU that loads the library until the
- * process exits.  Handles with more than 2^20 free nodes get SG_EINVAL.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  All calls share the array: calls whose device work
- * overlaps in time race and may read each other's values.  The call allocates nothing.  The paper
- * has no counterpart: this entry point exists only for allocation-restricted callers. */
+/* Capacity of sg_get_moments_noalloc: free nodes of the largest handle it accepts. */
+#define SG_NOALLOC_MAX_FREE (1 << 20)
+
+/* Same results as sg_get_moments(h, mean, var, 0) for callers that cannot allocate device memory:
+ * for example a host application whose own allocator owns the whole device and would fail or lose
+ * track of a cudaMalloc made behind its back, or a latency-critical loop that must not pay for
+ * cudaMalloc / cudaFree, which can synchronise the whole device.  mean / var are host arrays of
+ * n_free doubles; either may be NULL, not both (SG_EINVAL).  Instead of handle-owned memory, the
+ * device staging buffer is one fixed array inside the library: 2 x SG_NOALLOC_MAX_FREE doubles
+ * (16 MiB), held by every GPU that loads the library until the process exits.  Handles with more
+ * than SG_NOALLOC_MAX_FREE free nodes get SG_EINVAL.  The device current at the call must be the
+ * one the handle was set up on (else SG_EINVAL).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current.  All calls share the array and
+ * it keeps the last call's values: calls whose device work overlaps in time race and may read
+ * each other's values.  The call allocates nothing and synchronises the handle's stream.  The
+ * paper has no counterpart: this entry point exists only for allocation-restricted callers. */
 int sg_get_moments_noalloc(sg_handle h, double* mean, double* var);
 
 /* Checkpoint: state = [U | V | A] (3 * n_free * P doubles, layout above) followed by one

@@ -21,6 +21,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -71,6 +72,7 @@ struct Ctx {
 struct sg_handle_s {
   sgh::Problem pr;
   cudaStream_t st = nullptr;          // caller's stream (graph launches, copies)
+  int dev = -1;                       // CUDA device current at sg_setup (the handle's memory lives there)
   bool own_st = false;
   cudaStream_t cs[NSTREAMS] = {};     // private capture streams
   std::string err;
@@ -529,14 +531,33 @@ constexpr int TEAM_LS_MAX = 40;  // padded row length of the largest staged fact
 struct LineCfg {
   bool team;      // warp-team kernel with the factor staged in shared memory
   bool gs;        // block kernel reading the factor from global memory (widest subdomains)
+  bool wide;      // register-tiled kernel streaming the padded factor (wide subdomains)
   int G, NG;      // modes per block, blocks per problem
+  int GS;         // wide kernel: modes per block rounded up to a multiple of 4
   dim3 block;
   size_t smem;
 };
 
+// Register-tiled line solve (k_line_w): shared memory for the double-buffered padded factor and the
+// three [rows][GS] line buffers; threads for the 4 x 4 tiles and for the coalesced line I/O.
+template <typename T>
+static size_t wide_smem(int L, int GS) {
+  const size_t LSP = pad4(L);
+  return sizeof(T) * (2 * (size_t)L * LSP + (2 * (size_t)L + LSP) * GS + 4 * (size_t)L);
+}
+template <typename T>
+static int wide_threads(int L, int G, int GS) {
+  const int tiles = (pad4(L) / 2) * (GS / 4);                           // 2 x 4 tiles
+  const int io = G * ((L + sgk::lw_npf<T>() - 1) / sgk::lw_npf<T>());  // G x rows per pass
+  return 32 * ((std::max(tiles, io) + 31) / 32);
+}
+
 // line-solve launch shape: FP32 uses the warp-team kernel when the whole factor fits in shared
-// memory; otherwise the block-synchronous kernel with a double-buffered factor (G modes x Lp
-// rows, G * Lp a multiple of 32, FP64 spreads the modes over more blocks).
+// memory; wider subdomains use the register-tiled kernel (modes grouped so that the blocks about
+// fill the GPU, at most 32 modes per block); otherwise (or with SG_LINE_OLD) the block-synchronous
+// kernel with a double-buffered factor (G modes x Lp rows, G * Lp a multiple of 32, FP64 spreads the
+// modes over more blocks).
+constexpr int WIDE_LMIN = 41;  // subdomains at least this many nodes wide use k_line_w
 template <typename T>
 static LineCfg line_cfg(const sgh::Problem& pr, int nb_hint) {
   const int L = pr.L, P = pr.P;
@@ -557,6 +578,24 @@ static LineCfg line_cfg(const sgh::Problem& pr, int nb_hint) {
       c.G = (P + c.NG - 1) / c.NG;
       c.block = dim3(32 * ((L + 31) / 32) * c.G);
       c.smem = team_smem<T>(L, c.G);
+      return c;
+    }
+  }
+  if (L >= WIDE_LMIN && !std::getenv("SG_LINE_OLD")) {
+    const int nbp = std::max(1, nb_hint);
+    int ng = std::max((P + 31) / 32, (4 * 152 / 5 + nbp - 1) / nbp);
+    if (const int t = tuned(1, sizeof(T), pr, nb_hint)) ng = (P + std::min(t, 32) - 1) / std::min(t, 32);
+    ng = std::min(ng, P);
+    int G = (P + ng - 1) / ng;
+    ng = (P + G - 1) / G;
+    const int GS = pad4(G);
+    if (wide_smem<T>(L, GS) <= SMEM_TILE && wide_threads<T>(L, G, GS) <= sgk::LW_MAXT) {
+      c.wide = true;
+      c.G = G;
+      c.GS = GS;
+      c.NG = ng;
+      c.block = dim3(wide_threads<T>(L, G, GS));
+      c.smem = wide_smem<T>(L, GS);
       return c;
     }
   }
@@ -688,7 +727,11 @@ static int enq_inner(sg_handle h, Ctx& cx, int pat, int nb, int R, int s0, const
         default: break;
       }
 #undef SG_TEAM
-    } else if (lc.gs)
+    } else if (lc.wide)
+      sgk::k_line_w<T><<<lg, lc.block, lc.smem, s>>>(L, LSp, pr.nl, pr.P, R, NG, NT, lc.G, lc.GS, pstride_pad,
+                                                     Sinv_pad, Bd, Bu, nb, w.x, w.r, w.z, w.p0, w.p1, w.q, h->ctl,
+                                                     init, tol2, bb_min, imax, hh, use);
+    else if (lc.gs)
       sgk::k_line<T, true><<<lg, lc.block, lc.smem, s>>>(L, pr.nl, pr.P, R, NG, NT, pstride, Sinv, Bd, Bu, nb, w.x,
                                                          w.r, w.z, w.p0, w.p1, w.q, h->ctl, init, tol2, bb_min, imax,
                                                          hh, use);
@@ -1141,10 +1184,18 @@ static int build_line_factors(sg_handle h) {
     RET(dalloc(h, &h->lf32[pat].Bd, (long long)nsub * L * L));
     RET(dalloc(h, &h->lf32[pat].Bu, (long long)nsub * L * L));
     sgk::k_cvt<double, float><<<nblk(ns), 256, 0, h->st>>>(ns, h->lf[pat].Sinv, h->lf32[pat].Sinv);
-    if (pad4(L) <= TEAM_LS_MAX) {
+    {
+      // rows padded to pad4(L) values: the staged FP32 team kernel and the register-tiled kernel
+      // (FP32 and FP64 copies) read 16-byte pieces
       const long long nrows = (long long)nsub * L * L;
       RET(dalloc(h, &h->lf32[pat].Spad, nrows * pad4(L)));
-      sgk::k_pad_factor<<<nblk(nrows * pad4(L)), 256, 0, h->st>>>(nrows, L, pad4(L), h->lf[pat].Sinv, h->lf32[pat].Spad);
+      sgk::k_pad_factor<float><<<nblk(nrows * pad4(L)), 256, 0, h->st>>>(nrows, L, pad4(L), h->lf[pat].Sinv,
+                                                                        h->lf32[pat].Spad);
+      if (L >= WIDE_LMIN) {
+        RET(dalloc(h, &h->lf[pat].Spad, nrows * pad4(L)));
+        sgk::k_pad_factor<double><<<nblk(nrows * pad4(L)), 256, 0, h->st>>>(nrows, L, pad4(L), h->lf[pat].Sinv,
+                                                                           h->lf[pat].Spad);
+      }
     }
     sgk::k_cvt<double, float><<<nblk((long long)nsub * L * L), 256, 0, h->st>>>((long long)nsub * L * L, h->lf[pat].Bd,
                                                                                h->lf32[pat].Bd);
@@ -1485,10 +1536,18 @@ static int autotune_t(sg_handle h, int nb) {
       const long long pstride_pad = (long long)L * L * pad4(L);
       int best_g = 0;
       float best = 1e30f;
-      for (int g = 1; g <= std::min(pr.P, 15); ++g) {
+      std::vector<int> cands;
+      g_tune.erase(key);
+      if (line_cfg<T>(pr, nb).wide) {
+        // register-tiled kernel: whole mode groups of 1 .. 4 blocks per problem
+        for (int ng = 1; ng <= std::min(4, pr.P); ++ng) cands.push_back((pr.P + ng - 1) / ng);
+      } else {
+        for (int g = 1; g <= std::min(pr.P, 15); ++g) cands.push_back(g);
+      }
+      for (int g : cands) {
         g_tune[key] = g;
         const LineCfg lc = line_cfg<T>(pr, nb);
-        if (lc.G != g && !(lc.team && lc.G == (pr.P + lc.NG - 1) / lc.NG && lc.G <= g)) continue;
+        if (!lc.wide && lc.G != g && !(lc.team && lc.G == (pr.P + lc.NG - 1) / lc.NG && lc.G <= g)) continue;
         int TL, NT, stage;
         size_t sm;
         apply_cfg<T>(pr, nb, &TL, &NT, &sm, &stage);
@@ -1508,6 +1567,10 @@ static int autotune_t(sg_handle h, int nb) {
               default: break;
             }
 #undef SG_TEAM_T
+          } else if (lc.wide) {
+            sgk::k_line_w<T><<<lg, lc.block, lc.smem, st>>>(L, pad4(L), pr.nl, pr.P, 1, lc.NG, NT, lc.G, lc.GS,
+                                                            pstride_pad, lf.Spad, lf.Bd, lf.Bu, nb, w.x, w.r, w.z,
+                                                            w.p0, w.p1, w.q, h->ctl, 1, 1e-30, 1e300, 1, 0, 0);
           } else if (lc.gs) {
             sgk::k_line<T, true><<<lg, lc.block, lc.smem, st>>>(L, pr.nl, pr.P, 1, lc.NG, NT, pstride, lf.Sinv, lf.Bd,
                                                                 lf.Bu, nb, w.x, w.r, w.z, w.p0, w.p1, w.q, h->ctl, 1,
@@ -1608,6 +1671,8 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   h->warm_lr = prm->warm_lr > 0 ? (float)prm->warm_lr : 1e-3f;
   h->am = 1.0 / (ZETA * pr.dt * pr.dt) + pr.alpha0 * GAMMA / (ZETA * pr.dt);
   h->bk = 1.0 + pr.alpha1 * GAMMA / (ZETA * pr.dt);
+  // first CUDA call: every argument check is above
+  CK(cudaGetDevice(&h->dev));
   if (!h->st) {  // private stream when the caller passes none
     CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
     h->own_st = true;
@@ -1638,6 +1703,8 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
     RET(smem_attr(h, sgk::k_line<float>, lim));
     RET(smem_attr(h, sgk::k_line<double, true>, lim));
     RET(smem_attr(h, sgk::k_line<float, true>, lim));
+    RET(smem_attr(h, sgk::k_line_w<double>, lim));
+    RET(smem_attr(h, sgk::k_line_w<float>, lim));
     RET(smem_attr(h, sgk::k_apply<double, double, false, false, sgk::GDynNoDS>, lim));
     RET(smem_attr(h, sgk::k_apply<double, double, true, true, sgk::GDynNoDS>, lim));
     RET(smem_attr(h, sgk::k_apply<float, float, false, false, sgk::GDynNoDS>, lim));
@@ -1934,31 +2001,47 @@ int sg_get_moments(sg_handle h, double* mean, double* var, int on_device) {
 }
 
 // ---- moments without allocation: static device staging array ----
-// Capacity: SG_NOALLOC_MAX_FREE free nodes (mean and variance, 2 x 2^20 doubles = 16 MiB).  The array
-// is a file-scope device variable, so every GPU that loads this library holds it until exit.
-constexpr int SG_NOALLOC_MAX_FREE = 1 << 20;
+// Capacity: SG_NOALLOC_MAX_FREE (include/sg.h) free nodes, mean and variance: 2 x 2^20 doubles =
+// 16 MiB.  The array is a file-scope device variable, so every GPU that loads this library holds it
+// until the process exits.
 static __device__ __align__(256) double g_noalloc_stage[2 * (size_t)SG_NOALLOC_MAX_FREE];
 constexpr int SG_NOALLOC_MAX_DEV = 64;
-static double* g_noalloc_ptr[SG_NOALLOC_MAX_DEV] = {};
+// Device address of the array per device.  Threads that race on the first look-up on a device all
+// store the same address, so a relaxed atomic is enough.
+static std::atomic<double*> g_noalloc_ptr[SG_NOALLOC_MAX_DEV];
 
 int sg_get_moments_noalloc(sg_handle h, double* mean, double* var) {
-  if (!h || (!mean && !var)) return SG_EINVAL;
+  if (!h) return SG_EINVAL;
+  if (!mean && !var) {
+    h->err = "sg_get_moments_noalloc: mean and var are both NULL";
+    return SG_EINVAL;
+  }
   const auto& pr = h->pr;
   if (pr.n_free > SG_NOALLOC_MAX_FREE) {
     h->err = "sg_get_moments_noalloc: more free nodes than the static staging array holds (2^20)";
     return SG_EINVAL;
   }
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= SG_NOALLOC_MAX_DEV) { h->err = "sg_get_moments_noalloc: device index out of range"; return SG_EINVAL; }
-  if (!g_noalloc_ptr[dev]) {
-    // one-time set-up on this device: the host-side symbol is only a stand-in, the kernel needs
-    // the array's device address
+  // the kernel runs on the handle's stream, which belongs to the device of sg_setup: the array's
+  // address must be that device's
+  int cur = -1;
+  CK(cudaGetDevice(&cur));
+  if (cur != h->dev) {
+    h->err = "sg_get_moments_noalloc: the current device is not the one the handle was set up on";
+    return SG_EINVAL;
+  }
+  if (h->dev < 0 || h->dev >= SG_NOALLOC_MAX_DEV) {
+    h->err = "sg_get_moments_noalloc: device index out of range";
+    return SG_EINVAL;
+  }
+  double* dm = g_noalloc_ptr[h->dev].load(std::memory_order_relaxed);
+  if (!dm) {
+    // one-time set-up on this device, with it current: in host code the array's name is only a
+    // stand-in, the kernel needs the device address
     void* p = nullptr;
     CK(cudaGetSymbolAddress(&p, g_noalloc_stage));
-    g_noalloc_ptr[dev] = static_cast<double*>(p);
+    dm = static_cast<double*>(p);
+    g_noalloc_ptr[h->dev].store(dm, std::memory_order_relaxed);
   }
-  double* dm = g_noalloc_ptr[dev];
   double* dv = dm + SG_NOALLOC_MAX_FREE;
   // every entry that is copied out is written first, so nothing needs clearing between calls
   sgk::k_moments<<<nblk(pr.n_free), 256, 0, h->st>>>(pr.n_free, pr.P, h->free_owner, h->U, mean ? dm : nullptr,
@@ -2038,7 +2121,7 @@ int sg_plan_query(const sg_grid* grid, const sg_kl* kl, const sg_pce* pce, const
     p.apply_tiles[i] = NT;
     p.apply_smem[i] = (long long)sm;
     const LineCfg lc = line_cfg<T>(pr, pr.nsub);
-    p.line_kind[i] = lc.team ? 1 : lc.gs ? 2 : 0;
+    p.line_kind[i] = lc.team ? 1 : lc.gs ? 2 : lc.wide ? 3 : 0;
     p.line_modes[i] = lc.G;
     p.line_groups[i] = lc.NG;
     p.line_block[i][0] = (int)lc.block.x; p.line_block[i][1] = (int)lc.block.y; p.line_block[i][2] = (int)lc.block.z;

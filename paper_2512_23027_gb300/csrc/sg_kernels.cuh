@@ -8,6 +8,7 @@
 #pragma once
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include "sg_gfix.cuh"
@@ -886,6 +887,338 @@ __global__ void k_line_team(int L, int nl, int P, int R, int NG, int NT, int G, 
   line_control(s_rz, s_rr, b, grp, NG, NT, nb, ctl, init, tol2, bb_min, max_it, cond_handle, use_handle);
 }
 
+// Mean-operator line solve fused with the inner CG update, register-tiled form for wide subdomains
+// (one block per (problem, group of G modes); with G = P the factor of a subdomain is streamed once
+// per sweep).  Per line step the block forms Y = S_j^{-1} W for all L rows and its G modes; thread
+// (rt, mt) accumulates the 2 x 4 tile rows 2 rt, 2 rt + 1, modes 4 mt .. 4 mt + 3 in registers (two
+// accumulator sets, even and odd c, so consecutive multiply-adds never wait on one another).
+// Because S_j^{-1} is symmetric, row c of the stored factor holds column c, so the two factor
+// values of a tile for one c are one vector load, as are the four modes of W.  The factor is
+// stored with rows padded to LSP = 4 ceil(L / 4) values (zeros beyond L) and double-buffered by
+// 16-byte cp.async together with the coupling rows B_j.  Global vectors move in row order: thread t
+// keeps mode t mod G and visits rows t / G, t / G + RPI, ... (RPI = threads / G rows per pass), so a
+// line is read and written contiguously; the next line is prefetched into registers while the
+// current one is multiplied.  The forward sweep keeps y_j in shared memory for one step and parks
+// it in z; the backward sweep reads it back.  r . z = r^T A0^{-1} r is formed in the forward sweep as
+// sum_j w_j . y_j (block LDL^T: A0^{-1} = L^{-T} D^{-1} L^{-1}, w = L^{-1} r, y = D^{-1} w), so the
+// backward sweep needs no residual.  Shared memory: Sb [2][L][LSP], Ws [L][GS], Ys [L][GS],
+// Yp [LSP][GS], Bs [2][2][L] (GS = G rounded up to a multiple of 4).
+// One line product acc = S_j-tile x W over c = 0 .. L-1 (rows r0, r0 + 1 of the tile from row c of the
+// stored symmetric factor, four modes of W); even and odd c accumulate separately.
+template <typename T>
+__device__ __forceinline__ void tile_product(T (&acc)[2][4], const T* __restrict__ Sj, const T* __restrict__ Wc,
+                                             int L, int LSP, int GS) {
+  using V2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+  T acc2[2][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc2[i][k] = T(0);
+  auto ld4 = [](const T* p, T (&w)[4]) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 v = *reinterpret_cast<const float4*>(p);
+      w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    } else {
+      const double2 v0 = *reinterpret_cast<const double2*>(p), v1 = *reinterpret_cast<const double2*>(p + 2);
+      w[0] = v0.x; w[1] = v0.y; w[2] = v1.x; w[3] = v1.y;
+    }
+  };
+  int c = 0;
+#pragma unroll 2
+  for (; c + 1 < L; c += 2) {
+    const V2 s0 = *reinterpret_cast<const V2*>(Sj + c * LSP);
+    const V2 s1 = *reinterpret_cast<const V2*>(Sj + (c + 1) * LSP);
+    T w0[4], w1[4];
+    ld4(Wc + c * GS, w0);
+    ld4(Wc + (c + 1) * GS, w1);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      acc[0][k] = fma(s0.x, w0[k], acc[0][k]);
+      acc[1][k] = fma(s0.y, w0[k], acc[1][k]);
+      acc2[0][k] = fma(s1.x, w1[k], acc2[0][k]);
+      acc2[1][k] = fma(s1.y, w1[k], acc2[1][k]);
+    }
+  }
+  if (c < L) {
+    const V2 s0 = *reinterpret_cast<const V2*>(Sj + c * LSP);
+    T w0[4];
+    ld4(Wc + c * GS, w0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      acc[0][k] = fma(s0.x, w0[k], acc[0][k]);
+      acc[1][k] = fma(s0.y, w0[k], acc[1][k]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[i][k] += acc2[i][k];
+}
+
+// FP32 partial sums with a range guard: when every operand lies in [2^-60, 2^60] (or is zero),
+// products neither overflow nor lose their contribution to underflow, so a line's partial is summed
+// in FP32 and added to the FP64 total once; otherwise the line is summed in FP64.
+__device__ __forceinline__ bool f32_range_ok(float amax, float amin_nz) {
+  return amax <= 0x1p60f && amin_nz >= 0x1p-60f;
+}
+
+// rows per thread and line of the row-ordered line I/O: four arrays of them stay in registers
+template <typename T>
+__host__ __device__ constexpr int lw_npf() { return 8; }
+constexpr int LW_MAXT = 256;  // threads per block of k_line_w
+template <typename T>
+__host__ __device__ constexpr int lw_minb() { return sizeof(T) == 4 ? 2 : 1; }  // blocks per SM (register budget)
+
+template <typename T>
+__global__ void __launch_bounds__(LW_MAXT, lw_minb<T>()) k_line_w(int L, int LSP, int nl, int P, int R, int NG, int NT, int G, int GS,
+                                                    long long pat_stride, const T* __restrict__ Spad,
+                                                    const T* __restrict__ Bd, const T* __restrict__ Bu, int nb,
+                                                    T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, T* pbuf0,
+                                                    T* pbuf1, const T* __restrict__ q, CgCtl ctl, int init, double tol2,
+                                                    double bb_min, int max_it, cudaGraphConditionalHandle cond_handle,
+                                                    int use_handle) {
+  count_launch();
+  constexpr int NPF = lw_npf<T>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T alpha_s;
+  const int LLS = L * LSP;
+  T* Sb = reinterpret_cast<T*>(smem_raw);  // [2][L][LSP]
+  T* Ws = Sb + 2 * LLS;                    // [L][GS]
+  T* Ys = Ws + L * GS;                     // [L][GS]
+  T* Yp = Ys + L * GS;                     // [LSP][GS]
+  T* Bs = Yp + LSP * GS;                   // [2][2][L]: coupling row r at Bs[r & 1] (Bd, then Bu)
+  const int b = blockIdx.x / NG, grp = blockIdx.x % NG;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int NMT = GS >> 2, NRT = LSP >> 1;
+  const int mt = tid % NMT, rt = tid / NMT;
+  const bool worker = rt < NRT;
+  const int a0 = rt * 2, m0 = mt * 4;
+  const int kb = grp * G;
+  const int gl = min(G, P - kb);
+  // row-ordered I/O: fixed mode io_m, rows io_a + kk * RPI
+  const int RPI = nthr / gl;
+  const int io_m = tid % gl, io_a = tid / gl;
+  const bool io_on = io_a < RPI;
+  const int LP = L * P;
+  const int rstep = RPI * P, sstep = RPI * GS;
+  const bool act = init ? true : (ctl.active[b] != 0);
+  double s_rz = 0.0, s_rr = 0.0;
+  if (act) {
+    const int sub = b / R;
+    const T* S = Spad + (long long)sub * pat_stride;
+    const T* bd = Bd + (long long)sub * L * L;
+    const T* bu = Bu + (long long)sub * L * L;
+    const long long base = (long long)b * nl * P + kb + io_m;  // + (j L + a) P for element (j, a)
+    T* rb = r + base;
+    T* xb = x + base;
+    T* zb = z + base;
+    const T* qb = q + base;
+    auto copy_line = [&](int j) {  // S_j^{-1} -> Sb[j & 1] (16-byte pieces)
+      const int4* src = reinterpret_cast<const int4*>(S + (long long)j * LLS);
+      int4* dst = reinterpret_cast<int4*>(Sb + (j & 1) * LLS);
+      const int n16 = LLS * (int)sizeof(T) / 16;
+      for (int e = tid; e < n16; e += nthr) cp_async16(dst + e, src + e);
+    };
+    auto copy_coupling = [&](int row) {  // Bd, Bu of line `row` -> Bs[row & 1]
+      T* dst = Bs + (row & 1) * 2 * L;
+      for (int e = tid; e < 2 * L; e += nthr)
+        cp_async_elem(dst + e, e < L ? bd + (long long)row * L + e : bu + (long long)row * L + (e - L));
+    };
+    copy_line(0);
+    cp_async_commit();
+    for (int e = tid; e < L * GS; e += nthr) Ws[e] = T(0);
+    for (int e = tid; e < LSP * GS; e += nthr) Yp[e] = T(0);
+    const T* pb = nullptr;
+    if (!init) {
+      pb = ((*ctl.parity) ? pbuf0 : pbuf1) + base;  // p_new written by the apply kernel
+      if (tid < 32) {
+        double pq = 0.0;
+        for (int t = tid; t < NT; t += 32) pq += ctl.part_pq[(long long)b * NT + t];
+        for (int o = 16; o > 0; o >>= 1) pq += __shfl_down_sync(0xffffffffu, pq, o);
+        if (tid == 0) {
+          // a vanishing or non-finite p.q freezes the problem at its current iterate; the control
+          // step below then retires it
+          const double al = (pq > 0.0 && isfinite(pq)) ? ctl.rz[b] / pq : 0.0;
+          alpha_s = isfinite(al) ? (T)al : T(0);
+        }
+      }
+    }
+    T pr_r[NPF], pr_q[NPF], pr_p[NPF], pr_x[NPF];
+    auto fetch = [&](int j) {
+      if (!io_on) return;
+      const int o0 = j * LP + io_a * P;
+#pragma unroll
+      for (int kk = 0; kk < NPF; ++kk) {
+        if (io_a + kk * RPI < L) {
+          const int o = o0 + kk * rstep;
+          pr_r[kk] = rb[o];
+          if (!init) { pr_q[kk] = qb[o]; pr_p[kk] = pb[o]; pr_x[kk] = xb[o]; }
+        }
+      }
+    };
+    fetch(0);
+    __syncthreads();
+    const T alpha = init ? T(0) : alpha_s;
+    // ---- forward sweep: y_j = S_j^{-1} (r_j - B_{j-1}^T y_{j-1}) ----
+    for (int j = 0; j < L; ++j) {
+      if (io_on) {
+        const T* cb = Bs + ((j - 1) & 1) * 2 * L;
+        const int o0 = j * LP + io_a * P;
+        const int s0 = io_a * GS + io_m;
+        T amax = T(0), amin = T(1);
+        T rr = T(0);
+#pragma unroll
+        for (int kk = 0; kk < NPF; ++kk) {
+          const int a = io_a + kk * RPI;
+          if (a < L) {
+            const int o = o0 + kk * rstep, si = s0 + kk * sstep;
+            T rv = pr_r[kk];
+            if (!init) {
+              rv -= alpha * pr_q[kk];
+              rb[o] = rv;
+              xb[o] = pr_x[kk] + alpha * pr_p[kk];
+            }
+            const T av = abs(rv);
+            amax = max(amax, av);
+            if (av != T(0)) amin = min(amin, av);
+            rr = fma(rv, rv, rr);
+            T wv = rv;
+            if (j > 0) {
+              const T yp = Yp[si];
+              wv -= cb[a] * yp;
+              if (a > 0) wv -= cb[L + a - 1] * Yp[si - GS];
+              zb[o - LP] = yp;  // y_{j-1} parked in z
+            }
+            Ws[si] = wv;
+          }
+        }
+        if (sizeof(T) == 8 || f32_range_ok((float)amax, (float)amin)) {
+          s_rr += (double)rr;
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < NPF; ++kk)
+            if (io_a + kk * RPI < L) {
+              const double v = (double)rb[o0 + kk * rstep];
+              s_rr += v * v;
+            }
+        }
+      }
+      if (j + 1 < L) {
+        copy_line(j + 1);
+        copy_coupling(j);
+      }
+      cp_async_commit();
+      if (j + 1 < L) fetch(j + 1);
+      cp_async_wait1();
+      __syncthreads();
+      if (worker) {
+        T acc[2][4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc[i][k] = T(0);
+        const T* Sj = Sb + (j & 1) * LLS + a0;
+        const T* Wc = Ws + m0;
+        tile_product(acc, Sj, Wc, L, LSP, GS);
+        T rz = T(0), amax = T(0), amin = T(1);
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int a = a0 + i;
+            Yp[a * GS + m0 + k] = acc[i][k];
+            if (a < L) {
+              const T wv = Ws[a * GS + m0 + k];  // zero for modes beyond the block's
+              rz = fma(wv, acc[i][k], rz);
+              const T aw = abs(wv), ay = abs(acc[i][k]);
+              amax = max(amax, max(aw, ay));
+              if (aw != T(0)) amin = min(amin, aw);
+              if (ay != T(0)) amin = min(amin, ay);
+            }
+          }
+        if (sizeof(T) == 8 || f32_range_ok((float)amax, (float)amin)) {
+          s_rz += (double)rz;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              if (a0 + i < L) s_rz += (double)Ws[(a0 + i) * GS + m0 + k] * (double)acc[i][k];
+        }
+      }
+      __syncthreads();
+    }
+    // ---- backward sweep: x_j = y_j - S_j^{-1} B_j x_{j+1} (x_{L-1} = y_{L-1} is in Yp) ----
+    // y_j is read back by the thread that parked it (same row order); S_{L-2} and coupling row
+    // L - 2 are still in their buffers (the forward sweep loaded nothing after them)
+    T pr_y[NPF];
+    auto fetch_y = [&](int j) {
+      if (!io_on) return;
+      const int o0 = j * LP + io_a * P;
+#pragma unroll
+      for (int kk = 0; kk < NPF; ++kk)
+        if (io_a + kk * RPI < L) pr_y[kk] = zb[o0 + kk * rstep];
+    };
+    if (L >= 2) fetch_y(L - 2);
+    for (int j = L - 2; j >= 0; --j) {
+      if (io_on) {
+        const T* cb = Bs + (j & 1) * 2 * L;
+        const int o0 = j * LP + io_a * P;
+        const int s0 = io_a * GS + io_m;
+#pragma unroll
+        for (int kk = 0; kk < NPF; ++kk) {
+          const int a = io_a + kk * RPI;
+          if (a < L) {
+            const int o = o0 + kk * rstep, si = s0 + kk * sstep;
+            const T xn = Yp[si];
+            T tv = cb[a] * xn;
+            if (a + 1 < L) tv += cb[L + a] * Yp[si + GS];
+            zb[o + LP] = xn;  // x_{j+1} final
+            Ws[si] = tv;
+            Ys[si] = pr_y[kk];
+          }
+        }
+      }
+      if (j >= 1) {
+        copy_line(j - 1);
+        copy_coupling(j - 1);
+      }
+      cp_async_commit();
+      if (j >= 1) fetch_y(j - 1);
+      cp_async_wait1();
+      __syncthreads();
+      if (worker) {
+        T acc[2][4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc[i][k] = T(0);
+        const T* Sj = Sb + (j & 1) * LLS + a0;
+        const T* Wc = Ws + m0;
+        tile_product(acc, Sj, Wc, L, LSP, GS);
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int a = a0 + i;
+            Yp[a * GS + m0 + k] = a < L ? Ys[a * GS + m0 + k] - acc[i][k] : T(0);
+          }
+      }
+      __syncthreads();
+    }
+    cp_async_wait0();
+    // x_0
+    if (io_on) {
+      const int s0 = io_a * GS + io_m;
+      const int o0 = io_a * P;
+#pragma unroll
+      for (int kk = 0; kk < NPF; ++kk)
+        if (io_a + kk * RPI < L) zb[o0 + kk * rstep] = Yp[s0 + kk * sstep];
+    }
+  }
+  line_control(s_rz, s_rr, b, grp, NG, NT, nb, ctl, init, tol2, bb_min, max_it, cond_handle, use_handle);
+}
+
 // Line factorisation, FP64: one block per (subdomain, pattern).  D (within-line tridiagonal)
 // diag Dd[j][a], upper Du[j][a]; coupling Bd, Bu as above.  Writes Sinv[j] (L x L).
 // status[blk] = 1 when a pivot is not positive (the matrix is not SPD).
@@ -1486,13 +1819,14 @@ __global__ void k_axpby(long long n, T a, const T* __restrict__ x, T b, const T*
 }
 
 // FP64 line factor [sub][j][a][c] -> FP32 copy with rows zero-padded to LS columns
-__global__ void k_pad_factor(long long nrows, int L, int LS, const double* __restrict__ src, float* __restrict__ dst) {
+template <typename TO>
+__global__ void k_pad_factor(long long nrows, int L, int LS, const double* __restrict__ src, TO* __restrict__ dst) {
   count_launch();
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nrows * LS) return;
   const long long row = i / LS;
   const int c = (int)(i - row * LS);
-  dst[i] = c < L ? (float)src[row * L + c] : 0.0f;
+  dst[i] = c < L ? (TO)src[row * L + c] : TO(0);
 }
 
 // plain type conversion y = (TO) x

@@ -41,3 +41,14 @@ def test_binding_fails_loudly_without_library(tmp_path):
             binding.load_library(str(tmp_path / "missing.so"))
     finally:
         binding._LIB = saved
+
+
+def test_noalloc_capacity_is_the_header_constant():
+    """The static staging array of sg_get_moments_noalloc is sized by the header's
+    SG_NOALLOC_MAX_FREE (2^20 free nodes), which the library source does not redefine."""
+    hdr = open(os.path.join(ROOT, "include", "sg.h")).read()
+    m = re.search(r"#define\s+SG_NOALLOC_MAX_FREE\s+\(1 << (\d+)\)", hdr)
+    assert m and int(m.group(1)) == 20
+    src = open(os.path.join(ROOT, "paper_2512_23027_gb300", "csrc", "sg_cuda.cu")).read()
+    assert "g_noalloc_stage[2 * (size_t)SG_NOALLOC_MAX_FREE]" in src
+    assert not re.search(r"(constexpr|#define)\s+\w*\s*SG_NOALLOC_MAX_FREE", src)

@@ -1,9 +1,13 @@
-"""GPU test of sg_get_moments_noalloc, the entry point for callers that must not allocate device
-memory (it stages results in a fixed static device array instead of handle-owned memory).
+"""GPU test of sg_get_moments_noalloc, the entry point for callers that cannot allocate device
+memory (a host application whose allocator owns the device, or a latency-critical loop that must
+not pay for cudaMalloc): it stages its results in a fixed static device array inside the library
+instead of handle-owned memory.
 
 It is called through the C ABI directly and compared with sg_get_moments on the same handle, on
-two calls in a row with a time step in between.  This file sorts last so that a run stopping at the
-first failure has already run every other test; it also passes on its own in a fresh process."""
+two calls in a row with a time step in between, for each choice of outputs (mean and variance,
+mean only, variance only); asking for neither is an argument error.  This file sorts last so that
+a run stopping at the first failure has already run every other test; it also passes on its own in
+a fresh process."""
 import ctypes
 
 import numpy as np
@@ -13,26 +17,48 @@ import sg_workloads as w
 
 pytestmark = pytest.mark.gpu
 
+SG_EINVAL = -1
 
-def test_noalloc_moments_match_allocating_entry_point():
+
+def _solver():
     from paper_2512_23027_gb300 import build as b
     b.build()
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2512_23027_gb300 import Solver
-    s = Solver(w.config("small"))
+    return Solver(w.config("small"))
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else ctypes.c_void_p(0)
+
+
+@pytest.mark.parametrize("want", ["both", "mean", "var"])
+def test_noalloc_moments_match_allocating_entry_point(want):
+    s = _solver()
     lib = s.lib
     n = s.n_free
     for call in range(2):
         s.step(2)
         mean_ref, var_ref = s.moments()
-        mean = np.full(n, np.nan)
-        var = np.full(n, np.nan)
-        rc = lib.sg_get_moments_noalloc(s.h, ctypes.c_void_p(mean.ctypes.data), ctypes.c_void_p(var.ctypes.data))
+        mean = np.full(n, np.nan) if want in ("both", "mean") else None
+        var = np.full(n, np.nan) if want in ("both", "var") else None
+        rc = lib.sg_get_moments_noalloc(s.h, _ptr(mean), _ptr(var))
         assert rc == 0, (rc, lib.sg_last_error(s.h))
-        # identical kernel on identical data: agreement to the last bit (tolerance stated for form)
-        assert np.allclose(mean, mean_ref, rtol=1e-15, atol=0.0), call
-        assert np.allclose(var, var_ref, rtol=1e-15, atol=0.0), call
-        assert np.abs(mean).max() > 0.0
+        # the same kernel on the same data: agreement to the last bit (tolerance stated for form)
+        if mean is not None:
+            assert np.allclose(mean, mean_ref, rtol=1e-15, atol=0.0), call
+            assert np.abs(mean).max() > 0.0
+        if var is not None:
+            assert np.allclose(var, var_ref, rtol=1e-15, atol=0.0), call
+            assert np.abs(var).max() > 0.0
+    s.close()
+
+
+def test_noalloc_moments_rejects_no_outputs():
+    s = _solver()
+    rc = s.lib.sg_get_moments_noalloc(s.h, ctypes.c_void_p(0), ctypes.c_void_p(0))
+    assert rc == SG_EINVAL
+    assert b"NULL" in s.lib.sg_last_error(s.h)
     s.close()
