@@ -87,7 +87,9 @@ class DDSolver:
     of each subdomain only (Eq. ki), so that sum_s R_s^T K_GG^s R_s gives the global
     interface block (Eq. GAssembly_Sto)."""
 
-    def __init__(self, prob, explicit: bool = False):
+    def __init__(self, prob, explicit: bool = False, subs=None):
+        """subs: indices of the only subdomains whose local operators are built (timing samples of
+        large workloads); the coarse problem, which needs every subdomain, is then not assembled."""
         self.prob = prob
         N, s = prob.N, prob.s
         self.part = Partition(N, s)
@@ -99,7 +101,10 @@ class DDSolver:
         self.nG = nG
         self.nC = part.corner.size
         self.loc = []
-        for sub in part.subs:
+        self.sampled = subs is not None
+        for si, sub in enumerate(part.subs):
+            if subs is not None and si not in subs:
+                continue
             Mfull, Kfull = fem.assemble(N, self.coef, sub["elem_mask"])
             nd = sub["nodes"]
             M = Mfull[nd][:, nd].tocsr()
@@ -132,6 +137,8 @@ class DDSolver:
             L["ir_r"] = dofs(np.nonzero(cls[irpos] == "r")[0], P)
             L["ir_i"] = dofs(np.nonzero(cls[irpos] == "i")[0], P)
             self.loc.append(L)
+        if subs is not None:
+            return
         self._build_coarse()
         if explicit:
             self._build_explicit()
