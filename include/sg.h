@@ -24,7 +24,9 @@
  *     multi-index order (total degree, then descending lexicographic), orthonormal basis.
  *
  * Environment switches.  They select between complete implementations of the same step and never
- * skip work.  Set them before sg_setup; the tile choices also read them per launch.  Each is "on"
+ * skip work.  Set them before sg_setup and keep them set while the handle steps: the set-up reads
+ * some, and the launch shapes read the others when the step graph is captured at the first sg_step
+ * (and at every launch in the host-driven mode).  Each is "on"
  * when set, whatever its value (except SG_FORCE_NODS).
  *   SG_EAGER        sg_step enqueues the step's kernels from the host instead of launching the
  *                   captured graph: the same kernels, visible to profilers that cannot enter
@@ -32,8 +34,12 @@
  *   SG_PDL          programmatic dependent launch between the FP32 inner-loop kernels.
  *   SG_NO_MMA       FP32 subdomain CG preconditioned by the line sweeps of the mean operator
  *                   instead of its dense BF16 inverse on the tensor cores.
- *   SG_NO_GFIX      FP32 operator apply with the runtime triple-product table instead of the table
- *                   compiled for (M, p, p_in).
+ *   SG_NO_GFIX      FP32 and FP64 operator applies with the runtime triple-product table instead of
+ *                   the table compiled for (M, p, p_in).
+ *   SG_FP64_RT      FP64 operator applies with the runtime triple-product table (FP32 keeps the
+ *                   compiled one).
+ *   SG_LINE_OLD     mean-operator line sweeps of subdomains at least 41 nodes wide by the block kernel
+ *                   with the factor staged line by line, instead of the register-tiled kernel.
  *   SG_FORCE_NODS   apply without staged edge differences at every size; the value 2 also reads the
  *                   triple-product table from global memory (the variants of the widest subdomains).
  *   SG_FORCE_GLINE  line sweep reading the factor and residual from global memory at every size.

@@ -167,6 +167,7 @@ struct sg_handle_s {
     } else {
       o.kapE = (const T*)kapE32; o.kapN = (const T*)kapN32; o.gk_v = (const T*)gk_v32;
     }
+
     o.kapE += (size_t)s0 * pr.nl * pr.PI;
     o.kapN += (size_t)s0 * pr.nl * pr.PI;
     o.gk_ptr = gk_ptr; o.gk_i = gk_i; o.gk_j = gk_j; o.gk_pk = gk_pk;
@@ -360,18 +361,24 @@ static bool gfix_matches(const sgh::Problem& pr) {
   return true;
 }
 
-// FP64 applies keep the runtime-table kernel: FP64 arithmetic runs at about 1/60 of the FP32 rate on
-// this part, so the FP64 flux is bound by the DP pipe either way, and the register-resident variant
-// (about 200 registers, one block per SM) measured 3x slower (348 vs 104 us at 128^2, P = 20).
+// FP64 applies use the compiled table too (SG_FP64_RT selects the runtime-table kernel).  With every
+// subdomain problem active (1024^2 workload from step 200) the compiled FP64 apply takes 4.44 ms per
+// launch against 5.77 ms for the runtime table (FP64 step 2471 -> 2229 ms, mixed step 176 -> 168 ms).
+// An earlier measurement in the first steps of the 128^2 workload, where most subdomain problems are
+// inactive and the launch is latency-bound, had favoured the runtime table.
 template <class C>
-constexpr bool gfix_fp64_ok() { return false; }
+constexpr bool gfix_fp64_ok() { return true; }
 
-// compiled table usable for element type T (-1: runtime-table kernel)
+// compiled table usable for element type T (-1: runtime-table kernel): the table must match the PCE
+// sizes and a one-line tile of the compiled kernel (input lines and fluxes) must fit shared memory
+constexpr size_t SMEM_TILE_FIX = 200 * 1024;
 template <typename T>
 static int gfix_for(const sgh::Problem& pr) {
   if (pr.gfix < 0) return -1;
-  if (sizeof(T) == 8) return -1;
-  return pr.gfix;
+  if (sizeof(T) == 8 && std::getenv("SG_FP64_RT")) return -1;
+  const size_t L = pr.L, P = pr.P, PS = pr.P | 1;
+  const size_t one_line = sizeof(T) * (3 * L * P + ((L - 1) + 2 * L) * PS) + 16;
+  return one_line <= SMEM_TILE_FIX ? pr.gfix : -1;
 }
 
 // Kernel launch that may overlap its prologue with the tail of the previous kernel in the stream

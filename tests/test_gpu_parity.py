@@ -35,6 +35,22 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
+def rel_modes(a, b, floor=1e-3):
+    """||a_k - b_k|| / max(||b_k||, floor ||b||) for every PCE mode k (columns): each mode against its
+    own norm, except modes smaller than `floor` of the whole field (in early steps the highest modes
+    can be 1e-6 of the mean), which are measured against floor ||b||."""
+    return np.linalg.norm(a - b, axis=0) / np.maximum(np.linalg.norm(b, axis=0), floor * np.linalg.norm(b))
+
+
+# Bars of the FP64 path at PCG tolerance 1e-13 on both sides.  U: 1e-10 relative over all nodes and
+# modes, 1e-9 for every mode on its own (the higher modes are orders of magnitude smaller than the
+# mean).  V and A come from U through the Newmark relations: a_{n+1} = u_{n+1} / (zeta dt^2) - u~_m
+# subtracts two terms each about 1 / (omega dt)^2 times larger than a_{n+1} itself, so U's relative
+# error reaches A amplified by that factor (dt = 0.02 on the 8^2 problem: about 10^2) and V through
+# the trapezoidal update by about half of it.
+BAR_U, BAR_U_MODE, BAR_V, BAR_A = 1e-10, 1e-9, 1e-9, 1e-8
+
+
 @pytest.mark.parametrize("name,steps", [("tiny", 5), ("small", 4), ("pulse32", 5)])
 def test_fp64_matches_oracle(lib, name, steps):
     prob = w.config(name)
@@ -45,10 +61,41 @@ def test_fp64_matches_oracle(lib, name, steps):
     s.close()
     Ur, Vr, Ar, _ = oracle_run(prob, steps, 1e-13)
     n = prob.P * Ur.shape[0]
-    assert rel(U, Ur) <= TOL_FP64, rel(U, Ur)
-    assert rel(state[n:2 * n].reshape(Vr.shape), Vr) <= 1e-9
-    assert rel(state[2 * n:3 * n].reshape(Ar.shape), Ar) <= 1e-8
+    V = state[n:2 * n].reshape(Vr.shape)
+    A = state[2 * n:3 * n].reshape(Ar.shape)
+    print(f"{name}: U {rel(U, Ur):.2e} (worst mode {rel_modes(U, Ur).max():.2e}), V {rel(V, Vr):.2e}, "
+          f"A {rel(A, Ar):.2e}")
+    assert rel(U, Ur) <= BAR_U, rel(U, Ur)
+    assert rel_modes(U, Ur).max() <= BAR_U_MODE, rel_modes(U, Ur)
+    assert rel(V, Vr) <= BAR_V
+    assert rel(A, Ar) <= BAR_A
     assert st["step_index"] == steps
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_input_order_twice_output_order(lib, precision):
+    """p_in = 2 p: the log-normal coefficient expanded to order 4 with the solution at order 2 (the
+    projection of the truncated field is then exact), runtime triple-product table (no compiled
+    table for p_in != p), against the oracle at the same tolerance."""
+    prob = w.config("small").replace(name="pin4", p_in=4)
+    tol = 1e-13 if precision == 0 else 1e-10
+    steps = 3
+    s = lib(prob, precision=precision, tol=tol)
+    assert s.sizes["P_in"] == 15 and s.sizes["compiled_apply"] == 0
+    s.step(steps)
+    U = s.field()
+    its, rr = s.iters()
+    s.close()
+    Ur, _, _, its_ref = oracle_run(prob, steps, tol)
+    err, modes = rel(U, Ur), rel_modes(U, Ur).max()
+    print(f"p_in = 4, p = 2, {'fp64' if precision == 0 else 'mixed'}: rel err {err:.2e}, worst mode {modes:.2e}, "
+          f"iters {its} vs {its_ref}")
+    if precision == 0:
+        assert err <= BAR_U and modes <= BAR_U_MODE
+    else:
+        assert err <= BAR_MIXED * tol and modes <= BAR_MIXED_MODE * tol
+    assert all(r <= tol for r in rr)
+    assert all(abs(a - b) <= 1 for a, b in zip(its, its_ref))
 
 
 @pytest.mark.parametrize("name", ["small", "pulse32"])
@@ -91,9 +138,14 @@ def test_moments(lib):
 
 
 # Mixed precision: FP32 subdomain solves with one FP64 residual correction per Dirichlet solve
-# inside an FP64 outer PCG.  The outer stopping test is ||r|| <= tol ||G|| on the recursively
-# updated residual; the solution error is bounded by the conditioning of S times the residual
-# error, so the bar is stated per workload tolerance: 1e3 * tol relative to the FP64 oracle.
+# inside an FP64 outer PCG.  Both sides stop at ||r|| <= tol ||G||, so the fields differ by the
+# error both solvers leave at that residual: the bar is 10 tol relative over all nodes and modes
+# (measured 0.4 - 3 tol).  That bound holds for the whole field; a mode k holds at most all of it, so
+# its own relative error is bounded by 10 tol ||U|| / ||U_k||, at most 1e4 tol with the 1e-3 floor of
+# rel_modes (measured up to 2.1e3 tol on the 5-step pulse, whose second mode is 3e-3 of the field).
+BAR_MIXED, BAR_MIXED_MODE = 10.0, 1e4
+
+
 @pytest.mark.parametrize("name,steps", [("small", 4), ("pulse32", 5)])
 def test_mixed_matches_oracle(lib, name, steps):
     from paper_2512_23027_gb300.binding import SG_MIXED
@@ -104,9 +156,11 @@ def test_mixed_matches_oracle(lib, name, steps):
     its, rr = s.iters()
     s.close()
     Ur, _, _, its_ref = oracle_run(prob, steps, prob.tol)
-    err = rel(U, Ur)
-    print(f"{name}: mixed vs oracle rel err {err:.3e}, iters {its} vs {its_ref}")
-    assert err <= 1e3 * prob.tol, err
+    err, modes = rel(U, Ur), rel_modes(U, Ur).max()
+    print(f"{name}: mixed vs oracle rel err {err:.3e} ({err / prob.tol:.2f} tol), worst mode {modes:.3e}, "
+          f"iters {its} vs {its_ref}")
+    assert err <= BAR_MIXED * prob.tol, err
+    assert modes <= BAR_MIXED_MODE * prob.tol, modes
     assert all(r <= prob.tol for r in rr)
     assert all(a <= b + 2 for a, b in zip(its, its_ref))
 
@@ -150,13 +204,13 @@ def test_tensor_core_preconditioner_matches_line_sweeps(lib):
     os.environ["SG_NO_GFIX"] = "1"
     try:
         b = lib(prob, precision=SG_MIXED)
+        assert b.sizes["fp32_precond"] == 0 and b.sizes["compiled_apply"] == 0
+        b.step(steps)
+        ub, (ib, rb) = b.field(), b.iters()
+        b.close()
     finally:
         del os.environ["SG_NO_MMA"]
         del os.environ["SG_NO_GFIX"]
-    assert b.sizes["fp32_precond"] == 0 and b.sizes["compiled_apply"] == 0
-    b.step(steps)
-    ub, (ib, rb) = b.field(), b.iters()
-    b.close()
     err = rel(ua, ub)
     print(f"tensor-core vs line-sweep preconditioner: rel diff {err:.3e}, iters {ia} vs {ib}")
     assert err <= 1e2 * prob.tol, err
@@ -184,9 +238,11 @@ def test_tensor_core_preconditioner_empty_trailing_chunk(lib, N, M, p):
     its, rr = s.iters()
     s.close()
     Ur, _, _, its_ref = oracle_run(prob, steps, prob.tol)
-    err = rel(U, Ur)
-    print(f"L={L} P={prob.P}: tensor-core mixed vs oracle rel err {err:.3e}, iters {its} vs {its_ref}")
-    assert err <= 1e3 * prob.tol, err
+    err, modes = rel(U, Ur), rel_modes(U, Ur).max()
+    print(f"L={L} P={prob.P}: tensor-core mixed vs oracle rel err {err:.3e}, worst mode {modes:.3e}, "
+          f"iters {its} vs {its_ref}")
+    assert err <= BAR_MIXED * prob.tol, err
+    assert modes <= BAR_MIXED_MODE * prob.tol, modes
     assert all(r <= prob.tol for r in rr)
     assert all(a <= b + 2 for a, b in zip(its, its_ref))
 
@@ -208,25 +264,28 @@ def test_bench_workload_mixed_matches_oracle(lib):
     its, rr = s.iters()
     s.close()
     Ur, _, _, its_ref = oracle_run(prob, steps, prob.tol)
-    err = rel(U, Ur)
-    print(f"ricker128 (bench workload): mixed vs oracle rel err {err:.3e}, iters {its} vs {its_ref}")
-    assert err <= 1e3 * prob.tol, err
+    err, modes = rel(U, Ur), rel_modes(U, Ur).max()
+    print(f"ricker128: mixed vs oracle rel err {err:.3e}, worst mode {modes:.3e}, iters {its} vs {its_ref}")
+    assert err <= BAR_MIXED * prob.tol, err
+    assert modes <= BAR_MIXED_MODE * prob.tol, modes
     assert all(r <= prob.tol for r in rr)
     assert all(abs(a - b) <= 1 for a, b in zip(its, its_ref))
 
 
 def _run_env(lib, prob, precision, steps, env):
+    """Set-up and steps with the environment switches set: the step graph is captured at the first
+    step, and the launch shapes are read again at that point."""
     import os
     for k, v in env.items():
         os.environ[k] = v
     try:
         s = lib(prob, precision=precision)
+        s.step(steps)
+        u, (its, rr) = s.field(), s.iters()
+        s.close()
     finally:
         for k in env:
             del os.environ[k]
-    s.step(steps)
-    u, (its, rr) = s.field(), s.iters()
-    s.close()
     return u, its, rr
 
 
@@ -270,3 +329,24 @@ def test_widest_batch_subdomains_converge(lib, which):
           f"iters {im} vs {idd}")
     assert all(r <= prob.tol for r in rm + rd)
     assert err <= 1e2 * prob.tol, err
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_wide_line_kernel_matches_block_kernel(lib, precision):
+    """Subdomains of 41 x 41 nodes: the register-tiled line sweep (k_line_w, both precisions) and the
+    block kernel with the factor staged line by line (SG_LINE_OLD) give the same fields: up to the
+    summation order of the factor rows in FP64 (PCG tolerance 1e-13), within the solver tolerance in
+    mixed precision; the FP64 fields also match the oracle."""
+    prob = w.config("small").replace(name="w41", N=80, s=2, dt=w.cfl_dt(80), tol=1e-13 if precision == 0 else 1e-8)
+    ua, ia, ra = _run_env(lib, prob, precision, 3, {})
+    ub, ib, rb = _run_env(lib, prob, precision, 3, {"SG_LINE_OLD": "1"})
+    err = rel(ua, ub)
+    print(f"L = 41, {'fp64' if precision == 0 else 'mixed'}: register-tiled vs block line kernel rel diff {err:.3e}, "
+          f"iters {ia} vs {ib}")
+    assert err <= (1e-12 if precision == 0 else 1e2 * prob.tol), err
+    assert all(r <= prob.tol for r in ra + rb)
+    assert all(abs(x - y) <= 1 for x, y in zip(ia, ib))
+    if precision == 0:
+        Ur, _, _, its_ref = oracle_run(prob, 3, 1e-13)
+        assert rel(ua, Ur) <= BAR_U and rel_modes(ua, Ur).max() <= BAR_U_MODE
+

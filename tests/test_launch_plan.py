@@ -40,8 +40,8 @@ def check_plan(p, prob, precision):
         assert 1 <= tl <= L and nt == -(-L // tl)
         cap = SMEM_OPTIN if p["apply_variant"][i] == 2 else SMEM_DEFAULT
         assert 0 < p["apply_smem"][i] <= cap
-        if i == 0:
-            assert p["apply_variant"][i] != 3  # FP64 keeps the runtime-table kernel
+        if p["apply_variant"][i] == 3:  # compiled table: only where a one-line tile fits
+            assert p["P"] == prob.P and p["P_in"] == prob.P_in
     for i in lines:
         threads = p["line_block"][i][0] * p["line_block"][i][1] * p["line_block"][i][2]
         assert 32 <= threads <= 1024 and threads % 32 == 0
@@ -49,6 +49,11 @@ def check_plan(p, prob, precision):
         assert g * ng >= prob.P and (ng - 1) * g < prob.P
         cap = SMEM_OPTIN if p["line_kind"][i] == 1 else SMEM_DEFAULT
         assert 0 < p["line_smem"][i] <= cap
+        if p["line_kind"][i] == 3:  # register-tiled sweep of wide subdomains: <= 256 threads, 2 x 4 tiles
+            assert L >= 41 and threads <= 256
+            gs = -(-g // 4) * 4
+            lsp = -(-L // 4) * 4
+            assert threads >= (lsp // 2) * (gs // 4)
     expect_mma = precision == SG_MIXED and L <= 40 and prob.P <= 32
     assert p["mma"] == int(expect_mma)
     if expect_mma:
