@@ -63,9 +63,17 @@ extern "C" {
 #define SG_ETIMEOUT  -6   /* a bounded device-side wait expired                             */
 #define SG_ENOTSUP   -7   /* configuration outside what this build supports                 */
 
-/* ---- precision modes (sg_params.precision) ---- */
+/* ---- precision modes (sg_params.precision) ----
+ * The outer interface PCG (Schur matvec, dot products, residual recurrence, coarse solve) is FP64 in
+ * every mode; the modes differ in the subdomain solves of its matvec and preconditioner (Secs. 3, 5). */
 #define SG_FP64      0    /* every kernel computes in FP64                                  */
-#define SG_MIXED     1    /* FP32 subdomain solves + FP64 refinement inside an FP64 outer PCG */
+#define SG_MIXED     1    /* FP32 subdomain CG with one FP64 residual correction per Dirichlet
+                             solve; its mean-operator preconditioner is the BF16 tensor-core
+                             product where that applies (subdomains of at most 40 x 40 nodes,
+                             P <= 32) and the FP32 line sweeps elsewhere                     */
+#define SG_FP32      2    /* as SG_MIXED with the FP32 line sweeps at every size (no BF16)   */
+#define SG_BF16      3    /* as SG_MIXED with the BF16 tensor-core preconditioner required:
+                             SG_ENOTSUP where it does not apply                              */
 
 /* ---- warm start (sg_params.warm) ---- */
 #define SG_WARM_PREV     0   /* previous step's interface solution (Alg. 1)                 */
@@ -83,9 +91,24 @@ typedef struct sg_handle_s* sg_handle;
  * (N divisible by both). */
 typedef struct { int N; int nsub_x; int nsub_y; } sg_grid;
 
-/* Gaussian field g = g0 + sum_n sqrt(lambda_n) phi_n(x) xi_n with covariance
- * sigma^2 exp(-|dx|/bx - |dy|/by) (Sec. 4, Eqs. CovarKer2D, KLE); M random variables. */
-typedef struct { int M; double sigma; double bx; double by; double g0; } sg_kl;
+/* Gaussian field g = g0 + sum_n sigma sqrt(lambda_n) phi_n(x) xi_n with covariance
+ * sigma^2 exp(-|dx|/bx - |dy|/by) (Sec. 4, Eqs. CovarKer2D, KLE); M random variables.
+ * modes == NULL: the analytic eigenpairs of that separable kernel (top M by lambda).  Otherwise the
+ * caller's KL: modes[n * n_elem + e] = phi_n at the centroid of element e (n < M, n_elem = 2 N^2;
+ * element e = 2 (j N + i) + t of cell (i, j), t = 0 the triangle (i,j),(i+1,j),(i+1,j+1) with centroid
+ * ((i + 2/3) h, (j + 1/3) h), t = 1 the triangle (i,j),(i+1,j+1),(i,j+1), centroid ((i + 1/3) h,
+ * (j + 2/3) h)) and lambdas[n] > 0; bx, by are then unused.  Both arrays are read during sg_setup only.
+ * Errors: SG_EINVAL if modes is given without lambdas, or a lambda is not positive, or a value is not
+ * finite. */
+typedef struct {
+  int M;
+  double sigma;
+  double bx;
+  double by;
+  double g0;
+  const double* modes;    /* M x n_elem values, or NULL */
+  const double* lambdas;  /* M values (with modes)        */
+} sg_kl;
 
 /* Output PCE order p (P = C(M+p, p) terms) and input (coefficient) order p_in. */
 typedef struct { int p; int p_in; } sg_pce;
@@ -96,7 +119,7 @@ typedef struct {
   double alpha0;      /* Rayleigh damping C = alpha0 M + alpha1 K (Rayleigh appendix)       */
   double alpha1;
   int    max_iter;    /* outer PCG iteration cap (SG_ENOTCONV beyond)                       */
-  int    precision;   /* SG_FP64 or SG_MIXED                                                */
+  int    precision;   /* SG_FP64, SG_MIXED, SG_FP32 or SG_BF16                              */
   int    warm;        /* SG_WARM_PREV or SG_WARM_LEARNED                                    */
   double inner_tol;   /* subdomain solves: relative residual target (0 = automatic: 1e-14 in
                          FP64; in FP32 sqrt(0.1 tol) within [1e-6, 1e-4], since a corrected

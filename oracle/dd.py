@@ -87,15 +87,16 @@ class DDSolver:
     of each subdomain only (Eq. ki), so that sum_s R_s^T K_GG^s R_s gives the global
     interface block (Eq. GAssembly_Sto)."""
 
-    def __init__(self, prob, explicit: bool = False, subs=None):
+    def __init__(self, prob, explicit: bool = False, subs=None, coef=None):
         """subs: indices of the only subdomains whose local operators are built (timing samples of
-        large workloads); the coarse problem, which needs every subdomain, is then not assembled."""
+        large workloads); the coarse problem, which needs every subdomain, is then not assembled.
+        coef: element PCE coefficients from a KL other than the analytic one (see sg.SGProblem)."""
         self.prob = prob
         N, s = prob.N, prob.s
         self.part = Partition(N, s)
         self.G = pce.triple_products(prob.M, prob.p_in, prob.p)
         P = self.P = self.G.shape[1]
-        self.coef = fem.element_coefficients(prob)
+        self.coef = fem.element_coefficients(prob) if coef is None else coef
         part = self.part
         nG = part.iface.size
         self.nG = nG

@@ -70,12 +70,14 @@ class SGOperators:
 
 
 class SGProblem:
-    """Global SG system for a workload on the structured grid (free nodes only)."""
+    """Global SG system for a workload on the structured grid (free nodes only).  coef: the PCE
+    coefficients of c_s at the element centroids (P_in x 2 N^2) from a KL other than the analytic
+    one, or None for fem.element_coefficients(prob)."""
 
-    def __init__(self, prob):
+    def __init__(self, prob, coef=None):
         self.prob = prob
         N = prob.N
-        self.coef = fem.element_coefficients(prob)
+        self.coef = fem.element_coefficients(prob) if coef is None else coef
         Mfull, Kfull = fem.assemble(N, self.coef)
         self.free = fem.free_nodes(N)
         f = self.free

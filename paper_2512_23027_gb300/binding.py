@@ -9,7 +9,7 @@ import numpy as np
 
 from . import build as _build
 
-SG_FP64, SG_MIXED = 0, 1
+SG_FP64, SG_MIXED, SG_FP32, SG_BF16 = 0, 1, 2, 3
 SG_WARM_PREV, SG_WARM_LEARNED = 0, 1
 SG_ENOTCONV = -4
 
@@ -25,7 +25,8 @@ class Grid(C.Structure):
 
 
 class KL(C.Structure):
-    _fields_ = [("M", C.c_int), ("sigma", C.c_double), ("bx", C.c_double), ("by", C.c_double), ("g0", C.c_double)]
+    _fields_ = [("M", C.c_int), ("sigma", C.c_double), ("bx", C.c_double), ("by", C.c_double), ("g0", C.c_double),
+                ("modes", C.c_void_p), ("lambdas", C.c_void_p)]
 
 
 class PCE(C.Structure):
@@ -147,12 +148,22 @@ class Solver:
     def __init__(self, prob, precision: int = SG_FP64, warm: int = SG_WARM_PREV, stream=None,
                  tol: Optional[float] = None, inner_tol: float = 0.0, inner_max_iter: int = 0,
                  max_iter: Optional[int] = None, autotune: bool = False, warm_train_steps: int = 0,
-                 warm_lr: float = 0.0):
+                 warm_lr: float = 0.0, kl_modes=None, kl_lambdas=None):
+        """kl_modes / kl_lambdas: the caller's KL (M x 2 N^2 eigenfunction values at the element
+        centroids in the library's element order, and M eigenvalues), or None for the analytic one."""
         self.lib = load_library()
         self.prob = prob
         s = prob.source
         self._grid = Grid(prob.N, prob.s, prob.s)
-        self._kl = KL(prob.M, prob.sigma, prob.bx, prob.by, prob.g0)
+        self._kl_arrays = None
+        mp = lp = None
+        if kl_modes is not None:
+            m = np.ascontiguousarray(kl_modes, dtype=np.float64)
+            lam = np.ascontiguousarray(kl_lambdas, dtype=np.float64) if kl_lambdas is not None else None
+            self._kl_arrays = (m, lam)   # kept alive for the duration of sg_setup
+            mp = m.ctypes.data
+            lp = lam.ctypes.data if lam is not None else None
+        self._kl = KL(prob.M, prob.sigma, prob.bx, prob.by, prob.g0, mp, lp)
         self._pce = PCE(prob.p, prob.p_in)
         self._prm = Params(prob.dt, prob.tol if tol is None else tol, prob.alpha0, prob.alpha1,
                            prob.max_iter if max_iter is None else max_iter, precision, warm, inner_tol,

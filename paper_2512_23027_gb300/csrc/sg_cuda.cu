@@ -77,6 +77,7 @@ struct sg_handle_s {
   cudaStream_t cs[NSTREAMS] = {};     // private capture streams
   std::string err;
   int precision = SG_FP64, warm = SG_WARM_PREV;
+  int policy = SG_FP64;               // sg_params.precision as given (SG_FP32 / SG_BF16 select the preconditioner)
   double tol = 1e-8, inner_tol = 1e-14, inner_tol32 = 1e-6, prec_tol32 = 1e-3;
   int max_iter = 500, inner_max = 400;
   double am = 0, bk = 0;
@@ -1222,13 +1223,14 @@ static int build_line_factors(sg_handle h) {
 // map.  Used when the subdomains have at most MMA_LMAX nodes per side and P <= 32; larger subdomains
 // keep the line-sweep preconditioner (a dense inverse would grow as L^4).
 constexpr int MMA_LMAX = 40;
+static bool mma_applies(const sgh::Problem& pr) { return pr.L <= MMA_LMAX && pr.P <= 32; }
 static bool mma_eligible(const sgh::Problem& pr, int precision) {
-  return precision == SG_MIXED && pr.L <= MMA_LMAX && pr.P <= 32 && !std::getenv("SG_NO_MMA");
+  return (precision == SG_MIXED || precision == SG_BF16) && mma_applies(pr) && !std::getenv("SG_NO_MMA");
 }
 
 static int build_mma_precond(sg_handle h) {
   const auto& pr = h->pr;
-  if (!mma_eligible(pr, h->precision)) return SG_OK;
+  if (!mma_eligible(pr, h->policy)) return SG_OK;
   const int L = pr.L, LL = L * L;
   h->Kp = (LL + sgk::MMA_M - 1) / sgk::MMA_M * sgk::MMA_M;
   h->NC = h->Kp / sgk::MMA_KC;
@@ -1628,19 +1630,24 @@ static bool tiles_fit(const sgh::Problem& pr, int precision) {
     return lc.smem <= (lc.team ? SMEM_MAX : SMEM_TILE);
   };
   return fits_apply(double{}) &&
-         (precision == SG_MIXED ? (fits_apply(float{}) && fits_line(float{})) : fits_line(double{}));
+         (precision != SG_FP64 ? (fits_apply(float{}) && fits_line(float{})) : fits_line(double{}));
 }
 
 // Problem construction and the size limits shared by sg_setup and sg_plan_query.
 static int build_checked(sgh::Problem& pr, std::string& err, const sg_grid* grid, const sg_kl* kl,
                          const sg_pce* pce, const sg_params* prm, const sgh::SourceDesc& sd) {
-  if (prm->precision != SG_FP64 && prm->precision != SG_MIXED) { err = "precision"; return SG_EINVAL; }
+  if (prm->precision < SG_FP64 || prm->precision > SG_BF16) { err = "precision"; return SG_EINVAL; }
   std::string msg = sgh::build_problem(pr, grid->N, grid->nsub_x, grid->nsub_y, kl->M, kl->sigma, kl->bx,
-                                       kl->by, kl->g0, pce->p, pce->p_in, prm->dt, prm->alpha0, prm->alpha1, sd);
+                                       kl->by, kl->g0, pce->p, pce->p_in, prm->dt, prm->alpha0, prm->alpha1, sd,
+                                       kl->modes, kl->modes ? kl->lambdas : nullptr);
   if (!msg.empty()) { err = msg; return SG_EINVAL; }
   if (pr.L > 256 || pr.L * 2 > 1024) { err = "subdomains wider than 255 cells are not supported"; return SG_ENOTSUP; }
   if (pr.nsub < 2) { err = "at least 2 x 2 subdomains are required"; return SG_ENOTSUP; }
   pr.gfix = select_gfix(pr);
+  if (prm->precision == SG_BF16 && !mma_applies(pr)) {
+    err = "SG_BF16: the BF16 tensor-core preconditioner needs subdomains of at most 40 x 40 nodes and P <= 32";
+    return SG_ENOTSUP;
+  }
   return SG_OK;
 }
 
@@ -1656,7 +1663,10 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   }
   RET(build_checked(h->pr, h->err, grid, kl, pce, prm, sd));
   auto& pr = h->pr;
-  h->precision = prm->precision;
+  // the compute path: FP64, or FP32 subdomain solves inside the FP64 outer PCG (SG_MIXED, SG_FP32 and
+  // SG_BF16 differ only in the mean-operator preconditioner, chosen in build_mma_precond)
+  h->precision = prm->precision == SG_FP64 ? SG_FP64 : SG_MIXED;
+  h->policy = prm->precision;
   h->warm = prm->warm;
   h->tol = prm->tol > 0 ? prm->tol : 1e-8;
   h->max_iter = prm->max_iter > 0 ? prm->max_iter : 500;

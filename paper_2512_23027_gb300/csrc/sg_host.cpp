@@ -117,12 +117,21 @@ static void parallel_cyclic(int i0, int i1, F&& f) {
 
 std::string build_problem(Problem& pr, int N, int sx, int sy, int M, double sigma, double bx,
                           double by, double g0, int p, int p_in, double dt, double alpha0,
-                          double alpha1, const SourceDesc& src) {
+                          double alpha1, const SourceDesc& src, const double* modes,
+                          const double* lambdas) {
   if (N < 2 || sx < 1 || sy < 1 || sx != sy) return "grid: N >= 2 and nsub_x == nsub_y >= 1 required";
   if (N % sx) return "grid: N must be divisible by the subdomain count";
   if (M < 0 || M > 12 || p < 0 || p_in < 0 || p > 10 || p_in > 20) return "pce/kl: unsupported M, p or p_in";
   if (!(dt > 0) || !(sigma >= 0)) return "params: dt > 0 and sigma >= 0 required";
-  if (M > 0 && !(bx > 0 && by > 0)) return "kl: correlation lengths must be positive";
+  if (M > 0 && !modes && !(bx > 0 && by > 0)) return "kl: correlation lengths must be positive";
+  if (modes && M > 0) {
+    if (!lambdas) return "kl: modes given without lambdas";
+    for (int n = 0; n < M; ++n)
+      if (!(lambdas[n] > 0) || !std::isfinite(lambdas[n])) return "kl: lambdas must be positive and finite";
+    const size_t ne = (size_t)2 * N * N * M;
+    for (size_t e = 0; e < ne; ++e)
+      if (!std::isfinite(modes[e])) return "kl: modes must be finite";
+  }
   pr.N = N; pr.s = sx; pr.H = N / sx; pr.L = pr.H + 1; pr.nl = pr.L * pr.L; pr.nsub = sx * sx;
   pr.M = M; pr.p = p; pr.p_in = p_in; pr.sigma = sigma; pr.bx = bx; pr.by = by; pr.g0 = g0;
   pr.dt = dt; pr.alpha0 = alpha0; pr.alpha1 = alpha1; pr.h = 1.0 / N; pr.src = src;
@@ -159,7 +168,7 @@ std::string build_problem(Problem& pr, int N, int sx, int sy, int M, double sigm
   });
   cand.resize(M);
   pr.kl_lambda.resize(M);
-  for (int n = 0; n < M; ++n) pr.kl_lambda[n] = cand[n].lam;
+  for (int n = 0; n < M; ++n) pr.kl_lambda[n] = modes ? lambdas[n] : cand[n].lam;
 
   // PCE coefficients of exp(g) at the element centroids (Eqs. c0pce, LNL0):
   //   c_alpha = exp(g0 + |g|^2 / 2) prod_n g_n^{a_n} / sqrt(a_n!),  g_n = sigma sqrt(lambda_n) phi_n(x) psi_n(y).
@@ -211,12 +220,18 @@ std::string build_problem(Problem& pr, int N, int sx, int sy, int M, double sigm
   };
   // element coefficients of the whole mesh: T1 centroid (i+2/3, j+1/3) h, T2 (i+1/3, j+2/3) h
   std::vector<double> cT1((size_t)N * N * PI), cT2((size_t)N * N * PI);
+  std::vector<double> amp(M);
+  for (int n = 0; n < M; ++n) amp[n] = modes ? sigma * std::sqrt(lambdas[n]) : 0.0;
+  const size_t ne = (size_t)2 * N * N;
   parallel_cyclic(0, N, [&](int j) {  // grid rows are independent
     for (int i = 0; i < N; ++i) {
       double g[MAXM];
-      for (int n = 0; n < M; ++n) g[n] = fx1[(size_t)n * N + i] * fy1[(size_t)n * N + j];
+      const size_t e1 = 2 * ((size_t)j * N + i);  // element index of T1 (T2 is e1 + 1)
+      for (int n = 0; n < M; ++n)
+        g[n] = modes ? amp[n] * modes[(size_t)n * ne + e1] : fx1[(size_t)n * N + i] * fy1[(size_t)n * N + j];
       coef_from(g, &cT1[((size_t)j * N + i) * PI]);
-      for (int n = 0; n < M; ++n) g[n] = fx2[(size_t)n * N + i] * fy2[(size_t)n * N + j];
+      for (int n = 0; n < M; ++n)
+        g[n] = modes ? amp[n] * modes[(size_t)n * ne + e1 + 1] : fx2[(size_t)n * N + i] * fy2[(size_t)n * N + j];
       coef_from(g, &cT2[((size_t)j * N + i) * PI]);
     }
   });

@@ -59,9 +59,12 @@ struct Problem {
 };
 
 // Returns "" on success, else an error message.
+// modes / lambdas: the caller's KL (modes[n * 2 N^2 + e] = phi_n at the centroid of element e), or
+// both null for the analytic eigenpairs of the separable exponential kernel.
 std::string build_problem(Problem& pr, int N, int sx, int sy, int M, double sigma, double bx,
                           double by, double g0, int p, int p_in, double dt, double alpha0,
-                          double alpha1, const SourceDesc& src);
+                          double alpha1, const SourceDesc& src, const double* modes = nullptr,
+                          const double* lambdas = nullptr);
 
 std::vector<std::vector<int>> multi_indices(int M, int p);
 double hermite_triple(int a, int b, int c);

@@ -67,7 +67,7 @@ def main(only=None):
         rec = {"problem": {k: getattr(prob, k) for k in ("N", "s", "M", "p", "p_in", "sigma", "bx", "by", "g0", "dt",
                                                           "tol", "alpha0", "alpha1")},
                "source": {k: getattr(prob.source, k) for k in ("kind", "x0", "y0", "width", "freq", "amp")},
-               "steps": steps, "node": node.tolist(), "mode": mode.tolist()}
+               "steps": steps, "n_uniform": NSAMPLE // 2, "node": node.tolist(), "mode": mode.tolist()}
         for label, tol in (("tight", 1e-13), ("workload", prob.tol)):
             U, its = runs[label]
             rec[label] = {"tol": tol, "iters": its, "mode_norm": np.linalg.norm(U, axis=0).tolist(),

@@ -350,3 +350,60 @@ def test_wide_line_kernel_matches_block_kernel(lib, precision):
         Ur, _, _, its_ref = oracle_run(prob, 3, 1e-13)
         assert rel(ua, Ur) <= BAR_U and rel_modes(ua, Ur).max() <= BAR_U_MODE
 
+
+
+def _caller_kl(prob):
+    """Caller KL: the analytic modes times 1 + 0.3 sin(7x + 3y) at the element centroids (neither
+    separable nor symmetric), lambdas 0.37 and 0.11; returns (modes, lambdas, element PCE coefficients
+    the oracle builds from them)."""
+    from oracle import fem, field, kl
+    _, cen = fem.elements(prob.N)
+    bump = 1.0 + 0.3 * np.sin(7 * cen[:, 0] + 3 * cen[:, 1])
+    lam = np.array([0.37, 0.11])
+    phi = np.array([kl.phi1d(cen[:, 0], wx, px) * kl.phi1d(cen[:, 1], wy, py) * bump
+                    for _, (ix, wx, px), (iy, wy, py) in kl.kl_modes(prob.M, prob.bx, prob.by)])
+    coef = field.lognormal_pce(prob.sigma * np.sqrt(lam)[:, None] * phi, prob.g0, prob.p_in)
+    return phi, lam, coef
+
+
+def test_caller_kl_modes_match_oracle(lib):
+    """sg_kl.modes / lambdas: the same caller KL drives the library and the oracle (which builds its
+    element coefficients from the same centroid values); FP64 at PCG tolerance 1e-13."""
+    prob = w.config("small")
+    phi, lam, coef = _caller_kl(prob)
+    steps = 3
+    s = lib(prob, tol=1e-13, kl_modes=phi, kl_lambdas=lam)
+    s.step(steps)
+    U = s.field()
+    s.close()
+    sgp = osg.SGProblem(prob, coef=coef)
+    d = odd.DDSolver(prob, coef=coef)
+    Ur, _, _, _ = odd.run_dd(sgp, d, steps, tol=1e-13)
+    Ur = Ur.reshape(U.shape)
+    d0 = osg.SGProblem(prob)
+    U0, _, _, _ = odd.run_dd(d0, odd.DDSolver(prob), steps, tol=1e-13)
+    print(f"caller KL: rel err {rel(U, Ur):.2e}, worst mode {rel_modes(U, Ur).max():.2e}; differs from the "
+          f"analytic-KL field by {rel(U, U0.reshape(U.shape)):.2e}")
+    assert rel(U, Ur) <= BAR_U and rel_modes(U, Ur).max() <= BAR_U_MODE
+    assert rel(U, U0.reshape(U.shape)) > 1e-4   # the caller's modes were used
+
+
+@pytest.mark.parametrize("precision", [2, 3], ids=["fp32", "bf16"])
+def test_fp32_and_bf16_modes(lib, precision):
+    """SG_FP32 (FP32 line sweeps) and SG_BF16 (BF16 tensor-core preconditioner) inside the FP64 outer
+    PCG, against the oracle at the workload tolerance."""
+    prob = w.config("small")
+    steps = 4
+    s = lib(prob, precision=precision)
+    assert s.sizes["fp32_precond"] == (1 if precision == 3 else 0)
+    s.step(steps)
+    U = s.field()
+    its, rr = s.iters()
+    s.close()
+    Ur, _, _, its_ref = oracle_run(prob, steps, prob.tol)
+    err, modes = rel(U, Ur), rel_modes(U, Ur).max()
+    print(f"precision {precision}: rel err {err:.2e} ({err / prob.tol:.2f} tol), worst mode {modes:.2e}, "
+          f"iters {its} vs {its_ref}")
+    assert err <= BAR_MIXED * prob.tol and modes <= BAR_MIXED_MODE * prob.tol
+    assert all(r <= prob.tol for r in rr)
+    assert all(a <= b + 2 for a, b in zip(its, its_ref))

@@ -175,3 +175,81 @@ def test_initial_pulse(dump_exe):
     for o in range(u0.size):
         g = _global_of_local(prob, t["nl"], t["L"], o)
         assert np.isclose(u0[o], ref[g] if g in part.free_index else 0.0, rtol=1e-14, atol=1e-300)
+
+
+def _centroids(N):
+    _, cen = fem.elements(N)
+    return cen
+
+
+def _write_kl(path, lam, modes):
+    with open(path, "w") as f:
+        f.write(" ".join(repr(float(v)) for v in lam) + "\n")
+        f.write(" ".join(repr(float(v)) for v in np.ravel(modes)) + "\n")
+
+
+def host_tables_kl(exe, prob, lam, modes, path):
+    _write_kl(path, lam, modes)
+    src = prob.source
+    args = [prob.N, prob.s, prob.M, prob.sigma, prob.bx, prob.by, prob.g0, prob.p, prob.p_in, prob.dt,
+            src.kind, src.x0, src.y0, src.width, src.freq, src.amp]
+    txt = subprocess.run([exe] + [repr(a) for a in args] + [str(path)], check=True, capture_output=True,
+                         text=True).stdout
+    return {line.split()[0]: np.array([float(v) for v in line.split()[1:]]) for line in txt.splitlines()}
+
+
+def test_caller_kl_modes_analytic_equal_built_in(dump_exe, tmp_path):
+    """The analytic eigenpairs passed in as caller modes (the oracle's phi_n at the element centroids
+    and its lambda_n) give the tables of the built-in analytic KL."""
+    prob = w.config("small")
+    cen = _centroids(prob.N)
+    lam, phi = [], []
+    for lm, (ix, wx, px), (iy, wy, py) in kl.kl_modes(prob.M, prob.bx, prob.by):
+        lam.append(lm)
+        phi.append(kl.phi1d(cen[:, 0], wx, px) * kl.phi1d(cen[:, 1], wy, py))
+    a = host_tables(dump_exe, prob)
+    b = host_tables_kl(dump_exe, prob, lam, np.array(phi), tmp_path / "kl.txt")
+    assert np.allclose(b["kl_lambda"], a["kl_lambda"], rtol=1e-15, atol=0)
+    for t in ("kapE", "kapN"):
+        assert np.allclose(b[t], a[t], rtol=1e-12, atol=1e-15 * np.abs(a[t]).max())
+
+
+def test_caller_kl_modes_reach_the_edge_weights(dump_exe, tmp_path):
+    """Caller modes that are neither separable nor symmetric (the analytic modes times
+    1 + 0.3 sin(7x + 3y), an arbitrary positive lambda): every subdomain's edge weights equal minus
+    the oracle's stiffness entries assembled from the PCE of exp(g), g_n = sigma sqrt(lambda_n) phi_n
+    at the same centroids (a wrong element order, a T1 / T2 swap or a scaling slip fails this)."""
+    prob = w.config("small").replace(M=2, p=2, p_in=2)
+    N, s, H = prob.N, prob.s, prob.N // prob.s
+    cen = _centroids(N)
+    bump = 1.0 + 0.3 * np.sin(7 * cen[:, 0] + 3 * cen[:, 1])
+    lam = [0.37, 0.11]
+    phi = []
+    for lm, (ix, wx, px), (iy, wy, py) in kl.kl_modes(prob.M, prob.bx, prob.by):
+        phi.append(kl.phi1d(cen[:, 0], wx, px) * kl.phi1d(cen[:, 1], wy, py) * bump)
+    phi = np.array(phi)
+    t = host_tables_kl(dump_exe, prob, lam, phi, tmp_path / "kl.txt")
+    from oracle import field
+    gn = prob.sigma * np.sqrt(np.array(lam))[:, None] * phi
+    coef = field.lognormal_pce(gn, prob.g0, prob.p_in)
+    part = dd.Partition(N, s)
+    L = H + 1
+    PI = coef.shape[0]
+    kapE = t["kapE"].reshape(s * s, L * L, PI)
+    kapN = t["kapN"].reshape(s * s, L * L, PI)
+    worst = 0.0
+    for si, sub in enumerate(part.subs):
+        _, Ks = fem.assemble(N, coef, sub["elem_mask"])
+        sx, sy = si % s, si // s
+        for lj in range(L):
+            for li in range(L):
+                I, J = sx * H + li, sy * H + lj
+                a = fem.node_id(I, J, N)
+                for i in range(PI):
+                    if li < H:
+                        ref = -Ks[i][a, fem.node_id(I + 1, J, N)]
+                        worst = max(worst, abs(kapE[si, lj * L + li, i] - ref))
+                    if lj < H:
+                        ref = -Ks[i][a, fem.node_id(I, J + 1, N)]
+                        worst = max(worst, abs(kapN[si, lj * L + li, i] - ref))
+    assert worst < 1e-13, worst

@@ -20,11 +20,12 @@ def B():
     return binding
 
 
-def setup_rc(B, prob, precision=0, warm=0, warm_train_steps=0, grid=None, src_kind=None):
+def setup_rc(B, prob, precision=0, warm=0, warm_train_steps=0, grid=None, src_kind=None, modes=None, lambdas=None):
     lib = B.load_library()
     s = prob.source
     g = grid or B.Grid(prob.N, prob.s, prob.s)
-    kl = B.KL(prob.M, prob.sigma, prob.bx, prob.by, prob.g0)
+    kl = B.KL(prob.M, prob.sigma, prob.bx, prob.by, prob.g0, None if modes is None else modes.ctypes.data,
+              None if lambdas is None else lambdas.ctypes.data)
     pce = B.PCE(prob.p, prob.p_in)
     prm = B.Params(prob.dt, prob.tol, prob.alpha0, prob.alpha1, prob.max_iter, precision, warm, 0.0, 0, 0,
                    warm_train_steps, 0.0)
@@ -37,6 +38,7 @@ def setup_rc(B, prob, precision=0, warm=0, warm_train_steps=0, grid=None, src_ki
 CASES = [
     ("source kind", dict(src_kind=5), SG_EINVAL, "source"),
     ("precision", dict(precision=7), SG_EINVAL, "precision"),
+    ("negative precision", dict(precision=-1), SG_EINVAL, "precision"),
     ("warm-start mode", dict(warm=9), SG_EINVAL, "warm"),
     ("warm-start training steps", dict(warm_train_steps=-1), SG_EINVAL, "warm"),
 ]
@@ -80,3 +82,41 @@ def test_solver_raises_the_status(B):
     with pytest.raises(B.SGError) as e:
         B.Solver(w.config("small").replace(N=25))
     assert e.value.code == SG_EINVAL
+
+
+def _modes(prob, value=0.5):
+    import numpy as np
+    return np.full(prob.M * 2 * prob.N * prob.N, value)
+
+
+def test_caller_kl_arrays_are_checked(B):
+    """modes without lambdas, a non-positive lambda and a non-finite mode value are argument errors."""
+    import numpy as np
+    prob = w.config("small")
+    m = _modes(prob)
+    rc, h, err = setup_rc(B, prob, modes=m)
+    assert rc == SG_EINVAL and h is None and "lambdas" in err
+    rc, h, err = setup_rc(B, prob, modes=m, lambdas=np.array([0.3, -0.1]))
+    assert rc == SG_EINVAL and h is None and "lambda" in err
+    bad = m.copy()
+    bad[7] = np.nan
+    rc, h, err = setup_rc(B, prob, modes=bad, lambdas=np.array([0.3, 0.1]))
+    assert rc == SG_EINVAL and h is None and "finite" in err
+
+
+def test_bf16_mode_needs_the_tensor_core_preconditioner(B):
+    """SG_BF16 requires the BF16 tensor-core mean preconditioner, which covers subdomains of at most
+    40 x 40 nodes and P <= 32: wider subdomains get SG_ENOTSUP (before any CUDA call)."""
+    prob = w.config("small").replace(N=80, s=2)   # 41 x 41-node subdomains
+    rc, h, err = setup_rc(B, prob, precision=3)
+    assert rc == SG_ENOTSUP and h is None and "BF16" in err
+
+
+def test_precision_modes_in_the_launch_plan(B):
+    """sg_plan_query: SG_MIXED and SG_BF16 take the tensor-core preconditioner on 9 x 9-node
+    subdomains, SG_FP32 the line sweeps; every mode launches the FP32 kernels there."""
+    prob = w.config("small")
+    plans = {p: B.plan_query(prob, p) for p in (1, 2, 3)}
+    assert plans[1]["mma"] == 1 and plans[3]["mma"] == 1 and plans[2]["mma"] == 0
+    assert all(pl["fits"] == 1 for pl in plans.values())
+
