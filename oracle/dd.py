@@ -87,10 +87,14 @@ class DDSolver:
     of each subdomain only (Eq. ki), so that sum_s R_s^T K_GG^s R_s gives the global
     interface block (Eq. GAssembly_Sto)."""
 
-    def __init__(self, prob, explicit: bool = False, subs=None, coef=None):
+    def __init__(self, prob, explicit: bool = False, subs=None, coef=None, precond: str = "nn2"):
         """subs: indices of the only subdomains whose local operators are built (timing samples of
         large workloads); the coarse problem, which needs every subdomain, is then not assembled.
-        coef: element PCE coefficients from a KL other than the analytic one (see sg.SGProblem)."""
+        coef: element PCE coefficients from a KL other than the analytic one (see sg.SGProblem).
+        precond: the PCG preconditioner, "nn2" (two-level Neumann-Neumann, Eq. NNCP2), "nn1"
+        (one-level Neumann-Neumann) or "lumped" (the one-level comparison of Sec. 6.1)."""
+        assert precond in ("nn2", "nn1", "lumped")
+        self.pc_kind = precond
         self.prob = prob
         N, s = prob.N, prob.s
         self.part = Partition(N, s)
@@ -234,6 +238,39 @@ class DDSolver:
             np.add.at(z, L["R"], L["D"] * zl)
         return z
 
+    # ---------------- one-level preconditioners of the comparison (Sec. 6.1) ----------------
+    # The paper cites the one-level forms without restating them; these are the textbook ones:
+    #   lumped: M^{-1} = sum_s R_s^T D_s K~_GG^s D_s R_s
+    #   one-level Neumann-Neumann: M^{-1} = sum_s R_s^T D_s S_s^{-1} D_s R_s, with S_s the local Schur
+    #   complement on the whole local interface (remaining nodes and corners); S_s^{-1} w is the
+    #   interface part of the local Neumann solve K~^s [y; t] = [0; w] (nonsingular: the transient
+    #   operator carries the mass term, so no subdomain floats).
+    def precond_lumped(self, r):
+        z = np.zeros_like(r)
+        for L in self.loc:
+            w = L["D"] * r[L["R"]]
+            np.add.at(z, L["R"], L["D"] * (L["Kt"][L["Gam"]][:, L["Gam"]] @ w))
+        return z
+
+    def precond_nn1(self, r):
+        z = np.zeros_like(r)
+        for L in self.loc:
+            if "lu_F" not in L:
+                L["lu_F"] = spla.splu(L["Kt"].tocsc(), permc_spec="MMD_AT_PLUS_A")
+            rhs = np.zeros(L["Kt"].shape[0])
+            rhs[L["Gam"]] = L["D"] * r[L["R"]]
+            t = L["lu_F"].solve(rhs)[L["Gam"]]
+            np.add.at(z, L["R"], L["D"] * t)
+        return z
+
+    def apply_pc(self, r):
+        """The PCG preconditioner selected at construction."""
+        if self.pc_kind == "lumped":
+            return self.precond_lumped(r)
+        if self.pc_kind == "nn1":
+            return self.precond_nn1(r)
+        return self.precond(r)
+
     @staticmethod
     def _ir_vec(L, y, t):
         v = np.zeros(L["ir"].size)
@@ -250,6 +287,8 @@ class DDSolver:
         Minv_local = np.zeros((nGd, nGd))
         R0 = np.zeros((nCd, nGd))
         Fcc = np.zeros((nCd, nCd))
+        Mlumped = np.zeros((nGd, nGd))
+        Mnn1 = np.zeros((nGd, nGd))
         for L in self.loc:
             Kt = L["Kt"].toarray()
             I, Gm = L["I"], L["Gam"]
@@ -268,11 +307,15 @@ class DDSolver:
             Rc = np.zeros((L["Gc"].size, Gm.size)); Rc[np.arange(L["Gc"].size), L["Gc"]] = 1.0
             Srr_inv = np.linalg.inv(Srr)
             Minv_local += Rs.T @ Ds @ (Rr.T @ Srr_inv @ Rr) @ Ds @ Rs
+            Mlumped += Rs.T @ Ds @ Kt[np.ix_(Gm, Gm)] @ Ds @ Rs
+            Mnn1 += Rs.T @ Ds @ np.linalg.inv(Ss) @ Ds @ Rs
             if L["Gc"].size:
                 Bc = np.zeros((L["Gc"].size, nCd)); Bc[np.arange(L["Gc"].size), L["B"]] = 1.0
                 Fcc += Bc.T @ (Scc - Scr @ Srr_inv @ Src) @ Bc
                 R0 += Bc.T @ (Rc - Scr @ Srr_inv @ Rr) @ Ds @ Rs
         self.S_explicit = S
+        self.Mlumped_explicit = Mlumped
+        self.Mnn1_explicit = Mnn1
         self.Fcc_explicit = Fcc
         self.R0_explicit = R0
         Minv = Minv_local
@@ -302,7 +345,7 @@ class DDSolver:
         it = 0
         if rel <= tol:
             return x, 0, rel
-        z = self.precond(r)
+        z = self.apply_pc(r)
         p = z.copy()
         rz = r @ z
         while it < max_iter:
@@ -314,7 +357,7 @@ class DDSolver:
             rel = np.linalg.norm(r) / gn
             if rel <= tol:
                 break
-            z = self.precond(r)
+            z = self.apply_pc(r)
             rz_new = r @ z
             p = z + (rz_new / rz) * p
             rz = rz_new
