@@ -318,6 +318,34 @@ def ricker_nodal_load(prob, step_from, nsteps, nf):
     return out
 
 
+def run_precond_study(args):
+    """Comparison of the interface preconditioners (the paper's Sec. 6.1 experiment on structured
+    grids): a fixed 256^2 grid (the 1024^2 workload's field and PCE sizes: M = 5, order 2, sigma 0.3,
+    correlation length 0.1, Ricker source) split into s x s subdomains, s = 2, 4, 8, 16; for the
+    two-level Neumann-Neumann preconditioner of the method, the one-level Neumann-Neumann and the
+    lumped one: average outer PCG iterations per step and ms per step over `steps` steps (mixed
+    precision, tolerance 1e-8), after `warmup` steps."""
+    import sg_workloads as w
+    from paper_2512_23027_gb300 import Solver
+    from paper_2512_23027_gb300.binding import SG_MIXED
+    base = w.config("ricker1024").replace(name="pc256", N=256, dt=w.cfl_dt(256))
+    rows = []
+    for s in (2, 4, 8, 16):
+        for name, pc in (("two-level NN", 0), ("one-level NN", 1), ("lumped", 2)):
+            prob = base.replace(s=s)
+            sv = Solver(prob, precision=SG_MIXED, precond=pc)
+            sv.step(args.warmup)
+            st = sv.step(args.steps)
+            rows.append({"subdomains": f"{s}x{s}", "precond": name, "outer_iters_per_step": st["iters_total"] / args.steps,
+                         "inner_iters_per_step": st["inner_total"] / args.steps, "ms_per_step": st["ms"] / args.steps})
+            sv.close()
+    print(json.dumps({"metric": "outer PCG iterations per step vs number of subdomains, by preconditioner",
+                      "config": {"workload": "256x256 grid, M=5, order 2 (P=21), sigma 0.3, corr 0.1, Ricker, "
+                                             "mixed precision, tol 1e-8", "warmup": args.warmup, "steps": args.steps},
+                      "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -333,6 +361,9 @@ def main():
     ap.add_argument("--batch", type=int, default=0,
                     help="instead of the default line, run the first BATCH problems of the batched workload "
                          "(64^2..256^2 grids, uneven sizes) with sg_solve_batch and report problem-steps/s")
+    ap.add_argument("--precond-study", action="store_true",
+                    help="instead of the default line, compare the two-level NN, one-level NN and lumped "
+                         "preconditioners over 2x2..16x16 subdomains of a 256^2 grid (iterations per step)")
     ap.add_argument("--enqueue", default="graph", choices=["graph", "eager"],
                     help="graph: one CUDA graph per step (default); eager: host-driven enqueue of the same "
                          "kernels (per-kernel profilers cannot see inside graphs with conditional nodes)")
@@ -341,6 +372,8 @@ def main():
         return run_reference(args)
     if args.batch:
         return run_batch(args)
+    if args.precond_study:
+        return run_precond_study(args)
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -75,6 +75,12 @@ extern "C" {
 #define SG_BF16      3    /* as SG_MIXED with the BF16 tensor-core preconditioner required:
                              SG_ENOTSUP where it does not apply                              */
 
+/* ---- interface preconditioner (sg_params.precond) ---- */
+#define SG_PC_NN2     0   /* probabilistic two-level Neumann-Neumann (Eq. NNCP2; the method)     */
+#define SG_PC_NN1     1   /* one-level Neumann-Neumann, sum R^T D S_s^{-1} D R (comparison of
+                             Sec. 6.1; local Neumann solves with the whole interface free)     */
+#define SG_PC_LUMPED  2   /* lumped, sum R^T D K~_GG D R (comparison of Sec. 6.1)              */
+
 /* ---- warm start (sg_params.warm) ---- */
 #define SG_WARM_PREV     0   /* previous step's interface solution (Alg. 1)                 */
 #define SG_WARM_LEARNED  1   /* learned predictor (extension; falls back to SG_WARM_PREV)   */
@@ -129,6 +135,7 @@ typedef struct {
                          fastest per problem shape (process-wide table); 0: built-in heuristics */
   int    warm_train_steps; /* SG_WARM_LEARNED: steps of online training (0 = 20)              */
   double warm_lr;          /* SG_WARM_LEARNED: Adam learning rate (0 = 1e-3)                  */
+  int    precond;          /* SG_PC_NN2 (default), SG_PC_NN1 or SG_PC_LUMPED                  */
 } sg_params;
 
 typedef struct { int kind; double x0, y0, width, freq, amp; } sg_source;

@@ -11,6 +11,7 @@ from . import build as _build
 
 SG_FP64, SG_MIXED, SG_FP32, SG_BF16 = 0, 1, 2, 3
 SG_WARM_PREV, SG_WARM_LEARNED = 0, 1
+SG_PC_NN2, SG_PC_NN1, SG_PC_LUMPED = 0, 1, 2
 SG_ENOTCONV = -4
 
 
@@ -37,7 +38,7 @@ class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("tol", C.c_double), ("alpha0", C.c_double), ("alpha1", C.c_double),
                 ("max_iter", C.c_int), ("precision", C.c_int), ("warm", C.c_int),
                 ("inner_tol", C.c_double), ("inner_max_iter", C.c_int), ("autotune", C.c_int),
-                ("warm_train_steps", C.c_int), ("warm_lr", C.c_double)]
+                ("warm_train_steps", C.c_int), ("warm_lr", C.c_double), ("precond", C.c_int)]
 
 
 class Source(C.Structure):
@@ -148,7 +149,7 @@ class Solver:
     def __init__(self, prob, precision: int = SG_FP64, warm: int = SG_WARM_PREV, stream=None,
                  tol: Optional[float] = None, inner_tol: float = 0.0, inner_max_iter: int = 0,
                  max_iter: Optional[int] = None, autotune: bool = False, warm_train_steps: int = 0,
-                 warm_lr: float = 0.0, kl_modes=None, kl_lambdas=None):
+                 warm_lr: float = 0.0, kl_modes=None, kl_lambdas=None, precond: int = SG_PC_NN2):
         """kl_modes / kl_lambdas: the caller's KL (M x 2 N^2 eigenfunction values at the element
         centroids in the library's element order, and M eigenvalues), or None for the analytic one."""
         self.lib = load_library()
@@ -167,7 +168,7 @@ class Solver:
         self._pce = PCE(prob.p, prob.p_in)
         self._prm = Params(prob.dt, prob.tol if tol is None else tol, prob.alpha0, prob.alpha1,
                            prob.max_iter if max_iter is None else max_iter, precision, warm, inner_tol,
-                           inner_max_iter, int(bool(autotune)), warm_train_steps, warm_lr)
+                           inner_max_iter, int(bool(autotune)), warm_train_steps, warm_lr, precond)
         self._src = Source(s.kind, s.x0, s.y0, s.width, s.freq, s.amp)
         st = 0
         if stream is not None:

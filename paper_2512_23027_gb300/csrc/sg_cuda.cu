@@ -96,8 +96,11 @@ struct sg_handle_s {
   int* load_node = nullptr;
   double* load_w = nullptr;
   int nload = 0;
-  LineFactor<double> lf[2];  // 0: Dirichlet (interior free), 1: Neumann (interior + remaining free)
-  LineFactor<float> lf32[2];
+  // 0: Dirichlet (interior free), 1: Neumann (interior + remaining free), 2: all local free nodes
+  // (one-level Neumann-Neumann preconditioner only)
+  LineFactor<double> lf[3];
+  LineFactor<float> lf32[3];
+  int pc = SG_PC_NN2;                 // interface preconditioner
   // tensor-core mean preconditioner of the FP32 inner solves (mixed precision, small subdomains)
   bool mma = false;
   bool pdl = false;                // programmatic dependent launch inside the inner loop (opt-in)
@@ -700,7 +703,7 @@ static int enq_inner(sg_handle h, Ctx& cx, int pat, int nb, int R, int s0, const
   auto& w = wsT<T>(h);
   const long long n = (long long)pr.nl * pr.P * nb;
   const Op<T> op = h->op<T>(s0);
-  const int mask = pat == 0 ? sgk::MASK_I : sgk::MASK_N;
+  const int mask = pat == 0 ? sgk::MASK_I : pat == 1 ? sgk::MASK_N : sgk::MASK_FREE;
   const int L = pr.L;
   const LineCfg lc = line_cfg<T>(pr, nb);
   const int NG = lc.NG;
@@ -749,7 +752,7 @@ static int enq_inner(sg_handle h, Ctx& cx, int pat, int nb, int R, int s0, const
   };
   // tensor-core preconditioner (FP32 solves of small subdomains): CG update + residual image, then
   // the dense product with the inner-CG control
-  const bool use_mma = sizeof(T) == 4 && h->mma;
+  const bool use_mma = sizeof(T) == 4 && h->mma && pat < 2;  // the dense inverses cover patterns 0 and 1
   const int row0 = (pat * pr.nsub + s0) * h->Kp;
   auto pre_mma = [&](Ctx& cc, int init, cudaGraphConditionalHandle hh, int use) -> int {
     cudaStream_t s = cc.st;
@@ -891,7 +894,40 @@ static int enq_precond_t(sg_handle h, Ctx& cx, const double* r, double* z) {
   return SG_OK;
 }
 
+// One-level preconditioners of the comparison (Sec. 6.1), textbook forms:
+//   lumped:  z = sum_s R_s^T D_s K~_GG^s D_s R_s r  (one FP64 apply restricted to the interface)
+//   NN1:     z = sum_s R_s^T D_s S_s^{-1} D_s R_s r, S_s^{-1} w the interface part of the local Neumann
+//            solve with the whole local interface free (line-factor pattern 2; no coarse space)
+static int enq_precond_lumped(sg_handle h, Ctx& cx, const double* r, double* z) {
+  const auto& pr = h->pr;
+  cudaStream_t st = cx.st;
+  const long long n = h->nvec();
+  sgk::k_gather<double><<<nblk(n), 256, 0, st>>>(pr.nsub, 1, pr.nl, pr.P, h->cls, h->gidx, h->Dw, r, h->wa,
+                                                  sgk::MASK_G, 1);
+  RET((launch_apply<double, double, false, false>(h, st, h->op<double>(), pr.nsub, 1, h->wa, h->wa, h->we, nullptr,
+                                                  h->am, h->bk, sgk::MASK_G)));
+  sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, pr.P, h->owners, h->Dw, h->we, z, 1);
+  CKL();
+  return SG_OK;
+}
+
+template <typename T>
+static int enq_precond_nn1(sg_handle h, Ctx& cx, const double* r, double* z) {
+  const auto& pr = h->pr;
+  cudaStream_t st = cx.st;
+  const long long n = h->nvec();
+  T* wr = sizeof(T) == 8 ? (T*)h->wa : (T*)h->fa;
+  sgk::k_gather<T><<<nblk(n), 256, 0, st>>>(pr.nsub, 1, pr.nl, pr.P, h->cls, h->gidx, h->Dw, r, wr, sgk::MASK_G, 1);
+  RET(enq_inner<T>(h, cx, 2, pr.nsub, 1, 0, wr, sizeof(T) == 8 ? 0.0 : h->prec_tol32));
+  sgk::k_scatter<T><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, pr.P, h->owners, h->Dw, wsT<T>(h).x, z, 1);
+  CKL();
+  return SG_OK;
+}
+
 static int enq_precond(sg_handle h, Ctx& cx, const double* r, double* z) {
+  if (h->pc == SG_PC_LUMPED) return enq_precond_lumped(h, cx, r, z);
+  if (h->pc == SG_PC_NN1)
+    return h->precision == SG_FP64 ? enq_precond_nn1<double>(h, cx, r, z) : enq_precond_nn1<float>(h, cx, r, z);
   return h->precision == SG_FP64 ? enq_precond_t<double>(h, cx, r, z) : enq_precond_t<float>(h, cx, r, z);
 }
 
@@ -1146,14 +1182,17 @@ static int build_line_factors(sg_handle h) {
   const auto& pr = h->pr;
   const int L = pr.L, nl = pr.nl, nsub = pr.nsub, H = pr.H, PI = pr.PI;
   const double mh = pr.h * pr.h / 24.0;
-  for (int pat = 0; pat < 2; ++pat) {
+  const int npat = h->pc == SG_PC_NN1 ? 3 : 2;
+  for (int pat = 0; pat < npat; ++pat) {
     std::vector<double> Dd((size_t)nsub * L * L, 0.0), Du((size_t)nsub * L * L, 0.0);
     std::vector<double> Bd((size_t)nsub * L * L, 0.0), Bu((size_t)nsub * L * L, 0.0);
     for (int s = 0; s < nsub; ++s) {
       auto freep = [&](int li, int lj) {
         if (li < 0 || lj < 0 || li > H || lj > H) return false;
         int c = pr.cls[(size_t)s * nl + lj * L + li];
-        return pat == 0 ? c == sgh::INTERIOR : (c == sgh::INTERIOR || c == sgh::REMAINING);
+        if (pat == 0) return c == sgh::INTERIOR;
+        if (pat == 1) return c == sgh::INTERIOR || c == sgh::REMAINING;
+        return c != sgh::DIRICHLET;
       };
       auto cellp = [&](int ci, int cj) { return ci >= 0 && cj >= 0 && ci < H && cj < H; };
       auto kapE0 = [&](int li, int lj) { return pr.kapE[((size_t)s * nl + lj * L + li) * PI]; };
@@ -1637,6 +1676,7 @@ static bool tiles_fit(const sgh::Problem& pr, int precision) {
 static int build_checked(sgh::Problem& pr, std::string& err, const sg_grid* grid, const sg_kl* kl,
                          const sg_pce* pce, const sg_params* prm, const sgh::SourceDesc& sd) {
   if (prm->precision < SG_FP64 || prm->precision > SG_BF16) { err = "precision"; return SG_EINVAL; }
+  if (prm->precond < SG_PC_NN2 || prm->precond > SG_PC_LUMPED) { err = "precond"; return SG_EINVAL; }
   std::string msg = sgh::build_problem(pr, grid->N, grid->nsub_x, grid->nsub_y, kl->M, kl->sigma, kl->bx,
                                        kl->by, kl->g0, pce->p, pce->p_in, prm->dt, prm->alpha0, prm->alpha1, sd,
                                        kl->modes, kl->modes ? kl->lambdas : nullptr);
@@ -1667,6 +1707,7 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   // SG_BF16 differ only in the mean-operator preconditioner, chosen in build_mma_precond)
   h->precision = prm->precision == SG_FP64 ? SG_FP64 : SG_MIXED;
   h->policy = prm->precision;
+  h->pc = prm->precond;
   h->warm = prm->warm;
   h->tol = prm->tol > 0 ? prm->tol : 1e-8;
   h->max_iter = prm->max_iter > 0 ? prm->max_iter : 500;
@@ -1808,7 +1849,7 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   RET(build_line_factors(h));
   RET(build_mma_precond(h));
   if (prm->autotune) RET(autotune(h));
-  RET(build_coarse(h));
+  if (h->pc == SG_PC_NN2) RET(build_coarse(h));  // the one-level preconditioners have no coarse space
   if (h->warm == SG_WARM_LEARNED) RET(warm_setup(h));
   RET(initial_state(h));
   RET(warm_reset_history(h));

@@ -407,3 +407,34 @@ def test_fp32_and_bf16_modes(lib, precision):
     assert err <= BAR_MIXED * prob.tol and modes <= BAR_MIXED_MODE * prob.tol
     assert all(r <= prob.tol for r in rr)
     assert all(a <= b + 2 for a, b in zip(its, its_ref))
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("pc", [1, 2], ids=["nn1", "lumped"])
+def test_one_level_preconditioners_match_oracle(lib, pc, precision):
+    """The comparison preconditioners of Sec. 6.1 (one-level Neumann-Neumann: local Neumann solves
+    with the whole interface free, no coarse space; lumped: K~_GG on the interface) against the
+    oracle's PCG with the same preconditioner: FP64 at PCG tolerance 1e-13, mixed at the workload
+    tolerance; outer iteration counts within one of the oracle's."""
+    name = {1: "nn1", 2: "lumped"}[pc]
+    prob = w.config("small")
+    tol = 1e-13 if precision == 0 else prob.tol
+    steps = 3
+    s = lib(prob, precision=precision, tol=tol, precond=pc)
+    s.step(steps)
+    U = s.field()
+    its, rr = s.iters()
+    s.close()
+    d = odd.DDSolver(prob, precond=name)
+    Ur, _, _, it = odd.run_dd(osg.SGProblem(prob), d, steps, tol=tol)
+    Ur = Ur.reshape(U.shape)
+    its_ref = [i for i, _ in it]
+    err, modes = rel(U, Ur), rel_modes(U, Ur).max()
+    print(f"{name} {'fp64' if precision == 0 else 'mixed'}: rel err {err:.2e}, worst mode {modes:.2e}, "
+          f"iters {its} vs {its_ref}")
+    if precision == 0:
+        assert err <= BAR_U and modes <= BAR_U_MODE
+    else:
+        assert err <= BAR_MIXED * tol and modes <= BAR_MIXED_MODE * tol
+    assert all(r <= tol for r in rr)
+    assert all(abs(a - b) <= 1 for a, b in zip(its, its_ref))

@@ -20,7 +20,8 @@ def B():
     return binding
 
 
-def setup_rc(B, prob, precision=0, warm=0, warm_train_steps=0, grid=None, src_kind=None, modes=None, lambdas=None):
+def setup_rc(B, prob, precision=0, warm=0, warm_train_steps=0, grid=None, src_kind=None, modes=None, lambdas=None,
+             precond=0):
     lib = B.load_library()
     s = prob.source
     g = grid or B.Grid(prob.N, prob.s, prob.s)
@@ -28,7 +29,7 @@ def setup_rc(B, prob, precision=0, warm=0, warm_train_steps=0, grid=None, src_ki
               None if lambdas is None else lambdas.ctypes.data)
     pce = B.PCE(prob.p, prob.p_in)
     prm = B.Params(prob.dt, prob.tol, prob.alpha0, prob.alpha1, prob.max_iter, precision, warm, 0.0, 0, 0,
-                   warm_train_steps, 0.0)
+                   warm_train_steps, 0.0, precond)
     src = B.Source(s.kind if src_kind is None else src_kind, s.x0, s.y0, s.width, s.freq, s.amp)
     h = C.c_void_p(12345)
     rc = lib.sg_setup(C.byref(g), C.byref(kl), C.byref(pce), C.byref(prm), C.byref(src), None, C.byref(h))
@@ -39,6 +40,7 @@ CASES = [
     ("source kind", dict(src_kind=5), SG_EINVAL, "source"),
     ("precision", dict(precision=7), SG_EINVAL, "precision"),
     ("negative precision", dict(precision=-1), SG_EINVAL, "precision"),
+    ("preconditioner", dict(precond=3), SG_EINVAL, "precond"),
     ("warm-start mode", dict(warm=9), SG_EINVAL, "warm"),
     ("warm-start training steps", dict(warm_train_steps=-1), SG_EINVAL, "warm"),
 ]
