@@ -242,6 +242,18 @@ int sg_get_moments(sg_handle h, double* mean, double* var, int on_device);
  * paper has no counterpart: this entry point exists only for allocation-restricted callers. */
 int sg_get_moments_noalloc(sg_handle h, double* mean, double* var);
 
+/* Samples of the PCE surrogate of U_n (statistics and PDFs of the SG solution, Sec. 6.2): for each of
+ * nsamp draws xi_s (row s of xi: M values, standard normal for the method's measure) and each of npts
+ * free nodes nodes[j] (free-node index in the layout above),
+ *     out[s * npts + j] = sum_k U_k(x_j) Psi_k(xi_s),
+ * Psi_k the orthonormal multivariate Hermite polynomial of the k-th multi-index.  The caller draws xi,
+ * so the samples are reproducible.  xi, nodes and out are device arrays when on_device != 0, else host
+ * arrays (staged through handle-owned device buffers that grow to the largest call).  Errors:
+ * SG_EINVAL for empty sizes, null pointers or (host input) a node out of range (device input: NaN is
+ * written for such a node); SG_ENOTSUP for M > 12 or p > 10.  Synchronises the handle's stream. */
+int sg_sample_field(sg_handle h, int nsamp, const double* xi, int npts, const int* nodes, double* out,
+                    int on_device);
+
 /* Checkpoint: state = [U | V | A] (3 * n_free * P doubles, layout above) followed by one
  * double holding the step index.  sg_set_state restores it (the PCG warm start is reset to the
  * interface restriction of U). */

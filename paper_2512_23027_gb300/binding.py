@@ -125,6 +125,7 @@ def load_library(path: Optional[str] = None):
     lib.sg_strerror.restype = C.c_char_p
     lib.sg_last_error.argtypes = [C.c_void_p]
     lib.sg_last_error.restype = C.c_char_p
+    lib.sg_sample_field.restype = C.c_int
     for f in ("sg_setup", "sg_step", "sg_solve_batch", "sg_get_field", "sg_get_moments", "sg_get_state",
               "sg_set_state", "sg_step_host", "sg_get_sizes", "sg_get_iters", "sg_destroy"):
         getattr(lib, f).restype = C.c_int
@@ -219,6 +220,21 @@ class Solver:
         var = np.zeros(self.n_free)
         self._check(self.lib.sg_get_moments(self.h, C.c_void_p(_ptr(mean)), C.c_void_p(_ptr(var)), 0))
         return mean, var
+
+    def sample(self, xi, nodes):
+        """Surrogate samples u(x_j, xi_s) = sum_k U_k(x_j) Psi_k(xi_s): xi (nsamp, M), nodes (npts,) free-node
+        indices; numpy in, numpy out (host path), or CUDA torch tensors in and out (device path)."""
+        on_dev = _on_device(xi)
+        if on_dev:
+            import torch
+            out = torch.empty((xi.shape[0], nodes.shape[0]), dtype=torch.float64, device=xi.device)
+        else:
+            xi = np.ascontiguousarray(xi, dtype=np.float64)
+            nodes = np.ascontiguousarray(nodes, dtype=np.int32)
+            out = np.zeros((xi.shape[0], nodes.shape[0]))
+        self._check(self.lib.sg_sample_field(self.h, int(xi.shape[0]), C.c_void_p(_ptr(xi)), int(nodes.shape[0]),
+                                             C.c_void_p(_ptr(nodes)), C.c_void_p(_ptr(out)), on_dev))
+        return out
 
     def get_state(self, out=None):
         if out is None:

@@ -123,6 +123,11 @@ struct sg_handle_s {
   bool a6_rec = false;
   double* fext = nullptr;  // n_free
   double* outbuf = nullptr;
+  // surrogate sampling: multi-indices of the solution basis, staging of host inputs / outputs
+  signed char* alpha_d = nullptr;
+  double *samp_xi = nullptr, *samp_psi = nullptr, *samp_out = nullptr;
+  int* samp_nodes = nullptr;
+  long long samp_cap_s = 0, samp_cap_p = 0, samp_cap_out = 0;
   // interface vectors and outer control
   double *xG = nullptr, *rG = nullptr, *zG = nullptr, *pG = nullptr, *qG = nullptr, *gG = nullptr, *roG = nullptr;
   double *dC = nullptr, *uC = nullptr, *opart = nullptr, *opart2 = nullptr, *scal = nullptr;
@@ -2054,6 +2059,62 @@ int sg_get_moments(sg_handle h, double* mean, double* var, int on_device) {
     if (mean) CK(cudaMemcpyAsync(mean, dm, sizeof(double) * pr.n_free, cudaMemcpyDeviceToHost, h->st));
     if (var) CK(cudaMemcpyAsync(var, dv, sizeof(double) * pr.n_free, cudaMemcpyDeviceToHost, h->st));
   }
+  CK(cudaStreamSynchronize(h->st));
+  return SG_OK;
+}
+
+// ---- PCE surrogate sampling ----
+int sg_sample_field(sg_handle h, int nsamp, const double* xi, int npts, const int* nodes, double* out, int on_device) {
+  if (!h || nsamp < 1 || npts < 1 || !xi || !nodes || !out) return SG_EINVAL;
+  const auto& pr = h->pr;
+  if (pr.M > sgk::SURR_MAXM || pr.p > sgk::SURR_MAXA) {
+    h->err = "sg_sample_field: more random variables or a higher order than the sampler supports";
+    return SG_ENOTSUP;
+  }
+  if (!h->alpha_d) {
+    std::vector<signed char> a((size_t)pr.P * std::max(pr.M, 1), 0);
+    for (int k = 0; k < pr.P; ++k)
+      for (int n = 0; n < pr.M; ++n) a[(size_t)k * pr.M + n] = (signed char)pr.alpha_out[k][n];
+    RET(upload(h, &h->alpha_d, a));
+  }
+  if (!on_device)
+    for (int j = 0; j < npts; ++j)
+      if (nodes[j] < 0 || nodes[j] >= pr.n_free) { h->err = "sg_sample_field: node index out of range"; return SG_EINVAL; }
+  const long long ns = nsamp, np = npts;
+  if (h->samp_cap_s < ns) {
+    dfree(h, &h->samp_psi);
+    dfree(h, &h->samp_xi);
+    RET(dalloc(h, &h->samp_psi, ns * pr.P));
+    RET(dalloc(h, &h->samp_xi, ns * std::max(pr.M, 1)));
+    h->samp_cap_s = ns;
+  }
+  const double* dxi = xi;
+  const int* dnodes = nodes;
+  double* dout = out;
+  if (!on_device) {
+    if (h->samp_cap_p < np) {
+      dfree(h, &h->samp_nodes);
+      RET(dalloc(h, &h->samp_nodes, np));
+      h->samp_cap_p = np;
+    }
+    if (h->samp_cap_out < ns * np) {
+      dfree(h, &h->samp_out);
+      RET(dalloc(h, &h->samp_out, ns * np));
+      h->samp_cap_out = ns * np;
+    }
+    if (pr.M > 0)
+      CK(cudaMemcpyAsync(h->samp_xi, xi, sizeof(double) * ns * pr.M, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->samp_nodes, nodes, sizeof(int) * np, cudaMemcpyHostToDevice, h->st));
+    dxi = h->samp_xi;
+    dnodes = h->samp_nodes;
+    dout = h->samp_out;
+  }
+  const int pmax = pr.p;
+  sgk::k_psi<<<nblk(ns, 128), 128, 0, h->st>>>(nsamp, pr.M, pr.P, pmax, h->alpha_d, dxi, h->samp_psi);
+  sgk::k_surrogate<<<nblk(ns * np), 256, 0, h->st>>>(nsamp, npts, pr.P, pr.n_free, dnodes, h->free_owner, h->U,
+                                                     h->samp_psi, dout);
+  CKL();
+  if (!on_device) CK(cudaMemcpyAsync(out, dout, sizeof(double) * ns * np, cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   return SG_OK;
 }

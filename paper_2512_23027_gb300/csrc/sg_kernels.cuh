@@ -1796,6 +1796,52 @@ __global__ void k_moments(int nfree, int P, const int* owner, const double* __re
 }
 
 // local[sub][ln][k] = src[free_of_local][k] for free nodes (checkpoint restore)
+// PCE surrogate sampling (statistics of the SG solution, Sec. 6.2): psi[s][k] = Psi_k(xi_s), the
+// orthonormal multivariate Hermite polynomial of multi-index alpha_k (P x M exponents, row-major),
+// from the three-term recurrence He_{a+1} = x He_a - a He_{a-1} and the factor 1 / sqrt(a!).
+constexpr int SURR_MAXM = 12, SURR_MAXA = 10;
+__global__ void k_psi(int nsamp, int M, int P, int pmax, const signed char* __restrict__ alpha,
+                      const double* __restrict__ xi, double* __restrict__ psi) {
+  count_launch();
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsamp) return;
+  double he[SURR_MAXM][SURR_MAXA + 1];
+  for (int n = 0; n < M; ++n) {
+    const double x = xi[(long long)s * M + n];
+    he[n][0] = 1.0;
+    if (pmax >= 1) he[n][1] = x;
+    for (int a = 1; a < pmax; ++a) he[n][a + 1] = x * he[n][a] - a * he[n][a - 1];
+    double f = 1.0;  // a!
+    for (int a = 1; a <= pmax; ++a) {
+      f *= a;
+      he[n][a] /= sqrt(f);
+    }
+  }
+  for (int k = 0; k < P; ++k) {
+    double v = 1.0;
+    for (int n = 0; n < M; ++n) v *= he[n][alpha[k * M + n]];
+    psi[(long long)s * P + k] = v;
+  }
+}
+
+// out[s][j] = sum_k U[node_j][k] psi[s][k] (nodes are free-node indices; out of range -> NaN)
+__global__ void k_surrogate(int nsamp, int npts, int P, int nfree, const int* __restrict__ nodes,
+                            const int* __restrict__ free_owner, const double* __restrict__ U,
+                            const double* __restrict__ psi, double* __restrict__ out) {
+  count_launch();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)nsamp * npts) return;
+  const int j = (int)(i % npts);
+  const long long s = i / npts;
+  const int f = nodes[j];
+  if (f < 0 || f >= nfree) { out[i] = nan(""); return; }
+  const double* u = U + (long long)free_owner[f] * P;
+  const double* ps = psi + s * P;
+  double acc = 0.0;
+  for (int k = 0; k < P; ++k) acc = fma(u[k], ps[k], acc);
+  out[i] = acc;
+}
+
 __global__ void k_scatter_free(long long nloc, int P, const int* free_of_local, const double* __restrict__ src,
                                double* __restrict__ dst) {
   count_launch();
