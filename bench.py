@@ -39,8 +39,10 @@ sys.path.insert(0, ROOT)
 METRIC = "SG-DD time-steps/sec & PCG iters vs plain FP64 DD-PCG at rel resid 1e-8"
 
 # DRAM traffic (read + write bytes per launch) of the dominant kernel from one ncu capture, keyed by
-# the sha256 prefix of the kernel sources it was taken on; any other source reports null.
-KERNEL_TRAFFIC = {"a2da2e5eb3964d38": 46282069}
+# the sha256 prefix of the kernel sources it was taken on; any other source reports null.  The value
+# is k_line_w<float> at the 1024^2 workload from step 202 (every subdomain active), an iterate launch:
+# 1,014,472,192 B read + 329,161,728 B written (profiles/k_line_w_ricker1024_dram.md).
+KERNEL_TRAFFIC = {"e09409c99d5d3cfc": 1343633920}
 KERNEL_SOURCES = ("sg_kernels.cuh", "sg_mma.cuh", "sg_gfix.cuh")
 L2_FLUSH_BYTES = 256 << 20
 
@@ -346,6 +348,37 @@ def run_precond_study(args):
     return 0
 
 
+def run_profile_step(args):
+    """One step of the workload for profilers: fast-forward (graph mode), one untimed host-driven step,
+    then one host-driven step between cudaProfilerStart / cudaProfilerStop (run ncu with
+    --profile-from-start off).  Host-driven enqueue launches the same kernels as the step graph, which
+    per-kernel profilers cannot enter (conditional nodes)."""
+    import torch
+    import sg_workloads as w
+    from paper_2512_23027_gb300 import Solver
+    from paper_2512_23027_gb300.binding import SG_FP64, SG_MIXED
+    prob = w.config(args.config)
+    F = FORWARD.get(args.config, 0) if args.forward is None else args.forward
+    s = Solver(prob, precision=SG_MIXED)
+    if F:
+        s.step(F)
+    if args.profile_fp64:
+        st0 = s.get_state()
+        s.close()
+        s = Solver(prob, precision=SG_FP64)
+        s.set_state(st0)
+    s.set_eager(True)
+    s.step(1)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStart()
+    st = s.step(1)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    print(json.dumps({"profiled_step": st["step_index"], "iters": st["iters_total"], "inner": st["inner_total"]}))
+    s.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,6 +397,10 @@ def main():
     ap.add_argument("--precond-study", action="store_true",
                     help="instead of the default line, compare the two-level NN, one-level NN and lumped "
                          "preconditioners over 2x2..16x16 subdomains of a 256^2 grid (iterations per step)")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="instead of the default line: fast-forward, then one host-driven step between "
+                         "cudaProfilerStart/Stop (for ncu --profile-from-start off)")
+    ap.add_argument("--profile-fp64", action="store_true", help="with --profile-step: the plain FP64 solver")
     ap.add_argument("--enqueue", default="graph", choices=["graph", "eager"],
                     help="graph: one CUDA graph per step (default); eager: host-driven enqueue of the same "
                          "kernels (per-kernel profilers cannot see inside graphs with conditional nodes)")
@@ -374,6 +411,8 @@ def main():
         return run_batch(args)
     if args.precond_study:
         return run_precond_study(args)
+    if args.profile_step:
+        return run_profile_step(args)
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
