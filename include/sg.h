@@ -38,6 +38,8 @@
  *                   the table compiled for (M, p, p_in).
  *   SG_FP64_RT      FP64 operator applies with the runtime triple-product table (FP32 keeps the
  *                   compiled one).
+ *   SG_APPLY_LINES  grid lines per block of the compiled-table operator apply (1 .. L, when the tile
+ *                   fits shared memory), in place of the built-in choice.
  *   SG_LINE_OLD     mean-operator line sweeps of subdomains at least 41 nodes wide by the block kernel
  *                   with the factor staged line by line, instead of the register-tiled kernel.
  *   SG_FORCE_NODS   apply without staged edge differences at every size; the value 2 also reads the

@@ -440,6 +440,10 @@ static void apply_cfg(const sgh::Problem& pr, int nb, int* TL, int* NT, size_t* 
       if (bytes(t) <= 100 * 1024 && blocks >= 256) { best = t; break; }
     }
     if (const int t = tuned(0, sizeof(T), pr, nb)) best = t;
+    if (const char* f = std::getenv("SG_APPLY_LINES")) {  // explicit tile height (tuning)
+      const int t = std::atoi(f);
+      if (t >= 1 && t <= L && bytes(t) <= SMEM_TILE) best = t;
+    }
     *TL = best;
     *NT = (L + best - 1) / best;
     *stage = 0;

@@ -201,48 +201,95 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
                      ((FUSEDP ? ((reinterpret_cast<uintptr_t>(zin) | reinterpret_cast<uintptr_t>(pold) |
                                   reinterpret_cast<uintptr_t>(pnew)) & 15)
                               : (reinterpret_cast<uintptr_t>(xk) & 15)) == 0);
+  // Loads are issued in batches of UB per thread before any store: the output buffers may alias the
+  // inputs as far as the compiler knows, so a load-then-store loop would wait a full memory round
+  // trip per element.
+  constexpr int UB = 8;
   if (vec16) {
     // 16-byte vectors: a line of L x P values starts on a 16-byte boundary and holds whole vectors
     const int LP4 = (L * P) >> 2;
     const FD fLP4 = make_fd((unsigned)LP4);
-    for (int e4 = threadIdx.x; e4 < (nin >> 2); e4 += nt) {
-      const int t = fdiv(e4, fLP4);
-      const int jl = lj0 - 1 + t;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (jl >= 0 && jl < L) {
-        const long long g = pb + (long long)jl * L * P + 4LL * (e4 - t * LP4);
-        if (FUSEDP) {
-          v = *reinterpret_cast<const float4*>(zin + g);
-          if (bet != T(0)) {
-            const float4 o = *reinterpret_cast<const float4*>(pold + g);
-            v.x += (float)bet * o.x;
-            v.y += (float)bet * o.y;
-            v.z += (float)bet * o.z;
-            v.w += (float)bet * o.w;
+    const int nin4 = nin >> 2;
+    for (int e0 = threadIdx.x; e0 < nin4; e0 += nt * UB) {
+      float4 va[UB], vb[UB];
+      long long gg[UB];
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        const int e4 = e0 + u * nt;
+        va[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        vb[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        gg[u] = -1;
+        if (e4 < nin4) {
+          const int t = fdiv(e4, fLP4);
+          const int jl = lj0 - 1 + t;
+          if (jl >= 0 && jl < L) {
+            gg[u] = pb + (long long)jl * L * P + 4LL * (e4 - t * LP4);
+            if (FUSEDP) {
+              va[u] = *reinterpret_cast<const float4*>(zin + gg[u]);
+              if (bet != T(0)) vb[u] = *reinterpret_cast<const float4*>(pold + gg[u]);
+            } else {
+              va[u] = *reinterpret_cast<const float4*>(xk + gg[u]);
+            }
           }
-          if (t >= 1 && t <= nlin) *reinterpret_cast<float4*>(pnew + g) = v;
-        } else {
-          v = *reinterpret_cast<const float4*>(xk + g);
         }
       }
-      *reinterpret_cast<float4*>(xs + 4 * e4) = v;
-    }
-  } else
-  for (int e = threadIdx.x; e < nin; e += nt) {
-    const int t = fdiv(e, op.fLP);
-    const int jl = lj0 - 1 + t;
-    T v = T(0);
-    if (jl >= 0 && jl < L) {
-      const long long g = pb + (long long)jl * L * P + (e - t * L * P);
-      if (FUSEDP) {
-        v = zin[g];
-        if (bet != T(0)) v += bet * pold[g];
-        if (t >= 1 && t <= nlin) pnew[g] = v;
-      } else {
-        v = xk[g];
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        const int e4 = e0 + u * nt;
+        if (e4 < nin4) {
+          float4 v = va[u];
+          if (FUSEDP && gg[u] >= 0) {
+            if (bet != T(0)) {
+              v.x += (float)bet * vb[u].x;
+              v.y += (float)bet * vb[u].y;
+              v.z += (float)bet * vb[u].z;
+              v.w += (float)bet * vb[u].w;
+            }
+            const int t = fdiv(e4, fLP4);
+            if (t >= 1 && t <= nlin) *reinterpret_cast<float4*>(pnew + gg[u]) = v;
+          }
+          *reinterpret_cast<float4*>(xs + 4 * e4) = v;
+        }
       }
     }
-    xs[e] = v;
+  } else {
+    for (int e0 = threadIdx.x; e0 < nin; e0 += nt * UB) {
+      T va[UB], vb[UB];
+      long long gg[UB];
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        const int e = e0 + u * nt;
+        va[u] = T(0);
+        vb[u] = T(0);
+        gg[u] = -1;
+        if (e < nin) {
+          const int t = fdiv(e, op.fLP);
+          const int jl = lj0 - 1 + t;
+          if (jl >= 0 && jl < L) {
+            gg[u] = pb + (long long)jl * L * P + (e - t * L * P);
+            if (FUSEDP) {
+              va[u] = zin[gg[u]];
+              if (bet != T(0)) vb[u] = pold[gg[u]];
+            } else {
+              va[u] = xk[gg[u]];
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        const int e = e0 + u * nt;
+        if (e < nin) {
+          T v = va[u];
+          if (FUSEDP && gg[u] >= 0) {
+            if (bet != T(0)) v += bet * vb[u];
+            const int t = fdiv(e, op.fLP);
+            if (t >= 1 && t <= nlin) pnew[gg[u]] = v;
+          }
+          xs[e] = v;
+        }
+      }
+    }
   }
   __syncthreads();
   SG_MARK(1);
@@ -399,40 +446,63 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
   // phase 3: outputs of the owned lines (p.q partial in FP64: the FP32 products of a correction
   // solve can be far below the FP32 normal range)
   double dsum = 0.0;
-  for (int e = threadIdx.x; e < nlin * L * P; e += nt) {
-    const int nd = fdiv(e, op.fP), k = e - nd * P;
-    const int t = fdiv(nd, op.fL), i = nd - t * L;
-    const int lj = lj0 + t;
-    const long long so = so0 + (long long)lj * L + i;
-    const long long g = pb + ((long long)lj * L + i) * P + k;
-    const int c = op.cls[so];
-    TO out = TO(0);
-    if ((out_mask >> c) & 1) {
-      T acc = T(0);
-      if (ck != T(0)) {
-        T s = T(0);
-        if (i < L - 1) s += zs[((size_t)t * (L - 1) + i) * PS + k];
-        if (i > 0) s -= zs[((size_t)t * (L - 1) + i - 1) * PS + k];
-        s += zs[((size_t)nE + (size_t)(t + 1) * L + i) * PS + k];
-        s -= zs[((size_t)nE + (size_t)t * L + i) * PS + k];
-        acc += ck * s;
+  constexpr int UB3 = 4;  // batched loads, as in phase 1
+  const int nout = nlin * L * P;
+  for (int e0 = threadIdx.x; e0 < nout; e0 += nt * UB3) {
+    int cl[UB3], cbs[UB3];
+    TO ad[UB3];
+#pragma unroll
+    for (int u = 0; u < UB3; ++u) {
+      const int e = e0 + u * nt;
+      cl[u] = 0;
+      cbs[u] = 0;
+      ad[u] = TO(0);
+      if (e < nout) {
+        const int nd = fdiv(e, op.fP), k = e - nd * P;
+        const int t = fdiv(nd, op.fL), i = nd - t * L;
+        const long long so = so0 + (long long)(lj0 + t) * L + i;
+        cl[u] = op.cls[so];
+        if (cm != T(0)) cbs[u] = op.cells[so];
+        if (add) ad[u] = add[pb + ((long long)(lj0 + t) * L + i) * P + k];
       }
-      if (cm != T(0)) {
-        const int cb = op.cells[so];
-        T self = T(0), nbs = T(0);
-        const long long dN_ = (long long)L * P;
-        const T* xa = (FUSEDP || xm == xk) ? xs + ((size_t)(t + 1) * L + i) * P + k : xm + g;
-        if (cb & 1) { self += T(4); nbs += T(2) * xa[-dN_ - P] + xa[-dN_] + xa[-P]; }
-        if (cb & 2) { self += T(2); nbs += xa[-dN_] + xa[P]; }
-        if (cb & 4) { self += T(2); nbs += xa[-P] + xa[dN_]; }
-        if (cb & 8) { self += T(4); nbs += xa[P] + T(2) * xa[dN_ + P] + xa[dN_]; }
-        acc += cm * op.mass_h * (self * xa[0] + nbs);
-      }
-      out = (TO)acc;
-      if (add) out += add[g];
-      if (DOT) dsum += (double)xs[((size_t)(t + 1) * L + i) * P + k] * (double)out;
     }
-    y[g] = out;
+#pragma unroll
+    for (int u = 0; u < UB3; ++u) {
+      const int e = e0 + u * nt;
+      if (e >= nout) continue;
+      const int nd = fdiv(e, op.fP), k = e - nd * P;
+      const int t = fdiv(nd, op.fL), i = nd - t * L;
+      const int lj = lj0 + t;
+      const long long g = pb + ((long long)lj * L + i) * P + k;
+      const int c = cl[u];
+      TO out = TO(0);
+      if ((out_mask >> c) & 1) {
+        T acc = T(0);
+        if (ck != T(0)) {
+          T sz = T(0);
+          if (i < L - 1) sz += zs[((size_t)t * (L - 1) + i) * PS + k];
+          if (i > 0) sz -= zs[((size_t)t * (L - 1) + i - 1) * PS + k];
+          sz += zs[((size_t)nE + (size_t)(t + 1) * L + i) * PS + k];
+          sz -= zs[((size_t)nE + (size_t)t * L + i) * PS + k];
+          acc += ck * sz;
+        }
+        if (cm != T(0)) {
+          const int cb = cbs[u];
+          T self = T(0), nbs = T(0);
+          const long long dN_ = (long long)L * P;
+          const T* xa = (FUSEDP || xm == xk) ? xs + ((size_t)(t + 1) * L + i) * P + k : xm + g;
+          if (cb & 1) { self += T(4); nbs += T(2) * xa[-dN_ - P] + xa[-dN_] + xa[-P]; }
+          if (cb & 2) { self += T(2); nbs += xa[-dN_] + xa[P]; }
+          if (cb & 4) { self += T(2); nbs += xa[-P] + xa[dN_]; }
+          if (cb & 8) { self += T(4); nbs += xa[P] + T(2) * xa[dN_ + P] + xa[dN_]; }
+          acc += cm * op.mass_h * (self * xa[0] + nbs);
+        }
+        out = (TO)acc;
+        if (add) out += ad[u];
+        if (DOT) dsum += (double)xs[((size_t)(t + 1) * L + i) * P + k] * (double)out;
+      }
+      y[g] = out;
+    }
   }
   SG_MARK(4);
   if (DOT) {

@@ -66,8 +66,12 @@ def compare(U, rec, ref):
     return glob, np.array(per_mode), norm_rel, top
 
 
-# stated bars (sampled estimates of relative l2 errors); measured values are in the design doc
-BARS = {SG_FP64: {"glob": 1e-10, "mode": 1e-9}, SG_MIXED: {"glob": 1e-8, "mode": 1e-6}}
+# Stated bars (sampled estimates of relative l2 errors).  FP64 at PCG tolerance 1e-13: 1e-10 for the
+# field, 1e-9 per mode.  Mixed precision at the workload tolerance tol = 1e-8, the error model of the
+# small-problem tests: both solvers stop at ||r|| <= tol ||G||, so 10 tol for the field (the error of
+# the whole field), and a mode holds at most all of it: 10 tol ||U|| / ||U_k|| <= 1e4 tol per mode
+# with the 1e-3 floor.
+BARS = {SG_FP64: {"glob": 1e-10, "mode": 1e-9}, SG_MIXED: {"glob": 1e-7, "mode": 1e-4}}
 
 
 @pytest.mark.slow
