@@ -38,6 +38,9 @@
  *                   the table compiled for (M, p, p_in).
  *   SG_FP64_RT      FP64 operator applies with the runtime triple-product table (FP32 keeps the
  *                   compiled one).
+ *   SG_APPLY_FP64   FP64 arithmetic in the outer-loop operator applies of the mixed-precision path
+ *                   (effective load, residual corrections) instead of float-float pairs of FP32
+ *                   values (about 1e-13 relative; used when the compiled table applies).
  *   SG_APPLY_LINES  grid lines per block of the compiled-table operator apply (1 .. L, when the tile
  *                   fits shared memory), in place of the built-in choice.
  *   SG_LINE_OLD     mean-operator line sweeps of subdomains at least 41 nodes wide by the block kernel

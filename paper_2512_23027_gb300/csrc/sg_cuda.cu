@@ -87,6 +87,9 @@ struct sg_handle_s {
   uint8_t *cls = nullptr, *cells = nullptr;
   double *kapE = nullptr, *kapN = nullptr, *gk_v = nullptr;
   float *kapE32 = nullptr, *kapN32 = nullptr, *gk_v32 = nullptr;
+  // float-float copies of the edge weights (hi, lo) for the float-float outer applies (apply_f2)
+  float2 *kapE2 = nullptr, *kapN2 = nullptr;
+  bool apply_f2 = false;
   int *gk_ptr = nullptr, *gk_i = nullptr, *gk_j = nullptr;
   unsigned* gk_pk = nullptr;  // gk_i | gk_j << 16
   int *gidx = nullptr, *cidx = nullptr, *owners = nullptr, *cowners = nullptr, *gam_ln = nullptr;
@@ -501,6 +504,21 @@ static int launch_apply(sg_handle h, cudaStream_t st, const Op<T>& op, int nb, i
   const int fx = gfix_for<T>(h->pr);
   const unsigned grid = (unsigned)((long long)nb * NT);
   const int nnz = (int)h->pr.gk_v.size();
+  if constexpr (sizeof(T) == 8 && sizeof(TO) == 8 && !FUSEDP && !DOT) {
+    if (h->apply_f2 && fx >= 0) {
+      const size_t off = (size_t)(op.kapE - (const double*)h->kapE);  // the Op's first subdomain
+      const bool ok = with_gfix(fx, false, [&](auto c) -> bool {
+        using C = decltype(c);
+        sgk::k_apply_f2<C><<<grid, 256, sm, st>>>(op, nb, R, TL, NT, xm, xk, y, add, cm, ck, mask, h->kapE2 + off,
+                                                  h->kapN2 + off);
+        return true;
+      });
+      if (ok) {
+        CKL();
+        return SG_OK;
+      }
+    }
+  }
   bool done = with_gfix(fx, false, [&](auto c) -> bool {
     using C = decltype(c);
     if constexpr (sizeof(T) == 4 || gfix_fp64_ok<C>()) {
@@ -1803,7 +1821,12 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
         if constexpr (gfix_fp64_ok<C>()) {
           RET(smem_attr(h, sgk::k_apply<double, double, false, false, C>, lim));
           RET(smem_attr(h, sgk::k_apply<double, double, true, true, C>, lim));
+          RET(smem_attr(h, sgk::k_apply_f2<C>, lim));
         }
+        // low parts of the float-float table: G - (double)(float)G
+        std::vector<float> lo(C::NNZ);
+        for (int e = 0; e < C::NNZ; ++e) lo[e] = (float)(pr.gk_v[e] - (double)f[e]);
+        CK(cudaMemcpyToSymbol(sgk::c_gvf_lo, lo.data(), sizeof(float) * C::NNZ, sizeof(float) * C::OFF));
         return SG_OK;
       });
       RET(rc);
@@ -1816,6 +1839,22 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
     std::vector<float> e32(pr.kapE.begin(), pr.kapE.end()), n32(pr.kapN.begin(), pr.kapN.end());
     std::vector<float> g32(pr.gk_v.begin(), pr.gk_v.end());
     RET(upload(h, &h->kapE32, e32)); RET(upload(h, &h->kapN32, n32)); RET(upload(h, &h->gk_v32, g32));
+  }
+  // The FP64 applies of the mixed-precision outer loop (effective load, residual corrections) in
+  // float-float arithmetic: about 1e-13 relative, five orders below the smallest outer tolerance that
+  // a mixed-precision solve reaches, at a fraction of the FP64 cost.  The FP64 path keeps FP64
+  // arithmetic throughout; SG_APPLY_FP64 keeps it for the mixed path too.
+  h->apply_f2 = h->precision == SG_MIXED && gfix_for<double>(pr) >= 0 && !std::getenv("SG_APPLY_FP64");
+  if (h->apply_f2) {
+    auto split = [](const std::vector<double>& v) {
+      std::vector<float2> o(v.size());
+      for (size_t i = 0; i < v.size(); ++i) {
+        const float hi = (float)v[i];
+        o[i] = make_float2(hi, (float)(v[i] - (double)hi));
+      }
+      return o;
+    };
+    RET(upload(h, &h->kapE2, split(pr.kapE))); RET(upload(h, &h->kapN2, split(pr.kapN)));
   }
   RET(upload(h, &h->gk_ptr, pr.gk_ptr)); RET(upload(h, &h->gk_i, pr.gk_i)); RET(upload(h, &h->gk_j, pr.gk_j));
   {

@@ -135,6 +135,7 @@ constexpr int GV_CAP = C6::OFF + C6::NNZ;
 
 __constant__ float c_gvf[gfix::GV_CAP];   // G values of every compiled size (FP32 copy)
 __constant__ double c_gvd[gfix::GV_CAP];  // the same values in FP64
+__constant__ float c_gvf_lo[gfix::GV_CAP];  // G - (double) c_gvf: the low part of a float-float G
 
 template <typename T>
 __device__ __forceinline__ T gval(int e);
@@ -196,6 +197,109 @@ __device__ __forceinline__ void gflux(int g, const T* __restrict__ kp, const T* 
     case 1: if constexpr (C::KG > 1) gflux_group<C, T, 1>(kp, xa, xb, zo, live); break;
     case 2: if constexpr (C::KG > 2) gflux_group<C, T, 2>(kp, xa, xb, zo, live); break;
     case 3: if constexpr (C::KG > 3) gflux_group<C, T, 3>(kp, xa, xb, zo, live); break;
+    default: break;
+  }
+}
+
+// ---- float-float flux (unevaluated sums of two FP32 values, ~2^-44 relative) for FP64 applies ----
+// Error-free transformations: TwoSum (Knuth) for sums, the fused multiply-add for the exact rounding
+// error of a product.  A value is (h, l) with |l| <= ulp(h) / 2 after normalisation; the inner loop
+// keeps the accumulator's low part unnormalised (it only collects error terms).  The explicitly
+// rounded intrinsics (__fadd_rn, __fmul_rn) keep the compiler from contracting a rounded product
+// into a following sum, which would break the transformations.
+struct f2 {
+  float h, l;
+};
+__device__ __forceinline__ f2 f2_from(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double f2_to(f2 a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ f2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ f2 fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  f2 s = two_sum(a.h, b.h);
+  s.l = __fadd_rn(s.l, __fadd_rn(a.l, b.l));
+  return fast_two_sum(s.h, s.l);
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) { return f2_add(a, {-b.h, -b.l}); }
+// product with normalisation
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return fast_two_sum(p, e);
+}
+
+// one triple-product term in float-float: z[k] += G_ijk * (kappa[i] * d[j])
+template <class C, int E>
+__device__ __forceinline__ void gterm_f2(const f2 (&kap)[C::PI], const f2 (&d)[C::P], f2 (&z)[C::P]) {
+  using X = Ent<C, E>;
+  const f2 a = kap[X::I], b = d[X::J];
+  // t = a * b, unnormalised (p, e)
+  const float p = __fmul_rn(a.h, b.h);
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  // u = G * t
+  const float gh = c_gvf[C::OFF + E], gl = c_gvf_lo[C::OFF + E];
+  const float uh = __fmul_rn(gh, p);
+  float ue = fmaf(gh, p, -uh);
+  ue = fmaf(gh, e, ue);
+  ue = fmaf(gl, p, ue);
+  // z += u: TwoSum on the high parts, error terms into the low part
+  const f2 s = two_sum(z[X::K].h, uh);
+  z[X::K].h = s.h;
+  z[X::K].l = __fadd_rn(z[X::K].l, __fadd_rn(s.l, ue));
+}
+
+template <class C, int E0, int... E>
+__device__ __forceinline__ void gterms_f2(const f2 (&kap)[C::PI], const f2 (&d)[C::P], f2 (&z)[C::P],
+                                          std::integer_sequence<int, E...>) {
+  (gterm_f2<C, E0 + E>(kap, d, z), ...);
+}
+
+// Flux of one edge for the output modes of group G in float-float: kappa(e) from the float-float
+// copy of the edge weights (kp: PI pairs), end-point values from shared memory (pairs).
+template <class C, int G>
+__device__ __forceinline__ void gflux_group_f2(const float2* __restrict__ kp, const f2* xa, const f2* xb, f2* zo,
+                                               bool live) {
+  constexpr int K0 = Grp<C, G>::K0, K1 = Grp<C, G>::K1;
+  constexpr int E0 = Grp<C, G>::E0, E1 = Grp<C, G>::E1;
+  f2 z[C::P];
+#pragma unroll
+  for (int k = K0; k < K1; ++k) z[k] = {0.f, 0.f};
+  if (live) {
+    f2 kap[C::PI], d[C::P];
+#pragma unroll
+    for (int i = 0; i < C::PI; ++i) {
+      const float2 v = __ldg(kp + i);
+      kap[i] = {v.x, v.y};
+    }
+#pragma unroll
+    for (int j = 0; j < C::P; ++j) d[j] = f2_sub(xa[j], xb[j]);
+    gterms_f2<C, E0>(kap, d, z, std::make_integer_sequence<int, E1 - E0>{});
+  }
+#pragma unroll
+  for (int k = K0; k < K1; ++k) zo[k] = fast_two_sum(z[k].h, z[k].l);
+}
+
+template <class C>
+__device__ __forceinline__ void gflux_f2(int g, const float2* __restrict__ kp, const f2* xa, const f2* xb, f2* zo,
+                                         bool live) {
+  switch (g) {
+    case 0: gflux_group_f2<C, 0>(kp, xa, xb, zo, live); break;
+    case 1: if constexpr (C::KG > 1) gflux_group_f2<C, 1>(kp, xa, xb, zo, live); break;
+    case 2: if constexpr (C::KG > 2) gflux_group_f2<C, 2>(kp, xa, xb, zo, live); break;
+    case 3: if constexpr (C::KG > 3) gflux_group_f2<C, 3>(kp, xa, xb, zo, live); break;
     default: break;
   }
 }

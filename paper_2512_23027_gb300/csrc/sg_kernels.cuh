@@ -520,6 +520,175 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
 }
 
 // ------------------------------------------------------------------------------------------
+// Operator apply in float-float arithmetic (compiled triple-product table only):
+//   y = add + cm (M (x) I) xm + ck (sum_i K_i (x) G_i) xk       on nodes with class in out_mask
+// the operator of k_apply<double, double, false, false, C> with FP64 inputs and outputs.  The block's
+// input lines are scaled by a power of two (its largest |xk| maps into [1/2, 1), so the FP32 exponent
+// range of the pairs cannot flush small vectors) and staged as float-float pairs; each edge's
+// differences, weights (float-float copies of the FP64 edge weights) and triple products combine by
+// error-free transformations (about 2^-44 relative per operation, gflux_f2), and every output is formed
+// in float-float, rounded to FP64 once and unscaled exactly.  FP64 arithmetic runs at about 1/60 of the
+// FP32 rate on this part; a float-float triple product costs about 16 FP32 operations.  A mass input
+// xm other than xk is applied in FP64 from global memory.  Shared memory as the FP64 compiled variant:
+// xs [(TL+2)][L][P] pairs, zs [edges][PS] pairs.
+// ------------------------------------------------------------------------------------------
+template <class C>
+__global__ void __launch_bounds__(256) k_apply_f2(Op<double> op, int nb, int R, int TL, int NT,
+                                                  const double* __restrict__ xm, const double* __restrict__ xk,
+                                                  double* y, const double* add, double cm, double ck, int out_mask,
+                                                  const float2* __restrict__ kapE2, const float2* __restrict__ kapN2) {
+  count_launch();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  const int P = op.P, L = op.L, nl = op.nl, PI = op.PI;
+  const int PS = P | 1;
+  const int b = blockIdx.x / NT, tile = blockIdx.x % NT;
+  const int lj0 = tile * TL;
+  const int nlin = min(TL, L - lj0);
+  const int sub = b / R;
+  const int nE = nlin * (L - 1), nNr = nlin + 1;
+  const int nEd = nE + nNr * L;
+  f2* xs = reinterpret_cast<f2*>(smem_raw);      // [(TL+2)][L][P] (FP64 values until the scale is known)
+  double* xd = reinterpret_cast<double*>(smem_raw);
+  f2* zs = xs + (size_t)(TL + 2) * L * P;        // [edges][PS]
+  const long long pb = (long long)b * nl * P;
+  const long long so0 = (long long)sub * nl;
+  const int nt = blockDim.x;
+  const bool same = xm == xk;
+  // phase 1: input lines lj0-1 .. lj0+nlin (zeros outside the grid), loads in batches; block max |x|
+  constexpr int UB = 8;
+  const int nin = (nlin + 2) * L * P;
+  double amax = 0.0;
+  for (int e0 = threadIdx.x; e0 < nin; e0 += nt * UB) {
+    double v[UB];
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int e = e0 + u * nt;
+      v[u] = 0.0;
+      if (e < nin) {
+        const int t = fdiv(e, op.fLP);
+        const int jl = lj0 - 1 + t;
+        if (jl >= 0 && jl < L) v[u] = xk[pb + (long long)jl * L * P + (e - t * L * P)];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UB; ++u) {
+      const int e = e0 + u * nt;
+      if (e < nin) {
+        xd[e] = v[u];
+        amax = fmax(amax, fabs(v[u]));
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
+  __syncthreads();
+  amax = 0.0;
+  for (int w = 0; w < (nt >> 5); ++w) amax = fmax(amax, red[w]);
+  int ex = 0;
+  if (amax > 0.0) frexp(amax, &ex);                // amax = f 2^ex, f in [1/2, 1)
+  const double sc = ldexp(1.0, -ex), usc = ldexp(1.0, ex);
+  for (int e = threadIdx.x; e < nin; e += nt) xs[e] = f2_from(xd[e] * sc);   // the thread's own elements
+  __syncthreads();
+  // phase 2: fluxes, one work item per (edge, output-mode group), the group uniform across a warp
+  if (ck != 0.0) {
+    const int nEd32 = (nEd + 31) & ~31;
+    for (int it = threadIdx.x; it < nEd32 * C::KG; it += nt) {
+      const int wi = it >> 5, g = wi % C::KG;
+      const int ed = ((wi / C::KG) << 5) + (it & 31);
+      if (ed >= nEd) continue;
+      const f2* xa;
+      const f2* xb;
+      const float2* kp;
+      bool live = true;
+      if (ed < nE) {
+        const int t = fdiv(ed, op.fLm1), c = ed - t * (L - 1);
+        xa = xs + ((size_t)(t + 1) * L + c) * P;
+        xb = xa + P;
+        kp = kapE2 + (so0 + (long long)(lj0 + t) * L + c) * PI;
+      } else {
+        const int v = ed - nE, t = fdiv(v, op.fL), c = v - t * L;
+        const int jb = lj0 - 1 + t;
+        live = jb >= 0 && jb + 1 < L;
+        xa = xs + ((size_t)t * L + c) * P;
+        xb = xa + (size_t)L * P;
+        kp = kapN2 + (so0 + (long long)max(jb, 0) * L + c) * PI;
+      }
+      gflux_f2<C>(g, kp, xa, xb, zs + (size_t)ed * PS, live);
+    }
+  }
+  __syncthreads();
+  // phase 3: outputs of the owned lines
+  const f2 ckf = f2_from(ck), cmf = f2_from(cm * op.mass_h);
+  const double cmd = cm * op.mass_h;
+  constexpr int UB3 = 4;
+  const int nout = nlin * L * P;
+  const long long dN_ = (long long)L * P;
+  for (int e0 = threadIdx.x; e0 < nout; e0 += nt * UB3) {
+    int cl[UB3], cbs[UB3];
+    double ad[UB3];
+#pragma unroll
+    for (int u = 0; u < UB3; ++u) {
+      const int e = e0 + u * nt;
+      cl[u] = 0;
+      cbs[u] = 0;
+      ad[u] = 0.0;
+      if (e < nout) {
+        const int nd = fdiv(e, op.fP), k = e - nd * P;
+        const int t = fdiv(nd, op.fL), i = nd - t * L;
+        const long long so = so0 + (long long)(lj0 + t) * L + i;
+        cl[u] = op.cls[so];
+        if (cm != 0.0) cbs[u] = op.cells[so];
+        if (add) ad[u] = add[pb + ((long long)(lj0 + t) * L + i) * P + k];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UB3; ++u) {
+      const int e = e0 + u * nt;
+      if (e >= nout) continue;
+      const int nd = fdiv(e, op.fP), k = e - nd * P;
+      const int t = fdiv(nd, op.fL), i = nd - t * L;
+      const long long g = pb + ((long long)(lj0 + t) * L + i) * P + k;
+      double out = 0.0;
+      if ((out_mask >> cl[u]) & 1) {
+        f2 acc = {0.f, 0.f};
+        if (ck != 0.0) {
+          f2 sz = zs[((size_t)nE + (size_t)(t + 1) * L + i) * PS + k];
+          sz = f2_sub(sz, zs[((size_t)nE + (size_t)t * L + i) * PS + k]);
+          if (i < L - 1) sz = f2_add(sz, zs[((size_t)t * (L - 1) + i) * PS + k]);
+          if (i > 0) sz = f2_sub(sz, zs[((size_t)t * (L - 1) + i - 1) * PS + k]);
+          acc = f2_mul(ckf, sz);
+        }
+        const int cb = cbs[u];
+        double md = 0.0;
+        if (cm != 0.0 && same) {
+          const f2* xa = xs + ((size_t)(t + 1) * L + i) * P + k;
+          auto twice = [](f2 a) -> f2 { return {2.f * a.h, 2.f * a.l}; };  // exact
+          float self = 0.f;
+          f2 nbs = {0.f, 0.f};
+          if (cb & 1) { self += 4.f; nbs = f2_add(f2_add(f2_add(nbs, twice(xa[-dN_ - P])), xa[-dN_]), xa[-P]); }
+          if (cb & 2) { self += 2.f; nbs = f2_add(f2_add(nbs, xa[-dN_]), xa[P]); }
+          if (cb & 4) { self += 2.f; nbs = f2_add(f2_add(nbs, xa[-P]), xa[dN_]); }
+          if (cb & 8) { self += 4.f; nbs = f2_add(f2_add(f2_add(nbs, xa[P]), twice(xa[dN_ + P])), xa[dN_]); }
+          acc = f2_add(acc, f2_mul(cmf, f2_add(f2_mul({self, 0.f}, xa[0]), nbs)));
+        } else if (cm != 0.0) {
+          const double* xa = xm + g;
+          double self = 0.0, nbs = 0.0;
+          if (cb & 1) { self += 4.0; nbs += 2.0 * xa[-dN_ - P] + xa[-dN_] + xa[-P]; }
+          if (cb & 2) { self += 2.0; nbs += xa[-dN_] + xa[P]; }
+          if (cb & 4) { self += 2.0; nbs += xa[-P] + xa[dN_]; }
+          if (cb & 8) { self += 4.0; nbs += xa[P] + 2.0 * xa[dN_ + P] + xa[dN_]; }
+          md = cmd * (self * xa[0] + nbs);
+        }
+        out = f2_to(acc) * usc + md;
+        if (add) out += ad[u];
+      }
+      y[g] = out;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // Mean-operator preconditioner fused with the inner CG update and control.
 // A0 = cm M + ck K_0 on a pattern's free set is block tridiagonal over grid lines; the set-up
 // stores S_j^{-1} (dense L x L) with S_0 = D_0, S_j = D_j - B_{j-1}^T S_{j-1}^{-1} B_{j-1};

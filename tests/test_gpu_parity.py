@@ -165,6 +165,25 @@ def test_mixed_matches_oracle(lib, name, steps):
     assert all(a <= b + 2 for a, b in zip(its, its_ref))
 
 
+@pytest.mark.parametrize("name,steps", [("small", 4), ("pulse32", 5)])
+def test_float_float_outer_applies(lib, name, steps):
+    """The operator applies of the mixed path's FP64 outer loop (effective load, residual corrections)
+    run in float-float pairs where the compiled triple-product table applies, about 1e-13 relative;
+    SG_APPLY_FP64 runs them in FP64.  Both give the same outer iteration counts within one and fields
+    within the solver tolerance of each other, each within the mixed-precision bar of the oracle."""
+    from paper_2512_23027_gb300.binding import SG_MIXED
+    prob = w.config(name)
+    ua, ia, ra = _run_env(lib, prob, SG_MIXED, steps, {})
+    ub, ib, rb = _run_env(lib, prob, SG_MIXED, steps, {"SG_APPLY_FP64": "1"})
+    Ur, _, _, _ = oracle_run(prob, steps, prob.tol)
+    print(f"{name}: float-float vs FP64 outer applies rel diff {rel(ua, ub):.3e}, vs oracle {rel(ua, Ur):.3e} / "
+          f"{rel(ub, Ur):.3e}, iters {ia} vs {ib}")
+    assert rel(ua, ub) <= prob.tol
+    assert rel(ua, Ur) <= BAR_MIXED * prob.tol and rel(ub, Ur) <= BAR_MIXED * prob.tol
+    assert all(r <= prob.tol for r in ra + rb)
+    assert all(abs(x - y) <= 1 for x, y in zip(ia, ib))
+
+
 def test_graph_equals_eager(lib):
     """The captured step graph (conditional WHILE/IF nodes) and the host-driven enqueue of
     the same kernels give bitwise identical results."""
