@@ -305,8 +305,9 @@ int sg_set_enqueue_mode(sg_handle h, int eager);
  * launch count of the kernel class selected by the previous call, then selects `which` and
  * resets the totals.  which: 0 none, 1 preconditioner step of the FP32/FP64 subdomain CG (line
  * sweeps with the fused CG update, or CG update + residual pack + tensor-core product), 2 fused
- * SG operator apply, 3 the tensor-core product kernel alone.  Events are recorded on the stream
- * the kernel is launched on. */
+ * SG operator apply, 3 the tensor-core product kernel alone, 4 the operator applies with FP64
+ * inputs and outputs (effective load and residual corrections; float-float arithmetic in the
+ * mixed path).  Events are recorded on the stream the kernel is launched on. */
 int sg_kernel_timing(sg_handle h, int which, double* total_ms, long long* launches);
 
 /* Kernels launched by this library in this process so far (all handles), counted on the device

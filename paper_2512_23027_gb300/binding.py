@@ -258,7 +258,8 @@ class Solver:
 
     def kernel_timing(self, which: int):
         """Return (ms, launches) accumulated for the previously selected kernel class and
-        select `which` (0 none, 1 preconditioner step, 2 fused apply, 3 tensor-core product) for the
+        select `which` (0 none, 1 preconditioner step, 2 fused apply, 3 tensor-core product, 4 applies
+        with FP64 inputs and outputs) for the
         following eager steps."""
         ms = C.c_double()
         n = C.c_longlong()

@@ -495,9 +495,8 @@ static void apply_cfg(const sgh::Problem& pr, int nb, int* TL, int* NT, size_t* 
 }
 
 template <typename T, typename TO, bool FUSEDP, bool DOT>
-static int launch_apply(sg_handle h, cudaStream_t st, const Op<T>& op, int nb, int R, const T* xm, const T* xk, TO* y,
-                        const TO* add, double cm, double ck, int mask, T* p0 = nullptr, T* p1 = nullptr,
-                        const T* z = nullptr) {
+static int launch_apply_k(sg_handle h, cudaStream_t st, const Op<T>& op, int nb, int R, const T* xm, const T* xk,
+                          TO* y, const TO* add, double cm, double ck, int mask, T* p0, T* p1, const T* z) {
   int TL, NT, stage, nods;
   size_t sm;
   apply_cfg<T>(h->pr, nb, &TL, &NT, &sm, &stage, &nods);
@@ -551,6 +550,31 @@ static int launch_apply(sg_handle h, cudaStream_t st, const Op<T>& op, int nb, i
   return SG_OK;
 }
 
+// The apply launch; with kernel timing class 4 selected (sg_kernel_timing) the FP64-input applies
+// (float-float in the mixed path) are bracketed by CUDA events on their stream, outside capture.
+template <typename T, typename TO, bool FUSEDP, bool DOT>
+static int launch_apply(sg_handle h, cudaStream_t st, const Op<T>& op, int nb, int R, const T* xm, const T* xk, TO* y,
+                        const TO* add, double cm, double ck, int mask, T* p0 = nullptr, T* p1 = nullptr,
+                        const T* z = nullptr) {
+  bool timed = false;
+  if constexpr (sizeof(T) == 8 && sizeof(TO) == 8 && !FUSEDP && !DOT) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (h->kprof == 4) CK(cudaStreamIsCapturing(st, &cs));
+    timed = h->kprof == 4 && cs == cudaStreamCaptureStatusNone;
+  }
+  if (timed) CK(cudaEventRecord(h->kev0, st));
+  RET((launch_apply_k<T, TO, FUSEDP, DOT>(h, st, op, nb, R, xm, xk, y, add, cm, ck, mask, p0, p1, z)));
+  if (timed) {
+    CK(cudaEventRecord(h->kev1, st));
+    CK(cudaEventSynchronize(h->kev1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->kev0, h->kev1));
+    h->kprof_ms += ms;
+    h->kprof_n += 1;
+  }
+  return SG_OK;
+}
+
 // line-solve block: G modes (fast thread index) x Lp rows, G * Lp a multiple of 32; FP32 covers
 // the modes of a problem with about two blocks, FP64 spreads them over more blocks.
 template <typename T>
@@ -581,7 +605,7 @@ struct LineCfg {
 template <typename T>
 static size_t wide_smem(int L, int GS) {
   const size_t LSP = pad4(L);
-  return sizeof(T) * (2 * (size_t)L * LSP + (2 * (size_t)L + LSP) * GS + 4 * (size_t)L);
+  return sizeof(T) * (2 * (size_t)L * LSP + (2 * (size_t)L + LSP) * GS + 6 * (size_t)L);
 }
 template <typename T>
 static int wide_threads(int L, int G, int GS) {
@@ -2390,7 +2414,7 @@ int sg_set_enqueue_mode(sg_handle h, int eager) {
 }
 
 int sg_kernel_timing(sg_handle h, int which, double* total_ms, long long* launches) {
-  if (!h || which < 0 || which > 3) return SG_EINVAL;
+  if (!h || which < 0 || which > 4) return SG_EINVAL;
   if (total_ms) *total_ms = h->kprof_ms;
   if (launches) *launches = h->kprof_n;
   h->kprof = which;

@@ -215,6 +215,37 @@ __device__ __forceinline__ f2 f2_from(double x) {
   return {h, __double2float_rn(x - (double)h)};
 }
 __device__ __forceinline__ double f2_to(f2 a) { return (double)a.h + (double)a.l; }
+
+// FP64 <-> float-float with a power-of-two scale, by integer operations on the bit patterns (FP64
+// instructions, conversions included, issue at a small fraction of the FP32 rate on this part).
+// f2_split_scaled(x, ex) = x 2^-ex as (h, l): h is x's leading 24 significant bits (truncated), l the
+// rest of its 53 rounded to 24 bits, so h + l = x 2^-ex to about 2^-47 relative.  Values whose scaled
+// magnitude is below the FP32 normal range give 0 (l alone below it gives l = 0); Inf and NaN give NaN.
+__device__ __forceinline__ f2 f2_split_scaled(double x, int ex) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sgn = hi & 0x80000000u;
+  const int E = (int)((hi >> 20) & 0x7ffu);
+  if (E == 0x7ff) return {__uint_as_float(0x7fc00000u), 0.f};
+  const int Ef = E - ex - 1023 + 127;               // biased FP32 exponent of h
+  if (Ef <= 0) return {0.f, 0.f};
+  const float h = __uint_as_float(sgn | ((unsigned)Ef << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+  float l = 0.f;
+  if (Ef > 52) l = __fmul_rn(__uint2float_rn(lo & 0x1fffffffu), __uint_as_float((unsigned)(Ef - 52) << 23));
+  return {h, __uint_as_float(__float_as_uint(l) ^ sgn)};
+}
+// a (normal) FP32 value times 2^ex as FP64, exactly; FP32 zeros and subnormals give 0, overflow Inf
+__device__ __forceinline__ double f32_to_f64_scaled(float f, int ex) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sgn = u & 0x80000000u;
+  const int e8 = (int)((u >> 23) & 0xffu);
+  if (e8 == 0) return 0.0;
+  if (e8 == 0xff) return __hiloint2double((int)(sgn | 0x7ff80000u), 0);
+  const int E = e8 - 127 + 1023 + ex;
+  if (E <= 0) return 0.0;
+  if (E >= 0x7ff) return __hiloint2double((int)(sgn | 0x7ff00000u), 0);
+  const unsigned m = u & 0x7fffffu;
+  return __hiloint2double((int)(sgn | ((unsigned)E << 20) | (m >> 3)), (int)(m << 29));
+}
 __device__ __forceinline__ f2 two_sum(float a, float b) {
   const float s = __fadd_rn(a, b);
   const float bb = __fsub_rn(s, a);

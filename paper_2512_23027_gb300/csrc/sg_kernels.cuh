@@ -527,19 +527,20 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
 // range of the pairs cannot flush small vectors) and staged as float-float pairs; each edge's
 // differences, weights (float-float copies of the FP64 edge weights) and triple products combine by
 // error-free transformations (about 2^-44 relative per operation, gflux_f2), and every output is formed
-// in float-float, rounded to FP64 once and unscaled exactly.  FP64 arithmetic runs at about 1/60 of the
-// FP32 rate on this part; a float-float triple product costs about 16 FP32 operations.  A mass input
-// xm other than xk is applied in FP64 from global memory.  Shared memory as the FP64 compiled variant:
+// in float-float, unscaled exactly and summed in FP64.  FP64 instructions issue at about 1/64 of the
+// FP32 rate on this part: a float-float triple product costs about 16 FP32 operations, and the
+// staging and output conversions work on the bit patterns with integer operations (f2_split_scaled,
+// f32_to_f64_scaled).  A mass input xm other than xk is applied in FP64 from global memory.  Shared memory as the FP64 compiled variant:
 // xs [(TL+2)][L][P] pairs, zs [edges][PS] pairs.
 // ------------------------------------------------------------------------------------------
 template <class C>
-__global__ void __launch_bounds__(256) k_apply_f2(Op<double> op, int nb, int R, int TL, int NT,
+__global__ void __launch_bounds__(256, 2) k_apply_f2(Op<double> op, int nb, int R, int TL, int NT,
                                                   const double* __restrict__ xm, const double* __restrict__ xk,
                                                   double* y, const double* add, double cm, double ck, int out_mask,
                                                   const float2* __restrict__ kapE2, const float2* __restrict__ kapN2) {
   count_launch();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[32];
+  __shared__ unsigned red[32];
   const int P = op.P, L = op.L, nl = op.nl, PI = op.PI;
   const int PS = P | 1;
   const int b = blockIdx.x / NT, tile = blockIdx.x % NT;
@@ -555,10 +556,11 @@ __global__ void __launch_bounds__(256) k_apply_f2(Op<double> op, int nb, int R, 
   const long long so0 = (long long)sub * nl;
   const int nt = blockDim.x;
   const bool same = xm == xk;
-  // phase 1: input lines lj0-1 .. lj0+nlin (zeros outside the grid), loads in batches; block max |x|
+  // phase 1: input lines lj0-1 .. lj0+nlin (zeros outside the grid), loads in batches; the block's
+  // largest binary exponent (integer maximum of the high words of |x|)
   constexpr int UB = 8;
   const int nin = (nlin + 2) * L * P;
-  double amax = 0.0;
+  unsigned amax = 0u;
   for (int e0 = threadIdx.x; e0 < nin; e0 += nt * UB) {
     double v[UB];
 #pragma unroll
@@ -576,19 +578,18 @@ __global__ void __launch_bounds__(256) k_apply_f2(Op<double> op, int nb, int R, 
       const int e = e0 + u * nt;
       if (e < nin) {
         xd[e] = v[u];
-        amax = fmax(amax, fabs(v[u]));
+        amax = max(amax, (unsigned)__double2hiint(v[u]) & 0x7fffffffu);
       }
     }
   }
-  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  amax = __reduce_max_sync(0xffffffffu, amax);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
   __syncthreads();
-  amax = 0.0;
-  for (int w = 0; w < (nt >> 5); ++w) amax = fmax(amax, red[w]);
-  int ex = 0;
-  if (amax > 0.0) frexp(amax, &ex);                // amax = f 2^ex, f in [1/2, 1)
-  const double sc = ldexp(1.0, -ex), usc = ldexp(1.0, ex);
-  for (int e = threadIdx.x; e < nin; e += nt) xs[e] = f2_from(xd[e] * sc);   // the thread's own elements
+  amax = 0u;
+  for (int w = 0; w < (nt >> 5); ++w) amax = max(amax, red[w]);
+  // scale 2^-ex maps the largest |x| into [1/2, 1) (no scaling for an all-zero or subnormal block)
+  const int ex = (amax >> 20) ? (int)(amax >> 20) - 1022 : 0;
+  for (int e = threadIdx.x; e < nin; e += nt) xs[e] = f2_split_scaled(xd[e], ex);   // own elements
   __syncthreads();
   // phase 2: fluxes, one work item per (edge, output-mode group), the group uniform across a warp
   if (ck != 0.0) {
@@ -680,7 +681,8 @@ __global__ void __launch_bounds__(256) k_apply_f2(Op<double> op, int nb, int R, 
           if (cb & 8) { self += 4.0; nbs += xa[P] + 2.0 * xa[dN_ + P] + xa[dN_]; }
           md = cmd * (self * xa[0] + nbs);
         }
-        out = f2_to(acc) * usc + md;
+        out = f32_to_f64_scaled(acc.h, ex) + f32_to_f64_scaled(acc.l, ex);
+        if (md != 0.0) out += md;
         if (add) out += ad[u];
       }
       y[g] = out;
@@ -1141,7 +1143,9 @@ __global__ void k_line_team(int L, int nl, int P, int R, int NG, int NT, int G, 
 // it in z; the backward sweep reads it back.  r . z = r^T A0^{-1} r is formed in the forward sweep as
 // sum_j w_j . y_j (block LDL^T: A0^{-1} = L^{-T} D^{-1} L^{-1}, w = L^{-1} r, y = D^{-1} w), so the
 // backward sweep needs no residual.  Shared memory: Sb [2][L][LSP], Ws [L][GS], Ys [L][GS],
-// Yp [LSP][GS], Bs [2][2][L] (GS = G rounded up to a multiple of 4).
+// Yp [LSP][GS], Bs [3][2][L] (GS = G rounded up to a multiple of 4).  The factor of line j is copied
+// one step ahead (double buffer) and the coupling row j two steps ahead (three slots): the step that
+// uses either reads it only after a cp.async wait and a barrier that cover its copy.
 // One line product acc = S_j-tile x W over c = 0 .. L-1 (rows r0, r0 + 1 of the tile from row c of the
 // stored symmetric factor, four modes of W); even and odd c accumulate separately.
 template <typename T>
@@ -1225,7 +1229,7 @@ __global__ void __launch_bounds__(LW_MAXT, lw_minb<T>()) k_line_w(int L, int LSP
   T* Ws = Sb + 2 * LLS;                    // [L][GS]
   T* Ys = Ws + L * GS;                     // [L][GS]
   T* Yp = Ys + L * GS;                     // [LSP][GS]
-  T* Bs = Yp + LSP * GS;                   // [2][2][L]: coupling row r at Bs[r & 1] (Bd, then Bu)
+  T* Bs = Yp + LSP * GS;                   // [3][2][L]: coupling row r in slot r % 3 (Bd, then Bu)
   const int b = blockIdx.x / NG, grp = blockIdx.x % NG;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int NMT = GS >> 2, NRT = LSP >> 1;
@@ -1258,12 +1262,13 @@ __global__ void __launch_bounds__(LW_MAXT, lw_minb<T>()) k_line_w(int L, int LSP
       const int n16 = LLS * (int)sizeof(T) / 16;
       for (int e = tid; e < n16; e += nthr) cp_async16(dst + e, src + e);
     };
-    auto copy_coupling = [&](int row) {  // Bd, Bu of line `row` -> Bs[row & 1]
-      T* dst = Bs + (row & 1) * 2 * L;
+    auto copy_coupling = [&](int row) {  // Bd, Bu of line `row` -> slot row % 3
+      T* dst = Bs + (row % 3) * 2 * L;
       for (int e = tid; e < 2 * L; e += nthr)
         cp_async_elem(dst + e, e < L ? bd + (long long)row * L + e : bu + (long long)row * L + (e - L));
     };
     copy_line(0);
+    if (L >= 2) copy_coupling(0);
     cp_async_commit();
     for (int e = tid; e < L * GS; e += nthr) Ws[e] = T(0);
     for (int e = tid; e < LSP * GS; e += nthr) Yp[e] = T(0);
@@ -1301,7 +1306,7 @@ __global__ void __launch_bounds__(LW_MAXT, lw_minb<T>()) k_line_w(int L, int LSP
     // ---- forward sweep: y_j = S_j^{-1} (r_j - B_{j-1}^T y_{j-1}) ----
     for (int j = 0; j < L; ++j) {
       if (io_on) {
-        const T* cb = Bs + ((j - 1) & 1) * 2 * L;
+        const T* cb = Bs + ((j + 2) % 3) * 2 * L;  // coupling row j - 1
         const int o0 = j * LP + io_a * P;
         const int s0 = io_a * GS + io_m;
         T amax = T(0), amin = T(1);
@@ -1342,10 +1347,10 @@ __global__ void __launch_bounds__(LW_MAXT, lw_minb<T>()) k_line_w(int L, int LSP
             }
         }
       }
-      if (j + 1 < L) {
-        copy_line(j + 1);
-        copy_coupling(j);
-      }
+      // line j + 1 (used by this sweep's next step) and coupling row j + 1 (used by the input
+      // phase two steps on, after the next step's wait and barrier)
+      if (j + 1 < L) copy_line(j + 1);
+      if (j + 1 <= L - 2) copy_coupling(j + 1);
       cp_async_commit();
       if (j + 1 < L) fetch(j + 1);
       cp_async_wait1();
@@ -1388,8 +1393,8 @@ __global__ void __launch_bounds__(LW_MAXT, lw_minb<T>()) k_line_w(int L, int LSP
       __syncthreads();
     }
     // ---- backward sweep: x_j = y_j - S_j^{-1} B_j x_{j+1} (x_{L-1} = y_{L-1} is in Yp) ----
-    // y_j is read back by the thread that parked it (same row order); S_{L-2} and coupling row
-    // L - 2 are still in their buffers (the forward sweep loaded nothing after them)
+    // y_j is read back by the thread that parked it (same row order); S_{L-2} and coupling rows
+    // L - 2 and L - 3 are still in their buffers (the forward sweep loaded nothing after them)
     T pr_y[NPF];
     auto fetch_y = [&](int j) {
       if (!io_on) return;
@@ -1401,7 +1406,7 @@ __global__ void __launch_bounds__(LW_MAXT, lw_minb<T>()) k_line_w(int L, int LSP
     if (L >= 2) fetch_y(L - 2);
     for (int j = L - 2; j >= 0; --j) {
       if (io_on) {
-        const T* cb = Bs + (j & 1) * 2 * L;
+        const T* cb = Bs + (j % 3) * 2 * L;  // coupling row j
         const int o0 = j * LP + io_a * P;
         const int s0 = io_a * GS + io_m;
 #pragma unroll
@@ -1418,10 +1423,8 @@ __global__ void __launch_bounds__(LW_MAXT, lw_minb<T>()) k_line_w(int L, int LSP
           }
         }
       }
-      if (j >= 1) {
-        copy_line(j - 1);
-        copy_coupling(j - 1);
-      }
+      if (j >= 1) copy_line(j - 1);
+      if (j >= 2) copy_coupling(j - 2);
       cp_async_commit();
       if (j >= 1) fetch_y(j - 1);
       cp_async_wait1();

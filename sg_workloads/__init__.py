@@ -107,6 +107,9 @@ def config(name: str) -> Problem:
         return Problem("ricker1024", N=1024, s=16, M=5, p=2, p_in=2, sigma=0.3, bx=0.1, by=0.1,
                        g0=0.0, dt=cfl_dt(1024), steps=1000, tol=1e-8,
                        source=Source(SOURCE_RICKER, 0.3, 0.5, 0.0, 10.0, 1.0))
+    if name == "ricker1024q":  # the 1024^2 workload's subdomains and PCE on a quarter of its grid
+        # (512x512, 8x8 subdomains of 65x65 nodes, M=5, p=2): kernel profiles of a few GB
+        return dataclasses.replace(config("ricker1024"), name="ricker1024q", N=512, s=8, dt=cfl_dt(512))
     if name == "tiny":  # smallest useful DD problem for exhaustive checks
         return Problem("tiny", N=8, s=2, M=1, p=2, p_in=2, sigma=0.3, bx=0.5, by=0.5,
                        g0=0.0, dt=0.02, steps=5, tol=1e-12,
