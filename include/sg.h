@@ -77,8 +77,10 @@ extern "C" {
                              product where that applies (subdomains of at most 40 x 40 nodes,
                              P <= 32) and the FP32 line sweeps elsewhere                     */
 #define SG_FP32      2    /* as SG_MIXED with the FP32 line sweeps at every size (no BF16)   */
-#define SG_BF16      3    /* as SG_MIXED with the BF16 tensor-core preconditioner required:
-                             SG_ENOTSUP where it does not apply                              */
+#define SG_BF16      3    /* as SG_MIXED with the BF16 tensor-core preconditioner required: the
+                             dense inverse up to 40 x 40 nodes (P <= 32), the line sweeps with
+                             their per-line products on the tensor cores for 41 .. 65 nodes per
+                             side; SG_ENOTSUP elsewhere                                        */
 
 /* ---- interface preconditioner (sg_params.precond) ---- */
 #define SG_PC_NN2     0   /* probabilistic two-level Neumann-Neumann (Eq. NNCP2; the method)     */
@@ -179,7 +181,8 @@ typedef struct {
   int apply_tiles[2];       /* blocks per subdomain problem                                       */
   long long apply_smem[2];  /* dynamic shared memory per block, bytes                             */
   int line_kind[2];         /* mean-operator line solve: 0 block kernel with the factor staged,
-                               1 warp-team kernel, 2 factor and residual read from global memory  */
+                               1 warp-team kernel, 2 factor and residual read from global memory,
+                               3 register-tiled kernel, 4 per-line products on the tensor cores   */
   int line_modes[2];        /* PCE modes per block                                                */
   int line_groups[2];       /* blocks per subdomain problem                                       */
   int line_block[2][3];     /* block shape                                                        */

@@ -109,6 +109,12 @@ struct sg_handle_s {
   bool pdl = false;                // programmatic dependent launch inside the inner loop (opt-in)
   int mma_nb = 32;                 // N of the product: PCE modes padded to 16 or 32
   int Kp = 0, NC = 0, MT = 0;      // padded local node count, 64-node chunks, 128-row tiles
+  // tensor-core line sweeps of the FP32 solves (k_line_tc): BF16 factor images of patterns 0 and 1,
+  // their FP32 65th columns and TMA maps
+  bool line_tc = false;
+  __nv_bfloat16* limg[2] = {nullptr, nullptr};
+  float* lcol[2] = {nullptr, nullptr};
+  CUtensorMap tmL[2];
   __nv_bfloat16* ainv = nullptr;   // [pattern][subdomain][Kp][Kp] BF16 copy of A0^{-1}
   unsigned char* bimg = nullptr;   // [problem][chunk][hi, lo][NB x 64 swizzled] residual image
   int bimg_cap = 0;
@@ -687,6 +693,23 @@ static LineCfg line_cfg(const sgh::Problem& pr, int nb_hint) {
   return c;
 }
 
+// Tensor-core line sweeps (k_line_tc) for the FP32 solves of subdomains of WIDE_LMIN .. 65 nodes per
+// side whose line plan is the register-tiled kernel (at most 32 modes per block): the SG_BF16 policy
+// (BF16 mean-operator products on the tensor cores).  SG_MIXED keeps the FP32 products of k_line_w,
+// which measured faster: on the 1024^2 workload with every subdomain active 597 us per launch against
+// 631 us, since the line product is not what bounds a line step (input phase, barriers and the
+// dependent sweep are).
+constexpr int LTC_LMAX = 65;
+static bool line_tc_eligible(const sgh::Problem& pr, int policy) {
+  if (policy != SG_BF16) return false;
+  if (pr.L < WIDE_LMIN || pr.L > LTC_LMAX) return false;
+  const LineCfg lc = line_cfg<float>(pr, pr.nsub);
+  return lc.wide && lc.G <= 32;
+}
+static int ltc_nb(int G) { return G <= 16 ? 16 : 32; }
+// threads: four warps for the 128 accumulator lanes, and G x ceil(L / 8) for the line I/O
+static int ltc_threads(int L, int G) { return 32 * ((std::max(128, G * ((L + 7) / 8)) + 31) / 32); }
+
 static int ensure_ctl(sg_handle h, int nb, int nt, int ng) {
   if (h->ctl_cap_nb >= nb && h->ctl_cap_nt >= nt && h->ctl_cap_ng >= ng) return SG_OK;
   nb = std::max(nb, h->ctl_cap_nb);
@@ -789,11 +812,31 @@ static int enq_inner(sg_handle h, Ctx& cx, int pat, int nb, int R, int s0, const
         default: break;
       }
 #undef SG_TEAM
-    } else if (lc.wide)
-      sgk::k_line_w<T><<<lg, lc.block, lc.smem, s>>>(L, LSp, pr.nl, pr.P, R, NG, NT, lc.G, lc.GS, pstride_pad,
-                                                     Sinv_pad, Bd, Bu, nb, w.x, w.r, w.z, w.p0, w.p1, w.q, h->ctl,
-                                                     init, tol2, bb_min, imax, hh, use);
-    else if (lc.gs)
+    } else if (lc.wide) {
+      bool done = false;
+      if constexpr (sizeof(T) == 4) {
+        if (h->line_tc && pat < 2) {
+          const int nbv = ltc_nb(lc.G);
+          const dim3 thr((unsigned)ltc_threads(L, lc.G));
+          const size_t smb = sgk::ltc_smem(L, lc.G, nbv);
+          const long long row0 = (long long)s0 * L * L;
+          const float* colp = h->lcol[pat] + (size_t)s0 * L * sgk::LTC_COLN;
+          if (nbv == 16)
+            sgk::k_line_tc<16><<<lg, thr, smb, s>>>(h->tmL[pat], L, pr.nl, pr.P, R, NG, NT, lc.G, row0, colp, Bd, Bu,
+                                                    nb, w.x, w.r, w.z, w.p0, w.p1, w.q, h->ctl, init, tol2, bb_min,
+                                                    imax, hh, use);
+          else
+            sgk::k_line_tc<32><<<lg, thr, smb, s>>>(h->tmL[pat], L, pr.nl, pr.P, R, NG, NT, lc.G, row0, colp, Bd, Bu,
+                                                    nb, w.x, w.r, w.z, w.p0, w.p1, w.q, h->ctl, init, tol2, bb_min,
+                                                    imax, hh, use);
+          done = true;
+        }
+      }
+      if (!done)
+        sgk::k_line_w<T><<<lg, lc.block, lc.smem, s>>>(L, LSp, pr.nl, pr.P, R, NG, NT, lc.G, lc.GS, pstride_pad,
+                                                       Sinv_pad, Bd, Bu, nb, w.x, w.r, w.z, w.p0, w.p1, w.q, h->ctl,
+                                                       init, tol2, bb_min, imax, hh, use);
+    } else if (lc.gs)
       sgk::k_line<T, true><<<lg, lc.block, lc.smem, s>>>(L, pr.nl, pr.P, R, NG, NT, pstride, Sinv, Bd, Bu, nb, w.x,
                                                          w.r, w.z, w.p0, w.p1, w.q, h->ctl, init, tol2, bb_min, imax,
                                                          hh, use);
@@ -1363,6 +1406,44 @@ static int build_mma_precond(sg_handle h) {
   return ensure_ctl(h, pr.nsub, pr.L, std::max(pr.P, h->MT));
 }
 
+// BF16 images of the line factors (patterns 0 and 1) and their TMA maps for k_line_tc: rows
+// (subdomain, line, a) of 64 BF16 columns, boxes of 64 x L with the 128-byte swizzle.
+static int build_line_tc(sg_handle h) {
+  const auto& pr = h->pr;
+  if (!line_tc_eligible(pr, h->policy)) return SG_OK;
+  const int L = pr.L;
+  const long long nmat = (long long)pr.nsub * L;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  cudaDriverEntryPointQueryResult qr;
+  CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&enc, 12000, cudaEnableDefault, &qr));
+  if (!enc || qr != cudaDriverEntryPointSuccess) {
+    h->err = "cuTensorMapEncodeTiled is not available from the driver";
+    return SG_ECUDA;
+  }
+  for (int pat = 0; pat < 2; ++pat) {
+    RET(dalloc(h, &h->limg[pat], nmat * L * 64));
+    RET(dalloc(h, &h->lcol[pat], nmat * sgk::LTC_COLN));
+    sgk::k_line_img<<<nblk(nmat * L * 64), 256, 0, h->st>>>(nmat, L, h->lf[pat].Sinv, h->limg[pat], h->lcol[pat]);
+    CKL();
+    const cuuint64_t dims[2] = {64, (cuuint64_t)(nmat * L)};
+    const cuuint64_t strides[1] = {128};
+    const cuuint32_t box[2] = {64, (cuuint32_t)L};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult cr = enc(&h->tmL[pat], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, h->limg[pat], dims, strides, box, es,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) {
+      h->err = "tensor map encoding of the line-factor image failed";
+      return SG_ECUDA;
+    }
+  }
+  const int lim = (int)sgk::ltc_smem(L, 32, 32);
+  RET(smem_attr(h, sgk::k_line_tc<16>, lim));
+  RET(smem_attr(h, sgk::k_line_tc<32>, lim));
+  h->line_tc = true;
+  return SG_OK;
+}
+
 // Coarse basis Phi_s = -S_rr^{-1} S_rc (per local corner dof) and F_cc (Eq. Fcc_2), from one
 // Neumann solve per local corner dof: v = -N^{-1} K_[ir],c e, F^s e = (K~ (v + e))_c.  The right-hand
 // sides and F^s are formed in FP64; the Neumann solves run in T (FP64 in FP64 mode, FP32 in mixed
@@ -1735,8 +1816,9 @@ static int build_checked(sgh::Problem& pr, std::string& err, const sg_grid* grid
   if (pr.L > 256 || pr.L * 2 > 1024) { err = "subdomains wider than 255 cells are not supported"; return SG_ENOTSUP; }
   if (pr.nsub < 2) { err = "at least 2 x 2 subdomains are required"; return SG_ENOTSUP; }
   pr.gfix = select_gfix(pr);
-  if (prm->precision == SG_BF16 && !mma_applies(pr)) {
-    err = "SG_BF16: the BF16 tensor-core preconditioner needs subdomains of at most 40 x 40 nodes and P <= 32";
+  if (prm->precision == SG_BF16 && !mma_applies(pr) && !line_tc_eligible(pr, SG_BF16)) {
+    err = "SG_BF16: the BF16 tensor-core preconditioner needs subdomains of at most 40 x 40 nodes with P <= 32 "
+          "(dense inverse) or 41 .. 65 nodes per side (line products)";
     return SG_ENOTSUP;
   }
   return SG_OK;
@@ -1920,6 +2002,7 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   }
   RET(build_line_factors(h));
   RET(build_mma_precond(h));
+  RET(build_line_tc(h));
   if (prm->autotune) RET(autotune(h));
   if (h->pc == SG_PC_NN2) RET(build_coarse(h));  // the one-level preconditioners have no coarse space
   if (h->warm == SG_WARM_LEARNED) RET(warm_setup(h));
@@ -2312,6 +2395,11 @@ int sg_plan_query(const sg_grid* grid, const sg_kl* kl, const sg_pce* pce, const
     p.line_groups[i] = lc.NG;
     p.line_block[i][0] = (int)lc.block.x; p.line_block[i][1] = (int)lc.block.y; p.line_block[i][2] = (int)lc.block.z;
     p.line_smem[i] = (long long)lc.smem;
+    if (sizeof(T) == 4 && line_tc_eligible(pr, params->precision)) {
+      p.line_kind[i] = 4;
+      p.line_block[i][0] = ltc_threads(pr.L, lc.G); p.line_block[i][1] = 1; p.line_block[i][2] = 1;
+      p.line_smem[i] = (long long)sgk::ltc_smem(pr.L, lc.G, ltc_nb(lc.G));
+    }
   };
   fill(double{}, 0);
   fill(float{}, 1);

@@ -40,6 +40,47 @@ __device__ __forceinline__ void count_launch() {
     atomicAdd(g_nlaunch, 1ULL);
 }
 
+// FP32 partial sums at any magnitude: a thread's operands are scaled by powers of two (exactly) so
+// that the largest lies in [1, 2), the scaled products are summed in FP32 and the partial joins the
+// FP64 total with one multiplication by the inverse scale.  Scaled products can neither overflow nor
+// lose to underflow anything that the FP32 sum would keep, so subdomain problems whose values are
+// far from 1 (the far field of the wave reaches 1e-30 and below) are summed like any other; FP64
+// arithmetic, which runs at a small fraction of the FP32 rate on this part, stays out of the loop.
+// f32_exp: binary exponent of amax >= 0, clamped so that 2^-e is a normal FP32 value (0 for 0).
+__device__ __forceinline__ int f32_exp(float amax) {
+  const int f = (int)((__float_as_uint(amax) >> 23) & 0xffu);
+  if (f == 0) return amax == 0.f ? 0 : -126;
+  return min(f - 127, 126);
+}
+__device__ __forceinline__ float f32_pow2(int e) { return __uint_as_float((unsigned)(e + 127) << 23); }  // |e| <= 126
+__device__ __forceinline__ double f64_pow2(int e) { return __hiloint2double((e + 1023) << 20, 0); }      // |e| <= 1022
+// Running total (h + l) 2^e of such partials across the steps of a launch in FP32 arithmetic (TwoSum
+// keeps the rounding error of each addition in l), converted to FP64 once at the end.
+struct XAcc {
+  float h = 0.f, l = 0.f;
+  int e = -1000;  // exponent of an empty total
+  __device__ __forceinline__ void add(float v, int ev) {  // += v 2^ev, 0 <= |v| < 2^24
+    if (v == 0.f) return;
+    if (ev > e) {  // rescale the total to the new exponent (parts far below it vanish)
+      const int d = e - ev;
+      const float f = d >= -126 ? f32_pow2(d) : 0.f;
+      h *= f;
+      l *= f;
+      e = ev;
+    } else {
+      const int d = ev - e;
+      v = d >= -126 ? v * f32_pow2(d) : 0.f;
+    }
+    const float s = __fadd_rn(h, v);
+    const float bb = __fsub_rn(s, h);
+    l = __fadd_rn(l, __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(v, bb)));
+    h = s;
+  }
+  __device__ __forceinline__ double value() const {
+    return e == -1000 ? 0.0 : ((double)h + (double)l) * f64_pow2(max(min(e, 1022), -1022));
+  }
+};
+
 // Division by a runtime constant d >= 1 for 0 <= x < 2^31 without a divide instruction:
 // q = floor(x * m / 2^(31+s)) with s = ceil(log2 d) and m = ceil(2^(31+s) / d) < 2^32, which is
 // exact for every x < 2^31 (round-up multiplier method for 31-bit dividends).
@@ -205,6 +246,8 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
   // inputs as far as the compiler knows, so a load-then-store loop would wait a full memory round
   // trip per element.
   constexpr int UB = 8;
+  constexpr bool DOT32 = DOT && sizeof(T) == 4;  // p.q partial in scaled FP32 (see f32_exp)
+  float axm = 0.f;                                 // largest |p| this thread stages
   if (vec16) {
     // 16-byte vectors: a line of L x P values starts on a 16-byte boundary and holds whole vectors
     const int LP4 = (L * P) >> 2;
@@ -249,6 +292,7 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
             if (t >= 1 && t <= nlin) *reinterpret_cast<float4*>(pnew + gg[u]) = v;
           }
           *reinterpret_cast<float4*>(xs + 4 * e4) = v;
+          if constexpr (DOT32) axm = fmaxf(axm, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
         }
       }
     }
@@ -287,12 +331,26 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
             if (t >= 1 && t <= nlin) pnew[gg[u]] = v;
           }
           xs[e] = v;
+          if constexpr (DOT32) axm = fmaxf(axm, fabsf((float)v));
         }
       }
     }
   }
+  __shared__ unsigned red_ax[32];
+  if constexpr (DOT32) {
+    const unsigned w = __reduce_max_sync(0xffffffffu, __float_as_uint(axm));  // order-preserving for x >= 0
+    if ((threadIdx.x & 31) == 0) red_ax[threadIdx.x >> 5] = w;
+  }
   __syncthreads();
   SG_MARK(1);
+  int dex = 0;  // binary exponent of the block's largest |p|
+  if constexpr (DOT32) {
+    unsigned w = 0u;
+    for (int i = 0; i < (nt >> 5); ++i) w = max(w, red_ax[i]);
+    dex = f32_exp(__uint_as_float(w));
+  }
+  const float dsc = DOT32 ? f32_pow2(-dex) : 1.f;
+  float dsf = 0.f;
   if constexpr (C::fixed) {
     // phase 2 (compile-time table): one work item per (edge, output-mode group); the group is
     // uniform across a warp (32 consecutive edges), so the unrolled group code never diverges
@@ -499,12 +557,14 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, int nb, int R, int TL, 
         }
         out = (TO)acc;
         if (add) out += ad[u];
-        if (DOT) dsum += (double)xs[((size_t)(t + 1) * L + i) * P + k] * (double)out;
+        if constexpr (DOT32) dsf = fmaf(xs[((size_t)(t + 1) * L + i) * P + k] * dsc, (float)out * dsc, dsf);
+        else if (DOT) dsum += (double)xs[((size_t)(t + 1) * L + i) * P + k] * (double)out;
       }
       y[g] = out;
     }
   }
   SG_MARK(4);
+  if constexpr (DOT32) dsum = (double)dsf * f64_pow2(2 * dex);
   if (DOT) {
     __shared__ double red[32];
     for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
@@ -1198,12 +1258,6 @@ __device__ __forceinline__ void tile_product(T (&acc)[2][4], const T* __restrict
     for (int k = 0; k < 4; ++k) acc[i][k] += acc2[i][k];
 }
 
-// FP32 partial sums with a range guard: when every operand lies in [2^-60, 2^60] (or is zero),
-// products neither overflow nor lose their contribution to underflow, so a line's partial is summed
-// in FP32 and added to the FP64 total once; otherwise the line is summed in FP64.
-__device__ __forceinline__ bool f32_range_ok(float amax, float amin_nz) {
-  return amax <= 0x1p60f && amin_nz >= 0x1p-60f;
-}
 
 // rows per thread and line of the row-ordered line I/O: four arrays of them stay in registers
 template <typename T>
@@ -1246,6 +1300,7 @@ __global__ void __launch_bounds__(LW_MAXT, lw_minb<T>()) k_line_w(int L, int LSP
   const int rstep = RPI * P, sstep = RPI * GS;
   const bool act = init ? true : (ctl.active[b] != 0);
   double s_rz = 0.0, s_rr = 0.0;
+  XAcc x_rz, x_rr;  // FP32 per-thread totals over the launch's steps
   if (act) {
     const int sub = b / R;
     const T* S = Spad + (long long)sub * pat_stride;
@@ -1309,7 +1364,7 @@ __global__ void __launch_bounds__(LW_MAXT, lw_minb<T>()) k_line_w(int L, int LSP
         const T* cb = Bs + ((j + 2) % 3) * 2 * L;  // coupling row j - 1
         const int o0 = j * LP + io_a * P;
         const int s0 = io_a * GS + io_m;
-        T amax = T(0), amin = T(1);
+        T amax = T(0);
         T rr = T(0);
 #pragma unroll
         for (int kk = 0; kk < NPF; ++kk) {
@@ -1322,10 +1377,9 @@ __global__ void __launch_bounds__(LW_MAXT, lw_minb<T>()) k_line_w(int L, int LSP
               rb[o] = rv;
               xb[o] = pr_x[kk] + alpha * pr_p[kk];
             }
-            const T av = abs(rv);
-            amax = max(amax, av);
-            if (av != T(0)) amin = min(amin, av);
-            rr = fma(rv, rv, rr);
+            amax = max(amax, abs(rv));
+            if constexpr (sizeof(T) == 8) rr = fma(rv, rv, rr);
+            pr_r[kk] = rv;  // for the scaled FP32 partial below
             T wv = rv;
             if (j > 0) {
               const T yp = Yp[si];
@@ -1336,15 +1390,19 @@ __global__ void __launch_bounds__(LW_MAXT, lw_minb<T>()) k_line_w(int L, int LSP
             Ws[si] = wv;
           }
         }
-        if (sizeof(T) == 8 || f32_range_ok((float)amax, (float)amin)) {
+        if constexpr (sizeof(T) == 8) {
           s_rr += (double)rr;
         } else {
+          const int e = f32_exp((float)amax);
+          const float sc = f32_pow2(-e);
+          float rs = 0.f;
 #pragma unroll
           for (int kk = 0; kk < NPF; ++kk)
             if (io_a + kk * RPI < L) {
-              const double v = (double)rb[o0 + kk * rstep];
-              s_rr += v * v;
+              const float v = (float)pr_r[kk] * sc;
+              rs = fmaf(v, v, rs);
             }
+          x_rr.add(rs, 2 * e);
         }
       }
       // line j + 1 (used by this sweep's next step) and coupling row j + 1 (used by the input
@@ -1364,30 +1422,29 @@ __global__ void __launch_bounds__(LW_MAXT, lw_minb<T>()) k_line_w(int L, int LSP
         const T* Sj = Sb + (j & 1) * LLS + a0;
         const T* Wc = Ws + m0;
         tile_product(acc, Sj, Wc, L, LSP, GS);
-        T rz = T(0), amax = T(0), amin = T(1);
+        T rz = T(0), awm = T(0), aym = T(0), wt[2][4];
 #pragma unroll
         for (int i = 0; i < 2; ++i)
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const int a = a0 + i;
             Yp[a * GS + m0 + k] = acc[i][k];
-            if (a < L) {
-              const T wv = Ws[a * GS + m0 + k];  // zero for modes beyond the block's
-              rz = fma(wv, acc[i][k], rz);
-              const T aw = abs(wv), ay = abs(acc[i][k]);
-              amax = max(amax, max(aw, ay));
-              if (aw != T(0)) amin = min(amin, aw);
-              if (ay != T(0)) amin = min(amin, ay);
-            }
+            wt[i][k] = a < L ? Ws[a * GS + m0 + k] : T(0);  // zero for modes beyond the block's
+            if constexpr (sizeof(T) == 8) rz = fma(wt[i][k], acc[i][k], rz);
+            awm = max(awm, abs(wt[i][k]));
+            aym = max(aym, a < L ? abs(acc[i][k]) : T(0));
           }
-        if (sizeof(T) == 8 || f32_range_ok((float)amax, (float)amin)) {
+        if constexpr (sizeof(T) == 8) {
           s_rz += (double)rz;
         } else {
+          const int ew = f32_exp((float)awm), ey = f32_exp((float)aym);
+          const float sw = f32_pow2(-ew), sy = f32_pow2(-ey);
+          float rs = 0.f;
 #pragma unroll
           for (int i = 0; i < 2; ++i)
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-              if (a0 + i < L) s_rz += (double)Ws[(a0 + i) * GS + m0 + k] * (double)acc[i][k];
+            for (int k = 0; k < 4; ++k) rs = fmaf((float)wt[i][k] * sw, (float)acc[i][k] * sy, rs);
+          x_rz.add(rs, ew + ey);
         }
       }
       __syncthreads();
@@ -1458,7 +1515,358 @@ __global__ void __launch_bounds__(LW_MAXT, lw_minb<T>()) k_line_w(int L, int LSP
         if (io_a + kk * RPI < L) zb[o0 + kk * rstep] = Yp[s0 + kk * sstep];
     }
   }
+  if constexpr (sizeof(T) == 4) {
+    s_rz += x_rz.value();
+    s_rr += x_rr.value();
+  }
   line_control(s_rz, s_rr, b, grp, NG, NT, nb, ctl, init, tol2, bb_min, max_it, cond_handle, use_handle);
+}
+
+// ------------------------------------------------------------------------------------------
+// Line sweeps of the mean-operator preconditioner with the per-line products on the tensor cores
+// (FP32 subdomain CG; subdomains of 41 .. 65 nodes per side; at most 32 modes per block).  The same
+// sweeps, fused CG update and control as k_line_w; the product y = S_j^{-1} w of each line step is one
+// tcgen05.mma chain (M = 128, N = 2 NB, K = 4 x 16):
+//   A = S_j^{-1} in BF16, rows a < L and columns c < 64, K-major with the 128-byte swizzle (image of
+//       the symmetrised FP64 factor, fetched by TMA into one of two stages);
+//   B = [w_hi; w_lo]: w split into two BF16 terms (about 17 significant bits), written by the input
+//       phase in the same swizzled layout (modes beyond the block's and rows c >= L stay zero);
+//   D = 128 TMEM lanes x 2 NB FP32 columns; the epilogue adds the two column blocks.
+// For L = 65 the column c = 64 enters as an FP32 rank-one update with the BF16-rounded values of the
+// same symmetric image (col).  Rounding S_j^{-1} to BF16 is a fixed, symmetric perturbation of the
+// preconditioner; w keeps about 17 bits per application (the precision design of k_pre_mma).
+// Per step: input phase (all threads) -> proxy fence, barrier -> thread 0 waits for the stage's TMA,
+// issues the four MMAs and commits -> warps 0-3 (row a = 32 warp + lane) wait for the commit, read
+// the accumulator and finish the step -> barrier.  Thread 0 issues the next step's TMA at the start of
+// each step.  Every wait is bounded (1 s); on a timeout the block records 20 + where in
+// ctl.breakdown, stops its sweep, waits (bounded) for its copies in flight and frees its TMEM.
+// Shared memory (1024-aligned): A [2][128][64] BF16, B [2 NB][64] BF16, col [2][68], Ws, Ys, Yp
+// [L][WS] FP32 (WS = odd row stride >= G), the subdomain's coupling rows Bd, Bu [L][L] FP32.
+// ------------------------------------------------------------------------------------------
+constexpr int LTC_ABYTES = 128 * 128;  // one A stage: 128 rows x 64 BF16
+constexpr int LTC_COLN = 68;           // FP32 values of one column stage (65 used; 272 bytes)
+__host__ __device__ constexpr int ltc_ws(int G) { return G | 1; }
+__host__ __device__ constexpr size_t ltc_smem(int L, int G, int NB) {
+  return 1024 + 2 * (size_t)LTC_ABYTES + (size_t)2 * NB * 128 + 2 * LTC_COLN * 4 + 3 * (size_t)L * ltc_ws(G) * 4 +
+         2 * (size_t)L * L * 4;
+}
+
+template <int NB>
+__global__ void __maxnreg__(168) k_line_tc(const __grid_constant__ CUtensorMap tmS, int L, int nl, int P,
+                                                    int R, int NG, int NT, int G, long long img_row0,
+                                                    const float* __restrict__ col, const float* __restrict__ Bd,
+                                                    const float* __restrict__ Bu, int nb, float* __restrict__ x,
+                                                    float* __restrict__ r, float* __restrict__ z, float* pbuf0,
+                                                    float* pbuf1, const float* __restrict__ q, CgCtl ctl, int init,
+                                                    double tol2, double bb_min, int max_it,
+                                                    cudaGraphConditionalHandle cond_handle, int use_handle) {
+  count_launch();
+  constexpr int NPF = 8;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bars[3];  // full[0], full[1], mma done
+  __shared__ unsigned tmem_slot;
+  __shared__ float alpha_s;
+  __shared__ int s_abort;
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  unsigned char* As = sm;                                        // [2][128 x 128 B]
+  unsigned char* Bt = sm + 2 * LTC_ABYTES;                       // [2 NB x 128 B]
+  float* cols = reinterpret_cast<float*>(Bt + 2 * NB * 128);     // [2][LTC_COLN]
+  const int WS = ltc_ws(G);
+  float* Ws = cols + 2 * LTC_COLN;                               // [L][WS]
+  float* Ys = Ws + L * WS;
+  float* Yp = Ys + L * WS;
+  float* Bds = Yp + L * WS;  // [L][L] coupling rows of the subdomain
+  float* Bus = Bds + L * L;
+  const int b = blockIdx.x / NG, grp = blockIdx.x % NG;
+  const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  const int kb = grp * G;
+  const int gl = min(G, P - kb);
+  const int RPI = nthr / gl;
+  const int io_m = tid % gl, io_a = tid / gl;
+  const bool io_on = io_a < RPI;
+  const int LP = L * P;
+  const int rstep = RPI * P, sstep = RPI * WS;
+  const bool act = init ? true : (ctl.active[b] != 0);
+  double s_rz = 0.0, s_rr = 0.0;
+  XAcc x_rz, x_rr;  // FP32 per-thread totals over the launch's steps
+  if (act) {
+    const int sub = b / R;
+    const long long base = (long long)b * nl * P + kb + io_m;
+    float* rb = r + base;
+    float* xb = x + base;
+    float* zb = z + base;
+    const float* qb = q + base;
+    const float* bd = Bd + (long long)sub * L * L;
+    const float* bu = Bu + (long long)sub * L * L;
+    const long long irow = img_row0 + (long long)sub * L * L;    // image row of (line 0, a = 0)
+    const float* colp = col + (long long)sub * L * LTC_COLN;     // [line][LTC_COLN]
+    const unsigned full0 = smem_u32(&bars[0]), mdone = smem_u32(&bars[2]);
+    const bool wide_col = L == 65;
+    const unsigned tx = (unsigned)L * 128 + (wide_col ? LTC_COLN * 4 : 0);
+    auto issue = [&](int t) {  // TMA of step t's line into stage t & 1 (thread 0)
+      const int line = t < L ? t : 2 * L - 2 - t;
+      const int s = t & 1;
+      mbar_expect_tx(full0 + 8 * s, tx);
+      tma_load_2d(smem_u32(As + s * LTC_ABYTES), &tmS, full0 + 8 * s, 0, (int)(irow + (long long)line * L));
+      if (wide_col) bulk_load(smem_u32(cols + s * LTC_COLN), colp + (long long)line * LTC_COLN, LTC_COLN * 4,
+                              full0 + 8 * s);
+    };
+    // set-up: barriers, TMEM accumulator, zero B tile
+    if (tid == 0) {
+      mbar_init(full0, 1);
+      mbar_init(full0 + 8, 1);
+      mbar_init(mdone, 1);
+      s_abort = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                   "r"(2 * NB)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int e = tid; e < NB * 2 * 128 / 16; e += nthr) reinterpret_cast<uint4*>(Bt)[e] = make_uint4(0u, 0u, 0u, 0u);
+    for (int e = tid; e < L * L; e += nthr) {
+      Bds[e] = bd[e];
+      Bus[e] = bu[e];
+    }
+    const float* pb = nullptr;
+    if (!init) {
+      pb = ((*ctl.parity) ? pbuf0 : pbuf1) + base;  // p_new written by the apply kernel
+      if (tid < 32) {
+        double pq = 0.0;
+        for (int t = tid; t < NT; t += 32) pq += ctl.part_pq[(long long)b * NT + t];
+        for (int o = 16; o > 0; o >>= 1) pq += __shfl_down_sync(0xffffffffu, pq, o);
+        if (tid == 0) {
+          const double al = (pq > 0.0 && isfinite(pq)) ? ctl.rz[b] / pq : 0.0;
+          alpha_s = isfinite(al) ? (float)al : 0.f;
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = tmem_slot;
+    if (tid == 0) issue(0);
+    const float alpha = init ? 0.f : alpha_s;
+    // prefetched registers: forward r, q, p, x of line j; backward y_j (in pr_r)
+    float pr_r[NPF], pr_q[NPF], pr_p[NPF], pr_x[NPF];
+    auto fetch = [&](int j) {
+      if (!io_on) return;
+      const int o0 = j * LP + io_a * P;
+#pragma unroll
+      for (int kk = 0; kk < NPF; ++kk) {
+        const int a = io_a + kk * RPI;
+        if (a < L) {
+          const int o = o0 + kk * rstep;
+          pr_r[kk] = rb[o];
+          if (!init) { pr_q[kk] = qb[o]; pr_p[kk] = pb[o]; pr_x[kk] = xb[o]; }
+        }
+      }
+    };
+    auto fetch_y = [&](int j) {
+      if (!io_on) return;
+      const int o0 = j * LP + io_a * P;
+#pragma unroll
+      for (int kk = 0; kk < NPF; ++kk) {
+        const int a = io_a + kk * RPI;
+        if (a < L) pr_r[kk] = zb[o0 + kk * rstep];
+      }
+    };
+    // B tile entry (row n = mode, column c = a) of both terms
+    auto put_b = [&](int a, int m, float w) {
+      if (a < 64) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(w - __bfloat162float(hi));
+        *reinterpret_cast<__nv_bfloat16*>(Bt + sw128_offset(m, a)) = hi;
+        *reinterpret_cast<__nv_bfloat16*>(Bt + sw128_offset(NB + m, a)) = lo;
+      }
+    };
+    fetch(0);
+    __syncthreads();
+    const int T_END = 2 * L - 1;  // steps: forward t = j = 0 .. L-1, backward t = L .. 2L-2 (j = 2L-2-t)
+    int t = 0;
+    for (; t < T_END; ++t) {
+      const bool fwd = t < L;
+      const int j = fwd ? t : 2 * L - 2 - t;
+      const int s = t & 1;
+      if (tid == 0 && t + 1 < T_END) issue(t + 1);
+      // ---- input phase: w = r_j - B_{j-1}^T y_{j-1} (forward), w = B_j x_{j+1} (backward) ----
+      if (io_on) {
+        const int o0 = j * LP + io_a * P;
+        const int s0 = io_a * WS + io_m;
+        if (fwd) {
+          float amax = 0.f;
+#pragma unroll
+          for (int kk = 0; kk < NPF; ++kk) {
+            const int a = io_a + kk * RPI;
+            if (a < L) {
+              const int o = o0 + kk * rstep, si = s0 + kk * sstep;
+              float rv = pr_r[kk];
+              if (!init) {
+                rv -= alpha * pr_q[kk];
+                rb[o] = rv;
+                xb[o] = pr_x[kk] + alpha * pr_p[kk];
+              }
+              amax = fmaxf(amax, fabsf(rv));
+              pr_r[kk] = rv;  // for the scaled partial below
+              float wv = rv;
+              if (j > 0) {
+                const float yp = Yp[si];
+                wv -= Bds[(j - 1) * L + a] * yp;
+                if (a > 0) wv -= Bus[(j - 1) * L + a - 1] * Yp[si - WS];
+                zb[o - LP] = yp;  // y_{j-1} parked in z
+              }
+              Ws[si] = wv;
+              put_b(a, io_m, wv);
+            }
+          }
+          const int e = f32_exp(amax);
+          const float sc = f32_pow2(-e);
+          float rs = 0.f;
+#pragma unroll
+          for (int kk = 0; kk < NPF; ++kk)
+            if (io_a + kk * RPI < L) {
+              const float v = pr_r[kk] * sc;
+              rs = fmaf(v, v, rs);
+            }
+          x_rr.add(rs, 2 * e);
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < NPF; ++kk) {
+            const int a = io_a + kk * RPI;
+            if (a < L) {
+              const int o = o0 + kk * rstep, si = s0 + kk * sstep;
+              const float xn = Yp[si];
+              float tv = Bds[j * L + a] * xn;
+              if (a + 1 < L) tv += Bus[j * L + a] * Yp[si + WS];
+              zb[o + LP] = xn;  // x_{j+1} final
+              Ws[si] = tv;
+              Ys[si] = pr_r[kk];  // y_j
+              put_b(a, io_m, tv);
+            }
+          }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B tile -> tensor-core reads
+      if (fwd) {
+        if (j + 1 < L) fetch(j + 1);
+        else fetch_y(L - 2);  // first backward step (y_{L-2} was parked by this thread above)
+      } else if (j >= 1) {
+        fetch_y(j - 1);
+      }
+      __syncthreads();
+      // ---- product on the tensor cores ----
+      if (tid == 0) {
+        if (!mbar_wait(full0 + 8 * s, (unsigned)((t >> 1) & 1))) {
+          atomicExch(ctl.breakdown, 20);
+          s_abort = 1;
+        } else {
+          tc_fence_after();
+          const unsigned a0 = smem_u32(As + s * LTC_ABYTES), b0 = smem_u32(Bt);
+          constexpr unsigned idesc = idesc_bf16(128, 2 * NB);
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            umma_bf16(tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc, k > 0 ? 1u : 0u);
+          umma_commit(mdone);
+        }
+      }
+      // ---- epilogue: row a of y (warps 0-3 own TMEM lanes 32 warp ..) ----
+      if (warp < 4) {
+        const int a = 32 * warp + lane;
+        bool ok = mbar_wait(mdone, (unsigned)(t & 1));
+        if (ok && wide_col) ok = mbar_wait(full0 + 8 * s, (unsigned)((t >> 1) & 1));  // column stage landed
+        if (!ok) {
+          atomicExch(ctl.breakdown, 21);
+          s_abort = 1;
+        }
+        __syncwarp();
+        tc_fence_after();
+        const unsigned trow = tmem + ((unsigned)(warp * 32) << 16);
+        const float ca = (ok && wide_col && a < L) ? cols[s * LTC_COLN + a] : 0.f;
+        const float* w64 = Ws + 64 * WS;  // row c = 64 of w (read only when L = 65)
+        float* yrow = Yp + min(a, L - 1) * WS;
+        const float* wrow = Ws + min(a, L - 1) * WS;
+        const float* ysrc = Ys + min(a, L - 1) * WS;
+        float awm = 0.f, aym = 0.f;
+#pragma unroll
+        for (int c0 = 0; c0 < NB; c0 += 16) {
+          float hi[16], lo[16];
+          tmem_ld<16>(trow + c0, hi);        // warp-collective: every lane of warps 0-3
+          tmem_ld<16>(trow + NB + c0, lo);
+          if (ok && a < L) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int m = c0 + i;
+              if (m < gl) {
+                float y = hi[i] + lo[i];
+                if (wide_col) y = fmaf(ca, w64[m], y);
+                if (fwd) {
+                  yrow[m] = y;
+                  awm = fmaxf(awm, fabsf(wrow[m]));
+                  aym = fmaxf(aym, fabsf(y));
+                } else {
+                  yrow[m] = ysrc[m] - y;
+                }
+              }
+            }
+          }
+        }
+        if (fwd && ok && a < L) {  // r.z partial of row a: sum_m w y, scaled
+          const int ew = f32_exp(awm), ey = f32_exp(aym);
+          const float sw = f32_pow2(-ew), sy = f32_pow2(-ey);
+          float rs = 0.f;
+          for (int m = 0; m < gl; ++m) rs = fmaf(wrow[m] * sw, yrow[m] * sy, rs);
+          x_rz.add(rs, ew + ey);
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
+      if (s_abort) break;
+    }
+    if (!s_abort) {
+      // x_0
+      if (io_on) {
+        const int s0 = io_a * WS + io_m;
+        const int o0 = io_a * P;
+#pragma unroll
+        for (int kk = 0; kk < NPF; ++kk)
+          if (io_a + kk * RPI < L) zb[o0 + kk * rstep] = Yp[s0 + kk * sstep];
+      }
+    } else if (tid == 0) {
+      // timed out: let the copy and the products this block issued finish (bounded) before TMEM is freed
+      if (t + 1 < T_END) (void)mbar_wait(full0 + 8 * ((t + 1) & 1), (unsigned)(((t + 1) >> 1) & 1));
+      (void)mbar_wait(mdone, (unsigned)(t & 1));
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+      tc_fence_after();
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * NB) : "memory");
+    }
+  }
+  s_rz += x_rz.value();
+  s_rr += x_rr.value();
+  line_control(s_rz, s_rr, b, grp, NG, NT, nb, ctl, init, tol2, bb_min, max_it, cond_handle, use_handle);
+}
+
+// BF16 image of the line factors for k_line_tc: img[m][a][c] = S_m(a, c) for c < min(L, 64), zero
+// for L <= c < 64, with S_m = (S_m^{-1} + S_m^{-T}) / 2 of the FP64 factor (an exactly symmetric
+// BF16 matrix); col[m][a] = the BF16-rounded S_m(a, 64) as FP32 (L = 65), m = (subdomain, line).
+__global__ void k_line_img(long long nmat, int L, const double* __restrict__ Sinv, __nv_bfloat16* __restrict__ img,
+                           float* __restrict__ col) {
+  count_launch();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nmat * L * 64) return;
+  const long long mat = i / ((long long)L * 64);
+  const int rem = (int)(i - mat * L * 64), a = rem >> 6, c = rem & 63;
+  const double* S = Sinv + mat * L * L;
+  const double v = c < L ? 0.5 * (S[(long long)a * L + c] + S[(long long)c * L + a]) : 0.0;
+  img[i] = __float2bfloat16_rn((float)v);
+  if (L == 65 && c == 0) {
+    const double u = 0.5 * (S[(long long)a * L + 64] + S[64LL * L + a]);
+    col[mat * LTC_COLN + a] = __bfloat162float(__float2bfloat16_rn((float)u));
+  }
 }
 
 // Line factorisation, FP64: one block per (subdomain, pattern).  D (within-line tridiagonal)

@@ -5,7 +5,7 @@ it was written (a race) or read uninitialised memory.
 
 The workload is the 1024^2 problem's subdomain shape and PCE (65 x 65 nodes, M = 5, p = 2) on a
 512^2 grid with 8 x 8 subdomains: 64 subdomain problems, so the register-tiled line sweep splits the
-21 modes of each problem over two blocks."""
+21 modes of each problem over two blocks (the register-tiled sweep, or its tensor-core form)."""
 import pytest
 
 import sg_workloads as w
@@ -29,7 +29,7 @@ def test_two_solvers_stay_bitwise_identical(lib):
     from paper_2512_23027_gb300.binding import SG_MIXED, plan_query
     prob = w.config("ricker1024q")
     plan = plan_query(prob, SG_MIXED)
-    assert plan["line_kind"][0] == 3 and plan["line_groups"][0] == 2, plan
+    assert plan["line_kind"][1] in (3, 4) and plan["line_groups"][1] == 2, plan
     a = lib(prob, precision=SG_MIXED)
     b = lib(prob, precision=SG_MIXED)
     n = 3 * a.n_free * a.P + 1

@@ -350,17 +350,18 @@ def test_widest_batch_subdomains_converge(lib, which):
     assert err <= 1e2 * prob.tol, err
 
 
-@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("precision", [0, 1, 3], ids=["fp64", "mixed", "bf16"])
 def test_wide_line_kernel_matches_block_kernel(lib, precision):
-    """Subdomains of 41 x 41 nodes: the register-tiled line sweep (k_line_w, both precisions) and the
-    block kernel with the factor staged line by line (SG_LINE_OLD) give the same fields: up to the
-    summation order of the factor rows in FP64 (PCG tolerance 1e-13), within the solver tolerance in
-    mixed precision; the FP64 fields also match the oracle."""
+    """Subdomains of 41 x 41 nodes: the register-tiled line sweep (k_line_w, FP64 and FP32), its form
+    with the per-line products on the tensor cores (k_line_tc, SG_BF16) and the block kernel with the
+    factor staged line by line (SG_LINE_OLD) give the same fields: up to the summation order of the
+    factor rows in FP64 (PCG tolerance 1e-13), within the solver tolerance with FP32 solves; the FP64
+    fields also match the oracle."""
     prob = w.config("small").replace(name="w41", N=80, s=2, dt=w.cfl_dt(80), tol=1e-13 if precision == 0 else 1e-8)
     ua, ia, ra = _run_env(lib, prob, precision, 3, {})
-    ub, ib, rb = _run_env(lib, prob, precision, 3, {"SG_LINE_OLD": "1"})
+    ub, ib, rb = _run_env(lib, prob, 1 if precision == 3 else precision, 3, {"SG_LINE_OLD": "1"})
     err = rel(ua, ub)
-    print(f"L = 41, {'fp64' if precision == 0 else 'mixed'}: register-tiled vs block line kernel rel diff {err:.3e}, "
+    print(f"L = 41, {['fp64', 'mixed', '', 'bf16'][precision]}: wide vs block line kernel rel diff {err:.3e}, "
           f"iters {ia} vs {ib}")
     assert err <= (1e-12 if precision == 0 else 1e2 * prob.tol), err
     assert all(r <= prob.tol for r in ra + rb)

@@ -22,7 +22,7 @@ import sg_workloads as w
 pytestmark = pytest.mark.gpu
 
 GOLD_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_samples.json")
-SG_FP64, SG_MIXED = 0, 1
+SG_FP64, SG_MIXED, SG_BF16 = 0, 1, 3
 
 
 @pytest.fixture(scope="module")
@@ -71,16 +71,21 @@ def compare(U, rec, ref):
 # small-problem tests: both solvers stop at ||r|| <= tol ||G||, so 10 tol for the field (the error of
 # the whole field), and a mode holds at most all of it: 10 tol ||U|| / ||U_k|| <= 1e4 tol per mode
 # with the 1e-3 floor.
-BARS = {SG_FP64: {"glob": 1e-10, "mode": 1e-9}, SG_MIXED: {"glob": 1e-7, "mode": 1e-4}}
+BARS = {SG_FP64: {"glob": 1e-10, "mode": 1e-9}, SG_MIXED: {"glob": 1e-7, "mode": 1e-4},
+        SG_BF16: {"glob": 1e-7, "mode": 1e-4}}
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("precision", [SG_FP64, SG_MIXED], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("precision", [SG_FP64, SG_MIXED, SG_BF16], ids=["fp64", "mixed", "bf16"])
 @pytest.mark.parametrize("case", ["l65_m5p2", "l65_m4p3", "b240"])
 def test_wide_subdomains_match_oracle_samples(lib, case, precision):
+    """SG_BF16 runs the line sweeps with their per-line products on the tensor cores (65 x 65-node
+    subdomains; the 121 x 121-node case has no BF16 preconditioner and is skipped)."""
     g = gold()
     if case not in g:
         pytest.skip(f"{case} not in the stored oracle samples")
+    if precision == SG_BF16 and case == "b240":
+        pytest.skip("no BF16 tensor-core preconditioner for 121 x 121-node subdomains")
     rec = g[case]
     prob = problem(case, rec)
     ref = rec["tight"] if precision == SG_FP64 else rec["workload"]
@@ -91,7 +96,7 @@ def test_wide_subdomains_match_oracle_samples(lib, case, precision):
     its, rr = s.iters()
     s.close()
     glob, per_mode, norm_rel, top = compare(U, rec, ref)
-    print(f"{case} {'fp64' if precision == SG_FP64 else 'mixed'}: sampled rel err {glob:.3e}, largest entries "
+    print(f"{case} {({SG_FP64: 'fp64', SG_MIXED: 'mixed', SG_BF16: 'bf16'})[precision]}: sampled rel err {glob:.3e}, largest entries "
           f"{top:.3e}, worst mode {per_mode.max():.3e} (mode {int(per_mode.argmax())}), mode-norm rel diff "
           f"{norm_rel.max():.3e}, iters {its} vs {ref['iters']}, {plan_line['P']} modes")
     bar = BARS[precision]

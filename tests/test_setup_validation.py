@@ -107,11 +107,24 @@ def test_caller_kl_arrays_are_checked(B):
 
 
 def test_bf16_mode_needs_the_tensor_core_preconditioner(B):
-    """SG_BF16 requires the BF16 tensor-core mean preconditioner, which covers subdomains of at most
-    40 x 40 nodes and P <= 32: wider subdomains get SG_ENOTSUP (before any CUDA call)."""
-    prob = w.config("small").replace(N=80, s=2)   # 41 x 41-node subdomains
+    """SG_BF16 requires a BF16 tensor-core mean preconditioner: the dense inverse (subdomains of at most
+    40 x 40 nodes, P <= 32) or the line sweeps with per-line tensor-core products (41 .. 65 nodes per
+    side).  Wider subdomains get SG_ENOTSUP (before any CUDA call)."""
+    prob = w.config("small").replace(N=160, s=2)   # 81 x 81-node subdomains
     rc, h, err = setup_rc(B, prob, precision=3)
     assert rc == SG_ENOTSUP and h is None and "BF16" in err
+
+
+def test_bf16_line_products_in_the_launch_plan(B):
+    """41 x 41- and 65 x 65-node subdomains: SG_BF16 plans the line sweeps with tensor-core products
+    (line kind 4, no dense inverse), SG_MIXED and SG_FP32 the register-tiled FP32 sweeps (kind 3)."""
+    for N, s in ((80, 2), (128, 2)):
+        prob = w.config("small").replace(N=N, s=s)
+        plans = {p: B.plan_query(prob, p) for p in (1, 2, 3)}
+        assert plans[3]["line_kind"][1] == 4 and plans[3]["mma"] == 0, plans[3]
+        assert plans[1]["line_kind"][1] == 3 and plans[2]["line_kind"][1] == 3
+        assert plans[3]["line_block"][1][0] % 32 == 0 and plans[3]["line_block"][1][0] >= 128
+        assert all(pl["fits"] == 1 for pl in plans.values())
 
 
 def test_precision_modes_in_the_launch_plan(B):
