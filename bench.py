@@ -39,22 +39,27 @@ sys.path.insert(0, ROOT)
 METRIC = "SG-DD time-steps/sec & PCG iters vs plain FP64 DD-PCG at rel resid 1e-8"
 
 # DRAM traffic (read + write bytes per launch) of the dominant kernel from one ncu capture, keyed by
-# the sha256 prefix of that kernel's source region (KERNEL_REGION) it was taken on; any other source
-# reports null.  The value
-# is k_line_w<float> at the 1024^2 workload from step 202 (every subdomain active), an iterate launch:
-# 1,014,472,192 B read + 329,161,728 B written (profiles/k_line_w_ricker1024_dram.md).
-KERNEL_TRAFFIC = {"c1b0a1ddcf2eb977": 1343633920}
-# source region of the dominant kernel (k_line_w and its helpers) that the traffic figure is keyed to
-KERNEL_REGION = ("// Mean-operator line solve fused with the inner CG update, register-tiled form",
-                 "// Line factorisation, FP64")
+# the sha256 prefix of that kernel's source regions (KERNEL_REGIONS) it was taken on; any other source
+# reports null.  The value is k_line_w<float> at the 1024^2 workload from step 202 (every subdomain
+# active), the mean of three iterate launches: 1,018,883,840 B read + 330,724,267 B written
+# (profiles/k_line_w_ricker1024_dram.md).
+KERNEL_TRAFFIC = {"74f2ba0e6b1026f5": 1349608107}
+# source regions of the dominant kernel that the traffic figure is keyed to: k_line_w and the FP32
+# partial-sum helpers it uses
+KERNEL_REGIONS = (("// Mean-operator line solve fused with the inner CG update, register-tiled form",
+                   "// Line sweeps of the mean-operator preconditioner with the per-line products"),
+                  ("// FP32 partial sums at any magnitude", "// Division by a runtime constant"))
 
 
 def kernel_source_sha():
-    """sha256 prefix of the dominant kernel's source region (the traffic figure is valid for it)."""
+    """sha256 prefix of the dominant kernel's source regions (the traffic figure is valid for them)."""
     import hashlib
     src = open(os.path.join(ROOT, "paper_2512_23027_gb300", "csrc", "sg_kernels.cuh")).read()
-    a, b = src.index(KERNEL_REGION[0]), src.index(KERNEL_REGION[1])
-    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for r0, r1 in KERNEL_REGIONS:
+        a = src.index(r0)
+        h.update(src[a:src.index(r1, a)].encode())
+    return h.hexdigest()[:16]
 L2_FLUSH_BYTES = 256 << 20
 
 
