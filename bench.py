@@ -441,7 +441,7 @@ def main():
     import torch
     import sg_workloads as w
     from paper_2512_23027_gb300 import Solver
-    from paper_2512_23027_gb300.binding import SG_FP64, SG_MIXED
+    from paper_2512_23027_gb300.binding import SG_FP64, SG_MIXED, SG_WARM_LEARNED, SG_WARM_PREV
 
     torch.cuda.set_device(local)
     dist = None
@@ -471,15 +471,16 @@ def main():
 
     eager = args.enqueue == "eager"
 
-    def make(p, precision):
-        sv = Solver(p, precision=precision, stream=stream)
+    def make(p, precision, warm=SG_WARM_PREV):
+        sv = Solver(p, precision=precision, stream=stream, warm=warm)
         if eager:
             sv.set_eager(True)
         return sv
 
-    # ---- optimised solver (mixed precision, graph per step): fast-forward, warm-up, timed steps ----
+    # ---- optimised solver (mixed precision, learned warm start, graph per step): fast-forward,
+    # warm-up, timed steps ----
     t_setup = time.perf_counter()
-    s = make(prob, SG_MIXED)
+    s = make(prob, SG_MIXED, SG_WARM_LEARNED)
     t_setup = time.perf_counter() - t_setup
     t_fwd = time.perf_counter()
     if F:
@@ -553,7 +554,7 @@ def main():
 
     # ---- end to end through the C ABI with pinned host buffers, from the same state ----
     pe = prob.replace(source=w.Source())
-    se = make(pe, SG_MIXED)
+    se = make(pe, SG_MIXED, SG_WARM_LEARNED)
     se.set_state(state0)
     nf = se.n_free
     fw = torch.from_numpy(ricker_nodal_load(prob, F, W, nf)).pin_memory()
@@ -590,6 +591,8 @@ def main():
         return 0
     cpu = finish_cpu_baseline(cpu_proc, args.config, args.cpu_steps, timeout=900)
     cfg = workload_config(prob, "mixed (fp32 subdomain, fp64 outer)")
+    cfg["warm_start"] = ("learned: Newmark predictor + least-squares autoregressive model of its error, refitted "
+                         "every step, + gated network correction (plain FP64 arm: previous-step solution)")
     cfg["window"] = (f"steps {F + W + 1}..{F + W + K} of the run: {F} untimed fast-forward steps and {W} warm-up "
                      f"steps first" if F else f"steps {W + 1}..{W + K}")
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": W,

@@ -90,7 +90,8 @@ extern "C" {
 
 /* ---- warm start (sg_params.warm) ---- */
 #define SG_WARM_PREV     0   /* previous step's interface solution (Alg. 1)                 */
-#define SG_WARM_LEARNED  1   /* learned predictor (extension; falls back to SG_WARM_PREV)   */
+#define SG_WARM_LEARNED  1   /* Newmark predictor plus a learned estimate of its error
+                                (extension of the method)                                    */
 
 /* ---- sources (sg_source.kind) ---- */
 #define SG_SRC_NONE    0
@@ -281,13 +282,15 @@ int sg_get_sizes(sg_handle h, sg_sizes* out);
  * number written or a negative code. */
 int sg_get_iters(sg_handle h, int* iters, double* relres, int cap);
 
-/* Learned warm start (extension of the paper's method; with warm = SG_WARM_LEARNED).  Per interface
- * (dof, mode) row a 4-32-32-1 tanh MLP (BF16 weights, FP32 arithmetic) maps the normalised history
- * [u^n, u^{n-1}, u^{n-2}, p] / s, p = u^n + dt v^n + dt^2/2 a^n, to a correction c; the PCG starts
- * from p + s c.  The network trains online (Adam, hand-written kernels) on the first
- * warm_train_steps steps; until it has trained the previous-step guess is used.  The PCG still
- * stops at the same relative residual.  Weights: NN_NP = 1249 floats, order W1 (32x4, row-major),
- * b1 (32), W2 (32x32), b2 (32), W3 (32), b3 (1).
+/* Learned warm start (extension of the paper's method; with warm = SG_WARM_LEARNED).  The PCG
+ * starts from the Newmark predictor p = u^n + dt v^n + dt^2/2 a^n of the interface solution plus a
+ * learned estimate of the predictor's error: per interface (dof, mode) row a 4-32-32-1 tanh MLP
+ * (BF16 weights, FP32 arithmetic) maps the normalised history [e^n, e^{n-1}, e^{n-2}, e^{n-3}] / s of
+ * the predictor's errors e^k = u^k - p^k (s their RMS) to c; the guess is p + s c.  The network
+ * trains online (Adam, hand-written kernels) on the first warm_train_steps steps; until it has
+ * trained, and for rows without history, the guess is p.  The PCG still stops at the same relative
+ * residual.  Weights: NN_NP = 1249 floats, order W1 (32x4, row-major), b1 (32), W2 (32x32), b2 (32),
+ * W3 (32), b3 (1).
  * sg_warm_weights copies the FP32 master weights out (get_host) and/or in (set_host, which also
  * marks the network as trained and resets Adam); n must be 1249. */
 int sg_warm_weights(sg_handle h, float* get_host, const float* set_host, int n);

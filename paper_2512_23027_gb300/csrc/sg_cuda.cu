@@ -165,7 +165,10 @@ struct sg_handle_s {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // learned warm start
   sgk::WarmCtl wctl{};
-  double *wU0 = nullptr, *wU1 = nullptr, *wU2 = nullptr, *vG = nullptr, *aG = nullptr, *wpred = nullptr, *wscale = nullptr;
+  // learned warm start: predictor-error history (4 steps), interface velocity and acceleration,
+  // predictor and feature scale per row
+  double *wE0 = nullptr, *wE1 = nullptr, *wE2 = nullptr, *wE3 = nullptr, *vG = nullptr, *aG = nullptr;
+  double *wpred = nullptr, *wscale = nullptr;
   float *wX = nullptr, *wy = nullptr, *wt = nullptr;
   int warm_train = 20, warm_epochs = 4;
   float warm_lr = 1e-3f;
@@ -1097,11 +1100,12 @@ static int enq_warm_guess(sg_handle h, Ctx& cx) {
   const int nr = (int)h->nGd();
   sgk::k_scatter<double><<<nblk(nr), 256, 0, st>>>(pr.nG, pr.P, h->owners, h->Dw, h->V, h->vG, 1);
   sgk::k_scatter<double><<<nblk(nr), 256, 0, st>>>(pr.nG, pr.P, h->owners, h->Dw, h->A, h->aG, 1);
-  sgk::k_wfeat<<<nblk(nr), 256, 0, st>>>(nr, pr.dt, h->xG, h->wU1, h->wU2, h->vG, h->aG, h->wX, h->wpred, h->wscale);
-  CK(cudaMemcpyAsync(h->wU0, h->xG, sizeof(double) * nr, cudaMemcpyDeviceToDevice, st));
+  sgk::k_wfeat<<<nblk(nr), 256, 0, st>>>(nr, pr.dt, h->xG, h->wE0, h->wE1, h->wE2, h->wE3, h->vG, h->aG, h->wX,
+                                         h->wpred, h->wscale);
   sgk::k_mlp<false><<<(nr + sgk::NN_ROWS - 1) / sgk::NN_ROWS, sgk::NN_ROWS, 0, st>>>(nr, h->wX, nullptr, h->wctl.wb, h->wy,
                                                                                     nullptr, nullptr, nullptr);
-  sgk::k_wguess<<<nblk(nr), 256, 0, st>>>(nr, h->wctl.trained, h->wy, h->wpred, h->wscale, h->xG);
+  sgk::k_wguess<<<nblk(nr), 256, 0, st>>>(nr, h->wctl, h->wy, h->wpred, h->wscale, h->wE0, h->wE1, h->wE2, h->wE3,
+                                          h->xG);
   CKL();
   return SG_OK;
 }
@@ -1110,14 +1114,16 @@ static int enq_warm_train(sg_handle h, Ctx& cx) {
   cudaStream_t st = cx.st;
   const int nr = (int)h->nGd();
   const int nb = (nr + sgk::NN_ROWS - 1) / sgk::NN_ROWS;
-  sgk::k_wtarget<<<nblk(nr), 256, 0, st>>>(nr, h->wctl.train_left, h->xG, h->wpred, h->wscale, h->wt);
+  sgk::k_wstats<<<nblk(nr), 256, 0, st>>>(nr, h->wctl, h->xG, h->wpred, h->wscale, h->wy, h->wE0, h->wE1, h->wE2,
+                                          h->wE3, h->wt);
+  sgk::k_wsolve<<<1, 32, 0, st>>>((int)nblk(nr), h->wctl);
   for (int e = 0; e < h->warm_epochs; ++e) {
     sgk::k_mlp<true><<<nb, sgk::NN_ROWS, 0, st>>>(nr, h->wX, h->wt, h->wctl.wb, nullptr, h->wctl.part, h->wctl.loss_part,
                                                   h->wctl.train_left);
     sgk::k_mlp_adam<<<1, 256, 0, st>>>(nb, nr, h->wctl, h->warm_lr, h->wctl.train_left);
   }
   sgk::k_wdone<<<1, 32, 0, st>>>(h->wctl);
-  sgk::k_wshift<<<nblk(nr), 256, 0, st>>>(nr, h->wU1, h->wU2, h->wU0);
+  sgk::k_wshift<<<nblk(nr), 256, 0, st>>>(nr, h->wE0, h->wE1, h->wE2, h->wE3, h->xG, h->wpred);
   CKL();
   return SG_OK;
 }
@@ -1154,7 +1160,9 @@ static int warm_setup(sg_handle h) {
   RET(dalloc(h, &wc.part, (long long)nb * sgk::NN_NP)); RET(dalloc(h, &wc.loss_part, nb));
   RET(dalloc(h, &wc.loss, 1)); RET(dalloc(h, &wc.train_left, 1)); RET(dalloc(h, &wc.trained, 1));
   RET(dalloc(h, &wc.adam_it, 1));
-  for (double** p : {&h->wU0, &h->wU1, &h->wU2, &h->vG, &h->aG, &h->wpred, &h->wscale}) RET(dalloc(h, p, nr));
+  RET(dalloc(h, &wc.arw, 4)); RET(dalloc(h, &wc.use_net, 1));
+  RET(dalloc(h, &wc.spart, (long long)nblk(nr) * sgk::WS_NSTAT));
+  for (double** p : {&h->wE0, &h->wE1, &h->wE2, &h->wE3, &h->vG, &h->aG, &h->wpred, &h->wscale}) RET(dalloc(h, p, nr));
   RET(dalloc(h, &h->wX, 4LL * nr)); RET(dalloc(h, &h->wy, nr)); RET(dalloc(h, &h->wt, nr));
   const std::vector<float> th = warm_init_weights();
   CK(cudaMemcpyAsync(wc.theta, th.data(), sizeof(float) * th.size(), cudaMemcpyHostToDevice, h->st));
@@ -1165,12 +1173,13 @@ static int warm_setup(sg_handle h) {
   return SG_OK;
 }
 
-// history of the interface solution starts from the current one
+// the predictor-error history starts empty (guesses are the plain predictor until it fills)
 static int warm_reset_history(sg_handle h) {
   if (h->warm != SG_WARM_LEARNED) return SG_OK;
   const size_t nb = sizeof(double) * (size_t)h->nGd();
-  CK(cudaMemcpyAsync(h->wU1, h->xG, nb, cudaMemcpyDeviceToDevice, h->st));
-  CK(cudaMemcpyAsync(h->wU2, h->xG, nb, cudaMemcpyDeviceToDevice, h->st));
+  for (double* e : {h->wE0, h->wE1, h->wE2, h->wE3}) CK(cudaMemsetAsync(e, 0, nb, h->st));
+  CK(cudaMemsetAsync(h->wctl.arw, 0, 4 * sizeof(double), h->st));
+  CK(cudaMemsetAsync(h->wctl.use_net, 0, sizeof(int), h->st));
   return SG_OK;
 }
 

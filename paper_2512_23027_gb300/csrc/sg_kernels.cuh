@@ -2577,24 +2577,34 @@ struct WarmCtl {
   int* train_left;        // online training steps still to do
   int* trained;           // training steps done (the guess is used once > 0)
   int* adam_it;           // Adam iteration counter
+  double* arw;            // [4] autoregressive weights of the predictor-error model
+  int* use_net;           // 1: the network's correction beat the AR model on the last step
+  double* spart;          // [blocks][WS_NSTAT] statistics partials of k_wstats
 };
+constexpr int WS_NSTAT = 16;  // normal equations (10 + 4), squared errors without and with the network
 
-// features and predictor per row: pred = u + dt v + dt^2/2 a (second-order Taylor of u^{n+1})
-__global__ void k_wfeat(int nrows, double dt, const double* __restrict__ u0, const double* __restrict__ u1,
-                        const double* __restrict__ u2, const double* __restrict__ vG, const double* __restrict__ aG,
-                        float* __restrict__ X, double* __restrict__ pred, double* __restrict__ scale) {
+// Predictor and features per row (interface dof, mode).  pred = u + dt v + dt^2/2 a, the Taylor
+// predictor of u^{n+1} from the Newmark state (its error is O(dt^3), against O(dt) for the previous
+// step's solution).  Features: the predictor's errors e_k = u^k - pred^k at the last four steps,
+// divided by their RMS s; the network predicts the next error in units of s, so its BF16 weights set
+// the accuracy of a correction of size |e|, not of size |u|.  s = 0 (no history yet) leaves the guess
+// at the predictor.
+__global__ void k_wfeat(int nrows, double dt, const double* __restrict__ u0, const double* __restrict__ e0,
+                        const double* __restrict__ e1, const double* __restrict__ e2, const double* __restrict__ e3,
+                        const double* __restrict__ vG, const double* __restrict__ aG, float* __restrict__ X,
+                        double* __restrict__ pred, double* __restrict__ scale) {
   count_launch();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrows) return;
   const double p = u0[r] + dt * vG[r] + 0.5 * dt * dt * aG[r];
-  const double f[4] = {u0[r], u1[r], u2[r], p};
+  const double f[4] = {e0[r], e1[r], e2[r], e3[r]};
   double s = 0.0;
   for (int i = 0; i < 4; ++i) s += f[i] * f[i];
   s = sqrt(0.25 * s);
-  const bool z = !(s > 0.0);
+  const bool z = !(s > 0.0) || !isfinite(s);
   for (int i = 0; i < 4; ++i) X[(long long)r * 4 + i] = z ? 0.f : (float)(f[i] / s);
   pred[r] = p;
-  scale[r] = z ? 1.0 : s;
+  scale[r] = z ? 0.0 : s;
 }
 
 // Network forward (and, with TRAIN, backward to block-partial gradients and loss).  One thread per
@@ -2711,21 +2721,110 @@ __global__ void k_mlp_adam(int nblk, int nrows, WarmCtl c, float lr, const int* 
 }
 
 // guess = pred + s y once the network has been trained; otherwise keep the previous solution
-__global__ void k_wguess(int nrows, const int* trained, const float* __restrict__ y, const double* __restrict__ pred,
-                         const double* __restrict__ scale, double* __restrict__ xG) {
+// Initial guess u = pred + ar + c: the Taylor predictor, the autoregressive estimate of its error
+// ar = sum_k w_k e^{n-k} (weights fitted by least squares on the previous step, k_wsolve), and the
+// network's correction c = s y when it beat the AR model alone on the previous step.
+__global__ void k_wguess(int nrows, const WarmCtl c, const float* __restrict__ y, const double* __restrict__ pred,
+                         const double* __restrict__ scale, const double* __restrict__ e0, const double* __restrict__ e1,
+                         const double* __restrict__ e2, const double* __restrict__ e3, double* __restrict__ xG) {
   count_launch();
-  if (*trained <= 0) return;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < nrows) xG[r] = pred[r] + scale[r] * (double)y[r];
+  if (r >= nrows) return;
+  const double ar = c.arw[0] * e0[r] + c.arw[1] * e1[r] + c.arw[2] * e2[r] + c.arw[3] * e3[r];
+  const double cn = (*c.use_net > 0 && isfinite(y[r])) ? scale[r] * (double)y[r] : 0.0;
+  xG[r] = pred[r] + ar + cn;
 }
 
-// training target t = (u^{n+1} - pred) / s
-__global__ void k_wtarget(int nrows, const int* gate, const double* __restrict__ xG, const double* __restrict__ pred,
-                          const double* __restrict__ scale, float* __restrict__ t) {
+// After the solve (xG = u^{n+1}): per-block partials of the least-squares normal equations of the
+// predictor-error model (F = [e^n .. e^{n-3}] of the row, target e = u^{n+1} - pred), of the squared
+// error of the AR estimate and of AR plus the network's correction (the one this step's guess could
+// use); the network's training target t = (e - ar) / s while it trains.  Fixed-order reductions.
+__global__ void __launch_bounds__(256) k_wstats(int nrows, const WarmCtl c, const double* __restrict__ xG,
+                                                const double* __restrict__ pred, const double* __restrict__ scale,
+                                                const float* __restrict__ y, const double* __restrict__ e0,
+                                                const double* __restrict__ e1, const double* __restrict__ e2,
+                                                const double* __restrict__ e3, float* __restrict__ t) {
   count_launch();
-  if (*gate <= 0) return;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < nrows) t[r] = (float)((xG[r] - pred[r]) / scale[r]);
+  double v[WS_NSTAT];
+#pragma unroll
+  for (int i = 0; i < WS_NSTAT; ++i) v[i] = 0.0;
+  if (r < nrows) {
+    const double F[4] = {e0[r], e1[r], e2[r], e3[r]};
+    const double e = xG[r] - pred[r];
+    const double ar = c.arw[0] * F[0] + c.arw[1] * F[1] + c.arw[2] * F[2] + c.arw[3] * F[3];
+    const double r1 = e - ar;
+    const double r2 = isfinite(y[r]) ? r1 - scale[r] * (double)y[r] : r1;
+    int q = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = i; j < 4; ++j) v[q++] = F[i] * F[j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[10 + i] = F[i] * e;
+    v[14] = r1 * r1;
+    v[15] = r2 * r2;
+    if (*c.train_left > 0) t[r] = scale[r] > 0.0 ? (float)(r1 / scale[r]) : 0.f;
+  }
+  __shared__ double red[8][WS_NSTAT];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < WS_NSTAT; ++i) {
+    double x = v[i];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) red[wid][i] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < WS_NSTAT) {
+    double x = 0.0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) x += red[w2][threadIdx.x];
+    c.spart[(long long)blockIdx.x * WS_NSTAT + threadIdx.x] = x;
+  }
+}
+
+// Sum of the partials (block order), the ridge-regularised 4 x 4 least-squares solve for the AR
+// weights of the next guess (Gaussian elimination with partial pivoting), and the network gate: its
+// correction is used on the next step when it lowered the last step's error below 0.9 of the AR
+// estimate's.  One thread.
+__global__ void k_wsolve(int nblk, const WarmCtl c) {
+  count_launch();
+  if (threadIdx.x != 0) return;
+  double v[WS_NSTAT];
+  for (int i = 0; i < WS_NSTAT; ++i) v[i] = 0.0;
+  for (int b = 0; b < nblk; ++b)
+    for (int i = 0; i < WS_NSTAT; ++i) v[i] += c.spart[(long long)b * WS_NSTAT + i];
+  double G[4][5];
+  int q = 0;
+  for (int i = 0; i < 4; ++i)
+    for (int j = i; j < 4; ++j) G[i][j] = G[j][i] = v[q++];
+  const double tr = G[0][0] + G[1][1] + G[2][2] + G[3][3];
+  for (int i = 0; i < 4; ++i) {
+    G[i][i] += 1e-10 * tr;
+    G[i][4] = v[10 + i];
+  }
+  bool ok = tr > 0.0 && isfinite(tr);
+  for (int k = 0; k < 4 && ok; ++k) {
+    int pv = k;
+    for (int i = k + 1; i < 4; ++i)
+      if (fabs(G[i][k]) > fabs(G[pv][k])) pv = i;
+    if (!(fabs(G[pv][k]) > 0.0)) { ok = false; break; }
+    for (int j = 0; j < 5; ++j) { const double tmp = G[k][j]; G[k][j] = G[pv][j]; G[pv][j] = tmp; }
+    for (int i = k + 1; i < 4; ++i) {
+      const double f = G[i][k] / G[k][k];
+      for (int j = k; j < 5; ++j) G[i][j] -= f * G[k][j];
+    }
+  }
+  double wv[4] = {0.0, 0.0, 0.0, 0.0};
+  if (ok) {
+    for (int i = 3; i >= 0; --i) {
+      double x = G[i][4];
+      for (int j = i + 1; j < 4; ++j) x -= G[i][j] * wv[j];
+      wv[i] = x / G[i][i];
+    }
+    for (int i = 0; i < 4; ++i) ok = ok && isfinite(wv[i]);
+  }
+  for (int i = 0; i < 4; ++i) c.arw[i] = ok ? wv[i] : 0.0;
+  *c.use_net = (*c.trained > 0 && v[15] < 0.9 * v[14]) ? 1 : 0;
 }
 
 // FP32 -> BF16 copy of the parameters
@@ -2752,12 +2851,16 @@ __global__ void k_mlp_reduce(int nblk, int nrows, const float* __restrict__ part
 }
 
 // end of a step: history shift (u^{n-2} <- u^{n-1} <- u^n) and training bookkeeping
-__global__ void k_wshift(int nrows, double* __restrict__ u1, double* __restrict__ u2, const double* __restrict__ u0) {
+// history of predictor errors: e3 <- e2 <- e1 <- e0 <- u^{n+1} - pred
+__global__ void k_wshift(int nrows, double* __restrict__ e0, double* __restrict__ e1, double* __restrict__ e2,
+                         double* __restrict__ e3, const double* __restrict__ xG, const double* __restrict__ pred) {
   count_launch();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrows) return;
-  u2[r] = u1[r];
-  u1[r] = u0[r];
+  e3[r] = e2[r];
+  e2[r] = e1[r];
+  e1[r] = e0[r];
+  e0[r] = xG[r] - pred[r];
 }
 __global__ void k_wdone(WarmCtl c) {
   count_launch();

@@ -90,3 +90,29 @@ def test_weights_round_trip(env):
     assert s2.warm_status()["trained"] >= 1
     s.close()
     s2.close()
+
+
+def test_learned_warm_start_matches_oracle(env):
+    """The learned warm start changes the PCG's initial guess only: with it the mixed-precision
+    fields of the 24^2 problem (tol 1e-12) match the oracle's DD-PCG (previous-step guess) within the
+    mixed-precision bar, 10 tol, after 8 steps (the first steps run before the error history fills).
+    The iteration savings are checked after training (test_learned_warm_start_reduces_pcg_iterations)
+    and measured on the benchmark workloads."""
+    _, Solver, _ = env
+    from oracle import dd as odd, sg as osg
+    from paper_2512_23027_gb300.binding import SG_MIXED, SG_WARM_LEARNED
+    prob = w.config("small")
+    steps = 8
+    s = Solver(prob, precision=SG_MIXED, warm=SG_WARM_LEARNED, warm_train_steps=4)
+    s.step(steps)
+    U = s.field()
+    its, rr = s.iters()
+    s.close()
+    sgp = osg.SGProblem(prob)
+    Ur, _, _, it_ref = odd.run_dd(sgp, odd.DDSolver(prob), steps, tol=prob.tol)
+    Ur = Ur.reshape(-1, prob.P)
+    err = np.linalg.norm(U - Ur) / np.linalg.norm(Ur)
+    print(f"learned warm start vs oracle: rel err {err:.3e} ({err / prob.tol:.2f} tol), iters {its} vs "
+          f"{[i for i, _ in it_ref]}")
+    assert err <= 10 * prob.tol
+    assert all(r <= prob.tol for r in rr)
