@@ -365,17 +365,18 @@ def run_precond_study(args):
 
 
 def run_profile_step(args):
-    """One step of the workload for profilers: fast-forward (graph mode), one untimed host-driven step,
+    """One step of the workload for profilers (mixed precision, learned warm start; with --profile-fp64
+    the plain FP64 solver): fast-forward (graph mode), one untimed host-driven step,
     then one host-driven step between cudaProfilerStart / cudaProfilerStop (run ncu with
     --profile-from-start off).  Host-driven enqueue launches the same kernels as the step graph, which
     per-kernel profilers cannot enter (conditional nodes)."""
     import torch
     import sg_workloads as w
     from paper_2512_23027_gb300 import Solver
-    from paper_2512_23027_gb300.binding import SG_FP64, SG_MIXED
+    from paper_2512_23027_gb300.binding import SG_FP64, SG_MIXED, SG_WARM_LEARNED
     prob = w.config(args.config)
     F = FORWARD.get(args.config, 0) if args.forward is None else args.forward
-    s = Solver(prob, precision=SG_MIXED)
+    s = Solver(prob, precision=SG_MIXED, warm=SG_WARM_LEARNED)   # the benchmark's optimised configuration
     if F:
         s.step(F)
     if args.profile_fp64:

@@ -1116,7 +1116,7 @@ static int enq_warm_train(sg_handle h, Ctx& cx) {
   const int nb = (nr + sgk::NN_ROWS - 1) / sgk::NN_ROWS;
   sgk::k_wstats<<<nblk(nr), 256, 0, st>>>(nr, h->wctl, h->xG, h->wpred, h->wscale, h->wy, h->wE0, h->wE1, h->wE2,
                                           h->wE3, h->wt);
-  sgk::k_wsolve<<<1, 32, 0, st>>>((int)nblk(nr), h->wctl);
+  sgk::k_wsolve<<<1, 256, 0, st>>>((int)nblk(nr), h->wctl);
   for (int e = 0; e < h->warm_epochs; ++e) {
     sgk::k_mlp<true><<<nb, sgk::NN_ROWS, 0, st>>>(nr, h->wX, h->wt, h->wctl.wb, nullptr, h->wctl.part, h->wctl.loss_part,
                                                   h->wctl.train_left);

@@ -679,9 +679,10 @@ __global__ void __launch_bounds__(256, 2) k_apply_f2(Op<double> op, int nb, int 
     }
   }
   __syncthreads();
-  // phase 3: outputs of the owned lines
+  // phase 3: outputs of the owned lines (the FP64 tests on the coefficients are made once)
   const f2 ckf = f2_from(ck), cmf = f2_from(cm * op.mass_h);
   const double cmd = cm * op.mass_h;
+  const bool has_k = ck != 0.0, has_m = cm != 0.0, mass_f2 = has_m && same, mass_64 = has_m && !same;
   constexpr int UB3 = 4;
   const int nout = nlin * L * P;
   const long long dN_ = (long long)L * P;
@@ -699,7 +700,7 @@ __global__ void __launch_bounds__(256, 2) k_apply_f2(Op<double> op, int nb, int 
         const int t = fdiv(nd, op.fL), i = nd - t * L;
         const long long so = so0 + (long long)(lj0 + t) * L + i;
         cl[u] = op.cls[so];
-        if (cm != 0.0) cbs[u] = op.cells[so];
+        if (has_m) cbs[u] = op.cells[so];
         if (add) ad[u] = add[pb + ((long long)(lj0 + t) * L + i) * P + k];
       }
     }
@@ -713,7 +714,7 @@ __global__ void __launch_bounds__(256, 2) k_apply_f2(Op<double> op, int nb, int 
       double out = 0.0;
       if ((out_mask >> cl[u]) & 1) {
         f2 acc = {0.f, 0.f};
-        if (ck != 0.0) {
+        if (has_k) {
           f2 sz = zs[((size_t)nE + (size_t)(t + 1) * L + i) * PS + k];
           sz = f2_sub(sz, zs[((size_t)nE + (size_t)t * L + i) * PS + k]);
           if (i < L - 1) sz = f2_add(sz, zs[((size_t)t * (L - 1) + i) * PS + k]);
@@ -722,7 +723,7 @@ __global__ void __launch_bounds__(256, 2) k_apply_f2(Op<double> op, int nb, int 
         }
         const int cb = cbs[u];
         double md = 0.0;
-        if (cm != 0.0 && same) {
+        if (mass_f2) {
           const f2* xa = xs + ((size_t)(t + 1) * L + i) * P + k;
           auto twice = [](f2 a) -> f2 { return {2.f * a.h, 2.f * a.l}; };  // exact
           float self = 0.f;
@@ -732,7 +733,7 @@ __global__ void __launch_bounds__(256, 2) k_apply_f2(Op<double> op, int nb, int 
           if (cb & 4) { self += 2.f; nbs = f2_add(f2_add(nbs, xa[-P]), xa[dN_]); }
           if (cb & 8) { self += 4.f; nbs = f2_add(f2_add(f2_add(nbs, xa[P]), twice(xa[dN_ + P])), xa[dN_]); }
           acc = f2_add(acc, f2_mul(cmf, f2_add(f2_mul({self, 0.f}, xa[0]), nbs)));
-        } else if (cm != 0.0) {
+        } else if (mass_64) {
           const double* xa = xm + g;
           double self = 0.0, nbs = 0.0;
           if (cb & 1) { self += 4.0; nbs += 2.0 * xa[-dN_ - P] + xa[-dN_] + xa[-P]; }
@@ -742,7 +743,7 @@ __global__ void __launch_bounds__(256, 2) k_apply_f2(Op<double> op, int nb, int 
           md = cmd * (self * xa[0] + nbs);
         }
         out = f32_to_f64_scaled(acc.h, ex) + f32_to_f64_scaled(acc.l, ex);
-        if (md != 0.0) out += md;
+        if (mass_64) out += md;
         if (add) out += ad[u];
       }
       y[g] = out;
@@ -2782,17 +2783,27 @@ __global__ void __launch_bounds__(256) k_wstats(int nrows, const WarmCtl c, cons
   }
 }
 
-// Sum of the partials (block order), the ridge-regularised 4 x 4 least-squares solve for the AR
-// weights of the next guess (Gaussian elimination with partial pivoting), and the network gate: its
-// correction is used on the next step when it lowered the last step's error below 0.9 of the AR
-// estimate's.  One thread.
-__global__ void k_wsolve(int nblk, const WarmCtl c) {
+// Sum of the partials (each of 256 threads a fixed strided subset of the blocks, then a fixed-order
+// tree), the ridge-regularised 4 x 4 least-squares solve for the AR weights of the next guess
+// (Gaussian elimination with partial pivoting, one thread), and the network gate: its correction is
+// used on the next step when it lowered the last step's error below 0.9 of the AR estimate's.  One
+// block of 256 threads.
+__global__ void __launch_bounds__(256) k_wsolve(int nblk, const WarmCtl c) {
   count_launch();
-  if (threadIdx.x != 0) return;
+  __shared__ double red[256][WS_NSTAT + 1];
   double v[WS_NSTAT];
   for (int i = 0; i < WS_NSTAT; ++i) v[i] = 0.0;
-  for (int b = 0; b < nblk; ++b)
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x)
     for (int i = 0; i < WS_NSTAT; ++i) v[i] += c.spart[(long long)b * WS_NSTAT + i];
+  for (int i = 0; i < WS_NSTAT; ++i) red[threadIdx.x][i] = v[i];
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+      for (int i = 0; i < WS_NSTAT; ++i) red[threadIdx.x][i] += red[threadIdx.x + h][i];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  for (int i = 0; i < WS_NSTAT; ++i) v[i] = red[0][i];
   double G[4][5];
   int q = 0;
   for (int i = 0; i < 4; ++i)
