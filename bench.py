@@ -557,6 +557,7 @@ def main():
     pe = prob.replace(source=w.Source())
     se = make(pe, SG_MIXED, SG_WARM_LEARNED)
     se.set_state(state0)
+    se.warm_weights(s.warm_weights())   # the network the optimised leg trained (no retraining)
     nf = se.n_free
     fw = torch.from_numpy(ricker_nodal_load(prob, F, W, nf)).pin_memory()
     uw = torch.zeros((W, nf), dtype=torch.float64).pin_memory()

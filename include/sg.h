@@ -292,7 +292,7 @@ int sg_get_iters(sg_handle h, int* iters, double* relres, int cap);
  * residual.  Weights: NN_NP = 1249 floats, order W1 (32x4, row-major), b1 (32), W2 (32x32), b2 (32),
  * W3 (32), b3 (1).
  * sg_warm_weights copies the FP32 master weights out (get_host) and/or in (set_host, which also
- * marks the network as trained and resets Adam); n must be 1249. */
+ * marks the network as trained, ends its online training and resets Adam); n must be 1249. */
 int sg_warm_weights(sg_handle h, float* get_host, const float* set_host, int n);
 int sg_warm_status(sg_handle h, int* trained, int* train_left, float* loss);
 

@@ -2454,6 +2454,7 @@ int sg_warm_weights(sg_handle h, float* get_host, const float* set_host, int n) 
     CKL();
     const int one = 1;
     CK(cudaMemcpyAsync(h->wctl.trained, &one, sizeof(int), cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemsetAsync(h->wctl.train_left, 0, sizeof(int), h->st));  // a given network is not retrained
     CK(cudaMemsetAsync(h->wctl.m, 0, sizeof(float) * n, h->st));
     CK(cudaMemsetAsync(h->wctl.v, 0, sizeof(float) * n, h->st));
     CK(cudaMemsetAsync(h->wctl.adam_it, 0, sizeof(int), h->st));
