@@ -272,18 +272,20 @@ def run_reference(args):
 
 def run_batch(args):
     """Batched workload: independent problems of uneven size advanced together, one graph launch per
-    time step for the whole batch (mixed precision, autotuned tiles)."""
+    time step for the whole batch (mixed precision, autotuned tiles, learned warm start unless
+    --batch-warm prev)."""
     import torch
     import sg_workloads as w
     from paper_2512_23027_gb300 import Solver, solve_batch
-    from paper_2512_23027_gb300.binding import SG_MIXED
+    from paper_2512_23027_gb300.binding import SG_MIXED, SG_WARM_LEARNED, SG_WARM_PREV
     from paper_2512_23027_gb300.binding import SGError
     drawn = w.batch_problems(256)[: args.batch]
+    warm = SG_WARM_PREV if args.batch_warm == "prev" else SG_WARM_LEARNED
     t0 = time.perf_counter()
     probs, solvers, skipped = [], [], []
     for p in drawn:
         try:
-            solvers.append(Solver(p, precision=SG_MIXED, autotune=True))
+            solvers.append(Solver(p, precision=SG_MIXED, autotune=True, warm=warm))
             probs.append(p)
         except SGError as e:  # reported, never silently replaced
             if e.code != -7:
@@ -302,7 +304,7 @@ def run_batch(args):
             "steps": args.steps, "ms_per_batch_step": ms / args.steps, "wall_s": wall, "setup_s": setup,
             "total_sg_dofs": dofs, "pcg_iters_per_step": sum(s["iters_total"] for s in st) / (len(st) * args.steps),
             "max_iters_last": max(s["iters_last"] for s in st), "dtype": "f32+f64", "data": "synthetic",
-            "skipped": skipped,
+            "skipped": skipped, "warm_start": args.batch_warm,
             "config": {"workload": "batch (seed 20251227)", "grids": sorted({p.N for p in probs}),
                        "subdomains": sorted({p.s for p in probs}), "pce_terms": sorted({p.P for p in probs})}}
     print(json.dumps(line), flush=True)
@@ -411,6 +413,8 @@ def main():
     ap.add_argument("--batch", type=int, default=0,
                     help="instead of the default line, run the first BATCH problems of the batched workload "
                          "(64^2..256^2 grids, uneven sizes) with sg_solve_batch and report problem-steps/s")
+    ap.add_argument("--batch-warm", default="learned", choices=["learned", "prev"],
+                    help="with --batch: the PCG initial guess of every problem")
     ap.add_argument("--precond-study", action="store_true",
                     help="instead of the default line, compare the two-level NN, one-level NN and lumped "
                          "preconditioners over 2x2..16x16 subdomains of a 256^2 grid (iterations per step)")

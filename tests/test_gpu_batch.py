@@ -21,16 +21,21 @@ def Solver():
     return S
 
 
-def test_batch_equals_individual(Solver):
+@pytest.mark.parametrize("warm", ["prev", "learned"])
+def test_batch_equals_individual(Solver, warm):
+    """Batched and individual steps agree bitwise, with the previous-step guess and with the learned
+    warm start (its statistics, least-squares fit and network training run inside each problem's
+    branch of the batch graph)."""
     from paper_2512_23027_gb300 import solve_batch
-    from paper_2512_23027_gb300.binding import SG_FP64, SG_MIXED
+    from paper_2512_23027_gb300.binding import SG_FP64, SG_MIXED, SG_WARM_LEARNED, SG_WARM_PREV
+    wm = SG_WARM_LEARNED if warm == "learned" else SG_WARM_PREV
     probs = [(w.config("small"), SG_FP64), (w.config("tiny"), SG_FP64), (w.config("pulse32"), SG_MIXED),
              (w.config("small").replace(p=3, p_in=3, sigma=0.45), SG_MIXED)]
-    steps = 3
-    batch = [Solver(p, precision=pr) for p, pr in probs]
+    steps = 6 if warm == "learned" else 3   # the error history fills after four steps
+    batch = [Solver(p, precision=pr, warm=wm) for p, pr in probs]
     stats = solve_batch(batch, steps)
     for (p, pr), s, st in zip(probs, batch, stats):
-        ref = Solver(p, precision=pr)
+        ref = Solver(p, precision=pr, warm=wm)
         ref.step(steps)
         assert np.array_equal(s.field(), ref.field()), p.name
         its_b, _ = s.iters()
@@ -41,7 +46,7 @@ def test_batch_equals_individual(Solver):
     # a second batched call continues from the current state
     solve_batch(batch, 2)
     for (p, pr), s in zip(probs, batch):
-        ref = Solver(p, precision=pr)
+        ref = Solver(p, precision=pr, warm=wm)
         ref.step(steps + 2)
         assert np.array_equal(s.field(), ref.field()), p.name
         ref.close()

@@ -106,3 +106,30 @@ def test_wide_subdomains_match_oracle_samples(lib, case, precision):
     assert norm_rel.max() <= bar["mode"], norm_rel
     assert all(r <= ref["tol"] for r in rr)
     assert all(abs(a - b) <= 1 for a, b in zip(its, ref["iters"]))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("case", ["l65_m5p2", "l65_m4p3"])
+def test_learned_warm_start_on_wide_subdomains(lib, case):
+    """The benchmark's configuration (mixed precision with the learned warm start) on 65 x 65-node
+    subdomains against the stored oracle samples (previous-step guess, workload tolerance): the warm
+    start changes the PCG's starting point only, so the mixed-precision bars hold."""
+    from paper_2512_23027_gb300.binding import SG_WARM_LEARNED
+    g = gold()
+    if case not in g:
+        pytest.skip(f"{case} not in the stored oracle samples")
+    rec = g[case]
+    prob = problem(case, rec)
+    ref = rec["workload"]
+    s = lib(prob, precision=SG_MIXED, tol=ref["tol"], warm=SG_WARM_LEARNED)
+    s.step(rec["steps"])
+    U = s.field()
+    its, rr = s.iters()
+    s.close()
+    glob, per_mode, norm_rel, top = compare(U, rec, ref)
+    print(f"{case} mixed + learned warm start: sampled rel err {glob:.3e}, largest entries {top:.3e}, worst mode "
+          f"{per_mode.max():.3e}, iters {its} vs {ref['iters']}")
+    bar = BARS[SG_MIXED]
+    assert glob <= bar["glob"] and top <= bar["glob"]
+    assert per_mode.max() <= bar["mode"] and norm_rel.max() <= bar["mode"]
+    assert all(r <= ref["tol"] for r in rr)
