@@ -76,6 +76,12 @@ class Partition:
                 sub["elem_mask"] = ce
                 self.subs.append(sub)
 
+    def assemble(self, coef, elem_mask=None):
+        return fem.assemble(self.N, coef, elem_mask)
+
+    def element_coefficients(self, prob):
+        return fem.element_coefficients(prob)
+
 
 def dofs(node_pos: np.ndarray, P: int) -> np.ndarray:
     """Node positions -> node-major SG dof indices."""
@@ -87,20 +93,22 @@ class DDSolver:
     of each subdomain only (Eq. ki), so that sum_s R_s^T K_GG^s R_s gives the global
     interface block (Eq. GAssembly_Sto)."""
 
-    def __init__(self, prob, explicit: bool = False, subs=None, coef=None, precond: str = "nn2"):
+    def __init__(self, prob, explicit: bool = False, subs=None, coef=None, precond: str = "nn2", partition=None):
         """subs: indices of the only subdomains whose local operators are built (timing samples of
         large workloads); the coarse problem, which needs every subdomain, is then not assembled.
         coef: element PCE coefficients from a KL other than the analytic one (see sg.SGProblem).
         precond: the PCG preconditioner, "nn2" (two-level Neumann-Neumann, Eq. NNCP2), "nn1"
-        (one-level Neumann-Neumann) or "lumped" (the one-level comparison of Sec. 6.1)."""
+        (one-level Neumann-Neumann) or "lumped" (the one-level comparison of Sec. 6.1).
+        partition: node classes of another mesh and partition (umesh.UPartition); None for the
+        s x s partition of the structured grid."""
         assert precond in ("nn2", "nn1", "lumped")
         self.pc_kind = precond
         self.prob = prob
         N, s = prob.N, prob.s
-        self.part = Partition(N, s)
+        self.part = Partition(N, s) if partition is None else partition
         self.G = pce.triple_products(prob.M, prob.p_in, prob.p)
         P = self.P = self.G.shape[1]
-        self.coef = fem.element_coefficients(prob) if coef is None else coef
+        self.coef = self.part.element_coefficients(prob) if coef is None else coef
         part = self.part
         nG = part.iface.size
         self.nG = nG
@@ -110,7 +118,7 @@ class DDSolver:
         for si, sub in enumerate(part.subs):
             if subs is not None and si not in subs:
                 continue
-            Mfull, Kfull = fem.assemble(N, self.coef, sub["elem_mask"])
+            Mfull, Kfull = self.part.assemble(self.coef, sub["elem_mask"])
             nd = sub["nodes"]
             M = Mfull[nd][:, nd].tocsr()
             Ks = [K[nd][:, nd].tocsr() for K in Kfull]

@@ -198,3 +198,9 @@ def normal_samples(n: int, dim: int, seed: int = 0):
             row.append(buf.pop(0))
         out.append(row)
     return out
+
+
+def uniform_samples(n: int, seed: int = 0) -> List[float]:
+    """n uniform draws in [0, 1) from SplitMix64 (mesh jitter of the unstructured meshes)."""
+    g = SplitMix64(seed)
+    return [g.uniform() for _ in range(n)]
