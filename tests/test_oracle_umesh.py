@@ -156,3 +156,22 @@ def test_pulse_initial_state_on_the_structured_grid():
     b = sg.SGProblem(prob).initial_state()
     for x, y in zip(a, b):
         assert np.abs(x - y).max() <= 1e-12 * max(np.abs(y).max(), 1.0)
+
+
+@pytest.mark.parametrize("pc", ["nn1", "lumped"])
+def test_unstructured_one_level_preconditioners(pc):
+    """The comparison preconditioners of Sec. 6.1 on a general partition: DD-PCG at tol 1e-13 equals
+    the direct SG solve; the two-level preconditioner needs no more iterations than the one-level
+    NN (with four subdomains and few corners its coarse space adds little) and fewer than lumped."""
+    prob = w.config("small").replace(name="u10", N=10, s=2, dt=0.02)
+    m = umesh.delaunay_mesh(10, 0.3, 13)
+    up = umesh.UPartition(m, umesh.rcb_partition(m, 4))
+    usg = umesh.USGProblem(m, prob)
+    Ud, _, _, it = dd.run_dd(usg, dd.DDSolver(prob, partition=up, precond=pc), 2, tol=1e-13)
+    Ur, _, _ = sg.run_direct(usg, 2)
+    assert np.linalg.norm(Ud - Ur) <= 1e-10 * np.linalg.norm(Ur)
+    _, _, _, it2 = dd.run_dd(usg, dd.DDSolver(prob, partition=up), 2, tol=1e-13)
+    if pc == "nn1":
+        assert sum(i for i, _ in it2) <= sum(i for i, _ in it)
+    else:
+        assert sum(i for i, _ in it2) < sum(i for i, _ in it)
