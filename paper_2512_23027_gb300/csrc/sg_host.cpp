@@ -380,6 +380,201 @@ std::string build_problem(Problem& pr, int N, int sx, int sy, int M, double sigm
   return "";
 }
 
+// ---- general partitions of unstructured triangle meshes ----
+std::string build_mesh_problem(MeshProblem& mp, int nv, const double* xy, const uint8_t* dirichlet, int ne,
+                               const int* tri, const int* part, int M, double sigma, double bx, double by,
+                               double g0, int p, int p_in, const double* modes, const double* lambdas) {
+  if (nv < 3 || ne < 1 || !xy || !dirichlet || !tri || !part) return "mesh: vertices, triangles and partition required";
+  if (M < 0 || M > 12 || p < 0 || p_in < 0 || p > 10 || p_in > 20) return "pce/kl: unsupported M, p or p_in";
+  if (!(sigma >= 0)) return "kl: sigma >= 0 required";
+  if (M > 0 && !modes && !(bx > 0 && by > 0)) return "kl: correlation lengths must be positive";
+  if (modes && M > 0) {
+    if (!lambdas) return "kl: modes given without lambdas";
+    for (int n = 0; n < M; ++n)
+      if (!(lambdas[n] > 0) || !std::isfinite(lambdas[n])) return "kl: lambdas must be positive and finite";
+    for (size_t q = 0; q < (size_t)M * ne; ++q)
+      if (!std::isfinite(modes[q])) return "kl: modes must be finite";
+  }
+  int nsub = 0;
+  for (int e = 0; e < ne; ++e) {
+    for (int a = 0; a < 3; ++a)
+      if (tri[3 * e + a] < 0 || tri[3 * e + a] >= nv) return "mesh: triangle vertex out of range";
+    if (part[e] < 0) return "mesh: negative subdomain id";
+    nsub = std::max(nsub, part[e] + 1);
+  }
+  {
+    std::vector<char> used(nsub, 0);
+    for (int e = 0; e < ne; ++e) used[part[e]] = 1;
+    for (int s = 0; s < nsub; ++s)
+      if (!used[s]) return "mesh: subdomain ids must be 0 .. nsub - 1, each used";
+  }
+  mp = MeshProblem{};
+  mp.nv = nv; mp.ne = ne; mp.nsub = nsub; mp.M = M; mp.p = p; mp.p_in = p_in;
+  const auto Ain = multi_indices(M, p_in);
+  mp.P = (int)multi_indices(M, p).size();
+  mp.PI = (int)Ain.size();
+  const int PI = mp.PI;
+
+  // element geometry: doubled signed area, unit-coefficient P1 stiffness from the barycentric
+  // gradients grad(phi_a) = (y_b - y_c, x_c - x_b) / (2 area)
+  std::vector<double> area(ne), Ke((size_t)ne * 9), cx(ne), cy(ne);
+  for (int e = 0; e < ne; ++e) {
+    const int* v = tri + 3 * e;
+    const double x1 = xy[2 * v[0]], y1 = xy[2 * v[0] + 1], x2 = xy[2 * v[1]], y2 = xy[2 * v[1] + 1];
+    const double x3 = xy[2 * v[2]], y3 = xy[2 * v[2] + 1];
+    const double a2 = (x2 - x1) * (y3 - y1) - (x3 - x1) * (y2 - y1);
+    if (!(std::fabs(a2) > 0)) return "mesh: degenerate triangle";
+    area[e] = 0.5 * std::fabs(a2);
+    const double b[3] = {y2 - y3, y3 - y1, y1 - y2}, c[3] = {x3 - x2, x1 - x3, x2 - x1};
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Ke[(size_t)e * 9 + i * 3 + j] = (b[i] * b[j] + c[i] * c[j]) / (4.0 * area[e]);
+    cx[e] = (x1 + x2 + x3) / 3.0;
+    cy[e] = (y1 + y2 + y3) / 3.0;
+  }
+
+  // KL: top M products of the 1-D eigenpairs (ties: lower y index, then x index), or the caller's
+  std::vector<Eig1> ex = eig1d(bx > 0 ? bx : 1.0, M + 1), ey = eig1d(by > 0 ? by : 1.0, M + 1);
+  struct Cand { double lam; int ix, iy; };
+  std::vector<Cand> cand;
+  for (int ix = 0; ix <= M; ++ix)
+    for (int iy = 0; iy <= M; ++iy) cand.push_back({ex[ix].lam * ey[iy].lam, ix, iy});
+  std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) {
+    if (a.lam != b.lam) return a.lam > b.lam;
+    if (a.iy != b.iy) return a.iy < b.iy;
+    return a.ix < b.ix;
+  });
+  cand.resize(M);
+  mp.kl_lambda.resize(M);
+  for (int n = 0; n < M; ++n) mp.kl_lambda[n] = modes ? lambdas[n] : cand[n].lam;
+  // PCE coefficients of exp(g) per element centroid: exp(g0 + |g|^2 / 2) prod_n g_n^{a_n} / sqrt(a_n!)
+  std::vector<double> coef((size_t)ne * PI);
+  for (int e = 0; e < ne; ++e) {
+    std::vector<double> g(M);
+    double s2 = 0.0;
+    for (int n = 0; n < M; ++n) {
+      g[n] = modes ? sigma * std::sqrt(lambdas[n]) * modes[(size_t)n * ne + e]
+                   : sigma * std::sqrt(cand[n].lam) * phi1(cx[e], ex[cand[n].ix]) * phi1(cy[e], ey[cand[n].iy]);
+      s2 += g[n] * g[n];
+    }
+    const double c0 = std::exp(g0 + 0.5 * s2);
+    for (int i = 0; i < PI; ++i) {
+      double v = c0;
+      for (int n = 0; n < M; ++n)
+        for (int a = 0; a < Ain[i][n]; ++a) v *= g[n] / std::sqrt((double)(a + 1));
+      coef[(size_t)e * PI + i] = v;
+    }
+  }
+
+  // subdomains of each vertex, interface edges (two triangles of different subdomains) per vertex
+  std::vector<std::vector<int>> vsub(nv);
+  for (int e = 0; e < ne; ++e)
+    for (int a = 0; a < 3; ++a) {
+      auto& l = vsub[tri[3 * e + a]];
+      if (std::find(l.begin(), l.end(), part[e]) == l.end()) l.push_back(part[e]);
+    }
+  struct HalfEdge { int u, v, e; };
+  std::vector<HalfEdge> he;
+  he.reserve((size_t)3 * ne);
+  for (int e = 0; e < ne; ++e)
+    for (int a = 0; a < 3; ++a) {
+      const int u = tri[3 * e + a], v = tri[3 * e + (a + 1) % 3];
+      he.push_back({std::min(u, v), std::max(u, v), e});
+    }
+  std::sort(he.begin(), he.end(), [](const HalfEdge& a, const HalfEdge& b) {
+    return a.u != b.u ? a.u < b.u : a.v != b.v ? a.v < b.v : a.e < b.e;
+  });
+  std::vector<std::vector<std::pair<long long, int>>> icount(nv);  // (pair key, interface edges)
+  for (size_t q = 0; q < he.size();) {
+    size_t r = q;
+    while (r < he.size() && he[r].u == he[q].u && he[r].v == he[q].v) ++r;
+    if (r - q > 2) return "mesh: an edge shared by more than two triangles";
+    if (r - q == 2) {
+      const int pa = part[he[q].e], pb = part[he[q + 1].e];
+      if (pa != pb) {
+        const long long key = (long long)std::min(pa, pb) * nsub + std::max(pa, pb);
+        for (int x : {he[q].u, he[q].v}) {
+          auto& l = icount[x];
+          auto it = std::find_if(l.begin(), l.end(), [key](const std::pair<long long, int>& t) { return t.first == key; });
+          if (it == l.end()) l.push_back({key, 1});
+          else ++it->second;
+        }
+      }
+    }
+    q = r;
+  }
+  mp.vclass.assign(nv, DIRICHLET);
+  mp.vmult.assign(nv, 0);
+  mp.free_idx.assign(nv, -1);
+  mp.iface_idx.assign(nv, -1);
+  mp.corner_idx.assign(nv, -1);
+  for (int v = 0; v < nv; ++v) {
+    const int m = (int)vsub[v].size();
+    mp.vmult[v] = m;
+    if (dirichlet[v] || m == 0) continue;
+    if (m == 1) {
+      mp.vclass[v] = INTERIOR;
+    } else if (m >= 3) {
+      mp.vclass[v] = CORNER;
+    } else {
+      const long long key = (long long)std::min(vsub[v][0], vsub[v][1]) * nsub + std::max(vsub[v][0], vsub[v][1]);
+      int cnt = 0;
+      for (const auto& t : icount[v])
+        if (t.first == key) cnt = t.second;
+      mp.vclass[v] = cnt == 2 ? REMAINING : CORNER;
+    }
+  }
+  for (int v = 0; v < nv; ++v) {
+    if (mp.vclass[v] == DIRICHLET) continue;
+    mp.free_idx[v] = mp.n_free++;
+    if (mp.vclass[v] == REMAINING || mp.vclass[v] == CORNER) mp.iface_idx[v] = mp.nG++;
+    if (mp.vclass[v] == CORNER) mp.corner_idx[v] = mp.nC++;
+  }
+
+  // per subdomain: local vertices (interior, remaining, corners, Dirichlet; ascending within a
+  // class), edges with their weights per input mode, triangles
+  std::vector<std::vector<int>> selems(nsub);
+  for (int e = 0; e < ne; ++e) selems[part[e]].push_back(e);
+  std::vector<int> loc(nv, -1);
+  auto rank = [&](int v) { const int c = mp.vclass[v]; return c == DIRICHLET ? 4 : c; };
+  mp.sub_vptr.assign(1, 0);
+  mp.sub_eptr.assign(1, 0);
+  mp.sub_tptr.assign(1, 0);
+  for (int s = 0; s < nsub; ++s) {
+    std::vector<int> verts;
+    for (int e : selems[s])
+      for (int a = 0; a < 3; ++a) verts.push_back(tri[3 * e + a]);
+    std::sort(verts.begin(), verts.end());
+    verts.erase(std::unique(verts.begin(), verts.end()), verts.end());
+    std::stable_sort(verts.begin(), verts.end(), [&](int a, int b) { return rank(a) < rank(b); });
+    for (size_t k = 0; k < verts.size(); ++k) loc[verts[k]] = (int)k;
+    std::map<std::pair<int, int>, std::vector<double>> edges;
+    for (int e : selems[s]) {
+      const int* v = tri + 3 * e;
+      for (int a = 0; a < 3; ++a)
+        for (int b = a + 1; b < 3; ++b) {
+          const int la = loc[v[a]], lb = loc[v[b]];
+          auto& w = edges[{std::min(la, lb), std::max(la, lb)}];
+          if (w.empty()) w.assign(PI, 0.0);
+          const double k = Ke[(size_t)e * 9 + a * 3 + b];
+          for (int i = 0; i < PI; ++i) w[i] -= coef[(size_t)e * PI + i] * k;
+        }
+      for (int a = 0; a < 3; ++a) mp.tri_loc.push_back(loc[v[a]]);
+      mp.tri_area.push_back(area[e]);
+    }
+    for (const auto& kv : edges) {
+      mp.edge_u.push_back(kv.first.first);
+      mp.edge_v.push_back(kv.first.second);
+      mp.edge_w.insert(mp.edge_w.end(), kv.second.begin(), kv.second.end());
+    }
+    mp.sub_verts.insert(mp.sub_verts.end(), verts.begin(), verts.end());
+    mp.sub_vptr.push_back((int)mp.sub_verts.size());
+    mp.sub_eptr.push_back((int)mp.edge_u.size());
+    mp.sub_tptr.push_back((int)mp.tri_area.size());
+    for (int v : verts) loc[v] = -1;
+  }
+  return "";
+}
+
 bool spd_inverse(std::vector<double>& A, int n) {
   if (n <= 0) return true;
   if ((long long)A.size() < (long long)n * n) return false;

@@ -66,6 +66,41 @@ std::string build_problem(Problem& pr, int N, int sx, int sy, int M, double sigm
                           double alpha1, const SourceDesc& src, const double* modes = nullptr,
                           const double* lambdas = nullptr);
 
+// ---- general partitions of unstructured triangle meshes (host set-up of the general path) ----
+// Vertex classes with the corner reading of Sec. 3 (free vertices of three or more subdomains, and
+// end vertices of interface curves: a free vertex of exactly two subdomains A, B without exactly two
+// A|B interface edges, an edge whose two triangles lie in A and B), interface and corner numbering,
+// and per subdomain the local vertices, the edges with their P1 stiffness weights per PCE input mode
+// (K_i = sum_edges w_i (e_a - e_b)(e_a - e_b)^T over the subdomain's triangles, w_i = -K_i[a][b])
+// and the triangles with their areas (consistent mass area / 12 [2 1 1; 1 2 1; 1 1 2]).
+struct MeshProblem {
+  int nv = 0, ne = 0, nsub = 0;
+  int M = 0, p = 0, p_in = 0, P = 0, PI = 0;
+  std::vector<uint8_t> vclass;   // nv: DIRICHLET / INTERIOR / REMAINING / CORNER
+  std::vector<int> vmult;        // nv: number of subdomains whose triangles contain the vertex
+  int n_free = 0, nG = 0, nC = 0;
+  std::vector<int> free_idx, iface_idx, corner_idx;  // nv: index in the free / interface / corner order, or -1
+  // per subdomain s: local vertices [sub_vptr[s], sub_vptr[s+1]) of sub_verts (global ids; interior,
+  // remaining, corners, then Dirichlet, each ascending), local edges [sub_eptr[s], sub_eptr[s+1]) as
+  // local vertex indices (edge_u < edge_v) with PI weights each in edge_w, local triangles
+  // [sub_tptr[s], sub_tptr[s+1]) as three local vertex indices with their areas
+  std::vector<int> sub_vptr, sub_verts;
+  std::vector<int> sub_eptr, edge_u, edge_v;
+  std::vector<double> edge_w;
+  std::vector<int> sub_tptr, tri_loc;
+  std::vector<double> tri_area;
+  std::vector<double> kl_lambda;  // M
+};
+
+// xy: nv x 2 vertex coordinates in the unit square; dirichlet: nv flags (homogeneous Dirichlet
+// vertices, eliminated); tri: ne x 3 vertex ids; part: ne subdomain ids 0 .. nsub - 1 (every id
+// used).  KL and PCE as build_problem (modes, when given, hold phi_n at the element centroids:
+// modes[n * ne + e]).  Returns "" on success, else an error message.
+std::string build_mesh_problem(MeshProblem& mp, int nv, const double* xy, const uint8_t* dirichlet, int ne,
+                               const int* tri, const int* part, int M, double sigma, double bx, double by,
+                               double g0, int p, int p_in, const double* modes = nullptr,
+                               const double* lambdas = nullptr);
+
 std::vector<std::vector<int>> multi_indices(int M, int p);
 double hermite_triple(int a, int b, int c);
 double ricker(double t, double f);
