@@ -214,6 +214,42 @@ int sg_plan_query(const sg_grid* grid, const sg_kl* kl, const sg_pce* pce, const
 int sg_setup(const sg_grid* grid, const sg_kl* kl, const sg_pce* pce, const sg_params* params,
              const sg_source* src, void* stream, sg_handle* out);
 
+/* Unstructured triangle mesh of the unit square with an element partition (Sec. 3: any partition
+ * into non-overlapping subdomains; Sec. 6: unstructured meshes).  Arrays are caller-owned and read
+ * during sg_setup_mesh only. */
+typedef struct {
+  int nv;                          /* vertices                                                      */
+  const double* xy;                /* nv x 2 coordinates, row-major                                 */
+  const unsigned char* dirichlet;  /* nv flags: 1 marks a homogeneous Dirichlet vertex (eliminated) */
+  int ne;                          /* triangles                                                     */
+  const int* tri;                  /* ne x 3 vertex ids (either orientation)                        */
+  const int* part;                 /* ne subdomain ids 0 .. nsub - 1, every id used                 */
+} sg_mesh;
+
+/* Build the solver on a general partition of a triangle mesh: the same per-step method as sg_setup
+ * (SG operator of Eq. K_T_Sto, interface PCG on Eq. Sto_Schur, two-level preconditioner Eq. NNCP2
+ * or the comparison preconditioners of Sec. 6.1) with
+ *   - vertex classes by the corner reading of Sec. 3: an interface vertex is a free vertex of
+ *     triangles of two or more subdomains; it is a corner when it lies in three or more subdomains,
+ *     or in exactly two subdomains A, B without exactly two A|B interface edges (an edge whose two
+ *     triangles lie in A and B): the end points of interface curves;
+ *   - P1 mass and stiffness of each subdomain's own triangles (coefficient: the log-normal PCE at
+ *     the triangle centroids, Eqs. c0pce, LNL0), applied as sparse rows;
+ *   - subdomain solves by CG preconditioned by the dense inverse of the subdomain's mean operator
+ *     (FP64 in SG_FP64, FP32 in SG_MIXED / SG_FP32, where the operator applies of the outer loop
+ *     stay FP64).
+ * kl->modes, when given, holds phi_n at the triangle centroids in the mesh's triangle order
+ * (modes[n * ne + e]).  The source: a pulse is evaluated at the free vertices; a point source uses
+ * the P1 values at (x0, y0) in the first triangle (in the given order) that contains it.  Fields of
+ * a mesh handle (sg_get_field, sg_get_state, sg_set_state, sg_step_host, sg_sample_field) list the
+ * free vertices in ascending vertex id, PCE mode fastest.  sg_sizes.N is 0 for a mesh handle.
+ * Errors: SG_EINVAL for invalid meshes, partitions or parameters (vertex ids out of range, an edge in
+ * more than two triangles, unused subdomain ids, a degenerate triangle, a source outside the mesh),
+ * SG_ENOTSUP for SG_BF16 or fewer than two subdomains, SG_ENUMERIC if a mean operator is not
+ * positive definite, SG_ENOMEM, SG_ECUDA.  On error *out is NULL. */
+int sg_setup_mesh(const sg_mesh* mesh, const sg_kl* kl, const sg_pce* pce, const sg_params* params,
+                  const sg_source* src, void* stream, sg_handle* out);
+
 /* Advance nsteps Newmark steps (Alg. 1 loop, stochastic form of Sec. 5): effective load
  * (Eqs. fparts, UmCm), condensed RHS G_Gamma, PCG with M_NNC^{-1}, interior recovery, Newmark
  * update.  stats may be NULL.  Returns SG_ENOTCONV (state still advanced) if a step hit

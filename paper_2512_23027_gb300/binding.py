@@ -41,6 +41,11 @@ class Params(C.Structure):
                 ("warm_train_steps", C.c_int), ("warm_lr", C.c_double), ("precond", C.c_int)]
 
 
+class Mesh(C.Structure):
+    _fields_ = [("nv", C.c_int), ("xy", C.c_void_p), ("dirichlet", C.c_void_p), ("ne", C.c_int),
+                ("tri", C.c_void_p), ("part", C.c_void_p)]
+
+
 class Source(C.Structure):
     _fields_ = [("kind", C.c_int), ("x0", C.c_double), ("y0", C.c_double), ("width", C.c_double),
                 ("freq", C.c_double), ("amp", C.c_double)]
@@ -95,6 +100,7 @@ def load_library(path: Optional[str] = None):
     P = C.POINTER
     D = P(C.c_double)
     lib.sg_setup.argtypes = [P(Grid), P(KL), P(PCE), P(Params), P(Source), C.c_void_p, P(C.c_void_p)]
+    lib.sg_setup_mesh.argtypes = [P(Mesh), P(KL), P(PCE), P(Params), P(Source), C.c_void_p, P(C.c_void_p)]
     lib.sg_step.argtypes = [C.c_void_p, C.c_int, P(Stats)]
     lib.sg_solve_batch.argtypes = [P(C.c_void_p), C.c_int, C.c_int, P(Stats)]
     lib.sg_get_field.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int]
@@ -126,7 +132,7 @@ def load_library(path: Optional[str] = None):
     lib.sg_last_error.argtypes = [C.c_void_p]
     lib.sg_last_error.restype = C.c_char_p
     lib.sg_sample_field.restype = C.c_int
-    for f in ("sg_setup", "sg_step", "sg_solve_batch", "sg_get_field", "sg_get_moments", "sg_get_state",
+    for f in ("sg_setup", "sg_setup_mesh", "sg_step", "sg_solve_batch", "sg_get_field", "sg_get_moments", "sg_get_state",
               "sg_set_state", "sg_step_host", "sg_get_sizes", "sg_get_iters", "sg_destroy"):
         getattr(lib, f).restype = C.c_int
     _LIB = lib
@@ -150,9 +156,12 @@ class Solver:
     def __init__(self, prob, precision: int = SG_FP64, warm: int = SG_WARM_PREV, stream=None,
                  tol: Optional[float] = None, inner_tol: float = 0.0, inner_max_iter: int = 0,
                  max_iter: Optional[int] = None, autotune: bool = False, warm_train_steps: int = 0,
-                 warm_lr: float = 0.0, kl_modes=None, kl_lambdas=None, precond: int = SG_PC_NN2):
+                 warm_lr: float = 0.0, kl_modes=None, kl_lambdas=None, precond: int = SG_PC_NN2,
+                 mesh=None):
         """kl_modes / kl_lambdas: the caller's KL (M x 2 N^2 eigenfunction values at the element
-        centroids in the library's element order, and M eigenvalues), or None for the analytic one."""
+        centroids in the library's element order, and M eigenvalues), or None for the analytic one.
+        mesh: (xy (nv, 2), dirichlet (nv,), tri (ne, 3), part (ne,)) of a partitioned triangle mesh
+        (sg_setup_mesh; prob.N and prob.s are then unused, kl_modes hold the triangle centroids)."""
         self.lib = load_library()
         self.prob = prob
         s = prob.source
@@ -176,8 +185,20 @@ class Solver:
             st = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
         self.stream = st
         h = C.c_void_p()
-        rc = self.lib.sg_setup(C.byref(self._grid), C.byref(self._kl), C.byref(self._pce), C.byref(self._prm),
-                               C.byref(self._src), C.c_void_p(st), C.byref(h))
+        if mesh is not None:
+            xy, dirichlet, tri, part = mesh
+            xy = np.ascontiguousarray(xy, dtype=np.float64)
+            dirichlet = np.ascontiguousarray(dirichlet, dtype=np.uint8)
+            tri = np.ascontiguousarray(tri, dtype=np.int32)
+            part = np.ascontiguousarray(part, dtype=np.int32)
+            self._mesh_arrays = (xy, dirichlet, tri, part)   # kept alive for the duration of sg_setup_mesh
+            self._mesh = Mesh(xy.shape[0], xy.ctypes.data, dirichlet.ctypes.data, tri.shape[0], tri.ctypes.data,
+                              part.ctypes.data)
+            rc = self.lib.sg_setup_mesh(C.byref(self._mesh), C.byref(self._kl), C.byref(self._pce),
+                                        C.byref(self._prm), C.byref(self._src), C.c_void_p(st), C.byref(h))
+        else:
+            rc = self.lib.sg_setup(C.byref(self._grid), C.byref(self._kl), C.byref(self._pce), C.byref(self._prm),
+                                   C.byref(self._src), C.c_void_p(st), C.byref(h))
         if rc != 0:
             raise SGError(rc, self.lib.sg_last_error(None).decode())
         self.h = h

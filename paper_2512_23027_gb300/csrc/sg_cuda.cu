@@ -35,6 +35,7 @@
 #include "../../include/sg.h"
 #include "sg_host.hpp"
 #include "sg_kernels.cuh"
+#include "sg_mesh.cuh"
 
 using sgk::CgCtl;
 using sgk::Op;
@@ -172,6 +173,15 @@ struct sg_handle_s {
   float *wX = nullptr, *wy = nullptr, *wt = nullptr;
   int warm_train = 20, warm_epochs = 4;
   float warm_lr = 1e-3f;
+  // general partitions of unstructured meshes (sg_setup_mesh): sparse rows of the local layout (FP64
+  // and FP32 values), rows per pattern and subdomain, and the dense inverses of the subdomains' mean
+  // operators per pattern (0 Dirichlet, 1 Neumann, 2 every free vertex) in the subdomain-solve type
+  bool mesh = false;
+  int *m_rp = nullptr, *m_col = nullptr, *m_npat = nullptr;
+  double *m_kv = nullptr, *m_mv = nullptr;
+  float *m_kv32 = nullptr, *m_mv32 = nullptr;
+  double* m_ainv[3] = {nullptr, nullptr, nullptr};
+  float* m_ainv32[3] = {nullptr, nullptr, nullptr};
   // per-kernel timing (host-driven enqueue only): 0 off, 1 line kernel, 2 fused apply kernel
   int kprof = 0;
   double kprof_ms = 0.0;
@@ -181,6 +191,11 @@ struct sg_handle_s {
   template <typename T>
   Op<T> op(int s0 = 0) const {
     Op<T> o;
+    if (mesh) {  // the mesh apply reads the sparse rows; the Op only carries the first subdomain
+      o.cls = cls + (size_t)s0 * pr.nl;
+      o.nl = pr.nl; o.P = pr.P; o.PI = pr.PI;
+      return o;
+    }
     o.cls = cls + (size_t)s0 * pr.nl;
     o.cells = cells + (size_t)s0 * pr.nl;
     if constexpr (sizeof(T) == 8) {
@@ -196,6 +211,19 @@ struct sg_handle_s {
     o.fP = sgk::make_fd(pr.P); o.fPI = sgk::make_fd(pr.PI); o.fL = sgk::make_fd(pr.L);
     o.fLm1 = sgk::make_fd(pr.L - 1); o.fLP = sgk::make_fd(pr.L * pr.P);
     return o;
+  }
+  template <typename T>
+  sgm::Rows<T> mrows() const {
+    sgm::Rows<T> r;
+    r.rp = m_rp; r.col = m_col;
+    if constexpr (sizeof(T) == 8) {
+      r.kv = (const T*)m_kv; r.mv = (const T*)m_mv; r.gk_v = (const T*)gk_v;
+    } else {
+      r.kv = (const T*)m_kv32; r.mv = (const T*)m_mv32; r.gk_v = (const T*)gk_v32;
+    }
+    r.gk_ptr = gk_ptr; r.gk_i = gk_i; r.gk_j = gk_j;
+    r.nl = pr.nl; r.P = pr.P; r.PI = pr.PI;
+    return r;
   }
   long long nloc() const { return (long long)pr.nsub * pr.nl; }
   long long nvec() const { return (long long)pr.nsub * pr.nl * pr.P; }
@@ -506,6 +534,19 @@ static void apply_cfg(const sgh::Problem& pr, int nb, int* TL, int* NT, size_t* 
 template <typename T, typename TO, bool FUSEDP, bool DOT>
 static int launch_apply_k(sg_handle h, cudaStream_t st, const Op<T>& op, int nb, int R, const T* xm, const T* xk,
                           TO* y, const TO* add, double cm, double ck, int mask, T* p0, T* p1, const T* z) {
+  if (h->mesh) {  // general partitions: sparse-row apply (the fused-CG forms belong to the line solvers)
+    if constexpr (FUSEDP || DOT) {
+      h->err = "fused CG apply on a mesh problem";
+      return SG_ENOTSUP;
+    } else {
+      const int s0 = (int)((op.cls - h->cls) / h->pr.nl);
+      const long long n = (long long)nb * h->pr.nl * h->pr.P;
+      sgk::k_mapply<T, TO><<<nblk(n), 256, 0, st>>>(h->mrows<T>(), h->cls, s0, nb, R, xm, xk, y, add, (T)cm, (T)ck,
+                                                     mask, nullptr);
+      CKL();
+      return SG_OK;
+    }
+  }
   int TL, NT, stage, nods;
   size_t sm;
   apply_cfg<T>(h->pr, nb, &TL, &NT, &sm, &stage, &nods);
@@ -749,6 +790,7 @@ static int ensure_ws(sg_handle h, int nb) {
     RET(dalloc(h, &w.p0, len)); RET(dalloc(h, &w.p1, len)); RET(dalloc(h, &w.q, len));
     w.cap_nb = nb;
   }
+  if (h->mesh) return ensure_ctl(h, nb, 1, 1);  // one p.q, r.z, r.r per problem
   int TL, NT, stage;
   size_t sm;
   apply_cfg<T>(h->pr, nb, &TL, &NT, &sm, &stage);
@@ -775,7 +817,11 @@ static int kprof_end(sg_handle h, Ctx& cx, int which) {
 }
 
 template <typename T>
+static int enq_inner_mesh(sg_handle h, Ctx& cx, int pat, int nb, int R, int s0, const T* rhs, double tol_override);
+
+template <typename T>
 static int enq_inner(sg_handle h, Ctx& cx, int pat, int nb, int R, int s0, const T* rhs, double tol_override = 0.0) {
+  if (h->mesh) return enq_inner_mesh<T>(h, cx, pat, nb, R, s0, rhs, tol_override);
   const auto& pr = h->pr;
   auto& w = wsT<T>(h);
   const long long n = (long long)pr.nl * pr.P * nb;
@@ -919,6 +965,56 @@ static int enq_inner(sg_handle h, Ctx& cx, int pat, int nb, int R, int s0, const
   });
 }
 
+// The same batched solve on the sparse rows of a mesh problem: CG preconditioned by the dense inverse
+// of each subdomain's mean operator on the pattern's rows; per iteration the apply (active problems),
+// p.q, the update, the preconditioner, r.r and r.z, the control (loop condition) and the new
+// direction.  Same stopping rule, tolerances and iteration cap as the line solvers.
+template <typename T>
+static int enq_inner_mesh(sg_handle h, Ctx& cx, int pat, int nb, int R, int s0, const T* rhs, double tol_override) {
+  const auto& pr = h->pr;
+  auto& w = wsT<T>(h);
+  const T* Ainv = pat < 0 || pat > 2 ? nullptr : sizeof(T) == 8 ? (const T*)h->m_ainv[pat] : (const T*)h->m_ainv32[pat];
+  if (pat < 0 || pat > 2 || !Ainv || nb < 1 || R < 1 || s0 < 0 || w.cap_nb < nb || h->ctl_cap_nb < nb ||
+      s0 + (nb + R - 1) / R > pr.nsub) {
+    h->err = "mesh subdomain solve: pattern, workspace or batch out of range";
+    return SG_EINVAL;
+  }
+  const long long len = (long long)pr.nl * pr.P, n = len * nb;
+  const int mask = pat == 0 ? sgk::MASK_I : pat == 1 ? sgk::MASK_N : sgk::MASK_FREE;
+  const double tol = tol_override > 0.0 ? tol_override : (sizeof(T) == 8 ? h->inner_tol : h->inner_tol32);
+  const double tol2 = tol * tol;
+  const double bb_min = sizeof(T) == 8 ? 1e-280 : 1e-60;
+  const int imax = sizeof(T) == 8 ? h->inner_max : std::min(h->inner_max, 120);
+  const int* npat = h->m_npat + (size_t)pat * pr.nsub;
+  const sgm::Rows<T> rows = h->mrows<T>();
+  const T am = (T)h->am, bk = (T)h->bk;
+  cudaStream_t st = cx.st;
+  CK(cudaMemcpyAsync(w.r, rhs, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(w.x, 0, sizeof(T) * n, st));
+  sgk::k_mdense<T><<<nblk(n), 256, 0, st>>>(Ainv, npat, s0, nb, R, pr.nl, pr.P, w.r, w.z, nullptr);
+  sgk::k_mdot2<T><<<nb, sgk::MDOT_THREADS, 0, st>>>(len, w.r, w.r, h->ctl.part_rr, w.r, w.z, h->ctl.part_rz, nullptr);
+  cudaGraphConditionalHandle hnd;
+  RET(make_handle(h, cx, &hnd));
+  sgk::k_mcg_ctl<<<1, 256, 0, st>>>(nb, h->ctl, 1, tol2, bb_min, imax, hnd, cx.capture ? 1 : 0);
+  sgk::k_mcg_dir<T><<<nblk(n), 256, 0, st>>>(len, nb, h->ctl, 1, w.z, w.p0);
+  CKL();
+  return cond_node(h, cx, hnd, true, h->ctl.cond, [&](Ctx& c2) -> int {
+    cudaStream_t s = c2.st;
+    sgk::k_mapply<T, T><<<nblk(n), 256, 0, s>>>(rows, h->cls, s0, nb, R, w.p0, w.p0, w.q, nullptr, am, bk, mask,
+                                                 h->ctl.active);
+    sgk::k_mdot2<T><<<nb, sgk::MDOT_THREADS, 0, s>>>(len, w.p0, w.q, h->ctl.part_pq, nullptr, nullptr, nullptr,
+                                                      h->ctl.active);
+    sgk::k_mcg_upd<T><<<nblk(n), 256, 0, s>>>(len, nb, h->ctl, w.x, w.r, w.p0, w.q);
+    sgk::k_mdense<T><<<nblk(n), 256, 0, s>>>(Ainv, npat, s0, nb, R, pr.nl, pr.P, w.r, w.z, h->ctl.active);
+    sgk::k_mdot2<T><<<nb, sgk::MDOT_THREADS, 0, s>>>(len, w.r, w.r, h->ctl.part_rr, w.r, w.z, h->ctl.part_rz,
+                                                      h->ctl.active);
+    sgk::k_mcg_ctl<<<1, 256, 0, s>>>(nb, h->ctl, 0, tol2, bb_min, imax, hnd, c2.capture ? 1 : 0);
+    sgk::k_mcg_dir<T><<<nblk(n), 256, 0, s>>>(len, nb, h->ctl, 0, w.z, w.p0);
+    CKL();
+    return SG_OK;
+  });
+}
+
 // ---------------------------------------------------------------------------------------------
 // Interface operators
 // ---------------------------------------------------------------------------------------------
@@ -955,7 +1051,7 @@ static int enq_schur(sg_handle h, Ctx& cx, const double* p, double* q) {
     RET((launch_apply<float, double, false, false>(h, st, o32, nsub, 1, h->ws32.x, h->ws32.x, h->wb, h->wb, h->am,
                                                    h->bk, sgk::MASK_G)));
   }
-  sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, h->Dw, h->wb, q, 0);
+  sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, pr.mo, h->Dw, h->wb, q, 0);
   CKL();
   return SG_OK;
 }
@@ -980,13 +1076,13 @@ static int enq_precond_t(sg_handle h, Ctx& cx, const double* r, double* z) {
   if (pr.nC > 0) {
     // S_cr t = (K~ [y; t; 0])_c ;  d = sum_s B^T (w_c - S_cr t) ;  u_c = F_cc^{-1} d  (FP64)
     RET((launch_apply<T, T, false, false>(h, st, op, nsub, 1, v, v, wy, nullptr, h->am, h->bk, sgk::MASK_C)));
-    sgk::k_corner_rhs<T><<<nblk((long long)pr.nC * P), 256, 0, st>>>(pr.nC, P, h->cowners, h->wc, wy, h->dC);
+    sgk::k_corner_rhs<T><<<nblk((long long)pr.nC * P), 256, 0, st>>>(pr.nC, P, h->cowners, pr.mo, h->wc, wy, h->dC);
     sgk::k_gemv<<<nblk((long long)h->nCd * 32), 256, 0, st>>>(h->nCd, h->Finv, h->dC, h->uC);
   }
   sgk::k_coarse_extend<T><<<nblk((long long)nsub * pr.nGam * P), 256, 0, st>>>(
-      nsub, nl, P, pr.nGam, pr.max_corner, h->cls, h->cidx, h->gam_ln, h->n_gam, h->loc_corner, h->n_loc_corner,
-      h->Phi, h->uC, v, h->we);
-  sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, h->Dw, h->we, z, 1);
+      nsub, nl, P, pr.nGam, pr.max_corner, h->cls, h->cidx, h->gam_ln, h->n_gam, h->loc_corner, pr.mc,
+      h->n_loc_corner, h->Phi, h->uC, v, h->we);
+  sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, pr.mo, h->Dw, h->we, z, 1);
   CKL();
   return SG_OK;
 }
@@ -1003,7 +1099,7 @@ static int enq_precond_lumped(sg_handle h, Ctx& cx, const double* r, double* z) 
                                                   sgk::MASK_G, 1);
   RET((launch_apply<double, double, false, false>(h, st, h->op<double>(), pr.nsub, 1, h->wa, h->wa, h->we, nullptr,
                                                   h->am, h->bk, sgk::MASK_G)));
-  sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, pr.P, h->owners, h->Dw, h->we, z, 1);
+  sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, pr.P, h->owners, pr.mo, h->Dw, h->we, z, 1);
   CKL();
   return SG_OK;
 }
@@ -1016,7 +1112,7 @@ static int enq_precond_nn1(sg_handle h, Ctx& cx, const double* r, double* z) {
   T* wr = sizeof(T) == 8 ? (T*)h->wa : (T*)h->fa;
   sgk::k_gather<T><<<nblk(n), 256, 0, st>>>(pr.nsub, 1, pr.nl, pr.P, h->cls, h->gidx, h->Dw, r, wr, sgk::MASK_G, 1);
   RET(enq_inner<T>(h, cx, 2, pr.nsub, 1, 0, wr, sizeof(T) == 8 ? 0.0 : h->prec_tol32));
-  sgk::k_scatter<T><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, pr.P, h->owners, h->Dw, wsT<T>(h).x, z, 1);
+  sgk::k_scatter<T><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, pr.P, h->owners, pr.mo, h->Dw, wsT<T>(h).x, z, 1);
   CKL();
   return SG_OK;
 }
@@ -1098,8 +1194,8 @@ static int enq_warm_guess(sg_handle h, Ctx& cx) {
   const auto& pr = h->pr;
   cudaStream_t st = cx.st;
   const int nr = (int)h->nGd();
-  sgk::k_scatter<double><<<nblk(nr), 256, 0, st>>>(pr.nG, pr.P, h->owners, h->Dw, h->V, h->vG, 1);
-  sgk::k_scatter<double><<<nblk(nr), 256, 0, st>>>(pr.nG, pr.P, h->owners, h->Dw, h->A, h->aG, 1);
+  sgk::k_scatter<double><<<nblk(nr), 256, 0, st>>>(pr.nG, pr.P, h->owners, pr.mo, h->Dw, h->V, h->vG, 1);
+  sgk::k_scatter<double><<<nblk(nr), 256, 0, st>>>(pr.nG, pr.P, h->owners, pr.mo, h->Dw, h->A, h->aG, 1);
   sgk::k_wfeat<<<nblk(nr), 256, 0, st>>>(nr, pr.dt, h->xG, h->wE0, h->wE1, h->wE2, h->wE3, h->vG, h->aG, h->wX,
                                          h->wpred, h->wscale);
   sgk::k_mlp<false><<<(nr + sgk::NN_ROWS - 1) / sgk::NN_ROWS, sgk::NN_ROWS, 0, st>>>(nr, h->wX, nullptr, h->wctl.wb, h->wy,
@@ -1225,7 +1321,7 @@ static int enq_step(sg_handle h, Ctx& cx, bool ext) {
     if (h->a6_rec)
       sgk::k_wacc<<<nblk(n), 256, 0, st>>>(n, P, h->cls, nullptr, 1, h->wd, h->ws32.x, h->Wrec);
   }
-  sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, h->Dw, h->wc, h->gG, 0);
+  sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, pr.mo, h->Dw, h->wc, h->gG, 0);
   CKL();
   // a3: initial guess -- previous solution in xG (Alg. 1), or the learned predictor
   if (h->warm == SG_WARM_LEARNED) RET(enq_warm_guess(h, cx));
@@ -1482,7 +1578,7 @@ static int build_coarse_t(sg_handle h) {
     const long long n = len * nb;
     const Op<double> op = h->op<double>(s0);
     CK(cudaMemsetAsync(e, 0, sizeof(double) * n, st));
-    sgk::k_coarse_units<<<nblk((long long)nb), 256, 0, st>>>(ns, R, nl, P, s0, h->loc_corner, h->n_loc_corner, e);
+    sgk::k_coarse_units<<<nblk((long long)nb), 256, 0, st>>>(ns, R, nl, P, s0, h->loc_corner, pr.mc, h->n_loc_corner, e);
     RET((launch_apply<double, double, false, false>(h, st, op, nb, R, e, e, rhs, nullptr, -h->am, -h->bk, sgk::MASK_N)));
     const T* rhs_in = reinterpret_cast<const T*>(rhs);
     if (sizeof(T) != 8) {
@@ -1495,7 +1591,7 @@ static int build_coarse_t(sg_handle h) {
                                                                             h->gam_ln, h->n_gam, v, h->Phi);
     sgk::k_add_conv<T><<<nblk(n), 256, 0, st>>>(n, v, e, ve);
     RET((launch_apply<double, double, false, false>(h, st, op, nb, R, ve, ve, y, nullptr, h->am, h->bk, sgk::MASK_C)));
-    sgk::k_coarse_fs<<<nblk((long long)nb * R), 256, 0, st>>>(ns, s0, R, nl, P, h->loc_corner, h->n_loc_corner, y, Fs);
+    sgk::k_coarse_fs<<<nblk((long long)nb * R), 256, 0, st>>>(ns, s0, R, nl, P, h->loc_corner, pr.mc, h->n_loc_corner, y, Fs);
     CKL();
   }
   std::vector<double> hFs((size_t)nsub * R * R);
@@ -1513,9 +1609,9 @@ static int build_coarse_t(sg_handle h) {
   for (int s = 0; s < nsub; ++s) {
     const int nc = pr.n_loc_corner[s];
     for (int a = 0; a < nc; ++a) {
-      const int ga = pr.cidx[(size_t)s * nl + pr.loc_corner[s * 4 + a]];
+      const int ga = pr.cidx[(size_t)s * nl + pr.loc_corner[s * pr.mc + a]];
       for (int b = 0; b < nc; ++b) {
-        const int gb = pr.cidx[(size_t)s * nl + pr.loc_corner[s * 4 + b]];
+        const int gb = pr.cidx[(size_t)s * nl + pr.loc_corner[s * pr.mc + b]];
         for (int m = 0; m < P; ++m)
           for (int q = 0; q < P; ++q)
             F[(size_t)(ga * P + m) * nCd + gb * P + q] += hFs[((size_t)s * R + a * P + m) * R + b * P + q];
@@ -1570,7 +1666,7 @@ static int initial_state(sg_handle h) {
   if (h->nload)
     sgk::k_point_load<<<nblk(h->nload), 256, 0, st>>>(h->nload, h->load_node, h->load_w, nullptr, pr.dt, 0.0,
                                                        pr.src.freq, P, h->wa);
-  sgk::k_assemble_gamma<<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, h->wa);
+  sgk::k_assemble_gamma<<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, pr.mo, h->wa);
   CK(cudaMemsetAsync(h->A, 0, sizeof(double) * n, st));
   double rr, rr0, pq;
   RET(ldot_w(h, h->wa, h->wa, &rr));
@@ -1579,7 +1675,7 @@ static int initial_state(sg_handle h) {
   for (int it = 0; it < 500 && rr > 1e-30 * rr0 && rr0 > 0.0; ++it) {
     RET((launch_apply<double, double, false, false>(h, st, op, pr.nsub, 1, h->wb, h->wb, h->wc, nullptr, 1.0, 0.0,
                                                     sgk::MASK_FREE)));
-    sgk::k_assemble_gamma<<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, h->wc);
+    sgk::k_assemble_gamma<<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, pr.mo, h->wc);
     RET(ldot_w(h, h->wb, h->wc, &pq));
     const double a = rr / pq;
     sgk::k_axpby<double><<<nblk(n), 256, 0, st>>>(n, 1.0, h->A, a, h->wb, h->A);
@@ -1590,7 +1686,7 @@ static int initial_state(sg_handle h) {
     rr = rn;
   }
   CKL();
-  sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, h->Dw, h->U, h->xG, 1);
+  sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, st>>>(pr.nG, P, h->owners, pr.mo, h->Dw, h->U, h->xG, 1);
   CKL();
   return SG_OK;
 }
@@ -1833,9 +1929,9 @@ static int build_checked(sgh::Problem& pr, std::string& err, const sg_grid* grid
   return SG_OK;
 }
 
-static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const sg_pce* pce,
-                      const sg_params* prm, const sg_source* src) {
-  sgh::SourceDesc sd{src ? src->kind : 0, src ? src->x0 : 0.5, src ? src->y0 : 0.5,
+// Set-up pieces shared by the structured grid (sg_setup) and the general partitions (sg_setup_mesh).
+static int check_source(sg_handle h, const sg_source* src, sgh::SourceDesc* out) {
+  const sgh::SourceDesc sd{src ? src->kind : 0, src ? src->x0 : 0.5, src ? src->y0 : 0.5,
                      src ? src->width : 0.05, src ? src->freq : 10.0, src ? src->amp : 1.0};
   if (sd.kind < 0 || sd.kind > 2) { h->err = "source kind"; return SG_EINVAL; }
   if (sd.kind == 1 && !(sd.width > 0)) { h->err = "pulse width must be positive"; return SG_EINVAL; }
@@ -1843,8 +1939,12 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
     h->err = "ricker source outside the unit square or non-positive frequency";
     return SG_EINVAL;
   }
-  RET(build_checked(h->pr, h->err, grid, kl, pce, prm, sd));
-  auto& pr = h->pr;
+  *out = sd;
+  return SG_OK;
+}
+
+static int apply_params(sg_handle h, const sg_params* prm) {
+  const auto& pr = h->pr;
   // the compute path: FP64, or FP32 subdomain solves inside the FP64 outer PCG (SG_MIXED, SG_FP32 and
   // SG_BF16 differ only in the mean-operator preconditioner, chosen in build_mma_precond)
   h->precision = prm->precision == SG_FP64 ? SG_FP64 : SG_MIXED;
@@ -1871,6 +1971,10 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   h->warm_lr = prm->warm_lr > 0 ? (float)prm->warm_lr : 1e-3f;
   h->am = 1.0 / (ZETA * pr.dt * pr.dt) + pr.alpha0 * GAMMA / (ZETA * pr.dt);
   h->bk = 1.0 + pr.alpha1 * GAMMA / (ZETA * pr.dt);
+  return SG_OK;
+}
+
+static int init_device(sg_handle h) {
   // first CUDA call: every argument check is above
   CK(cudaGetDevice(&h->dev));
   if (!h->st) {  // private stream when the caller passes none
@@ -1891,6 +1995,66 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
     CK(cudaMemcpyToSymbol(sgk::g_nlaunch, &g_nlaunch_dev, sizeof(void*)));
   }
   h->nlaunch = g_nlaunch_dev;
+  return SG_OK;
+}
+
+// triple products, interface / corner / output maps, point load, node weights and the step buffers
+static int upload_common(sg_handle h) {
+  const auto& pr = h->pr;
+  RET(upload(h, &h->gk_ptr, pr.gk_ptr)); RET(upload(h, &h->gk_i, pr.gk_i)); RET(upload(h, &h->gk_j, pr.gk_j));
+  {
+    std::vector<unsigned> pk(pr.gk_i.size());
+    for (size_t e = 0; e < pk.size(); ++e) pk[e] = (unsigned)pr.gk_i[e] | ((unsigned)pr.gk_j[e] << 16);
+    RET(upload(h, &h->gk_pk, pk));
+  }
+  RET(upload(h, &h->gk_v, pr.gk_v));
+  RET(upload(h, &h->gidx, pr.gidx)); RET(upload(h, &h->cidx, pr.cidx));
+  RET(upload(h, &h->owners, pr.owners)); RET(upload(h, &h->cowners, pr.cowners));
+  RET(upload(h, &h->Dw, pr.Dw)); RET(upload(h, &h->gam_ln, pr.gam_ln)); RET(upload(h, &h->n_gam, pr.n_gam));
+  RET(upload(h, &h->loc_corner, pr.loc_corner)); RET(upload(h, &h->n_loc_corner, pr.n_loc_corner));
+  RET(upload(h, &h->free_owner, pr.free_owner)); RET(upload(h, &h->free_of_local, pr.free_of_local));
+  RET(upload(h, &h->load_node, pr.load_node)); RET(upload(h, &h->load_w, pr.load_w));
+  h->nload = (int)pr.load_node.size();
+  RET(dalloc(h, &h->nodew, h->nloc()));
+  sgk::k_node_weight<<<nblk(h->nloc()), 256, 0, h->st>>>((int)h->nloc(), h->cls, h->gidx, h->Dw, h->nodew);
+  const long long n = h->nvec();
+  for (double** p : {&h->U, &h->V, &h->A, &h->um, &h->uc, &h->xm, &h->ft, &h->Unew, &h->wa, &h->wb, &h->wc, &h->wd, &h->we})
+    RET(dalloc(h, p, n));
+  h->a6_rec = h->precision == SG_MIXED && std::getenv("SG_A6_SOLVE") == nullptr;
+  if (h->a6_rec) RET(dalloc(h, &h->Wrec, n));
+  RET(dalloc(h, &h->fa, n)); RET(dalloc(h, &h->fb, n));
+  RET(dalloc(h, &h->fext, pr.n_free));
+  RET(dalloc(h, &h->outbuf, 2LL * pr.n_free * pr.P));
+  for (double** p : {&h->xG, &h->rG, &h->zG, &h->pG, &h->qG, &h->gG, &h->roG}) RET(dalloc(h, p, h->nGd()));
+  RET(dalloc(h, &h->opart, NB_OUT)); RET(dalloc(h, &h->opart2, NB_OUT));
+  RET(dalloc(h, &h->scal, 16));
+  RET(dalloc(h, &h->octl, 1)); RET(dalloc(h, &h->omirror, 2));
+  RET(dalloc(h, &h->stepctr, 1)); RET(dalloc(h, &h->rec_iters, REC_CAP)); RET(dalloc(h, &h->rec_rel, REC_CAP));
+  RET(dalloc(h, &h->rec_flags, 1));
+  RET(ensure_ws<double>(h, pr.nsub));
+  RET(ensure_ws<float>(h, pr.nsub));
+  CKL();
+  return SG_OK;
+}
+
+// coarse space, warm start, initial state
+static int finish_setup(sg_handle h) {
+  if (h->pc == SG_PC_NN2) RET(build_coarse(h));  // the one-level preconditioners have no coarse space
+  if (h->warm == SG_WARM_LEARNED) RET(warm_setup(h));
+  RET(initial_state(h));
+  RET(warm_reset_history(h));
+  CK(cudaStreamSynchronize(h->st));
+  return SG_OK;
+}
+
+static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const sg_pce* pce,
+                      const sg_params* prm, const sg_source* src) {
+  sgh::SourceDesc sd;
+  RET(check_source(h, src, &sd));
+  RET(build_checked(h->pr, h->err, grid, kl, pce, prm, sd));
+  auto& pr = h->pr;
+  RET(apply_params(h, prm));
+  RET(init_device(h));
   // shared-memory opt-in of the apply variants
   {
     const int lim = (int)SMEM_TILE;
@@ -1971,39 +2135,7 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
     };
     RET(upload(h, &h->kapE2, split(pr.kapE))); RET(upload(h, &h->kapN2, split(pr.kapN)));
   }
-  RET(upload(h, &h->gk_ptr, pr.gk_ptr)); RET(upload(h, &h->gk_i, pr.gk_i)); RET(upload(h, &h->gk_j, pr.gk_j));
-  {
-    std::vector<unsigned> pk(pr.gk_i.size());
-    for (size_t e = 0; e < pk.size(); ++e) pk[e] = (unsigned)pr.gk_i[e] | ((unsigned)pr.gk_j[e] << 16);
-    RET(upload(h, &h->gk_pk, pk));
-  }
-  RET(upload(h, &h->gk_v, pr.gk_v));
-  RET(upload(h, &h->gidx, pr.gidx)); RET(upload(h, &h->cidx, pr.cidx));
-  RET(upload(h, &h->owners, pr.owners)); RET(upload(h, &h->cowners, pr.cowners));
-  RET(upload(h, &h->Dw, pr.Dw)); RET(upload(h, &h->gam_ln, pr.gam_ln)); RET(upload(h, &h->n_gam, pr.n_gam));
-  RET(upload(h, &h->loc_corner, pr.loc_corner)); RET(upload(h, &h->n_loc_corner, pr.n_loc_corner));
-  RET(upload(h, &h->free_owner, pr.free_owner)); RET(upload(h, &h->free_of_local, pr.free_of_local));
-  RET(upload(h, &h->load_node, pr.load_node)); RET(upload(h, &h->load_w, pr.load_w));
-  h->nload = (int)pr.load_node.size();
-  RET(dalloc(h, &h->nodew, h->nloc()));
-  sgk::k_node_weight<<<nblk(h->nloc()), 256, 0, h->st>>>((int)h->nloc(), h->cls, h->gidx, h->Dw, h->nodew);
-  const long long n = h->nvec();
-  for (double** p : {&h->U, &h->V, &h->A, &h->um, &h->uc, &h->xm, &h->ft, &h->Unew, &h->wa, &h->wb, &h->wc, &h->wd, &h->we})
-    RET(dalloc(h, p, n));
-  h->a6_rec = h->precision == SG_MIXED && std::getenv("SG_A6_SOLVE") == nullptr;
-  if (h->a6_rec) RET(dalloc(h, &h->Wrec, n));
-  RET(dalloc(h, &h->fa, n)); RET(dalloc(h, &h->fb, n));
-  RET(dalloc(h, &h->fext, pr.n_free));
-  RET(dalloc(h, &h->outbuf, 2LL * pr.n_free * pr.P));
-  for (double** p : {&h->xG, &h->rG, &h->zG, &h->pG, &h->qG, &h->gG, &h->roG}) RET(dalloc(h, p, h->nGd()));
-  RET(dalloc(h, &h->opart, NB_OUT)); RET(dalloc(h, &h->opart2, NB_OUT));
-  RET(dalloc(h, &h->scal, 16));
-  RET(dalloc(h, &h->octl, 1)); RET(dalloc(h, &h->omirror, 2));
-  RET(dalloc(h, &h->stepctr, 1)); RET(dalloc(h, &h->rec_iters, REC_CAP)); RET(dalloc(h, &h->rec_rel, REC_CAP));
-  RET(dalloc(h, &h->rec_flags, 1));
-  RET(ensure_ws<double>(h, pr.nsub));
-  RET(ensure_ws<float>(h, pr.nsub));
-  CKL();
+  RET(upload_common(h));
   // shared-memory fit of the hot kernels at this subdomain size (per precision in use)
   if (!tiles_fit(pr, h->precision)) {
     h->err = "subdomain too large for the shared-memory tiles of this build (H = " + std::to_string(pr.H) + " cells)";
@@ -2013,12 +2145,68 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   RET(build_mma_precond(h));
   RET(build_line_tc(h));
   if (prm->autotune) RET(autotune(h));
-  if (h->pc == SG_PC_NN2) RET(build_coarse(h));  // the one-level preconditioners have no coarse space
-  if (h->warm == SG_WARM_LEARNED) RET(warm_setup(h));
-  RET(initial_state(h));
-  RET(warm_reset_history(h));
-  CK(cudaStreamSynchronize(h->st));
-  return SG_OK;
+  return finish_setup(h);
+}
+
+// General partition of a triangle mesh: host tables (vertex classes with the Sec. 3 corners, sparse
+// rows, maps), the dense mean-operator inverses in the subdomain-solve precision, then the shared
+// uploads, coarse space and initial state.
+static int setup_mesh_impl(sg_handle h, const sg_mesh* m, const sg_kl* kl, const sg_pce* pce, const sg_params* prm,
+                           const sg_source* src) {
+  sgh::SourceDesc sd;
+  RET(check_source(h, src, &sd));
+  if (prm->precision < SG_FP64 || prm->precision > SG_BF16) { h->err = "precision"; return SG_EINVAL; }
+  if (prm->precond < SG_PC_NN2 || prm->precond > SG_PC_LUMPED) { h->err = "precond"; return SG_EINVAL; }
+  if (prm->precision == SG_BF16) {
+    h->err = "SG_BF16: the tensor-core preconditioners need the structured grid";
+    return SG_ENOTSUP;
+  }
+  if (m->nv < 3 || m->ne < 1 || !m->xy || !m->dirichlet || !m->tri || !m->part) {
+    h->err = "mesh: vertices, triangles and partition required";
+    return SG_EINVAL;
+  }
+  sgh::MeshProblem mp;
+  std::string msg = sgh::build_mesh_problem(mp, m->nv, m->xy, m->dirichlet, m->ne, m->tri, m->part, kl->M, kl->sigma,
+                                            kl->bx, kl->by, kl->g0, pce->p, pce->p_in, kl->modes,
+                                            kl->modes ? kl->lambdas : nullptr);
+  if (!msg.empty()) { h->err = msg; return SG_EINVAL; }
+  if (mp.nsub < 2 || mp.nG == 0) { h->err = "mesh: at least two subdomains with an interface are required"; return SG_ENOTSUP; }
+  sgh::MeshRows mr;
+  msg = sgh::mesh_to_problem(h->pr, mr, mp, m->xy, m->tri, prm->dt, prm->alpha0, prm->alpha1, sd);
+  if (!msg.empty()) { h->err = msg; return SG_EINVAL; }
+  auto& pr = h->pr;
+  pr.sigma = kl->sigma; pr.bx = kl->bx; pr.by = kl->by; pr.g0 = kl->g0;
+  h->mesh = true;
+  RET(apply_params(h, prm));
+  // dense inverses of the mean operators (FP64 on the host): Dirichlet and Neumann patterns, and the
+  // all-free pattern for the one-level Neumann-Neumann comparison
+  const int npat = h->pc == SG_PC_NN1 ? 3 : 2;
+  std::vector<double> inv[3];
+  for (int pat = 0; pat < npat; ++pat)
+    if (!sgh::mesh_mean_inverse(pr, mr, pat, h->am, h->bk, inv[pat])) {
+      h->err = "mean operator of a subdomain not positive definite";
+      return SG_ENUMERIC;
+    }
+  RET(init_device(h));
+  RET(upload(h, &h->cls, pr.cls));
+  RET(upload(h, &h->m_rp, mr.row_ptr)); RET(upload(h, &h->m_col, mr.col)); RET(upload(h, &h->m_npat, mr.npat));
+  RET(upload(h, &h->m_kv, mr.kval)); RET(upload(h, &h->m_mv, mr.mval));
+  {
+    std::vector<float> k32(mr.kval.begin(), mr.kval.end()), m32(mr.mval.begin(), mr.mval.end());
+    std::vector<float> g32(pr.gk_v.begin(), pr.gk_v.end());
+    RET(upload(h, &h->m_kv32, k32)); RET(upload(h, &h->m_mv32, m32)); RET(upload(h, &h->gk_v32, g32));
+  }
+  for (int pat = 0; pat < npat; ++pat) {
+    if (h->precision == SG_FP64) {
+      RET(upload(h, &h->m_ainv[pat], inv[pat]));
+    } else {
+      std::vector<float> f(inv[pat].begin(), inv[pat].end());
+      RET(upload(h, &h->m_ainv32[pat], f));
+    }
+    std::vector<double>().swap(inv[pat]);
+  }
+  RET(upload_common(h));
+  return finish_setup(h);
 }
 
 static int fill_stats(sg_handle h, int nsteps, long long inner0, sg_stats* stats) {
@@ -2051,6 +2239,25 @@ int sg_setup(const sg_grid* grid, const sg_kl* kl, const sg_pce* pce, const sg_p
   if (!h) return SG_ENOMEM;
   h->st = (cudaStream_t)stream;
   int rc = setup_impl(h, grid, kl, pce, params, src);
+  if (rc != SG_OK) {
+    g_setup_err = h->err;
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return SG_OK;
+}
+
+int sg_setup_mesh(const sg_mesh* mesh, const sg_kl* kl, const sg_pce* pce, const sg_params* params,
+                  const sg_source* src, void* stream, sg_handle* out) {
+  if (!out) return SG_EINVAL;
+  *out = nullptr;
+  if (!mesh || !kl || !pce || !params) { g_setup_err = "null argument"; return SG_EINVAL; }
+  sg_handle h = new (std::nothrow) sg_handle_s();
+  if (!h) return SG_ENOMEM;
+  h->st = (cudaStream_t)stream;
+  int rc = setup_mesh_impl(h, mesh, kl, pce, params, src);
   if (rc != SG_OK) {
     g_setup_err = h->err;
     free_all(h);
@@ -2364,7 +2571,7 @@ int sg_set_state(sg_handle h, const double* src, int on_device) {
   }
   h->step = (long long)stepd;
   CK(cudaMemcpyAsync(h->stepctr, &h->step, sizeof(long long), cudaMemcpyHostToDevice, h->st));
-  sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, h->st>>>(pr.nG, pr.P, h->owners, h->Dw, h->U, h->xG, 1);
+  sgk::k_scatter<double><<<nblk(h->nGd()), 256, 0, h->st>>>(pr.nG, pr.P, h->owners, pr.mo, h->Dw, h->U, h->xG, 1);
   CKL();
   RET(warm_reset_history(h));
   CK(cudaStreamSynchronize(h->st));

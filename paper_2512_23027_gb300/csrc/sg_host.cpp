@@ -115,6 +115,23 @@ static void parallel_cyclic(int i0, int i1, F&& f) {
   for (auto& x : th) x.join();
 }
 
+// Triple products <psi_i psi_j psi_k> (input mode i, output modes j, k), grouped by the output mode k.
+static void triple_table(Problem& pr, const std::vector<std::vector<int>>& Ain,
+                         const std::vector<std::vector<int>>& Aout) {
+  const int P = (int)Aout.size(), PI = (int)Ain.size(), M = pr.M;
+  pr.gk_ptr.assign(P + 1, 0);
+  pr.gk_i.clear(); pr.gk_j.clear(); pr.gk_v.clear();
+  for (int k = 0; k < P; ++k) {
+    for (int i = 0; i < PI; ++i)
+      for (int j = 0; j < P; ++j) {
+        double v = 1.0;
+        for (int d = 0; d < M && v != 0.0; ++d) v *= hermite_triple(Ain[i][d], Aout[j][d], Aout[k][d]);
+        if (v != 0.0) { pr.gk_i.push_back(i); pr.gk_j.push_back(j); pr.gk_v.push_back(v); }
+      }
+    pr.gk_ptr[k + 1] = (int)pr.gk_v.size();
+  }
+}
+
 std::string build_problem(Problem& pr, int N, int sx, int sy, int M, double sigma, double bx,
                           double by, double g0, int p, int p_in, double dt, double alpha0,
                           double alpha1, const SourceDesc& src, const double* modes,
@@ -135,25 +152,15 @@ std::string build_problem(Problem& pr, int N, int sx, int sy, int M, double sigm
   pr.N = N; pr.s = sx; pr.H = N / sx; pr.L = pr.H + 1; pr.nl = pr.L * pr.L; pr.nsub = sx * sx;
   pr.M = M; pr.p = p; pr.p_in = p_in; pr.sigma = sigma; pr.bx = bx; pr.by = by; pr.g0 = g0;
   pr.dt = dt; pr.alpha0 = alpha0; pr.alpha1 = alpha1; pr.h = 1.0 / N; pr.src = src;
+  pr.mo = 4; pr.mc = 4;  // at most four subdomains meet at a node of the structured partition
   auto Aout = multi_indices(M, p);
   auto Ain = multi_indices(M, p_in);
   pr.P = (int)Aout.size();
   pr.PI = (int)Ain.size();
   pr.alpha_out = Aout;
-  const int P = pr.P, PI = pr.PI, H = pr.H, L = pr.L, nl = pr.nl, nsub = pr.nsub;
+  const int PI = pr.PI, H = pr.H, L = pr.L, nl = pr.nl, nsub = pr.nsub;
 
-  // triple products grouped by output mode k
-  pr.gk_ptr.assign(P + 1, 0);
-  pr.gk_i.clear(); pr.gk_j.clear(); pr.gk_v.clear();
-  for (int k = 0; k < P; ++k) {
-    for (int i = 0; i < PI; ++i)
-      for (int j = 0; j < P; ++j) {
-        double v = 1.0;
-        for (int d = 0; d < M && v != 0.0; ++d) v *= hermite_triple(Ain[i][d], Aout[j][d], Aout[k][d]);
-        if (v != 0.0) { pr.gk_i.push_back(i); pr.gk_j.push_back(j); pr.gk_v.push_back(v); }
-      }
-    pr.gk_ptr[k + 1] = (int)pr.gk_v.size();
-  }
+  triple_table(pr, Ain, Aout);
 
   // KL modes: products of 1-D eigenpairs, top M by lambda, ties -> lower y index, then x index
   std::vector<Eig1> ex = eig1d(bx > 0 ? bx : 1.0, M + 1), ey = eig1d(by > 0 ? by : 1.0, M + 1);
@@ -573,6 +580,277 @@ std::string build_mesh_problem(MeshProblem& mp, int nv, const double* xy, const 
     for (int v : verts) loc[v] = -1;
   }
   return "";
+}
+
+// Every index the device kernels follow stays inside its table: local columns and owners inside the
+// subdomain's rows, interface / corner indices inside their ranges, patterns inside nl.
+static std::string check_mesh_tables(const Problem& pr, const MeshRows& mr) {
+  const long long nloc = (long long)pr.nsub * pr.nl;
+  if ((long long)mr.row_ptr.size() != nloc + 1 || mr.row_ptr[0] != 0) return "mesh tables: row pointers";
+  for (long long r = 0; r < nloc; ++r) {
+    if (mr.row_ptr[r + 1] < mr.row_ptr[r]) return "mesh tables: row pointers";
+    for (int q = mr.row_ptr[r]; q < mr.row_ptr[r + 1]; ++q)
+      if (mr.col[q] < 0 || mr.col[q] >= pr.nl || pr.cls[(size_t)(r / pr.nl) * pr.nl + mr.col[q]] == DIRICHLET)
+        return "mesh tables: column outside the subdomain's free rows";
+  }
+  if ((long long)mr.col.size() != mr.row_ptr[nloc] || mr.mval.size() != mr.col.size() ||
+      mr.kval.size() != mr.col.size() * (size_t)pr.PI)
+    return "mesh tables: entry arrays";
+  for (int s = 0; s < pr.nsub; ++s)
+    for (int pat = 0; pat < 3; ++pat) {
+      const int n = mr.npat[(size_t)pat * pr.nsub + s];
+      if (n < 0 || n > pr.nl) return "mesh tables: pattern rows";
+    }
+  auto in_loc = [&](int o) { return o >= 0 && o < nloc; };
+  for (long long o = 0; o < nloc; ++o) {
+    const int c = pr.cls[o];
+    if ((c == REMAINING || c == CORNER) != (pr.gidx[o] >= 0) || pr.gidx[o] >= pr.nG) return "mesh tables: gidx";
+    if ((c == CORNER) != (pr.cidx[o] >= 0) || pr.cidx[o] >= pr.nC) return "mesh tables: cidx";
+    if ((c != DIRICHLET) != (pr.free_of_local[o] >= 0) || pr.free_of_local[o] >= pr.n_free)
+      return "mesh tables: free_of_local";
+  }
+  for (int g = 0; g < pr.nG; ++g)
+    for (int q = 0; q < pr.mo; ++q) {
+      const int o = pr.owners[(size_t)g * pr.mo + q];
+      if (o != -1 && (!in_loc(o) || pr.gidx[o] != g)) return "mesh tables: owners";
+    }
+  for (int c = 0; c < pr.nC; ++c)
+    for (int q = 0; q < pr.mo; ++q) {
+      const int o = pr.cowners[(size_t)c * pr.mo + q];
+      if (o != -1 && (!in_loc(o) || pr.cidx[o] != c)) return "mesh tables: cowners";
+    }
+  for (int s = 0; s < pr.nsub; ++s) {
+    if (pr.n_gam[s] < 0 || pr.n_gam[s] > pr.nGam || pr.n_loc_corner[s] < 0 || pr.n_loc_corner[s] > pr.mc)
+      return "mesh tables: local interface counts";
+    for (int q = 0; q < pr.n_gam[s]; ++q) {
+      const int a = pr.gam_ln[(size_t)s * pr.nGam + q];
+      if (a < 0 || a >= pr.nl || pr.gidx[(size_t)s * pr.nl + a] < 0) return "mesh tables: gam_ln";
+    }
+    for (int q = 0; q < pr.n_loc_corner[s]; ++q) {
+      const int a = pr.loc_corner[(size_t)s * pr.mc + q];
+      if (a < 0 || a >= pr.nl || pr.cidx[(size_t)s * pr.nl + a] < 0) return "mesh tables: loc_corner";
+    }
+  }
+  for (int f = 0; f < pr.n_free; ++f)
+    if (!in_loc(pr.free_owner[f]) || pr.free_of_local[pr.free_owner[f]] != f) return "mesh tables: free_owner";
+  for (int o : pr.load_node)
+    if (!in_loc(o) || pr.cls[o] == DIRICHLET) return "mesh tables: load_node";
+  return "";
+}
+
+std::string mesh_to_problem(Problem& pr, MeshRows& mr, const MeshProblem& mp, const double* xy, const int* tri,
+                            double dt, double alpha0, double alpha1, const SourceDesc& src) {
+  if (!(dt > 0)) return "params: dt > 0 required";
+  if (mp.nsub < 1 || (int)mp.sub_vptr.size() != mp.nsub + 1) return "mesh: set-up tables missing";
+  const int nsub = mp.nsub, PI = mp.PI, nv = mp.nv;
+  pr = Problem{};
+  pr.nsub = nsub; pr.M = mp.M; pr.p = mp.p; pr.p_in = mp.p_in; pr.P = mp.P; pr.PI = PI;
+  pr.dt = dt; pr.alpha0 = alpha0; pr.alpha1 = alpha1; pr.src = src;
+  pr.kl_lambda = mp.kl_lambda;
+  pr.alpha_out = multi_indices(mp.M, mp.p);
+  triple_table(pr, multi_indices(mp.M, mp.p_in), pr.alpha_out);
+
+  // local layout: the free vertices of each subdomain (they come first in sub_verts)
+  std::vector<int> nfree(nsub, 0), nint(nsub, 0), nrem(nsub, 0), ncor(nsub, 0);
+  int nl = 1;
+  for (int s = 0; s < nsub; ++s) {
+    for (int q = mp.sub_vptr[s]; q < mp.sub_vptr[s + 1]; ++q) {
+      const int c = mp.vclass[mp.sub_verts[q]];
+      if (c == DIRICHLET) break;
+      ++nfree[s];
+      if (c == INTERIOR) ++nint[s];
+      else if (c == REMAINING) ++nrem[s];
+      else ++ncor[s];
+    }
+    nl = std::max(nl, nfree[s]);
+  }
+  pr.nl = nl;
+  pr.nG = mp.nG; pr.nC = mp.nC; pr.n_free = mp.n_free;
+  int mo = 1;
+  for (int v = 0; v < nv; ++v)
+    if (mp.iface_idx[v] >= 0) mo = std::max(mo, mp.vmult[v]);
+  int mc = 1;
+  for (int s = 0; s < nsub; ++s) mc = std::max(mc, ncor[s]);
+  pr.mo = mo; pr.mc = mc;
+  pr.cls.assign((size_t)nsub * nl, DIRICHLET);
+  pr.gidx.assign((size_t)nsub * nl, -1);
+  pr.cidx.assign((size_t)nsub * nl, -1);
+  pr.owners.assign((size_t)std::max(pr.nG, 1) * mo, -1);
+  pr.cowners.assign((size_t)std::max(pr.nC, 1) * mo, -1);
+  pr.Dw.assign(std::max(pr.nG, 1), 0.0);
+  pr.n_gam.assign(nsub, 0);
+  pr.loc_corner.assign((size_t)nsub * mc, -1);
+  pr.n_loc_corner.assign(nsub, 0);
+  pr.free_of_local.assign((size_t)nsub * nl, -1);
+  pr.free_owner.assign(std::max(pr.n_free, 1), -1);
+  pr.u0_local.assign((size_t)nsub * nl, 0.0);
+  std::vector<int> mult(std::max(pr.nG, 1), 0), cmult(std::max(pr.nC, 1), 0);
+  pr.nGam = 1;
+  for (int s = 0; s < nsub; ++s) {
+    pr.n_gam[s] = nfree[s] - nint[s];
+    pr.nGam = std::max(pr.nGam, pr.n_gam[s]);
+  }
+  pr.gam_ln.assign((size_t)nsub * pr.nGam, -1);
+  for (int s = 0; s < nsub; ++s) {
+    const int base = mp.sub_vptr[s];
+    for (int a = 0; a < nfree[s]; ++a) {
+      const int v = mp.sub_verts[base + a];
+      const size_t o = (size_t)s * nl + a;
+      const uint8_t c = mp.vclass[v];
+      pr.cls[o] = c;
+      const int f = mp.free_idx[v];
+      if (f < 0 || f >= pr.n_free) return "mesh: free numbering inconsistent";
+      pr.free_of_local[o] = f;
+      if (pr.free_owner[f] < 0) pr.free_owner[f] = (int)o;
+      if (c == REMAINING || c == CORNER) {
+        const int g = mp.iface_idx[v];
+        if (g < 0 || g >= pr.nG || mult[g] >= mo) return "mesh: interface numbering inconsistent";
+        pr.gidx[o] = g;
+        pr.owners[(size_t)g * mo + mult[g]++] = (int)o;
+        pr.gam_ln[(size_t)s * pr.nGam + (a - nint[s])] = a;
+      }
+      if (c == CORNER) {
+        const int cc = mp.corner_idx[v];
+        if (cc < 0 || cc >= pr.nC || cmult[cc] >= mo) return "mesh: corner numbering inconsistent";
+        pr.cidx[o] = cc;
+        pr.cowners[(size_t)cc * mo + cmult[cc]++] = (int)o;
+        pr.loc_corner[(size_t)s * mc + pr.n_loc_corner[s]++] = a;
+      }
+      if (src.kind == 1) {
+        const double x = xy[2 * v] - src.x0, y = xy[2 * v + 1] - src.y0;
+        pr.u0_local[o] = src.amp * std::exp(-(x * x + y * y) / (src.width * src.width));
+      }
+    }
+  }
+  for (int g = 0; g < pr.nG; ++g) {
+    if (mult[g] < 2) return "mesh: interface vertex with fewer than two owners";
+    pr.Dw[g] = 1.0 / mult[g];
+  }
+  pr.max_corner = 0;
+  for (int s = 0; s < nsub; ++s) pr.max_corner = std::max(pr.max_corner, pr.n_loc_corner[s]);
+  mr.npat.assign((size_t)3 * nsub, 0);
+  for (int s = 0; s < nsub; ++s) {
+    mr.npat[s] = nint[s];
+    mr.npat[nsub + s] = nint[s] + nrem[s];
+    mr.npat[2 * nsub + s] = nfree[s];
+  }
+
+  // sparse rows: stiffness K_i[a][a] = sum of the weights of a's edges (P1 element rows sum to zero),
+  // K_i[a][b] = -w_i(a, b) between free vertices; mass area / 12 off the diagonal and area / 6 on it
+  mr.row_ptr.assign((size_t)nsub * nl + 1, 0);
+  mr.col.clear(); mr.kval.clear(); mr.mval.clear();
+  for (int s = 0; s < nsub; ++s) {
+    const int nf = nfree[s];
+    std::vector<std::map<int, size_t>> rows(nf);   // column -> entry index in the row's buffer
+    std::vector<std::vector<double>> kb(nf), mb(nf);
+    auto entry = [&](int a, int b) -> size_t {
+      auto it = rows[a].find(b);
+      if (it != rows[a].end()) return it->second;
+      const size_t q = mb[a].size();
+      rows[a][b] = q;
+      mb[a].push_back(0.0);
+      kb[a].resize(kb[a].size() + PI, 0.0);
+      return q;
+    };
+    for (int a = 0; a < nf; ++a) entry(a, a);
+    for (int e = mp.sub_eptr[s]; e < mp.sub_eptr[s + 1]; ++e) {
+      const int u = mp.edge_u[e], v = mp.edge_v[e];
+      const double* w = &mp.edge_w[(size_t)e * PI];
+      if (u < nf) { const size_t q = entry(u, u); for (int i = 0; i < PI; ++i) kb[u][q * PI + i] += w[i]; }
+      if (v < nf) { const size_t q = entry(v, v); for (int i = 0; i < PI; ++i) kb[v][q * PI + i] += w[i]; }
+      if (u < nf && v < nf) {
+        const size_t q1 = entry(u, v), q2 = entry(v, u);
+        for (int i = 0; i < PI; ++i) {
+          kb[u][q1 * PI + i] -= w[i];
+          kb[v][q2 * PI + i] -= w[i];
+        }
+      }
+    }
+    for (int t = mp.sub_tptr[s]; t < mp.sub_tptr[s + 1]; ++t) {
+      const int* lv = &mp.tri_loc[(size_t)t * 3];
+      const double ar = mp.tri_area[t];
+      for (int x = 0; x < 3; ++x)
+        for (int y = 0; y < 3; ++y) {
+          const int a = lv[x], b = lv[y];
+          if (a >= nf || b >= nf) continue;
+          mb[a][entry(a, b)] += (x == y ? ar / 6.0 : ar / 12.0);
+        }
+    }
+    for (int a = 0; a < nl; ++a) {
+      const size_t row = (size_t)s * nl + a;
+      if (a < nf) {
+        // diagonal first, then ascending columns
+        std::vector<int> cols;
+        cols.push_back(a);
+        for (const auto& kv : rows[a])
+          if (kv.first != a) cols.push_back(kv.first);
+        for (int b : cols) {
+          const size_t q = rows[a][b];
+          mr.col.push_back(b);
+          mr.mval.push_back(mb[a][q]);
+          mr.kval.insert(mr.kval.end(), kb[a].begin() + q * PI, kb[a].begin() + (q + 1) * PI);
+        }
+      }
+      mr.row_ptr[row + 1] = (int)mr.col.size();
+    }
+  }
+
+  // point source: P1 values in the first triangle containing (x0, y0), split over the owning
+  // subdomains with D_s
+  pr.load_node.clear(); pr.load_w.clear();
+  if (src.kind == 2) {
+    int found = -1;
+    double lam[3] = {0, 0, 0};
+    for (int e = 0; e < mp.ne && found < 0; ++e) {
+      const int* v = tri + 3 * e;
+      const double ax = xy[2 * v[0]], ay = xy[2 * v[0] + 1], bx = xy[2 * v[1]], by = xy[2 * v[1] + 1];
+      const double cx = xy[2 * v[2]], cy = xy[2 * v[2] + 1];
+      const double det = (bx - ax) * (cy - ay) - (cx - ax) * (by - ay);
+      const double l1 = ((src.x0 - ax) * (cy - ay) - (cx - ax) * (src.y0 - ay)) / det;
+      const double l2 = ((bx - ax) * (src.y0 - ay) - (src.x0 - ax) * (by - ay)) / det;
+      const double l0 = 1.0 - l1 - l2;
+      if (l0 >= -1e-12 && l1 >= -1e-12 && l2 >= -1e-12) {
+        found = e;
+        lam[0] = l0; lam[1] = l1; lam[2] = l2;
+      }
+    }
+    if (found < 0) return "source: the point (x0, y0) lies in no triangle of the mesh";
+    for (int k = 0; k < 3; ++k) {
+      const int v = tri[3 * found + k];
+      if (lam[k] == 0.0 || mp.vclass[v] == DIRICHLET) continue;
+      std::vector<int> own;
+      for (int s = 0; s < nsub; ++s)
+        for (int a = 0; a < nfree[s]; ++a)
+          if (mp.sub_verts[mp.sub_vptr[s] + a] == v) own.push_back(s * nl + a);
+      for (int o : own) {
+        pr.load_node.push_back(o);
+        pr.load_w.push_back(src.amp * lam[k] / (double)own.size());
+      }
+    }
+  }
+  return check_mesh_tables(pr, mr);
+}
+
+bool mesh_mean_inverse(const Problem& pr, const MeshRows& mr, int pat, double am, double bk,
+                       std::vector<double>& out) {
+  const int nsub = pr.nsub, nl = pr.nl, PI = pr.PI;
+  out.assign((size_t)nsub * nl * nl, 0.0);
+  for (int s = 0; s < nsub; ++s) {
+    const int n = mr.npat[(size_t)pat * nsub + s];
+    if (n == 0) continue;
+    std::vector<double> A((size_t)n * n, 0.0);
+    for (int a = 0; a < n; ++a) {
+      const size_t row = (size_t)s * nl + a;
+      for (int q = mr.row_ptr[row]; q < mr.row_ptr[row + 1]; ++q) {
+        const int b = mr.col[q];
+        if (b < n) A[(size_t)a * n + b] += am * mr.mval[q] + bk * mr.kval[(size_t)q * PI];
+      }
+    }
+    if (!spd_inverse(A, n)) return false;
+    for (int a = 0; a < n; ++a)
+      for (int c = 0; c < n; ++c) out[((size_t)s * nl + a) * nl + c] = A[(size_t)a * n + c];
+  }
+  return true;
 }
 
 bool spd_inverse(std::vector<double>& A, int n) {

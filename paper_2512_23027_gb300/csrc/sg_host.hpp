@@ -36,14 +36,15 @@ struct Problem {
   int nG = 0, nC = 0, nGam = 0;            // global interface nodes, corners, max local interface nodes
   std::vector<int> gidx;                   // nsub * nl : global interface index or -1
   std::vector<int> cidx;                   // nsub * nl : global corner index or -1
-  std::vector<int> owners;                 // nG * 4 : (sub * nl + ln) of owning subdomains, -1 padded
-  std::vector<int> cowners;                // nC * 4 : same for corners
+  std::vector<int> owners;                 // nG * mo : (sub * nl + ln) of owning subdomains, -1 padded
+  std::vector<int> cowners;                // nC * mo : same for corners
   std::vector<double> Dw;                  // nG : 1 / multiplicity
   std::vector<int> gam_ln;                 // nsub * nGam : local interface nodes (ascending ln), -1 padded
   std::vector<int> n_gam;                  // nsub
-  std::vector<int> loc_corner;             // nsub * 4 : local corner ln, -1 padded
+  std::vector<int> loc_corner;             // nsub * mc : local corner ln, -1 padded
   std::vector<int> n_loc_corner;           // nsub
   int max_corner = 0;                      // max local corners per subdomain
+  int mo = 4, mc = 4;                      // row strides of owners / cowners and of loc_corner
   // free nodes (global order) -> owning (sub * nl + ln) used for output
   int n_free = 0;
   std::vector<int> free_owner;             // n_free
@@ -91,6 +92,33 @@ struct MeshProblem {
   std::vector<double> tri_area;
   std::vector<double> kl_lambda;  // M
 };
+
+// Device-layout problem of a mesh (the general-partition path of the solver).  The local layout of
+// subdomain s holds its free vertices in the MeshProblem order (interior, remaining, corners), padded
+// to nl = the largest free count with DIRICHLET rows; the generic tables of Problem (classes, interface
+// and corner maps with strides mo / mc, output maps, initial displacement, point load) are filled for
+// it, and MeshRows holds the operators as sparse rows of that layout.  L = N = 0 (no grid).
+struct MeshRows {
+  std::vector<int> row_ptr;    // nsub * nl + 1 (padding rows empty)
+  std::vector<int> col;        // local column of each entry, same subdomain; the diagonal first in its row
+  std::vector<double> kval;    // entries x PI: K_i[a][b] of the subdomain's own triangles
+  std::vector<double> mval;    // entries: consistent mass M[a][b] of the subdomain's own triangles
+  std::vector<int> npat;       // 3 * nsub, [pat * nsub + s]: local rows of pattern 0 (interior),
+                               // 1 (interior + remaining: the Neumann problem), 2 (every free vertex)
+};
+
+// xy / tri: the mesh given to build_mesh_problem; dt, alpha0, alpha1: Newmark step and Rayleigh
+// damping; src: the initial pulse (kind 1, at the free vertices) or the point source (kind 2: P1 values
+// at (x0, y0) in the first triangle that contains it, split over the owning subdomains with D_s).
+// Returns "" on success, else an error message.
+std::string mesh_to_problem(Problem& pr, MeshRows& mr, const MeshProblem& mp, const double* xy, const int* tri,
+                            double dt, double alpha0, double alpha1, const SourceDesc& src);
+
+// Dense inverse of the mean operator am M + bk K_0 (K_0: the mean-coefficient stiffness, input mode
+// 0) of every subdomain on the rows of pattern pat, in the local layout: out[(s * nl + a) * nl + c]
+// for a, c < npat, zero elsewhere.  Returns false if a matrix is not positive definite.
+bool mesh_mean_inverse(const Problem& pr, const MeshRows& mr, int pat, double am, double bk,
+                       std::vector<double>& out);
 
 // xy: nv x 2 vertex coordinates in the unit square; dirichlet: nv flags (homogeneous Dirichlet
 // vertices, eliminated); tri: ne x 3 vertex ids; part: ne subdomain ids 0 .. nsub - 1 (every id

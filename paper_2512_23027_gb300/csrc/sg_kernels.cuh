@@ -2172,17 +2172,18 @@ __global__ void k_gather(int nb, int R, int nl, int P, const uint8_t* cls, const
   dst[idx] = v;
 }
 
-// dst[g][k] = sum over owners o of src[o][k] (* D[g] when useD); owners are (sub * nl + ln), R = 1
+// dst[g][k] = sum over owners o of src[o][k] (* D[g] when useD); owners are (sub * nl + ln), mo per
+// interface node (-1 padded), R = 1
 template <typename T>
-__global__ void k_scatter(int nG, int P, const int* owners, const double* D, const T* __restrict__ src,
+__global__ void k_scatter(int nG, int P, const int* owners, int mo, const double* D, const T* __restrict__ src,
                           double* __restrict__ dst, int useD) {
   count_launch();
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nG * P) return;
   const int k = (int)(idx % P), g = (int)(idx / P);
   double s = 0.0;
-  for (int q = 0; q < 4; ++q) {
-    const int o = owners[g * 4 + q];
+  for (int q = 0; q < mo; ++q) {
+    const int o = owners[g * mo + q];
     if (o >= 0) s += (double)src[(long long)o * P + k];
   }
   if (useD) s *= D[g];
@@ -2191,18 +2192,18 @@ __global__ void k_scatter(int nG, int P, const int* owners, const double* D, con
 
 // Sum the interface values of all owners and write the sum back to every owner (global
 // assembly of a local-layout vector on the interface).
-__global__ void k_assemble_gamma(int nG, int P, const int* owners, double* __restrict__ v) {
+__global__ void k_assemble_gamma(int nG, int P, const int* owners, int mo, double* __restrict__ v) {
   count_launch();
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nG * P) return;
   const int k = (int)(idx % P), g = (int)(idx / P);
   double s = 0.0;
-  for (int q = 0; q < 4; ++q) {
-    const int o = owners[g * 4 + q];
+  for (int q = 0; q < mo; ++q) {
+    const int o = owners[g * mo + q];
     if (o >= 0) s += v[(long long)o * P + k];
   }
-  for (int q = 0; q < 4; ++q) {
-    const int o = owners[g * 4 + q];
+  for (int q = 0; q < mo; ++q) {
+    const int o = owners[g * mo + q];
     if (o >= 0) v[(long long)o * P + k] = s;
   }
 }
@@ -2242,7 +2243,7 @@ __global__ void k_dot_w(long long nnodes, int P, const double* w, const double* 
 template <typename TV>
 __global__ void k_coarse_extend(int nsub, int nl, int P, int nGam, int maxc, const uint8_t* cls,
                                 const int* cidx, const int* gam_ln, const int* n_gam, const int* loc_corner,
-                                const int* n_loc_corner, const double* __restrict__ Phi,
+                                int mc, const int* n_loc_corner, const double* __restrict__ Phi,
                                 const double* __restrict__ uc, const TV* __restrict__ v,
                                 double* __restrict__ zloc) {
   count_launch();
@@ -2262,7 +2263,7 @@ __global__ void k_coarse_extend(int nsub, int nl, int P, int nGam, int maxc, con
     const int nc = n_loc_corner[sub];
     const int ncolmax = maxc * P;
     for (int lc = 0; lc < nc; ++lc) {
-      const int cg = cidx[(long long)sub * nl + loc_corner[sub * 4 + lc]];
+      const int cg = cidx[(long long)sub * nl + loc_corner[sub * mc + lc]];
       for (int m = 0; m < P; ++m) {
         const int col = lc * P + m;
         val += Phi[(((long long)sub * ncolmax + col) * nGam + q) * P + k] * uc[(long long)cg * P + m];
@@ -2274,15 +2275,15 @@ __global__ void k_coarse_extend(int nsub, int nl, int P, int nGam, int maxc, con
 
 // d[c][k] = sum over owners o of (wc - y)[o][k]
 template <typename TY>
-__global__ void k_corner_rhs(int nC, int P, const int* cowners, const double* __restrict__ wc,
+__global__ void k_corner_rhs(int nC, int P, const int* cowners, int mo, const double* __restrict__ wc,
                              const TY* __restrict__ y, double* __restrict__ d) {
   count_launch();
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)nC * P) return;
   const int k = (int)(idx % P), c = (int)(idx / P);
   double s = 0.0;
-  for (int q = 0; q < 4; ++q) {
-    const int o = cowners[c * 4 + q];
+  for (int q = 0; q < mo; ++q) {
+    const int o = cowners[c * mo + q];
     if (o >= 0) s += wc[(long long)o * P + k] - (double)y[(long long)o * P + k];
   }
   d[idx] = s;
@@ -2303,7 +2304,7 @@ __global__ void k_gemv(int n, const double* __restrict__ A, const double* __rest
 }
 
 // unit vectors of the coarse basis problems: problem b = sub * R + (lc * P + m)
-__global__ void k_coarse_units(int nsub, int R, int nl, int P, int sub0, const int* loc_corner,
+__global__ void k_coarse_units(int nsub, int R, int nl, int P, int sub0, const int* loc_corner, int mc,
                                const int* n_loc_corner, double* e) {
   count_launch();
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -2312,7 +2313,7 @@ __global__ void k_coarse_units(int nsub, int R, int nl, int P, int sub0, const i
   const int sub = sub0 + sl;
   const int lc = col / P, m = col % P;
   if (lc >= n_loc_corner[sub]) return;
-  const int ln = loc_corner[sub * 4 + lc];
+  const int ln = loc_corner[sub * mc + lc];
   e[(((long long)sl * R + col) * nl + ln) * P + m] = 1.0;
 }
 
@@ -2339,7 +2340,7 @@ __global__ void k_coarse_phi(int nsub_chunk, int sub0, int R, int nl, int P, int
 }
 
 // local coarse matrix entries: Fs[sub][row = lc'*P+m'][col] = y[b(col)][loc_corner[lc']][m']
-__global__ void k_coarse_fs(int nsub_chunk, int sub0, int R, int nl, int P, const int* loc_corner,
+__global__ void k_coarse_fs(int nsub_chunk, int sub0, int R, int nl, int P, const int* loc_corner, int mc,
                             const int* n_loc_corner, const double* __restrict__ y, double* __restrict__ Fs) {
   count_launch();
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -2351,7 +2352,7 @@ __global__ void k_coarse_fs(int nsub_chunk, int sub0, int R, int nl, int P, cons
   const int lr = row / P, mr = row % P;
   double val = 0.0;
   if (lr < n_loc_corner[sub] && col / P < n_loc_corner[sub]) {
-    const int ln = loc_corner[sub * 4 + lr];
+    const int ln = loc_corner[sub * mc + lr];
     val = y[(((long long)sl * R + col) * nl + ln) * P + mr];
   }
   Fs[((long long)sub * R + row) * R + col] = val;

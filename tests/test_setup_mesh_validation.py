@@ -1,0 +1,128 @@
+"""sg_setup_mesh rejects invalid and unsupported meshes, partitions and parameters before its first
+CUDA call (no device needed): each failure returns its status code with a message in
+sg_last_error(NULL) and leaves the output handle NULL.  On a machine without a GPU, a valid mesh
+passes every host step (mesh tables, corner detection, sparse rows, index checks, the dense
+mean-operator inverses) and stops at the first CUDA call with SG_ECUDA."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import sg_workloads as w
+from oracle import umesh
+
+SG_EINVAL, SG_ECUDA, SG_ENOTSUP = -1, -3, -7
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2512_23027_gb300 import build as b
+    b.build()
+    from paper_2512_23027_gb300 import binding
+    binding.load_library()
+    return binding
+
+
+def base_mesh():
+    m = umesh.delaunay_mesh(6, 0.3, 5)
+    return m.xy.copy(), m.boundary.astype(np.uint8), m.tri.astype(np.int32).copy(), umesh.rcb_partition(m, 3).astype(np.int32)
+
+
+def setup_rc(B, xy, dirichlet, tri, part, precision=0, warm=0, src=None, modes=None, lambdas=None, null_mesh=False,
+             prob=None, precond=0):
+    lib = B.load_library()
+    prob = prob or w.config("tiny")
+    s = src or prob.source
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    dirichlet = np.ascontiguousarray(dirichlet, dtype=np.uint8)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    part = np.ascontiguousarray(part, dtype=np.int32)
+    mesh = B.Mesh(xy.shape[0], xy.ctypes.data, dirichlet.ctypes.data, tri.shape[0], tri.ctypes.data,
+                  part.ctypes.data)
+    kl = B.KL(prob.M, prob.sigma, prob.bx, prob.by, prob.g0, None if modes is None else modes.ctypes.data,
+              None if lambdas is None else lambdas.ctypes.data)
+    pce = B.PCE(prob.p, prob.p_in)
+    prm = B.Params(prob.dt, prob.tol, prob.alpha0, prob.alpha1, prob.max_iter, precision, warm, 0.0, 0, 0, 0, 0.0,
+                   precond)
+    srcs = B.Source(s.kind, s.x0, s.y0, s.width, s.freq, s.amp)
+    h = C.c_void_p(12345)
+    rc = lib.sg_setup_mesh(None if null_mesh else C.byref(mesh), C.byref(kl), C.byref(pce), C.byref(prm),
+                           C.byref(srcs), None, C.byref(h))
+    return rc, h.value, lib.sg_last_error(None).decode()
+
+
+def bad(kind):
+    xy, d, tri, part = base_mesh()
+    kw = {}
+    if kind == "vertex id":
+        tri[3, 1] = xy.shape[0]
+    elif kind == "unused subdomain id":
+        part = np.where(part == 1, 2, part)
+    elif kind == "single subdomain":
+        part = np.zeros_like(part)
+    elif kind == "degenerate triangle":
+        xy[tri[0, 2]] = 0.5 * (xy[tri[0, 0]] + xy[tri[0, 1]])
+    elif kind == "edge in three triangles":
+        a, b = tri[0, 0], tri[0, 1]
+        xy = np.vstack([xy, [[0.5, 0.5]]])
+        d = np.append(d, 0)
+        tri = np.vstack([tri, [[a, b, xy.shape[0] - 1]]])
+        part = np.append(part, 0)
+    elif kind == "source outside the mesh":
+        xy = 0.5 * xy                       # the mesh covers [0, 1/2]^2 only
+        kw["src"] = w.Source(2, 0.8, 0.8, 0.0, 10.0, 1.0)
+    elif kind == "source kind":
+        kw["src"] = w.Source(5, 0.5, 0.5, 0.05, 10.0, 1.0)
+    elif kind == "precision":
+        kw["precision"] = 7
+    elif kind == "bf16":
+        kw["precision"] = 3
+    elif kind == "warm-start mode":
+        kw["warm"] = 9
+    elif kind == "modes without lambdas":
+        kw["modes"] = np.zeros((w.config("tiny").M, tri.shape[0]))
+    elif kind == "too few vertices":
+        xy, d = xy[:2], d[:2]
+    return (xy, d, tri, part), kw
+
+
+CASES = [
+    ("vertex id", SG_EINVAL, "out of range"),
+    ("unused subdomain id", SG_EINVAL, "subdomain ids"),
+    ("single subdomain", SG_ENOTSUP, "two subdomains"),
+    ("degenerate triangle", SG_EINVAL, "degenerate"),
+    ("edge in three triangles", SG_EINVAL, "more than two"),
+    ("source outside the mesh", SG_EINVAL, "no triangle"),
+    ("source kind", SG_EINVAL, "source"),
+    ("precision", SG_EINVAL, "precision"),
+    ("bf16", SG_ENOTSUP, "SG_BF16"),
+    ("warm-start mode", SG_EINVAL, "warm"),
+    ("modes without lambdas", SG_EINVAL, "lambdas"),
+    ("too few vertices", SG_EINVAL, "mesh"),
+]
+
+
+@pytest.mark.parametrize("kind,code,msg", CASES, ids=[c[0] for c in CASES])
+def test_mesh_setup_rejects(B, kind, code, msg):
+    args, kw = bad(kind)
+    rc, h, err = setup_rc(B, *args, **kw)
+    assert rc == code and h is None and msg in err, (rc, err)
+
+
+def test_null_mesh(B):
+    rc, h, err = setup_rc(B, *base_mesh(), null_mesh=True)
+    assert rc == SG_EINVAL and h is None and "null" in err
+
+
+def test_valid_mesh_passes_the_host_steps(B):
+    """Without a GPU the first CUDA call fails: every host step before it accepted the mesh (an RCB
+    partition of a Delaunay mesh into three subdomains, which meet at a corner; pulse and Ricker
+    sources; FP64 and mixed precision; the two-level and the one-level preconditioner, whose third
+    pattern adds one more mean-operator inverse)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is visible: this checks the host steps on a machine without one")
+    for src in (w.Source(1, 0.5, 0.5, 0.1, 0.0, 1.0), w.Source(2, 0.37, 0.61, 0.0, 10.0, 1.0)):
+        for precision, precond in ((0, 0), (1, 0), (0, 1)):
+            rc, h, err = setup_rc(B, *base_mesh(), src=src, precision=precision, precond=precond)
+            assert rc == SG_ECUDA and h is None, (rc, err)
