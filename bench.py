@@ -366,6 +366,51 @@ def run_precond_study(args):
     return 0
 
 
+def run_mesh(args):
+    """Mesh workload (a seeded unstructured mesh with an RCB partition, sg_setup_mesh): steps/s of the
+    mixed solver with the learned warm start and of the plain FP64 solver with the previous-step guess,
+    on the same GPU, from the same initial state; `warmup` untimed steps each, then one sg_step per
+    timed step (CUDA events on the solver's stream) with a 256 MB buffer written between steps."""
+    import torch
+    import sg_workloads as w
+    from paper_2512_23027_gb300 import Solver
+    from paper_2512_23027_gb300.binding import SG_FP64, SG_MIXED, SG_WARM_LEARNED, SG_WARM_PREV
+    c = w.mesh_config(args.mesh)
+    mesh = c.build()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    legs = {}
+    for key, precision, warm, K in (("mixed_learned", SG_MIXED, SG_WARM_LEARNED, args.steps),
+                                    ("fp64", SG_FP64, SG_WARM_PREV, min(args.steps, args.fp64_steps))):
+        t0 = time.perf_counter()
+        sv = Solver(c.prob, precision=precision, warm=warm, stream=stream, mesh=mesh)
+        setup = time.perf_counter() - t0
+        sv.step(max(3, args.warmup))
+        ms, outer, inner = 0.0, 0, 0
+        for k in range(K):
+            flush.fill_(float(k))
+            st = sv.step(1)
+            ms += st["ms"]
+            outer += st["iters_total"]
+            inner += st["inner_total"]
+        legs[key] = {"steps_per_s": K / (ms / 1e3), "ms_per_step": ms / K, "outer_iters_per_step": outer / K,
+                     "inner_iters_per_step": inner / K, "steps": K, "setup_s": setup,
+                     "device_bytes": sv.sizes["device_bytes"]}
+        sv.close()
+    p = c.prob
+    line = {"metric": "time-steps/sec on a general partition of an unstructured mesh (mixed precision + learned "
+                      "warm start; plain FP64 beside it)",
+            "value": legs["mixed_learned"]["steps_per_s"], "unit": "steps/s", "higher_is_better": True,
+            "steps": args.steps, "warmup": max(3, args.warmup), "dtype": "f32+f64", "data": "synthetic",
+            "speedup_vs_fp64": legs["mixed_learned"]["steps_per_s"] / legs["fp64"]["steps_per_s"],
+            "mixed_learned": legs["mixed_learned"], "fp64": legs["fp64"],
+            "config": {"workload": c.name, "vertices": int(mesh[0].shape[0]), "triangles": int(mesh[2].shape[0]),
+                       "subdomains": c.nparts, "M": p.M, "p": p.p, "P": p.P, "dt": p.dt, "tol": p.tol,
+                       "l2": "256 MB buffer written between timed steps"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_profile_step(args):
     """One step of the workload for profilers (mixed precision, learned warm start; with --profile-fp64
     the plain FP64 solver): fast-forward (graph mode), one untimed host-driven step,
@@ -422,6 +467,9 @@ def main():
                     help="instead of the default line: fast-forward, then one host-driven step between "
                          "cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--profile-fp64", action="store_true", help="with --profile-step: the plain FP64 solver")
+    ap.add_argument("--mesh", default=None,
+                    help="time a mesh workload instead (umesh_small, umesh13k, umesh37k, umesh37k_rv9): a seeded "
+                         "unstructured mesh with an RCB partition, mixed + learned warm start and plain FP64")
     ap.add_argument("--enqueue", default="graph", choices=["graph", "eager"],
                     help="graph: one CUDA graph per step (default); eager: host-driven enqueue of the same "
                          "kernels (per-kernel profilers cannot see inside graphs with conditional nodes)")
@@ -434,6 +482,8 @@ def main():
         return run_precond_study(args)
     if args.profile_step:
         return run_profile_step(args)
+    if args.mesh:
+        return run_mesh(args)
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

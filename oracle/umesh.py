@@ -4,11 +4,13 @@ with corners defined in Sec. 3).
 
 * `Mesh`: vertex coordinates, counter-clockwise triangles, Dirichlet (boundary) vertices.
   `structured_mesh(N)` is the structured grid of `fem` with the same numbering (the pin that ties
-  this module to the structured oracle); `delaunay_mesh(n, jitter, seed)` is a seeded unstructured
-  mesh: n + 1 boundary vertices per side, an (n - 1)^2 interior grid jittered by up to `jitter`
-  cells (SplitMix64 draws), Delaunay triangulation.
+  this module to the structured oracle); `delaunay_mesh(n, jitter, seed)` wraps the seeded
+  unstructured mesh of the shared input generator (sg_workloads.meshes): n + 1 boundary vertices
+  per side, an (n - 1)^2 interior grid jittered by up to `jitter` cells (SplitMix64 draws),
+  Delaunay triangulation.
 * `rcb_partition(mesh, nparts)`: recursive coordinate bisection of the elements (by centroid,
-  across the longer extent, at the count-weighted median), for any number of subdomains.
+  across the longer extent, at the count-weighted median), for any number of subdomains, from the
+  same input generator.
 * `UPartition`: node classes and restriction maps of an element partition, with the attributes of
   `dd.Partition`.  Interface nodes are free vertices of elements of two or more subdomains.
   Corners (reading of Sec. 3: nodes shared by more than two subdomains, plus the end nodes of
@@ -30,6 +32,7 @@ from . import fem, field, kl, pce
 from .sg import SGOperators
 
 import sg_workloads as w
+from sg_workloads import meshes
 
 
 class Mesh:
@@ -76,49 +79,16 @@ def structured_mesh(N: int) -> Mesh:
 
 
 def delaunay_mesh(n: int, jitter: float = 0.3, seed: int = 7) -> Mesh:
-    """Seeded unstructured mesh of the unit square (see the module docstring)."""
-    from scipy.spatial import Delaunay
-    h = 1.0 / n
-    pts = []
-    for k in range(n + 1):  # boundary, every vertex once
-        pts += [(k * h, 0.0), (k * h, 1.0)]
-    for k in range(1, n):
-        pts += [(0.0, k * h), (1.0, k * h)]
-    u = w.uniform_samples(2 * (n - 1) ** 2, seed)
-    q = 0
-    for j in range(1, n):
-        for i in range(1, n):
-            dx = (2.0 * u[q] - 1.0) * jitter * h
-            dy = (2.0 * u[q + 1] - 1.0) * jitter * h
-            q += 2
-            pts.append((i * h + dx, j * h + dy))
-    xy = np.array(pts)
-    tri = Delaunay(xy).simplices
-    # drop slivers a Delaunay triangulation of co-circular boundary points can leave
-    a, b, c = xy[tri[:, 0]], xy[tri[:, 1]], xy[tri[:, 2]]
-    area = 0.5 * np.abs((b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (c[:, 0] - a[:, 0]) * (b[:, 1] - a[:, 1]))
-    tri = tri[area > 1e-12 * h * h]
-    return Mesh(xy, tri, _on_boundary(xy))
+    """Seeded unstructured mesh of the unit square (the shared input generator
+    sg_workloads.meshes.delaunay_square; see the module docstring)."""
+    xy, tri, boundary = meshes.delaunay_square(n, jitter, seed)
+    return Mesh(xy, tri, boundary)
 
 
 def rcb_partition(mesh: Mesh, nparts: int) -> np.ndarray:
-    """Element -> subdomain by recursive coordinate bisection of the centroids."""
-    part = np.zeros(mesh.tri.shape[0], dtype=np.int64)
-
-    def split(ids: np.ndarray, k: int, first: int):
-        if k == 1:
-            part[ids] = first
-            return
-        c = mesh.cen[ids]
-        ax = 0 if np.ptp(c[:, 0]) >= np.ptp(c[:, 1]) else 1
-        order = ids[np.lexsort((c[:, 1 - ax], c[:, ax]))]
-        k0 = k // 2
-        n0 = (ids.size * k0) // k
-        split(order[:n0], k0, first)
-        split(order[n0:], k - k0, first + k0)
-
-    split(np.arange(mesh.tri.shape[0]), nparts, 0)
-    return part
+    """Element -> subdomain by recursive coordinate bisection of the centroids (the shared input
+    generator sg_workloads.meshes.rcb_partition on this mesh's triangles)."""
+    return meshes.rcb_partition(mesh.xy, mesh.tri, nparts)
 
 
 class UPartition:

@@ -126,3 +126,22 @@ def test_valid_mesh_passes_the_host_steps(B):
         for precision, precond in ((0, 0), (1, 0), (0, 1)):
             rc, h, err = setup_rc(B, *base_mesh(), src=src, precision=precision, precond=precond)
             assert rc == SG_ECUDA and h is None, (rc, err)
+
+
+@pytest.mark.parametrize("name,nv,nsub", [("umesh_small", 625, 6), ("umesh13k", 13689, 32), ("umesh37k", 37249, 720)])
+def test_mesh_workloads(B, name, nv, nsub):
+    """The mesh workloads: seeded (the same mesh twice), the vertex counts of the paper-sized meshes,
+    balanced RCB partitions (triangle counts within one), and every host step of sg_setup_mesh accepts
+    them (on a machine without a GPU the set-up stops at the first CUDA call)."""
+    c = w.mesh_config(name)
+    xy, d, tri, part = c.build()
+    xy2, _, tri2, part2 = c.build()
+    assert np.array_equal(xy, xy2) and np.array_equal(tri, tri2) and np.array_equal(part, part2)
+    assert xy.shape[0] == nv and int(part.max()) + 1 == nsub
+    cnt = np.bincount(part, minlength=nsub)
+    assert cnt.max() - cnt.min() <= 1
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        return
+    rc, h, err = setup_rc(B, xy, d, tri, part, prob=c.prob, precision=1)
+    assert rc == SG_ECUDA and h is None, (rc, err)
