@@ -468,7 +468,7 @@ def main():
                          "cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--profile-fp64", action="store_true", help="with --profile-step: the plain FP64 solver")
     ap.add_argument("--mesh", default=None,
-                    help="time a mesh workload instead (umesh_small, umesh13k, umesh37k, umesh37k_rv9): a seeded "
+                    help="time a mesh workload instead (umesh_small, umesh13k, umesh37k, umesh37k_rv9, umesh37k_720): a seeded "
                          "unstructured mesh with an RCB partition, mixed + learned warm start and plain FP64")
     ap.add_argument("--enqueue", default="graph", choices=["graph", "eager"],
                     help="graph: one CUDA graph per step (default); eager: host-driven enqueue of the same "

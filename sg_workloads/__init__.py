@@ -220,27 +220,34 @@ class MeshConfig:
 
 
 def mesh_config(name: str) -> MeshConfig:
-    """Mesh workloads sized after the paper's unstructured experiments (Sec. 6): the mesh sizes and
-    subdomain counts are the paper's (its meshes are not available; seeded Delaunay meshes of the
-    same vertex count stand in), the KL / PCE sizes those of the experiment quoted.
+    """Mesh workloads sized after the paper's unstructured experiments (Sec. 6): the mesh sizes are the
+    paper's (its meshes are not available; seeded Delaunay meshes of the same vertex count stand in),
+    the KL / PCE sizes those of the experiment quoted.  The paper spreads its subdomains over CPU cores
+    (up to 720); on one GPU fewer, larger subdomains keep the coarse problem small, so the 37k-vertex
+    mesh comes with a 64-subdomain partition and, separately, with the paper's 720.
       umesh_small   24 cells per side (625 vertices), 6 subdomains, M = 3, order 2 (test size).
       umesh13k      117^2 = 13689 vertices (paper: 13472), 32 subdomains, M = 7, order 3 (P = 120):
                     the strong-scaling problem (Sec. 6.3, 1.6 million unknowns), dt 6.5e-3.
-      umesh37k      193^2 = 37249 vertices (paper: 37267), 720 subdomains, M = 3, order 3 (P = 20):
+      umesh37k      193^2 = 37249 vertices (paper: 37267), 64 subdomains, M = 3, order 3 (P = 20):
                     the smallest case of the scaling-with-random-variables study (Sec. 6.4), dt 3.9e-3.
       umesh37k_rv9  the same mesh and partition with M = 9, order 3 (P = 220, 8.19 million unknowns),
-                    the largest case of that study."""
+                    the largest case of that study.
+      umesh37k_720  umesh37k on the paper's 720 subdomains (1284 corners: a dense coarse matrix of
+                    25680^2 values, 5.3 GB, whose inverse takes minutes of host set-up)."""
     ricker = Source(SOURCE_RICKER, 0.3, 0.5, 0.0, 10.0, 1.0)
     base = Problem(name=name, N=0, s=0, M=3, p=2, p_in=2, sigma=0.3, bx=0.3, by=0.3, g0=0.0, dt=0.02,
                    steps=20, tol=1e-8, source=ricker)
+    rv3 = base.replace(M=3, p=3, p_in=3, dt=3.9e-3, steps=128)
     if name == "umesh_small":
         return MeshConfig(name, 24, 0.3, 11, 6, base)
     if name == "umesh13k":
         return MeshConfig(name, 116, 0.3, 13, 32, base.replace(M=7, p=3, p_in=3, dt=6.5e-3, steps=77))
     if name == "umesh37k":
-        return MeshConfig(name, 192, 0.3, 37, 720, base.replace(M=3, p=3, p_in=3, dt=3.9e-3, steps=128))
+        return MeshConfig(name, 192, 0.3, 37, 64, rv3)
     if name == "umesh37k_rv9":
-        return MeshConfig(name, 192, 0.3, 37, 720, base.replace(M=9, p=3, p_in=3, dt=3.9e-3, steps=128))
+        return MeshConfig(name, 192, 0.3, 37, 64, rv3.replace(M=9))
+    if name == "umesh37k_720":
+        return MeshConfig(name, 192, 0.3, 37, 720, rv3)
     raise KeyError(name)
 
 

@@ -128,7 +128,8 @@ def test_valid_mesh_passes_the_host_steps(B):
             assert rc == SG_ECUDA and h is None, (rc, err)
 
 
-@pytest.mark.parametrize("name,nv,nsub", [("umesh_small", 625, 6), ("umesh13k", 13689, 32), ("umesh37k", 37249, 720)])
+@pytest.mark.parametrize("name,nv,nsub", [("umesh_small", 625, 6), ("umesh13k", 13689, 32), ("umesh37k", 37249, 64),
+                                          ("umesh37k_720", 37249, 720)])
 def test_mesh_workloads(B, name, nv, nsub):
     """The mesh workloads: seeded (the same mesh twice), the vertex counts of the paper-sized meshes,
     balanced RCB partitions (triangle counts within one), and every host step of sg_setup_mesh accepts
