@@ -94,6 +94,25 @@ static double phi1(double x, const Eig1& e) {
   return std::sin(e.w * u) / std::sqrt(0.5 - std::sin(e.w) / (2 * e.w));
 }
 
+// The top M 2-D KL modes of the separable exponential kernel: products of the 1-D eigenpairs (ex in x,
+// ey in y, the first M + 1 of each), sorted by eigenvalue; ties go to the lower y index, then the lower
+// x index.  A non-positive correlation length stands for 1 (its modes are then unused: caller KL).
+struct KLCand { double lam; int ix, iy; };
+static std::vector<KLCand> kl_select(int M, double bx, double by, std::vector<Eig1>& ex, std::vector<Eig1>& ey) {
+  ex = eig1d(bx > 0 ? bx : 1.0, M + 1);
+  ey = eig1d(by > 0 ? by : 1.0, M + 1);
+  std::vector<KLCand> cand;
+  for (int ix = 0; ix <= M; ++ix)
+    for (int iy = 0; iy <= M; ++iy) cand.push_back({ex[ix].lam * ey[iy].lam, ix, iy});
+  std::stable_sort(cand.begin(), cand.end(), [](const KLCand& a, const KLCand& b) {
+    if (a.lam != b.lam) return a.lam > b.lam;
+    if (a.iy != b.iy) return a.iy < b.iy;
+    return a.ix < b.ix;
+  });
+  cand.resize(M);
+  return cand;
+}
+
 // Runs f(i) for i in [i0, i1) on up to 16 host threads, rows assigned cyclically (thread t takes
 // i0 + t, i0 + t + T, ...) so that triangular work stays balanced.
 template <class F>
@@ -163,17 +182,8 @@ std::string build_problem(Problem& pr, int N, int sx, int sy, int M, double sigm
   triple_table(pr, Ain, Aout);
 
   // KL modes: products of 1-D eigenpairs, top M by lambda, ties -> lower y index, then x index
-  std::vector<Eig1> ex = eig1d(bx > 0 ? bx : 1.0, M + 1), ey = eig1d(by > 0 ? by : 1.0, M + 1);
-  struct Cand { double lam; int ix, iy; };
-  std::vector<Cand> cand;
-  for (int ix = 0; ix <= M; ++ix)
-    for (int iy = 0; iy <= M; ++iy) cand.push_back({ex[ix].lam * ey[iy].lam, ix, iy});
-  std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) {
-    if (a.lam != b.lam) return a.lam > b.lam;
-    if (a.iy != b.iy) return a.iy < b.iy;
-    return a.ix < b.ix;
-  });
-  cand.resize(M);
+  std::vector<Eig1> ex, ey;
+  const std::vector<KLCand> cand = kl_select(M, bx, by, ex, ey);
   pr.kl_lambda.resize(M);
   for (int n = 0; n < M; ++n) pr.kl_lambda[n] = modes ? lambdas[n] : cand[n].lam;
 
@@ -440,17 +450,8 @@ std::string build_mesh_problem(MeshProblem& mp, int nv, const double* xy, const 
   }
 
   // KL: top M products of the 1-D eigenpairs (ties: lower y index, then x index), or the caller's
-  std::vector<Eig1> ex = eig1d(bx > 0 ? bx : 1.0, M + 1), ey = eig1d(by > 0 ? by : 1.0, M + 1);
-  struct Cand { double lam; int ix, iy; };
-  std::vector<Cand> cand;
-  for (int ix = 0; ix <= M; ++ix)
-    for (int iy = 0; iy <= M; ++iy) cand.push_back({ex[ix].lam * ey[iy].lam, ix, iy});
-  std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) {
-    if (a.lam != b.lam) return a.lam > b.lam;
-    if (a.iy != b.iy) return a.iy < b.iy;
-    return a.ix < b.ix;
-  });
-  cand.resize(M);
+  std::vector<Eig1> ex, ey;
+  const std::vector<KLCand> cand = kl_select(M, bx, by, ex, ey);
   mp.kl_lambda.resize(M);
   for (int n = 0; n < M; ++n) mp.kl_lambda[n] = modes ? lambdas[n] : cand[n].lam;
   // PCE coefficients of exp(g) per element centroid: exp(g0 + |g|^2 / 2) prod_n g_n^{a_n} / sqrt(a_n!)
