@@ -146,3 +146,27 @@ def test_mesh_workloads(B, name, nv, nsub):
         return
     rc, h, err = setup_rc(B, xy, d, tri, part, prob=c.prob, precision=1)
     assert rc == SG_ECUDA and h is None, (rc, err)
+
+
+def test_mesh_golden_matches_the_generator():
+    """The stored oracle samples of the 37k-vertex mesh workload (tests/golden/mesh_oracle_samples.json)
+    were taken on the mesh and partition that sg_workloads builds here (sha256 of the sorted triangles
+    and of the partition), with the sample layout the GPU test reads."""
+    import importlib.util
+    import json
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    path = os.path.join(here, "golden", "mesh_oracle_samples.json")
+    if not os.path.exists(path):
+        pytest.skip("mesh_oracle_samples.json not generated")
+    spec = importlib.util.spec_from_file_location("mk", os.path.join(here, "golden", "make_mesh_oracle_samples.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    rec = json.load(open(path))["umesh37k"]
+    xy, d, tri, part = w.mesh_config("umesh37k").build()
+    assert mk.mesh_hash(tri, part) == (rec["mesh_sha"], rec["part_sha"])
+    assert rec["vertices"] == xy.shape[0] and rec["triangles"] == tri.shape[0]
+    n = len(rec["node"])
+    assert n == len(rec["mode"]) == len(rec["tight"]["values"]) == len(rec["workload"]["values"])
+    assert max(rec["node"]) < rec["n_free"] and max(rec["mode"]) < w.mesh_config("umesh37k").prob.P
+    assert rec["tight"]["tol"] == 1e-13 and len(rec["tight"]["iters"]) == rec["steps"]
