@@ -237,7 +237,8 @@ typedef struct {
  *     the triangle centroids, Eqs. c0pce, LNL0), applied as sparse rows;
  *   - subdomain solves by CG preconditioned by the dense inverse of the subdomain's mean operator
  *     (FP64 in SG_FP64, FP32 in SG_MIXED / SG_FP32, where the operator applies of the outer loop
- *     stay FP64).
+ *     stay FP64); SG_BF16 applies that inverse as a BF16 product on the tensor cores in the FP32
+ *     Dirichlet and Neumann solves (P <= 32, at most 1600 free vertices per subdomain).
  * kl->modes, when given, holds phi_n at the triangle centroids in the mesh's triangle order
  * (modes[n * ne + e]).  The source: a pulse is evaluated at the free vertices; a point source uses
  * the P1 values at (x0, y0) in the first triangle (in the given order) that contains it.  Fields of
@@ -245,7 +246,7 @@ typedef struct {
  * free vertices in ascending vertex id, PCE mode fastest.  sg_sizes.N is 0 for a mesh handle.
  * Errors: SG_EINVAL for invalid meshes, partitions or parameters (vertex ids out of range, an edge in
  * more than two triangles, unused subdomain ids, a degenerate triangle, a source outside the mesh),
- * SG_ENOTSUP for SG_BF16 or fewer than two subdomains, SG_ENUMERIC if a mean operator is not
+ * SG_ENOTSUP for SG_BF16 beyond its limits or fewer than two subdomains, SG_ENUMERIC if a mean operator is not
  * positive definite, SG_ENOMEM, SG_ECUDA.  On error *out is NULL. */
 int sg_setup_mesh(const sg_mesh* mesh, const sg_kl* kl, const sg_pce* pce, const sg_params* params,
                   const sg_source* src, void* stream, sg_handle* out);

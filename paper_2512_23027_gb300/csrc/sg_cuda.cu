@@ -226,6 +226,7 @@ struct sg_handle_s {
     return r;
   }
   long long nloc() const { return (long long)pr.nsub * pr.nl; }
+  long long nl_len() const { return (long long)pr.nl * pr.P; }
   long long nvec() const { return (long long)pr.nsub * pr.nl * pr.P; }
   long long nGd() const { return (long long)pr.nG * pr.P; }
 };
@@ -790,7 +791,11 @@ static int ensure_ws(sg_handle h, int nb) {
     RET(dalloc(h, &w.p0, len)); RET(dalloc(h, &w.p1, len)); RET(dalloc(h, &w.q, len));
     w.cap_nb = nb;
   }
-  if (h->mesh) return ensure_ctl(h, nb, 1, 1);  // one p.q, r.z, r.r per problem
+  if (h->mesh) {
+    // one p.q, r.z, r.r per problem; the tensor-core loop keeps per-block p.q and per-row-tile partials
+    const int nt = h->mma ? (int)((h->nl_len() + 255) / 256) : 1;
+    return ensure_ctl(h, nb, nt, h->mma ? std::max(h->pr.P, h->MT) : 1);
+  }
   int TL, NT, stage;
   size_t sm;
   apply_cfg<T>(h->pr, nb, &TL, &NT, &sm, &stage);
@@ -965,6 +970,55 @@ static int enq_inner(sg_handle h, Ctx& cx, int pat, int nb, int R, int s0, const
   });
 }
 
+// FP32 mesh solves with the mean-operator inverse on the tensor cores (SG_BF16 on a mesh): the loop of
+// the structured tensor-core path (k_cg_pack: CG update and BF16 residual image; k_pre_mma: the product
+// and the loop control) behind the mesh's fused direction-and-apply kernel.  The inverse image holds
+// patterns 0 and 1.
+static int enq_inner_mesh_mma(sg_handle h, Ctx& cx, int pat, int nb, int R, int s0, const float* rhs, double tol2,
+                              double bb_min, int imax, int mask) {
+  const auto& pr = h->pr;
+  auto& w = h->ws32;
+  const long long len = h->nl_len(), n = len * nb;
+  const int NT = (int)((len + 255) / 256);
+  if (h->bimg_cap < nb || h->ctl_cap_nt < NT || h->ctl_cap_ng < h->MT) {
+    h->err = "mesh tensor-core solve: residual image or control arrays smaller than the batch";
+    return SG_EINVAL;
+  }
+  const sgm::Rows<float> rows = h->mrows<float>();
+  const int row0 = (pat * pr.nsub + s0) * h->Kp;
+  auto pre = [&](Ctx& cc, int init, cudaGraphConditionalHandle hh, int use) -> int {
+    cudaStream_t s = cc.st;
+    const unsigned gp = (unsigned)nb * h->NC, gm = (unsigned)nb * h->MT;
+    if (h->mma_nb == 32)
+      sgk::k_cg_pack<32, 2><<<gp, 256, 0, s>>>(0, pr.nl, pr.P, h->NC, NT, w.x, w.r, w.p0, w.p1, w.q, h->ctl, init,
+                                                h->bimg);
+    else
+      sgk::k_cg_pack<16, 2><<<gp, 256, 0, s>>>(0, pr.nl, pr.P, h->NC, NT, w.x, w.r, w.p0, w.p1, w.q, h->ctl, init,
+                                                h->bimg);
+    if (h->mma_nb == 32)
+      sgk::k_pre_mma<32><<<gm, 256, (size_t)sgk::PreShape<32, 2>::SMEM, s>>>(
+          h->tmA, 0, pr.nl, pr.P, R, h->MT, h->NC, NT, h->Kp, row0, nb, h->bimg, w.r, w.z, h->ctl, init, tol2, bb_min,
+          imax, hh, use, h->ctl.breakdown);
+    else
+      sgk::k_pre_mma<16><<<gm, 256, (size_t)sgk::PreShape<16, 2>::SMEM, s>>>(
+          h->tmA, 0, pr.nl, pr.P, R, h->MT, h->NC, NT, h->Kp, row0, nb, h->bimg, w.r, w.z, h->ctl, init, tol2, bb_min,
+          imax, hh, use, h->ctl.breakdown);
+    CKL();
+    return SG_OK;
+  };
+  CK(cudaMemcpyAsync(w.r, rhs, sizeof(float) * n, cudaMemcpyDeviceToDevice, cx.st));
+  CK(cudaMemsetAsync(w.x, 0, sizeof(float) * n, cx.st));
+  cudaGraphConditionalHandle hnd;
+  RET(make_handle(h, cx, &hnd));
+  RET(pre(cx, 1, hnd, cx.capture ? 1 : 0));
+  return cond_node(h, cx, hnd, true, h->ctl.cond, [&](Ctx& c2) -> int {
+    sgk::k_mapply_cg<float><<<(unsigned)nb * NT, 256, 0, c2.st>>>(rows, h->cls, s0, R, NT, w.z, w.p0, w.p1, w.q,
+                                                                  (float)h->am, (float)h->bk, mask, h->ctl);
+    CKL();
+    return pre(c2, 0, hnd, c2.capture ? 1 : 0);
+  });
+}
+
 // The same batched solve on the sparse rows of a mesh problem: CG preconditioned by the dense inverse
 // of each subdomain's mean operator on the pattern's rows; per iteration the apply (active problems),
 // p.q, the update, the preconditioner, r.r and r.z, the control (loop condition) and the new
@@ -989,6 +1043,9 @@ static int enq_inner_mesh(sg_handle h, Ctx& cx, int pat, int nb, int R, int s0, 
   const sgm::Rows<T> rows = h->mrows<T>();
   const T am = (T)h->am, bk = (T)h->bk;
   cudaStream_t st = cx.st;
+  if constexpr (sizeof(T) == 4) {
+    if (h->mma && pat < 2) return enq_inner_mesh_mma(h, cx, pat, nb, R, s0, rhs, tol2, bb_min, imax, mask);
+  }
   CK(cudaMemcpyAsync(w.r, rhs, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemsetAsync(w.x, 0, sizeof(T) * n, st));
   sgk::k_mdense<T><<<nblk(n), 256, 0, st>>>(Ainv, npat, s0, nb, R, pr.nl, pr.P, w.r, w.z, nullptr);
@@ -2148,6 +2205,52 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
   return finish_setup(h);
 }
 
+// BF16 image of the mesh's mean-operator inverses (patterns 0 and 1, rows padded to Kp = nl rounded up to
+// the 128-row tile) and its tensor map, as build_mma_precond lays out the grid's.
+constexpr int MESH_MMA_NL_MAX = 1600;  // the grid's limit: 40 x 40 nodes
+static int build_mesh_mma(sg_handle h, const std::vector<double>* inv) {
+  const auto& pr = h->pr;
+  const int nl = pr.nl;
+  h->Kp = (nl + sgk::MMA_M - 1) / sgk::MMA_M * sgk::MMA_M;
+  h->NC = h->Kp / sgk::MMA_KC;
+  h->MT = h->Kp / sgk::MMA_M;
+  h->mma_nb = pr.P <= 16 ? 16 : 32;
+  const long long per = (long long)pr.nsub * h->Kp * h->Kp;
+  {
+    std::vector<__nv_bfloat16> img((size_t)(2 * per), __float2bfloat16_rn(0.f));
+    for (int pat = 0; pat < 2; ++pat)
+      for (int s = 0; s < pr.nsub; ++s)
+        for (int a = 0; a < nl; ++a)
+          for (int c = 0; c < nl; ++c)
+            img[(size_t)pat * per + ((size_t)s * h->Kp + a) * h->Kp + c] =
+                __float2bfloat16_rn((float)inv[pat][((size_t)s * nl + a) * nl + c]);
+    RET(upload(h, &h->ainv, img));
+  }
+  PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  cudaDriverEntryPointQueryResult qr;
+  CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&enc, 12000, cudaEnableDefault, &qr));
+  if (!enc || qr != cudaDriverEntryPointSuccess) {
+    h->err = "cuTensorMapEncodeTiled is not available from the driver";
+    return SG_ECUDA;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)h->Kp, (cuuint64_t)(2LL * pr.nsub * h->Kp)};
+  const cuuint64_t strides[1] = {(cuuint64_t)h->Kp * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)sgk::MMA_KC, (cuuint32_t)sgk::MMA_M};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult cr = enc(&h->tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, h->ainv, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) {
+    h->err = "tensor map encoding of the mean-operator inverse failed";
+    return SG_ECUDA;
+  }
+  RET(smem_attr(h, sgk::k_pre_mma<32>, sgk::PreShape<32, 2>::SMEM));
+  RET(smem_attr(h, sgk::k_pre_mma<16>, sgk::PreShape<16, 2>::SMEM));
+  h->mma = true;
+  RET(ensure_bimg(h, pr.nsub));
+  return ensure_ws<float>(h, pr.nsub);
+}
+
 // General partition of a triangle mesh: host tables (vertex classes with the Sec. 3 corners, sparse
 // rows, maps), the dense mean-operator inverses in the subdomain-solve precision, then the shared
 // uploads, coarse space and initial state.
@@ -2157,10 +2260,6 @@ static int setup_mesh_impl(sg_handle h, const sg_mesh* m, const sg_kl* kl, const
   RET(check_source(h, src, &sd));
   if (prm->precision < SG_FP64 || prm->precision > SG_BF16) { h->err = "precision"; return SG_EINVAL; }
   if (prm->precond < SG_PC_NN2 || prm->precond > SG_PC_LUMPED) { h->err = "precond"; return SG_EINVAL; }
-  if (prm->precision == SG_BF16) {
-    h->err = "SG_BF16: the tensor-core preconditioners need the structured grid";
-    return SG_ENOTSUP;
-  }
   if (m->nv < 3 || m->ne < 1 || !m->xy || !m->dirichlet || !m->tri || !m->part) {
     h->err = "mesh: vertices, triangles and partition required";
     return SG_EINVAL;
@@ -2176,6 +2275,11 @@ static int setup_mesh_impl(sg_handle h, const sg_mesh* m, const sg_kl* kl, const
   if (!msg.empty()) { h->err = msg; return SG_EINVAL; }
   auto& pr = h->pr;
   pr.sigma = kl->sigma; pr.bx = kl->bx; pr.by = kl->by; pr.g0 = kl->g0;
+  if (prm->precision == SG_BF16 && (pr.P > 32 || pr.nl > MESH_MMA_NL_MAX)) {
+    h->err = "SG_BF16: the BF16 tensor-core preconditioner needs P <= 32 and at most " +
+             std::to_string(MESH_MMA_NL_MAX) + " free vertices per subdomain";
+    return SG_ENOTSUP;
+  }
   h->mesh = true;
   RET(apply_params(h, prm));
   // dense inverses of the mean operators (FP64 on the host): Dirichlet and Neumann patterns, and the
@@ -2196,6 +2300,8 @@ static int setup_mesh_impl(sg_handle h, const sg_mesh* m, const sg_kl* kl, const
     std::vector<float> g32(pr.gk_v.begin(), pr.gk_v.end());
     RET(upload(h, &h->m_kv32, k32)); RET(upload(h, &h->m_mv32, m32)); RET(upload(h, &h->gk_v32, g32));
   }
+  // SG_BF16: the FP32 solves of patterns 0 and 1 take the inverse's BF16 image on the tensor cores
+  if (h->policy == SG_BF16) RET(build_mesh_mma(h, inv));
   for (int pat = 0; pat < npat; ++pat) {
     if (h->precision == SG_FP64) {
       RET(upload(h, &h->m_ainv[pat], inv[pat]));

@@ -2985,7 +2985,7 @@ __global__ void __launch_bounds__(256) k_cg_pack(int L, int nl, int P, int NC, i
       vq = lane < NT ? ctl.part_pq[(long long)b * NT + lane] : 0.0;
     }
   }
-  const int LL = L * L;
+  const int LL = nl;  // nodes per problem (L^2 on the grid, the padded vertex count on a mesh)
   const long long base = (long long)b * nl * P;
   const int n0 = c * 64;
   // values of the chunk's nodes (contiguous); the last chunks of the padded Kp rows may hold none
@@ -3160,7 +3160,7 @@ __global__ void __launch_bounds__(256, 1) k_pre_mma(const __grid_constant__ CUte
   // product, so that its latency overlaps the pipeline instead of following it
   constexpr int EPT = MMA_M * NB / 256;
   const int m0 = tile * MMA_M;
-  const int rows = min(MMA_M, L * L - m0);
+  const int rows = min(MMA_M, nl - m0);  // nl = L^2 on the grid
   const int cnt = rows > 0 ? rows * P : 0;
   const long long o = (long long)b * nl * P + (long long)m0 * P;
   float rpre[EPT];

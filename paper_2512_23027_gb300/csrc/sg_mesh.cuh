@@ -169,4 +169,45 @@ __global__ void __launch_bounds__(256) k_mcg_dir(long long len, int nb, CgCtl ct
   p[idx] = init ? z[idx] : z[idx] + (T)ctl.beta[b] * p[idx];
 }
 
+// Direction and product of the tensor-core CG loop (the contract of the structured fused apply, which
+// k_cg_pack and k_pre_mma follow): p_new = z + beta p_old with p_old = parity ? p1 : p0 and p_new the
+// other buffer, q = A p_new on the pattern rows (0 elsewhere; p_new at the neighbours is formed on
+// the fly from z and p_old), and the partial of p_new . q of block (b, tile) in part_pq[b * NT + tile].
+// Grid: nb x NT blocks of 256 threads, block tile covering entries [256 tile, 256 tile + 256) of the
+// problem's nl * P values.  Inactive problems are skipped.
+template <typename T>
+__global__ void __launch_bounds__(256) k_mapply_cg(sgm::Rows<T> r, const uint8_t* __restrict__ cls, int s0, int R,
+                                                   int NT, const T* __restrict__ z, T* p0, T* p1, T* __restrict__ q,
+                                                   T am, T bk, int out_mask, CgCtl ctl) {
+  count_launch();
+  const int b = blockIdx.x / NT, tile = blockIdx.x - (blockIdx.x / NT) * NT;
+  if (!ctl.active[b]) return;  // uniform over the block
+  const int par = *ctl.parity;
+  const T* pold = par ? p1 : p0;
+  T* pnew = par ? p0 : p1;
+  const T bet = (T)ctl.beta[b];
+  const long long len = (long long)r.nl * r.P;
+  const long long t = (long long)tile * 256 + threadIdx.x;
+  double s = 0.0;
+  if (t < len) {
+    const long long o = (long long)b * len;
+    const int a = (int)(t / r.P), k = (int)(t - (long long)a * r.P);
+    const long long row = (long long)(s0 + b / R) * r.nl + a;
+    const T pn = bet != T(0) ? z[o + t] + bet * pold[o + t] : z[o + t];
+    pnew[o + t] = pn;
+    T out = T(0);
+    if ((out_mask >> cls[row]) & 1) out = sgm::apply_row_dir(r, row, k, z + o, pold + o, bet, am, bk);
+    q[o + t] = out;
+    s = (double)pn * (double)out;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ctl.part_pq[(long long)b * NT + tile] = red[0];
+}
+
 }  // namespace sgk

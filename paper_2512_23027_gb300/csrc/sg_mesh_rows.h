@@ -50,6 +50,30 @@ SG_HD T apply_row(const Rows<T>& r, long long row, int k, const T* xm, const T* 
   return acc;
 }
 
+// Mode k of row `row` of (am M (x) I + bk sum_i K_i (x) G_i) p for a CG direction formed on the fly,
+// p = z + bet pold (pold is read only when bet != 0, so that it may hold anything before the first
+// direction): am sum_b M[a][b] p[b][k] + bk sum_b sum_{(i,j)} G_ijk K_i[a][b] p[b][j].
+template <typename T>
+SG_HD T apply_row_dir(const Rows<T>& r, long long row, int k, const T* z, const T* pold, T bet, T am, T bk) {
+  T acc = T(0);
+  const int e0 = r.rp[row], e1 = r.rp[row + 1];
+  const int g0 = r.gk_ptr[k], g1 = r.gk_ptr[k + 1];
+  const bool usep = bet != T(0);
+  for (int e = e0; e < e1; ++e) {
+    const long long cb = (long long)r.col[e] * r.P;
+    const T pk = usep ? z[cb + k] + bet * pold[cb + k] : z[cb + k];
+    T s = T(0);
+    const T* kw = r.kv + (long long)e * r.PI;
+    for (int g = g0; g < g1; ++g) {
+      const long long j = cb + r.gk_j[g];
+      const T pj = usep ? z[j] + bet * pold[j] : z[j];
+      s += r.gk_v[g] * kw[r.gk_i[g]] * pj;
+    }
+    acc += am * r.mv[e] * pk + bk * s;
+  }
+  return acc;
+}
+
 // Mode k of row a of (I (x) A0^{-1}) rv on a pattern of n rows: sum_{c < n} Ainv[a][c] rv[c][k], with
 // `arow` row a of the subdomain's inverse (nl columns, zero beyond n) and rv the problem's vector.
 template <typename T>

@@ -3,9 +3,13 @@
 // device layout built by sg_host.cpp, for comparison with the oracle (tests/test_host_mesh.py).
 // Plain C++17, no GPU.
 // Usage: mesh_rows_check mesh_file layout_file x_file.  mesh_file and layout_file as mesh_dump;
-// x_file holds "cm ck" and then nsub * nl * P values (one local vector per subdomain, node-major).
+// x_file holds "cm ck" and then two vectors of nsub * nl * P values, x and w (one local vector per
+// subdomain, node-major).
 // Output: "y v..." = cm (M (x) I) x + ck (sum_i K_i (x) G_i) x on every free row (0 on padding rows),
-// "z0 v...", "z1 v..." = (I (x) A0^{-1}) x on patterns 0 and 1 (x restricted to the pattern's rows).
+// "z0 v...", "z1 v..." = (I (x) A0^{-1}) x on patterns 0 and 1 (x restricted to the pattern's rows),
+// "d1 v..." = the same operator as y applied to the direction x + 0.25 w formed on the fly
+// (apply_row_dir), "d0 v..." = apply_row_dir with beta 0 and w replaced by NaN (never read).
+#include <cmath>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -61,8 +65,10 @@ int main(int argc, char** argv) {
   if (!h) return 2;
   double cm, ck;
   if (std::fscanf(h, "%lf %lf", &cm, &ck) != 2) return 2;
-  std::vector<double> x((size_t)nsub * len);
+  std::vector<double> x((size_t)nsub * len), wv((size_t)nsub * len);
   for (auto& v : x)
+    if (std::fscanf(h, "%lf", &v) != 1) return 2;
+  for (auto& v : wv)
     if (std::fscanf(h, "%lf", &v) != 1) return 2;
   std::fclose(h);
   sgm::Rows<double> r;
@@ -79,6 +85,21 @@ int main(int argc, char** argv) {
     if (pr.cls[rw] != sgh::DIRICHLET) y[idx] = sgm::apply_row(r, rw, k, x.data() + b * len, x.data() + b * len, cm, ck);
   }
   row("y", y);
+  const std::vector<double> nanv((size_t)nsub * len, std::nan(""));
+  for (int pass = 0; pass < 2; ++pass) {
+    const double bet = pass == 0 ? 0.25 : 0.0;
+    const double* pold = pass == 0 ? wv.data() : nanv.data();
+    std::vector<double> d((size_t)nsub * len, 0.0);
+    for (long long idx = 0; idx < nsub * len; ++idx) {
+      const int b = (int)(idx / len);
+      const long long t = idx - (long long)b * len;
+      const int a = (int)(t / P), k = (int)(t - (long long)a * P);
+      const long long rw = (long long)b * nl + a;
+      if (pr.cls[rw] != sgh::DIRICHLET)
+        d[idx] = sgm::apply_row_dir(r, rw, k, x.data() + b * len, pold + b * len, bet, cm, ck);
+    }
+    row(pass == 0 ? "d1" : "d0", d);
+  }
   for (int pat = 0; pat < 2; ++pat) {
     std::vector<double> inv;
     if (!sgh::mesh_mean_inverse(pr, mr, pat, am, bk, inv)) return 1;

@@ -290,8 +290,11 @@ def rows_exe(tmp_path_factory):
 def test_mesh_kernel_rows_match_oracle(dump_exe, rows_exe, tmp_path, name, mesh, part):
     """The per-row functions the mesh kernels call (sg_mesh_rows.h), run on the host with the kernels'
     index decomposition: the SG operator apply equals cm (M (x) I) x + ck sum_i (K_i (x) G_i) x formed
-    from the oracle's subdomain matrices and triple products (Sec. 4, Eq. stok), and the dense
-    preconditioner solves the oracle's mean operator am M + bk K_0 on the Dirichlet and Neumann rows."""
+    from the oracle's subdomain matrices and triple products (Sec. 4, Eq. stok), also on a CG direction
+    formed on the fly (and the plain apply, to rounding, when beta = 0: the old direction, NaN here, is
+    then never read), and
+    the dense preconditioner solves the oracle's mean operator am M + bk K_0 on the Dirichlet and
+    Neumann rows."""
     prob = w.config("small").replace(M=3, p=2, p_in=4, sigma=0.4, bx=0.4, by=0.6)
     dt, a0, a1 = 0.02, 0.3, 0.002
     am = 1.0 / (0.25 * dt * dt) + a0 * 0.5 / (0.25 * dt)
@@ -303,12 +306,14 @@ def test_mesh_kernel_rows_match_oracle(dump_exe, rows_exe, tmp_path, name, mesh,
     nsub, P = up.nsub, prob.P
     rng = np.random.default_rng(3)
     x = rng.standard_normal((nsub, nl, P))
+    wv = rng.standard_normal((nsub, nl, P))
     cm, ck = 0.7, -1.3
-    (tmp_path / "x.txt").write_text(f"{cm!r} {ck!r}\n" + " ".join(f"{v:.17g}" for v in x.ravel()) + "\n")
+    (tmp_path / "x.txt").write_text(f"{cm!r} {ck!r}\n" + " ".join(f"{v:.17g}" for v in x.ravel()) + "\n" +
+                                    " ".join(f"{v:.17g}" for v in wv.ravel()) + "\n")
     out = subprocess.run([rows_exe, str(tmp_path / "mesh.txt"), str(tmp_path / "layout.txt"), str(tmp_path / "x.txt")],
                          check=True, capture_output=True, text=True).stdout
     res = {ln.split()[0]: np.array([float(v) for v in ln.split()[1:]]) for ln in out.splitlines()}
-    y, z0, z1 = (res[k].reshape(nsub, nl, P) for k in ("y", "z0", "z1"))
+    y, z0, z1, d1, d0 = (res[k].reshape(nsub, nl, P) for k in ("y", "z0", "z1", "d1", "d0"))
     coef = up.element_coefficients(prob)
     G = pce_triple(prob)
     vcls = np.zeros(mesh.nn, dtype=int)
@@ -328,6 +333,14 @@ def test_mesh_kernel_rows_match_oracle(dump_exe, rows_exe, tmp_path, name, mesh,
             ref += ck * (Kr[i] @ X) @ G[i]        # [(K_i X) G_i]_{a,k} = sum_j G_ijk (K_i X_j)_a
         assert np.abs(y[s, :n] - ref).max() <= 1e-12 * np.abs(ref).max()
         assert np.all(y[s, n:] == 0.0)
+        # the CG direction formed on the fly (the tensor-core loop's apply): p = x + 0.25 w, and with
+        # beta 0 the old direction is never read
+        Pd = X + 0.25 * wv[s, :n]
+        refd = cm * Mr @ Pd
+        for i in range(len(Kr)):
+            refd += ck * (Kr[i] @ Pd) @ G[i]
+        assert np.abs(d1[s, :n] - refd).max() <= 1e-12 * np.abs(refd).max()
+        assert np.all(np.isfinite(d0[s])) and np.abs(d0[s] - y[s]).max() <= 1e-14 * np.abs(y[s]).max()
         A0 = am * Mr + bk * Kr[0]
         c = vcls[v]
         for z, m in ((z0, int((c == 1).sum())), (z1, int((c <= 2).sum()))):

@@ -75,8 +75,9 @@ def bad(kind):
         kw["src"] = w.Source(5, 0.5, 0.5, 0.05, 10.0, 1.0)
     elif kind == "precision":
         kw["precision"] = 7
-    elif kind == "bf16":
+    elif kind == "bf16 with P > 32":
         kw["precision"] = 3
+        kw["prob"] = w.config("tiny").replace(M=4, p=3, p_in=3)    # P = 35
     elif kind == "warm-start mode":
         kw["warm"] = 9
     elif kind == "modes without lambdas":
@@ -95,7 +96,7 @@ CASES = [
     ("source outside the mesh", SG_EINVAL, "no triangle"),
     ("source kind", SG_EINVAL, "source"),
     ("precision", SG_EINVAL, "precision"),
-    ("bf16", SG_ENOTSUP, "SG_BF16"),
+    ("bf16 with P > 32", SG_ENOTSUP, "SG_BF16"),
     ("warm-start mode", SG_EINVAL, "warm"),
     ("modes without lambdas", SG_EINVAL, "lambdas"),
     ("too few vertices", SG_EINVAL, "mesh"),
@@ -117,13 +118,14 @@ def test_null_mesh(B):
 def test_valid_mesh_passes_the_host_steps(B):
     """Without a GPU the first CUDA call fails: every host step before it accepted the mesh (an RCB
     partition of a Delaunay mesh into three subdomains, which meet at a corner; pulse and Ricker
-    sources; FP64 and mixed precision; the two-level and the one-level preconditioner, whose third
-    pattern adds one more mean-operator inverse)."""
+    sources; FP64, mixed precision and SG_BF16 (its tensor-core image is built after the first CUDA
+    call); the two-level and the one-level preconditioner, whose third pattern adds one more
+    mean-operator inverse)."""
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
         pytest.skip("a GPU is visible: this checks the host steps on a machine without one")
     for src in (w.Source(1, 0.5, 0.5, 0.1, 0.0, 1.0), w.Source(2, 0.37, 0.61, 0.0, 10.0, 1.0)):
-        for precision, precond in ((0, 0), (1, 0), (0, 1)):
+        for precision, precond in ((0, 0), (1, 0), (0, 1), (3, 0)):
             rc, h, err = setup_rc(B, *base_mesh(), src=src, precision=precision, precond=precond)
             assert rc == SG_ECUDA and h is None, (rc, err)
 
