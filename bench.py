@@ -374,14 +374,17 @@ def run_mesh(args):
     import torch
     import sg_workloads as w
     from paper_2512_23027_gb300 import Solver
-    from paper_2512_23027_gb300.binding import SG_FP64, SG_MIXED, SG_WARM_LEARNED, SG_WARM_PREV
+    from paper_2512_23027_gb300.binding import SG_BF16, SG_FP64, SG_MIXED, SG_WARM_LEARNED, SG_WARM_PREV
     c = w.mesh_config(args.mesh)
     mesh = c.build()
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     legs = {}
-    for key, precision, warm, K in (("mixed_learned", SG_MIXED, SG_WARM_LEARNED, args.steps),
-                                    ("fp64", SG_FP64, SG_WARM_PREV, min(args.steps, args.fp64_steps))):
+    plan = [("mixed_learned", SG_MIXED, SG_WARM_LEARNED, args.steps),
+            ("fp64", SG_FP64, SG_WARM_PREV, min(args.steps, args.fp64_steps))]
+    if c.prob.P <= 32:   # the tensor-core mean-operator product (SG_BF16) where it applies
+        plan.insert(1, ("bf16_learned", SG_BF16, SG_WARM_LEARNED, args.steps))
+    for key, precision, warm, K in plan:
         t0 = time.perf_counter()
         sv = Solver(c.prob, precision=precision, warm=warm, stream=stream, mesh=mesh)
         setup = time.perf_counter() - t0
@@ -403,7 +406,7 @@ def run_mesh(args):
             "value": legs["mixed_learned"]["steps_per_s"], "unit": "steps/s", "higher_is_better": True,
             "steps": args.steps, "warmup": max(3, args.warmup), "dtype": "f32+f64", "data": "synthetic",
             "speedup_vs_fp64": legs["mixed_learned"]["steps_per_s"] / legs["fp64"]["steps_per_s"],
-            "mixed_learned": legs["mixed_learned"], "fp64": legs["fp64"],
+            "mixed_learned": legs["mixed_learned"], "fp64": legs["fp64"], "bf16_learned": legs.get("bf16_learned"),
             "config": {"workload": c.name, "vertices": int(mesh[0].shape[0]), "triangles": int(mesh[2].shape[0]),
                        "subdomains": c.nparts, "M": p.M, "p": p.p, "P": p.P, "dt": p.dt, "tol": p.tol,
                        "l2": "256 MB buffer written between timed steps"}}
