@@ -251,6 +251,31 @@ typedef struct {
 int sg_setup_mesh(const sg_mesh* mesh, const sg_kl* kl, const sg_pce* pce, const sg_params* params,
                   const sg_source* src, void* stream, sg_handle* out);
 
+/* Sizes and device-memory needs of a mesh problem, from the host set-up of sg_setup_mesh alone (no
+ * device memory, no CUDA call; works without a GPU): to choose a partition that fits before building
+ * the solver.  Byte counts are the large device arrays sg_setup_mesh allocates for params->precision
+ * and params->precond. */
+typedef struct {
+  int nsub, n_free, n_gamma, n_corner;  /* subdomains, free vertices, interface vertices, corners     */
+  int P, P_in, nnz_G;                   /* PCE terms (output, input), nonzero triple products        */
+  int n_sub_nodes;                      /* free vertices of the largest subdomain (local layout rows) */
+  int max_owners;                       /* most subdomains sharing one interface vertex              */
+  int max_corners;                      /* most corners of one subdomain                             */
+  int max_gamma;                        /* most interface vertices of one subdomain                  */
+  long long row_entries;                /* sparse-row entries of all subdomains                      */
+  long long coarse_dim;                 /* n_corner * P: order of the coarse matrix F_cc             */
+  long long bytes_rows;                 /* sparse rows (FP64 and FP32 values)                        */
+  long long bytes_inverses;             /* dense mean-operator inverses (+ the BF16 image for SG_BF16) */
+  long long bytes_coarse_basis;         /* local coarse bases of the two-level preconditioner        */
+  long long bytes_coarse_matrix;        /* dense FP64 inverse of F_cc                                */
+  long long bytes_vectors;              /* state, step and subdomain-solve vectors                   */
+  int mma;                              /* 1: SG_BF16's tensor-core product applies                  */
+} sg_mesh_plan;
+
+/* Errors as sg_setup_mesh's host checks (SG_EINVAL with a message in sg_last_error(NULL)). */
+int sg_mesh_plan_query(const sg_mesh* mesh, const sg_kl* kl, const sg_pce* pce, const sg_params* params,
+                       sg_mesh_plan* out);
+
 /* Advance nsteps Newmark steps (Alg. 1 loop, stochastic form of Sec. 5): effective load
  * (Eqs. fparts, UmCm), condensed RHS G_Gamma, PCG with M_NNC^{-1}, interior recovery, Newmark
  * update.  stats may be NULL.  Returns SG_ENOTCONV (state still advanced) if a step hit

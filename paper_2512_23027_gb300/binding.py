@@ -46,6 +46,15 @@ class Mesh(C.Structure):
                 ("tri", C.c_void_p), ("part", C.c_void_p)]
 
 
+class MeshPlan(C.Structure):
+    _fields_ = [("nsub", C.c_int), ("n_free", C.c_int), ("n_gamma", C.c_int), ("n_corner", C.c_int), ("P", C.c_int),
+                ("P_in", C.c_int), ("nnz_G", C.c_int), ("n_sub_nodes", C.c_int), ("max_owners", C.c_int),
+                ("max_corners", C.c_int), ("max_gamma", C.c_int), ("row_entries", C.c_longlong),
+                ("coarse_dim", C.c_longlong), ("bytes_rows", C.c_longlong), ("bytes_inverses", C.c_longlong),
+                ("bytes_coarse_basis", C.c_longlong), ("bytes_coarse_matrix", C.c_longlong),
+                ("bytes_vectors", C.c_longlong), ("mma", C.c_int)]
+
+
 class Source(C.Structure):
     _fields_ = [("kind", C.c_int), ("x0", C.c_double), ("y0", C.c_double), ("width", C.c_double),
                 ("freq", C.c_double), ("amp", C.c_double)]
@@ -112,6 +121,8 @@ def load_library(path: Optional[str] = None):
     lib.sg_step_host.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, P(Stats)]
     lib.sg_get_sizes.argtypes = [C.c_void_p, P(Sizes)]
     lib.sg_plan_query.argtypes = [P(Grid), P(KL), P(PCE), P(Params), P(Plan)]
+    lib.sg_mesh_plan_query.argtypes = [P(Mesh), P(KL), P(PCE), P(Params), P(MeshPlan)]
+    lib.sg_mesh_plan_query.restype = C.c_int
     lib.sg_plan_query.restype = C.c_int
     lib.sg_get_iters.argtypes = [C.c_void_p, P(C.c_int), D, C.c_int]
     lib.sg_destroy.argtypes = [C.c_void_p]
@@ -335,6 +346,26 @@ def plan_query(prob, precision: int = SG_FP64) -> dict:
     if rc != 0:
         raise SGError(rc, lib.sg_last_error(None).decode())
     return {f: _plain(getattr(out, f)) for f, _ in Plan._fields_}
+
+
+def mesh_plan_query(prob, mesh, precision: int = SG_FP64, precond: int = SG_PC_NN2) -> dict:
+    """Sizes and device-memory needs of `prob` on mesh = (xy, dirichlet, tri, part) (host-only; no GPU
+    needed), as a dict of the sg_mesh_plan fields."""
+    lib = load_library()
+    xy, dirichlet, tri, part = mesh
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    dirichlet = np.ascontiguousarray(dirichlet, dtype=np.uint8)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    part = np.ascontiguousarray(part, dtype=np.int32)
+    m = Mesh(xy.shape[0], xy.ctypes.data, dirichlet.ctypes.data, tri.shape[0], tri.ctypes.data, part.ctypes.data)
+    kl, pce = KL(prob.M, prob.sigma, prob.bx, prob.by, prob.g0), PCE(prob.p, prob.p_in)
+    prm = Params(prob.dt, prob.tol, prob.alpha0, prob.alpha1, prob.max_iter, precision, SG_WARM_PREV, 0.0, 0, 0, 0, 0.0,
+                 precond)
+    out = MeshPlan()
+    rc = lib.sg_mesh_plan_query(C.byref(m), C.byref(kl), C.byref(pce), C.byref(prm), C.byref(out))
+    if rc != 0:
+        raise SGError(rc, lib.sg_last_error(None).decode())
+    return {f: getattr(out, f) for f, _ in MeshPlan._fields_}
 
 
 def solve_batch(solvers: Sequence[Solver], nsteps: int):

@@ -2694,6 +2694,56 @@ int sg_get_sizes(sg_handle h, sg_sizes* out) {
   return SG_OK;
 }
 
+int sg_mesh_plan_query(const sg_mesh* mesh, const sg_kl* kl, const sg_pce* pce, const sg_params* params,
+                       sg_mesh_plan* out) {
+  if (!mesh || !kl || !pce || !params || !out) { g_setup_err = "null argument"; return SG_EINVAL; }
+  if (params->precision < SG_FP64 || params->precision > SG_BF16) { g_setup_err = "precision"; return SG_EINVAL; }
+  if (params->precond < SG_PC_NN2 || params->precond > SG_PC_LUMPED) { g_setup_err = "precond"; return SG_EINVAL; }
+  if (mesh->nv < 3 || mesh->ne < 1 || !mesh->xy || !mesh->dirichlet || !mesh->tri || !mesh->part) {
+    g_setup_err = "mesh: vertices, triangles and partition required";
+    return SG_EINVAL;
+  }
+  sgh::MeshProblem mp;
+  std::string msg = sgh::build_mesh_problem(mp, mesh->nv, mesh->xy, mesh->dirichlet, mesh->ne, mesh->tri, mesh->part,
+                                            kl->M, kl->sigma, kl->bx, kl->by, kl->g0, pce->p, pce->p_in, kl->modes,
+                                            kl->modes ? kl->lambdas : nullptr);
+  if (!msg.empty()) { g_setup_err = msg; return SG_EINVAL; }
+  sgh::Problem pr;
+  sgh::MeshRows mr;
+  const sgh::SourceDesc sd{0, 0.5, 0.5, 0.05, 10.0, 1.0};
+  msg = sgh::mesh_to_problem(pr, mr, mp, mesh->xy, mesh->tri, params->dt, params->alpha0, params->alpha1, sd);
+  if (!msg.empty()) { g_setup_err = msg; return SG_EINVAL; }
+  sg_mesh_plan p{};
+  p.nsub = pr.nsub; p.n_free = pr.n_free; p.n_gamma = pr.nG; p.n_corner = pr.nC;
+  p.P = pr.P; p.P_in = pr.PI; p.nnz_G = (int)pr.gk_v.size();
+  p.n_sub_nodes = pr.nl; p.max_owners = pr.mo; p.max_corners = pr.max_corner; p.max_gamma = pr.nGam;
+  p.row_entries = (long long)mr.col.size();
+  p.coarse_dim = (long long)pr.nC * pr.P;
+  const bool fp64 = params->precision == SG_FP64;
+  const long long nloc = (long long)pr.nsub * pr.nl, nvec = nloc * pr.P;
+  // sparse rows: columns, FP64 and FP32 values (mass and every input-mode stiffness), row pointers
+  p.bytes_rows = p.row_entries * (4 + 12LL * (pr.PI + 1)) + 4 * (nloc + 1);
+  // dense mean-operator inverses in the subdomain-solve type, plus the BF16 image for SG_BF16
+  const int npat = params->precond == SG_PC_NN1 ? 3 : 2;
+  p.bytes_inverses = (long long)npat * pr.nsub * pr.nl * pr.nl * (fp64 ? 8 : 4);
+  p.mma = params->precision == SG_BF16 && pr.P <= 32 && pr.nl <= MESH_MMA_NL_MAX ? 1 : 0;
+  if (p.mma) {
+    const long long kp = (pr.nl + sgk::MMA_M - 1) / sgk::MMA_M * sgk::MMA_M;
+    p.bytes_inverses += 2LL * pr.nsub * kp * kp * 2;
+  }
+  // coarse space of the two-level preconditioner: local bases Phi and the dense inverse of F_cc
+  if (params->precond == SG_PC_NN2) {
+    p.bytes_coarse_basis = (long long)pr.nsub * std::max(pr.max_corner * pr.P, 1) * pr.nGam * pr.P * 8;
+    p.bytes_coarse_matrix = p.coarse_dim * p.coarse_dim * 8;
+  }
+  // state and step vectors of the local layout (FP64: U, V, A, the Newmark and work vectors, the
+  // interior accumulator of the mixed path; FP32: two work vectors) and the inner-CG workspaces of
+  // both types (six vectors each, one problem per subdomain)
+  p.bytes_vectors = nvec * (14 * 8 + 2 * 4) + 6 * nvec * (8 + 4);
+  *out = p;
+  return SG_OK;
+}
+
 int sg_plan_query(const sg_grid* grid, const sg_kl* kl, const sg_pce* pce, const sg_params* params, sg_plan* out) {
   if (!grid || !kl || !pce || !params || !out) { g_setup_err = "null argument"; return SG_EINVAL; }
   sgh::Problem pr;

@@ -172,3 +172,54 @@ def test_mesh_golden_matches_the_generator():
     assert n == len(rec["mode"]) == len(rec["tight"]["values"]) == len(rec["workload"]["values"])
     assert max(rec["node"]) < rec["n_free"] and max(rec["mode"]) < w.mesh_config("umesh37k").prob.P
     assert rec["tight"]["tol"] == 1e-13 and len(rec["tight"]["iters"]) == rec["steps"]
+
+
+def test_mesh_plan_query_matches_the_oracle_partition(B):
+    """sg_mesh_plan_query (host-only) reports the partition's sizes as the oracle's UPartition counts them
+    (free, interface and corner vertices, the largest subdomain, multiplicities, local corners and
+    interface vertices), the sparse-row entries (diagonal plus the free neighbours along triangle edges,
+    per subdomain), the coarse order n_corner * P, and byte counts that follow from them."""
+    from oracle import umesh
+    c = w.mesh_config("umesh_small")
+    xy, d, tri, part = c.build()
+    up = umesh.UPartition(umesh.Mesh(xy, tri, d), part)
+    p = c.prob
+    plan = B.mesh_plan_query(p, (xy, d, tri, part), precision=0)
+    assert (plan["nsub"], plan["n_free"], plan["n_gamma"], plan["n_corner"]) == \
+        (up.nsub, up.free.size, up.iface.size, up.corner.size)
+    nl = max(s["nodes"].size for s in up.subs)
+    assert plan["n_sub_nodes"] == nl and plan["P"] == p.P
+    assert plan["max_owners"] == max(len(up.node_subs[int(g)]) for g in up.iface)
+    assert plan["max_corners"] == max(int((s["cls"] == "c").sum()) for s in up.subs)
+    assert plan["max_gamma"] == max(s["gamma"].size for s in up.subs)
+    free = set(up.free.tolist())
+    entries = 0
+    for s in range(up.nsub):
+        pairs = set()
+        for t in tri[part == s]:
+            for a in t:
+                for b in t:
+                    if int(a) in free and int(b) in free:
+                        pairs.add((int(a), int(b)))
+        entries += len(pairs)
+    assert plan["row_entries"] == entries
+    assert plan["coarse_dim"] == up.corner.size * p.P
+    assert plan["bytes_coarse_matrix"] == (up.corner.size * p.P) ** 2 * 8
+    assert plan["bytes_inverses"] == 2 * up.nsub * nl * nl * 8 and plan["mma"] == 0
+    mixed = B.mesh_plan_query(p, (xy, d, tri, part), precision=1)
+    assert mixed["bytes_inverses"] == 2 * up.nsub * nl * nl * 4
+    bf16 = B.mesh_plan_query(p, (xy, d, tri, part), precision=3)
+    kp = (nl + 127) // 128 * 128
+    assert bf16["mma"] == 1 and bf16["bytes_inverses"] == mixed["bytes_inverses"] + 2 * up.nsub * kp * kp * 2
+    nn1 = B.mesh_plan_query(p, (xy, d, tri, part), precision=0, precond=1)
+    assert nn1["bytes_inverses"] == 3 * up.nsub * nl * nl * 8 and nn1["bytes_coarse_matrix"] == 0
+
+
+def test_mesh_plan_query_of_the_paper_partition(B):
+    """The 37k-vertex mesh on the paper's 720 subdomains: 1284 corners, a coarse matrix of order 25680
+    (5.3 GB dense) at P = 20; on 64 subdomains 49 corners."""
+    for name, corners in (("umesh37k_720", 1284), ("umesh37k", 49)):
+        c = w.mesh_config(name)
+        plan = B.mesh_plan_query(c.prob, c.build())
+        assert plan["n_corner"] == corners and plan["coarse_dim"] == corners * 20
+        assert plan["bytes_coarse_matrix"] == (corners * 20) ** 2 * 8
