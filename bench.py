@@ -424,15 +424,20 @@ def run_profile_step(args):
     import sg_workloads as w
     from paper_2512_23027_gb300 import Solver
     from paper_2512_23027_gb300.binding import SG_FP64, SG_MIXED, SG_WARM_LEARNED
-    prob = w.config(args.config)
-    F = FORWARD.get(args.config, 0) if args.forward is None else args.forward
-    s = Solver(prob, precision=SG_MIXED, warm=SG_WARM_LEARNED)   # the benchmark's optimised configuration
+    if args.mesh:   # a mesh workload (--mesh NAME): its mixed solver with the learned warm start
+        c = w.mesh_config(args.mesh)
+        prob, mesh = c.prob, c.build()
+        F = 20 if args.forward is None else args.forward
+    else:
+        prob, mesh = w.config(args.config), None
+        F = FORWARD.get(args.config, 0) if args.forward is None else args.forward
+    s = Solver(prob, precision=SG_MIXED, warm=SG_WARM_LEARNED, mesh=mesh)   # the benchmark's optimised configuration
     if F:
         s.step(F)
     if args.profile_fp64:
         st0 = s.get_state()
         s.close()
-        s = Solver(prob, precision=SG_FP64)
+        s = Solver(prob, precision=SG_FP64, mesh=mesh)
         s.set_state(st0)
     s.set_eager(True)
     s.step(1)
@@ -484,7 +489,7 @@ def main():
     if args.precond_study:
         return run_precond_study(args)
     if args.profile_step:
-        return run_profile_step(args)
+        return run_profile_step(args)   # with --mesh NAME: a step of that mesh workload
     if args.mesh:
         return run_mesh(args)
 
