@@ -348,6 +348,8 @@ def run_precond_study(args):
     import sg_workloads as w
     from paper_2512_23027_gb300 import Solver
     from paper_2512_23027_gb300.binding import SG_MIXED
+    if args.mesh:
+        return run_precond_study_mesh(args)
     base = w.config("ricker1024").replace(name="pc256", N=256, dt=w.cfl_dt(256))
     rows = []
     for s in (2, 4, 8, 16):
@@ -411,6 +413,34 @@ def run_mesh(args):
                        "subdomains": c.nparts, "M": p.M, "p": p.p, "P": p.P, "dt": p.dt, "tol": p.tol,
                        "l2": "256 MB buffer written between timed steps"}}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_precond_study_mesh(args):
+    """The preconditioner comparison on a mesh workload (--mesh NAME; umesh_e1 is the paper's Sec. 6.1
+    setting: a 1600-vertex unstructured mesh, deterministic medium, dt 0.01): RCB partitions into 2 .. 64
+    subdomains, the two-level NN, one-level NN and lumped preconditioners, mixed precision, tolerance
+    1e-8; average outer PCG iterations and ms per step over `steps` steps after `warmup` steps."""
+    import sg_workloads as w
+    from sg_workloads import meshes
+    from paper_2512_23027_gb300 import Solver
+    from paper_2512_23027_gb300.binding import SG_MIXED
+    c = w.mesh_config(args.mesh)
+    xy, d, tri, _ = c.build()
+    rows = []
+    for nparts in (2, 4, 8, 16, 32, 64):
+        part = meshes.rcb_partition(xy, tri, nparts)
+        for name, pc in (("two-level NN", 0), ("one-level NN", 1), ("lumped", 2)):
+            sv = Solver(c.prob, precision=SG_MIXED, precond=pc, mesh=(xy, d, tri, part))
+            sv.step(args.warmup)
+            st = sv.step(args.steps)
+            rows.append({"subdomains": nparts, "precond": name, "outer_iters_per_step": st["iters_total"] / args.steps,
+                         "inner_iters_per_step": st["inner_total"] / args.steps, "ms_per_step": st["ms"] / args.steps})
+            sv.close()
+    print(json.dumps({"metric": "outer PCG iterations per step vs number of subdomains, by preconditioner (mesh)",
+                      "config": {"workload": c.name, "vertices": int(xy.shape[0]), "M": c.prob.M, "P": c.prob.P,
+                                 "dt": c.prob.dt, "precision": "mixed", "tol": c.prob.tol, "warmup": args.warmup,
+                                 "steps": args.steps}, "rows": rows}), flush=True)
     return 0
 
 
@@ -487,7 +517,7 @@ def main():
     if args.batch:
         return run_batch(args)
     if args.precond_study:
-        return run_precond_study(args)
+        return run_precond_study(args)   # with --mesh NAME: on that mesh
     if args.profile_step:
         return run_profile_step(args)   # with --mesh NAME: a step of that mesh workload
     if args.mesh:

@@ -233,7 +233,9 @@ def mesh_config(name: str) -> MeshConfig:
       umesh37k_rv9  the same mesh and partition with M = 9, order 3 (P = 220, 8.19 million unknowns),
                     the largest case of that study.
       umesh37k_720  umesh37k on the paper's 720 subdomains (1284 corners: a dense coarse matrix of
-                    25680^2 values, 5.3 GB, whose inverse takes minutes of host set-up)."""
+                    25680^2 values, 5.3 GB, whose inverse takes minutes of host set-up).
+      umesh_e1      40^2 = 1600 vertices (paper: 1563), deterministic medium (M = 0, P = 1), dt 0.01:
+                    the preconditioner comparison of Sec. 6.1 (its subdomain counts vary; 4 here)."""
     ricker = Source(SOURCE_RICKER, 0.3, 0.5, 0.0, 10.0, 1.0)
     base = Problem(name=name, N=0, s=0, M=3, p=2, p_in=2, sigma=0.3, bx=0.3, by=0.3, g0=0.0, dt=0.02,
                    steps=20, tol=1e-8, source=ricker)
@@ -248,6 +250,8 @@ def mesh_config(name: str) -> MeshConfig:
         return MeshConfig(name, 192, 0.3, 37, 64, rv3.replace(M=9))
     if name == "umesh37k_720":
         return MeshConfig(name, 192, 0.3, 37, 720, rv3)
+    if name == "umesh_e1":
+        return MeshConfig(name, 39, 0.3, 61, 4, base.replace(M=0, p=0, p_in=0, sigma=0.0, dt=0.01, steps=50))
     raise KeyError(name)
 
 

@@ -131,7 +131,7 @@ def test_valid_mesh_passes_the_host_steps(B):
 
 
 @pytest.mark.parametrize("name,nv,nsub", [("umesh_small", 625, 6), ("umesh13k", 13689, 32), ("umesh37k", 37249, 64),
-                                          ("umesh37k_720", 37249, 720)])
+                                          ("umesh37k_720", 37249, 720), ("umesh_e1", 1600, 4)])
 def test_mesh_workloads(B, name, nv, nsub):
     """The mesh workloads: seeded (the same mesh twice), the vertex counts of the paper-sized meshes,
     balanced RCB partitions (triangle counts within one), and every host step of sg_setup_mesh accepts
