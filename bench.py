@@ -506,8 +506,10 @@ def main():
                          "cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--profile-fp64", action="store_true", help="with --profile-step: the plain FP64 solver")
     ap.add_argument("--mesh", default=None,
-                    help="time a mesh workload instead (umesh_small, umesh13k, umesh37k, umesh37k_rv9, umesh37k_720): a seeded "
-                         "unstructured mesh with an RCB partition, mixed + learned warm start and plain FP64")
+                    help="time a mesh workload instead (umesh_small, umesh13k, umesh37k, umesh37k_rv9, umesh37k_720, "
+                         "umesh_e1): a seeded unstructured mesh with an RCB partition, mixed + learned warm start, "
+                         "SG_BF16 where P <= 32, and plain FP64; with --precond-study the preconditioner comparison "
+                         "on that mesh, with --profile-step one host-driven step of it")
     ap.add_argument("--enqueue", default="graph", choices=["graph", "eager"],
                     help="graph: one CUDA graph per step (default); eager: host-driven enqueue of the same "
                          "kernels (per-kernel profilers cannot see inside graphs with conditional nodes)")
