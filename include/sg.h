@@ -251,6 +251,14 @@ typedef struct {
 int sg_setup_mesh(const sg_mesh* mesh, const sg_kl* kl, const sg_pce* pce, const sg_params* params,
                   const sg_source* src, void* stream, sg_handle* out);
 
+/* Element partition of a triangle mesh for sg_setup_mesh by recursive coordinate bisection (host only,
+ * no CUDA call): the triangles of a part that is to become k subdomains are ordered by centroid along
+ * the part's longer extent (ties by the other coordinate, then by triangle index) and cut after
+ * floor(n floor(k/2) / k) of its n triangles into floor(k/2) and k - floor(k/2) subdomains.  xy: nv x 2,
+ * tri: ne x 3 vertex ids; part (caller-owned, ne ints) receives ids 0 .. nparts - 1, every id used.
+ * Errors: SG_EINVAL (null arrays, nparts outside 1 .. ne, a vertex id out of range). */
+int sg_partition_rcb(int nv, const double* xy, int ne, const int* tri, int nparts, int* part);
+
 /* Sizes and device-memory needs of a mesh problem, from the host set-up of sg_setup_mesh alone (no
  * device memory, no CUDA call; works without a GPU): to choose a partition that fits before building
  * the solver.  Byte counts are the large device arrays sg_setup_mesh allocates for params->precision

@@ -122,6 +122,8 @@ def load_library(path: Optional[str] = None):
     lib.sg_get_sizes.argtypes = [C.c_void_p, P(Sizes)]
     lib.sg_plan_query.argtypes = [P(Grid), P(KL), P(PCE), P(Params), P(Plan)]
     lib.sg_mesh_plan_query.argtypes = [P(Mesh), P(KL), P(PCE), P(Params), P(MeshPlan)]
+    lib.sg_partition_rcb.argtypes = [C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]
+    lib.sg_partition_rcb.restype = C.c_int
     lib.sg_mesh_plan_query.restype = C.c_int
     lib.sg_plan_query.restype = C.c_int
     lib.sg_get_iters.argtypes = [C.c_void_p, P(C.c_int), D, C.c_int]
@@ -346,6 +348,18 @@ def plan_query(prob, precision: int = SG_FP64) -> dict:
     if rc != 0:
         raise SGError(rc, lib.sg_last_error(None).decode())
     return {f: _plain(getattr(out, f)) for f, _ in Plan._fields_}
+
+
+def partition_rcb(xy, tri, nparts: int) -> np.ndarray:
+    """Triangle -> subdomain ids by the library's recursive coordinate bisection (host only)."""
+    lib = load_library()
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    part = np.zeros(tri.shape[0], dtype=np.int32)
+    rc = lib.sg_partition_rcb(xy.shape[0], xy.ctypes.data, tri.shape[0], tri.ctypes.data, int(nparts), part.ctypes.data)
+    if rc != 0:
+        raise SGError(rc, lib.sg_last_error(None).decode())
+    return part
 
 
 def mesh_plan_query(prob, mesh, precision: int = SG_FP64, precond: int = SG_PC_NN2) -> dict:

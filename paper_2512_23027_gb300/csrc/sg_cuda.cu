@@ -2694,6 +2694,12 @@ int sg_get_sizes(sg_handle h, sg_sizes* out) {
   return SG_OK;
 }
 
+int sg_partition_rcb(int nv, const double* xy, int ne, const int* tri, int nparts, int* part) {
+  const std::string msg = sgh::partition_rcb(nv, xy, ne, tri, nparts, part);
+  if (!msg.empty()) { g_setup_err = msg; return SG_EINVAL; }
+  return SG_OK;
+}
+
 int sg_mesh_plan_query(const sg_mesh* mesh, const sg_kl* kl, const sg_pce* pce, const sg_params* params,
                        sg_mesh_plan* out) {
   if (!mesh || !kl || !pce || !params || !out) { g_setup_err = "null argument"; return SG_EINVAL; }

@@ -832,6 +832,48 @@ std::string mesh_to_problem(Problem& pr, MeshRows& mr, const MeshProblem& mp, co
   return check_mesh_tables(pr, mr);
 }
 
+std::string partition_rcb(int nv, const double* xy, int ne, const int* tri, int nparts, int* part) {
+  if (nv < 3 || ne < 1 || !xy || !tri || !part) return "partition: vertices and triangles required";
+  if (nparts < 1 || nparts > ne) return "partition: 1 <= nparts <= triangles required";
+  std::vector<double> cx(ne), cy(ne);
+  for (int e = 0; e < ne; ++e) {
+    const int a = tri[3 * e], b = tri[3 * e + 1], c = tri[3 * e + 2];
+    if (a < 0 || a >= nv || b < 0 || b >= nv || c < 0 || c >= nv) return "partition: triangle vertex out of range";
+    cx[e] = (xy[2 * a] + xy[2 * b] + xy[2 * c]) / 3.0;
+    cy[e] = (xy[2 * a + 1] + xy[2 * b + 1] + xy[2 * c + 1]) / 3.0;
+  }
+  std::vector<int> ids(ne);
+  for (int e = 0; e < ne; ++e) ids[e] = e;
+  // explicit stack of (first, count, k, first id) ranges of ids
+  struct Range { int lo, n, k, first; };
+  std::vector<Range> todo{{0, ne, nparts, 0}};
+  while (!todo.empty()) {
+    const Range r = todo.back();
+    todo.pop_back();
+    if (r.k == 1) {
+      for (int q = r.lo; q < r.lo + r.n; ++q) part[ids[q]] = r.first;
+      continue;
+    }
+    double x0 = cx[ids[r.lo]], x1 = x0, y0 = cy[ids[r.lo]], y1 = y0;
+    for (int q = r.lo; q < r.lo + r.n; ++q) {
+      x0 = std::min(x0, cx[ids[q]]); x1 = std::max(x1, cx[ids[q]]);
+      y0 = std::min(y0, cy[ids[q]]); y1 = std::max(y1, cy[ids[q]]);
+    }
+    const bool alongx = (x1 - x0) >= (y1 - y0);
+    const std::vector<double>& major = alongx ? cx : cy;
+    const std::vector<double>& minor = alongx ? cy : cx;
+    std::stable_sort(ids.begin() + r.lo, ids.begin() + r.lo + r.n, [&](int a, int b) {
+      if (major[a] != major[b]) return major[a] < major[b];
+      return minor[a] < minor[b];
+    });
+    const int k0 = r.k / 2;
+    const int n0 = (int)(((long long)r.n * k0) / r.k);
+    todo.push_back({r.lo + n0, r.n - n0, r.k - k0, r.first + k0});
+    todo.push_back({r.lo, n0, k0, r.first});
+  }
+  return "";
+}
+
 bool mesh_mean_inverse(const Problem& pr, const MeshRows& mr, int pat, double am, double bk,
                        std::vector<double>& out) {
   const int nsub = pr.nsub, nl = pr.nl, PI = pr.PI;

@@ -129,6 +129,12 @@ std::string build_mesh_problem(MeshProblem& mp, int nv, const double* xy, const 
                                double g0, int p, int p_in, const double* modes = nullptr,
                                const double* lambdas = nullptr);
 
+// Recursive coordinate bisection of the triangles by centroid: a set of triangles going to k subdomains
+// is ordered along the longer extent of its centroids (ties by the other coordinate, then by triangle
+// index) and split at floor(size * floor(k/2) / k) into floor(k/2) and k - floor(k/2) subdomains.
+// part receives ne ids 0 .. nparts - 1.  Returns "" on success, else an error message.
+std::string partition_rcb(int nv, const double* xy, int ne, const int* tri, int nparts, int* part);
+
 std::vector<std::vector<int>> multi_indices(int M, int p);
 double hermite_triple(int a, int b, int c);
 double ricker(double t, double f);

@@ -223,3 +223,29 @@ def test_mesh_plan_query_of_the_paper_partition(B):
         plan = B.mesh_plan_query(c.prob, c.build())
         assert plan["n_corner"] == corners and plan["coarse_dim"] == corners * 20
         assert plan["bytes_coarse_matrix"] == (corners * 20) ** 2 * 8
+
+
+@pytest.mark.parametrize("n,seed,nparts", [(12, 11, 3), (12, 11, 5), (24, 11, 6), (39, 61, 17), (192, 37, 64),
+                                           (192, 37, 720)])
+def test_native_rcb_partition_equals_the_generator(B, n, seed, nparts):
+    """sg_partition_rcb (C++, host) gives the same partition as the workloads' RCB (sg_workloads.meshes),
+    element for element, with balanced triangle counts."""
+    from sg_workloads import meshes
+    xy, tri, _ = meshes.delaunay_square(n, 0.3, seed)
+    ref = meshes.rcb_partition(xy, tri, nparts)
+    got = B.partition_rcb(xy, tri, nparts)
+    assert np.array_equal(got, ref)
+    cnt = np.bincount(got, minlength=nparts)
+    assert cnt.size == nparts and cnt.min() >= 1 and cnt.max() - cnt.min() <= 1
+
+
+def test_native_rcb_partition_rejects(B):
+    from sg_workloads import meshes
+    xy, tri, _ = meshes.delaunay_square(6, 0.3, 5)
+    for nparts in (0, tri.shape[0] + 1):
+        with pytest.raises(B.SGError):
+            B.partition_rcb(xy, tri, nparts)
+    bad = tri.copy()
+    bad[0, 0] = xy.shape[0]
+    with pytest.raises(B.SGError):
+        B.partition_rcb(xy, bad, 3)
