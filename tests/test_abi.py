@@ -52,3 +52,18 @@ def test_noalloc_capacity_is_the_header_constant():
     src = open(os.path.join(ROOT, "paper_2512_23027_gb300", "csrc", "sg_cuda.cu")).read()
     assert "g_noalloc_stage[2 * (size_t)SG_NOALLOC_MAX_FREE]" in src
     assert not re.search(r"(constexpr|#define)\s+\w*\s*SG_NOALLOC_MAX_FREE", src)
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/sg.h is a C header (C99, pedantic, no warnings): the boundary carries no C++ or torch types."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "h.c"
+    src.write_text('#include "sg.h"\nint main(void) { sg_mesh m; sg_mesh_plan p; sg_plan q; sg_sizes z;\n'
+                   '  (void)m; (void)p; (void)q; (void)z; return 0; }\n')
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        "-c", str(src), "-o", str(tmp_path / "h.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
