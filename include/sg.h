@@ -246,7 +246,8 @@ typedef struct {
  * free vertices in ascending vertex id, PCE mode fastest.  sg_sizes.N is 0 for a mesh handle.
  * Errors: SG_EINVAL for invalid meshes, partitions or parameters (vertex ids out of range, an edge in
  * more than two triangles, unused subdomain ids, a degenerate triangle, a source outside the mesh),
- * SG_ENOTSUP for SG_BF16 beyond its limits or fewer than two subdomains, SG_ENUMERIC if a mean operator is not
+ * SG_ENOTSUP for SG_BF16 beyond its limits, fewer than two subdomains or a subdomain with more than 4096
+ * free vertices (the dense mean-operator inverse), SG_ENUMERIC if a mean operator is not
  * positive definite, SG_ENOMEM, SG_ECUDA.  On error *out is NULL. */
 int sg_setup_mesh(const sg_mesh* mesh, const sg_kl* kl, const sg_pce* pce, const sg_params* params,
                   const sg_source* src, void* stream, sg_handle* out);

@@ -2208,6 +2208,9 @@ static int setup_impl(sg_handle h, const sg_grid* grid, const sg_kl* kl, const s
 // BF16 image of the mesh's mean-operator inverses (patterns 0 and 1, rows padded to Kp = nl rounded up to
 // the 128-row tile) and its tensor map, as build_mma_precond lays out the grid's.
 constexpr int MESH_MMA_NL_MAX = 1600;  // the grid's limit: 40 x 40 nodes
+// Largest subdomain (free vertices) of the mesh path: its dense mean-operator inverse holds nl^2 values
+// per pattern (128 MB in FP64 at 4096) and takes O(nl^3) host work at set-up.
+constexpr int MESH_NL_MAX = 4096;
 static int build_mesh_mma(sg_handle h, const std::vector<double>* inv) {
   const auto& pr = h->pr;
   const int nl = pr.nl;
@@ -2275,6 +2278,11 @@ static int setup_mesh_impl(sg_handle h, const sg_mesh* m, const sg_kl* kl, const
   if (!msg.empty()) { h->err = msg; return SG_EINVAL; }
   auto& pr = h->pr;
   pr.sigma = kl->sigma; pr.bx = kl->bx; pr.by = kl->by; pr.g0 = kl->g0;
+  if (pr.nl > MESH_NL_MAX) {
+    h->err = "mesh: a subdomain has " + std::to_string(pr.nl) + " free vertices; the dense mean-operator "
+             "inverse allows at most " + std::to_string(MESH_NL_MAX) + " (use more subdomains)";
+    return SG_ENOTSUP;
+  }
   if (prm->precision == SG_BF16 && (pr.P > 32 || pr.nl > MESH_MMA_NL_MAX)) {
     h->err = "SG_BF16: the BF16 tensor-core preconditioner needs P <= 32 and at most " +
              std::to_string(MESH_MMA_NL_MAX) + " free vertices per subdomain";

@@ -84,6 +84,11 @@ def bad(kind):
         kw["modes"] = np.zeros((w.config("tiny").M, tri.shape[0]))
     elif kind == "too few vertices":
         xy, d = xy[:2], d[:2]
+    elif kind == "subdomain too large":
+        from sg_workloads import meshes
+        xy, tri, bnd = meshes.delaunay_square(100, 0.3, 5)     # 10201 vertices in 2 subdomains
+        d = bnd.astype(np.uint8)
+        part = meshes.rcb_partition(xy, tri, 2)
     return (xy, d, tri, part), kw
 
 
@@ -100,6 +105,7 @@ CASES = [
     ("warm-start mode", SG_EINVAL, "warm"),
     ("modes without lambdas", SG_EINVAL, "lambdas"),
     ("too few vertices", SG_EINVAL, "mesh"),
+    ("subdomain too large", SG_ENOTSUP, "at most 4096"),
 ]
 
 
