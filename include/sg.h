@@ -243,7 +243,8 @@ typedef struct {
  * (modes[n * ne + e]).  The source: a pulse is evaluated at the free vertices; a point source uses
  * the P1 values at (x0, y0) in the first triangle (in the given order) that contains it.  Fields of
  * a mesh handle (sg_get_field, sg_get_state, sg_set_state, sg_step_host, sg_sample_field) list the
- * free vertices in ascending vertex id, PCE mode fastest.  sg_sizes.N is 0 for a mesh handle.
+ * free vertices (not Dirichlet and in at least one triangle; a vertex of no triangle carries no
+ * unknown) in ascending vertex id, PCE mode fastest.  sg_sizes.N is 0 for a mesh handle.
  * Errors: SG_EINVAL for invalid meshes, partitions or parameters (vertex ids out of range, an edge in
  * more than two triangles, unused subdomain ids, a degenerate triangle, a source outside the mesh),
  * SG_ENOTSUP for SG_BF16 beyond its limits, fewer than two subdomains or a subdomain with more than 4096
