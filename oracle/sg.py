@@ -69,6 +69,48 @@ class SGOperators:
         return spla.spsolve(self.Mb.tocsc(), rhs)
 
 
+def galerkin_apply(G: np.ndarray, mats, X: np.ndarray) -> np.ndarray:
+    """sg_block(G, mats) @ x without forming the Kronecker products: with x node-major as X (n, P),
+    kron(A_i, G_i) x is A_i X G_i^T = A_i X G_i (G_ijk is symmetric in j, k), summed over i.  For
+    full-size checks, where the block matrix would not fit in memory."""
+    Y = np.zeros_like(X)
+    for i, A in enumerate(mats):
+        Y += (A @ X) @ G[i]
+    return Y
+
+
+class SGMatrixForm:
+    """The operators of SGOperators applied in matrix form (X of shape (n, P), node-major rows), for
+    systems too large to assemble as Kronecker block matrices: mass I (x) M, damping with C_0 = alpha0 M +
+    alpha1 K_0 and C_k = alpha1 K_k, stiffness sum_i K_i (x) G_i, the transient operator (Eq. K_T_Sto),
+    the effective load (Eqs. fparts, UmCm)."""
+
+    def __init__(self, M, Ks, G, alpha0, alpha1, dt):
+        self.M, self.Ks, self.G = M, Ks, G
+        self.alpha0, self.alpha1, self.dt = alpha0, alpha1, dt
+
+    def stiffness(self, X):
+        return galerkin_apply(self.G, self.Ks, X)
+
+    def damping(self, X):
+        return self.alpha0 * (self.M @ X) + self.alpha1 * self.stiffness(X)
+
+    def transient(self, X):
+        dt = self.dt
+        return (self.M @ X) / (ZETA * dt * dt) + self.damping(X) * (GAMMA / (ZETA * dt)) + self.stiffness(X)
+
+    def effective_load(self, F, U, V, A):
+        dt = self.dt
+        um = (U + dt * V) / (ZETA * dt * dt) + (1.0 - 2.0 * ZETA) * A / (2.0 * ZETA)
+        uc = GAMMA * dt * um - V - (1.0 - GAMMA) * A * dt
+        return F + self.M @ um + self.damping(uc), um
+
+    def residual(self, F, U, V, A, Unew):
+        """||f~_{n+1} - K~ U_{n+1}|| / ||f~_{n+1}||: how well U_{n+1} solves the step's transient system."""
+        Ft, _ = self.effective_load(F, U, V, A)
+        return np.linalg.norm(Ft - self.transient(Unew)) / np.linalg.norm(Ft)
+
+
 class SGProblem:
     """Global SG system for a workload on the structured grid (free nodes only).  coef: the PCE
     coefficients of c_s at the element centroids (P_in x 2 N^2) from a KL other than the analytic

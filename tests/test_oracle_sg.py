@@ -91,3 +91,34 @@ def test_monte_carlo_within_standard_error():
     assert np.all(np.abs(sg_mean - mean) <= 4 * se + 1e-12)
     # variance: SE of the sample variance ~ var * sqrt(2 / (n - 1)) for near-Gaussian output
     assert abs(sg_var[k] - var[k]) <= 4 * var[k] * math.sqrt(2.0 / (n - 1)) + 1e-12
+
+
+def test_matrix_form_operators_equal_the_block_matrices():
+    """The matrix-form operators used for full-size checks (oracle.sg.SGMatrixForm) equal the
+    Kronecker block matrices of SGOperators (Eq. K_T_Sto, damping of the Rayleigh appendix) on a small
+    problem with p_in = 2p, and the direct solve's step leaves a residual at the rounding level."""
+    import numpy as np
+    import sg_workloads as w
+    from oracle import sg
+    prob = w.config("tiny").replace(p_in=4, alpha0=0.3, alpha1=0.01)
+    sgp = sg.SGProblem(prob)
+    ops = sgp.ops
+    mf = sg.SGMatrixForm(sgp.M, sgp.Ks, sgp.G, prob.alpha0, prob.alpha1, prob.dt)
+    rng = np.random.default_rng(5)
+    n, P = sgp.free.size, sgp.P
+    X = rng.standard_normal((n, P))
+    x = X.ravel()
+    for a, b in ((mf.stiffness(X), ops.Kb @ x), (mf.damping(X), ops.Cb @ x), (mf.transient(X), ops.Kt @ x)):
+        assert np.abs(a.ravel() - b).max() <= 1e-12 * np.abs(b).max()
+    U, V, A = sgp.initial_state()
+    F = sgp.load(prob.dt)
+    Ft, um = ops.effective_load(F, U, V, A)
+    Ft2, um2 = mf.effective_load(F.reshape(n, P), U.reshape(n, P), V.reshape(n, P), A.reshape(n, P))
+    assert np.abs(Ft2.ravel() - Ft).max() <= 1e-12 * np.abs(Ft).max() and np.allclose(um2.ravel(), um)
+    import scipy.sparse.linalg as spla
+    Unew = spla.spsolve(ops.Kt.tocsc(), Ft)
+    r = mf.residual(F.reshape(n, P), U.reshape(n, P), V.reshape(n, P), A.reshape(n, P), Unew.reshape(n, P))
+    assert r < 1e-13
+    # a perturbed solution shows up in the residual
+    assert mf.residual(F.reshape(n, P), U.reshape(n, P), V.reshape(n, P), A.reshape(n, P),
+                       Unew.reshape(n, P) * (1 + 1e-6)) > 1e-8
