@@ -280,6 +280,8 @@ typedef struct {
   long long bytes_coarse_matrix;        /* dense FP64 inverse of F_cc                                */
   long long bytes_vectors;              /* state, step and subdomain-solve vectors                   */
   int mma;                              /* 1: SG_BF16's tensor-core product applies                  */
+  int fits;                             /* 1: sg_setup_mesh accepts the sizes (at most 4096 free
+                                           vertices per subdomain; SG_BF16 within its limits)        */
 } sg_mesh_plan;
 
 /* Errors as sg_setup_mesh's host checks (SG_EINVAL with a message in sg_last_error(NULL)). */

@@ -52,7 +52,7 @@ class MeshPlan(C.Structure):
                 ("max_corners", C.c_int), ("max_gamma", C.c_int), ("row_entries", C.c_longlong),
                 ("coarse_dim", C.c_longlong), ("bytes_rows", C.c_longlong), ("bytes_inverses", C.c_longlong),
                 ("bytes_coarse_basis", C.c_longlong), ("bytes_coarse_matrix", C.c_longlong),
-                ("bytes_vectors", C.c_longlong), ("mma", C.c_int)]
+                ("bytes_vectors", C.c_longlong), ("mma", C.c_int), ("fits", C.c_int)]
 
 
 class Source(C.Structure):

@@ -2754,6 +2754,7 @@ int sg_mesh_plan_query(const sg_mesh* mesh, const sg_kl* kl, const sg_pce* pce, 
   // interior accumulator of the mixed path; FP32: two work vectors) and the inner-CG workspaces of
   // both types (six vectors each, one problem per subdomain)
   p.bytes_vectors = nvec * (14 * 8 + 2 * 4) + 6 * nvec * (8 + 4);
+  p.fits = pr.nl <= MESH_NL_MAX && (params->precision != SG_BF16 || p.mma) ? 1 : 0;
   *out = p;
   return SG_OK;
 }

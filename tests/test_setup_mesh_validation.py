@@ -211,7 +211,7 @@ def test_mesh_plan_query_matches_the_oracle_partition(B):
     assert plan["row_entries"] == entries
     assert plan["coarse_dim"] == up.corner.size * p.P
     assert plan["bytes_coarse_matrix"] == (up.corner.size * p.P) ** 2 * 8
-    assert plan["bytes_inverses"] == 2 * up.nsub * nl * nl * 8 and plan["mma"] == 0
+    assert plan["bytes_inverses"] == 2 * up.nsub * nl * nl * 8 and plan["mma"] == 0 and plan["fits"] == 1
     mixed = B.mesh_plan_query(p, (xy, d, tri, part), precision=1)
     assert mixed["bytes_inverses"] == 2 * up.nsub * nl * nl * 4
     bf16 = B.mesh_plan_query(p, (xy, d, tri, part), precision=3)
@@ -228,7 +228,12 @@ def test_mesh_plan_query_of_the_paper_partition(B):
         c = w.mesh_config(name)
         plan = B.mesh_plan_query(c.prob, c.build())
         assert plan["n_corner"] == corners and plan["coarse_dim"] == corners * 20
-        assert plan["bytes_coarse_matrix"] == (corners * 20) ** 2 * 8
+        assert plan["bytes_coarse_matrix"] == (corners * 20) ** 2 * 8 and plan["fits"] == 1
+    # two subdomains of a 10201-vertex mesh exceed the dense inverse's 4096 free vertices
+    from sg_workloads import meshes
+    xy, tri, bnd = meshes.delaunay_square(100, 0.3, 5)
+    plan = B.mesh_plan_query(w.config("tiny"), (xy, bnd.astype(np.uint8), tri, meshes.rcb_partition(xy, tri, 2)))
+    assert plan["n_sub_nodes"] > 4096 and plan["fits"] == 0
 
 
 @pytest.mark.parametrize("n,seed,nparts", [(12, 11, 3), (12, 11, 5), (24, 11, 6), (39, 61, 17), (192, 37, 64),
