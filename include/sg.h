@@ -387,7 +387,9 @@ int sg_set_enqueue_mode(sg_handle h, int eager);
  * sweeps with the fused CG update, or CG update + residual pack + tensor-core product), 2 fused
  * SG operator apply, 3 the tensor-core product kernel alone, 4 the operator applies with FP64
  * inputs and outputs (effective load and residual corrections; float-float arithmetic in the
- * mixed path).  Events are recorded on the stream the kernel is launched on. */
+ * mixed path).  On a mesh handle, class 1 is the dense mean-operator product (or the pack and
+ * tensor-core product with SG_BF16) and class 2 the sparse-row apply of the subdomain CG; class 4
+ * times its FP64 applies.  Events are recorded on the stream the kernel is launched on. */
 int sg_kernel_timing(sg_handle h, int which, double* total_ms, long long* launches);
 
 /* Kernels launched by this library in this process so far (all handles), counted on the device

@@ -1012,10 +1012,14 @@ static int enq_inner_mesh_mma(sg_handle h, Ctx& cx, int pat, int nb, int R, int 
   RET(make_handle(h, cx, &hnd));
   RET(pre(cx, 1, hnd, cx.capture ? 1 : 0));
   return cond_node(h, cx, hnd, true, h->ctl.cond, [&](Ctx& c2) -> int {
+    RET(kprof_begin(h, c2, 2));   // kernel timing class 2: the operator apply of the inner loop
     sgk::k_mapply_cg<float><<<(unsigned)nb * NT, 256, 0, c2.st>>>(rows, h->cls, s0, R, NT, w.z, w.p0, w.p1, w.q,
                                                                   (float)h->am, (float)h->bk, mask, h->ctl);
     CKL();
-    return pre(c2, 0, hnd, c2.capture ? 1 : 0);
+    RET(kprof_end(h, c2, 2));
+    RET(kprof_begin(h, c2, 1));   // class 1: the preconditioner step (pack and tensor-core product)
+    RET(pre(c2, 0, hnd, c2.capture ? 1 : 0));
+    return kprof_end(h, c2, 1);
   });
 }
 
@@ -1057,12 +1061,16 @@ static int enq_inner_mesh(sg_handle h, Ctx& cx, int pat, int nb, int R, int s0, 
   CKL();
   return cond_node(h, cx, hnd, true, h->ctl.cond, [&](Ctx& c2) -> int {
     cudaStream_t s = c2.st;
+    RET(kprof_begin(h, c2, 2));   // kernel timing class 2: the operator apply of the inner loop
     sgk::k_mapply<T, T><<<nblk(n), 256, 0, s>>>(rows, h->cls, s0, nb, R, w.p0, w.p0, w.q, nullptr, am, bk, mask,
                                                  h->ctl.active);
+    RET(kprof_end(h, c2, 2));
     sgk::k_mdot2<T><<<nb, sgk::MDOT_THREADS, 0, s>>>(len, w.p0, w.q, h->ctl.part_pq, nullptr, nullptr, nullptr,
                                                       h->ctl.active);
     sgk::k_mcg_upd<T><<<nblk(n), 256, 0, s>>>(len, nb, h->ctl, w.x, w.r, w.p0, w.q);
+    RET(kprof_begin(h, c2, 1));   // class 1: the preconditioner step
     sgk::k_mdense<T><<<nblk(n), 256, 0, s>>>(Ainv, npat, s0, nb, R, pr.nl, pr.P, w.r, w.z, h->ctl.active);
+    RET(kprof_end(h, c2, 1));
     sgk::k_mdot2<T><<<nb, sgk::MDOT_THREADS, 0, s>>>(len, w.r, w.r, h->ctl.part_rr, w.r, w.z, h->ctl.part_rz,
                                                       h->ctl.active);
     sgk::k_mcg_ctl<<<1, 256, 0, s>>>(nb, h->ctl, 0, tol2, bb_min, imax, hnd, c2.capture ? 1 : 0);
