@@ -401,6 +401,18 @@ def run_mesh(args):
         legs[key] = {"steps_per_s": K / (ms / 1e3), "ms_per_step": ms / K, "outer_iters_per_step": outer / K,
                      "inner_iters_per_step": inner / K, "steps": K, "setup_s": setup,
                      "device_bytes": sv.sizes["device_bytes"]}
+        if key != "fp64":
+            # per-kernel CUDA-event times of one host-driven step each: class 1 the preconditioner product
+            # of the subdomain CG, class 2 its operator apply (untimed for the line above)
+            sv.set_eager(True)
+            sv.kernel_timing(1)
+            sv.step(1)
+            ms1, n1 = sv.kernel_timing(2)
+            sv.step(1)
+            ms2, n2 = sv.kernel_timing(0)
+            sv.set_eager(False)
+            legs[key]["kernels"] = {"precond_product": {"avg_launch_us": 1e3 * ms1 / n1 if n1 else None, "launches": n1},
+                                    "inner_apply": {"avg_launch_us": 1e3 * ms2 / n2 if n2 else None, "launches": n2}}
         sv.close()
     p = c.prob
     line = {"metric": "time-steps/sec on a general partition of an unstructured mesh (mixed precision + learned "
