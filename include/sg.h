@@ -18,7 +18,8 @@
  *     the legacy default stream); the calls below synchronise that stream before returning
  *     unless stated otherwise.
  *   - A handle is not thread-safe: one host thread at a time.
- *   - Field layout for sg_get_field / sg_get_state / sg_set_state: node-major over the free
+ *   - Field layout for sg_get_field / sg_get_state / sg_set_state (handles of sg_setup; for
+ *     sg_setup_mesh handles see there): node-major over the free
  *     nodes (x index fastest, then y; node (i, j) for 1 <= i, j <= N-1), PCE mode fastest:
  *     value(i, j, k) is element ((j-1) (N-1) + (i-1)) * P + k.  PCE modes follow the graded
  *     multi-index order (total degree, then descending lexicographic), orthonormal basis.
