@@ -260,3 +260,16 @@ def test_native_rcb_partition_rejects(B):
     bad[0, 0] = xy.shape[0]
     with pytest.raises(B.SGError):
         B.partition_rcb(xy, bad, 3)
+
+
+def test_binding_marshals_the_mesh(B):
+    """Solver(prob, mesh=...) passes the mesh arrays through sg_setup_mesh: on a machine without a GPU the
+    host steps accept them and the set-up stops at the first CUDA call (SGError with SG_ECUDA)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is visible: this checks the host steps on a machine without one")
+    from paper_2512_23027_gb300 import Solver
+    c = w.mesh_config("umesh_small")
+    with pytest.raises(B.SGError) as e:
+        Solver(c.prob, precision=1, mesh=c.build())
+    assert e.value.code == SG_ECUDA
